@@ -1,0 +1,169 @@
+"""Iterative solvers for the oracle (test infrastructure only; see package header).
+
+A slab problem is a dict with
+  N, L            quadrature order (even) and scattering order (L <= N-1)
+  h[K]            cell widths
+  sigma_t[K]      total cross section per cell
+  sigma_s[K,L+1]  Legendre moments sigma_{s,l} per cell (Eq. treq)
+  Q[K,2,L+1]      external source as Legendre moments at the two LD nodes; the
+                  angular source is q_n = sum_l (2l+1)/2 P_l(mu_n) Q_l, so an
+                  isotropic scalar source of strength S has Q_0 = S (q_n = S/2)
+  bc              'vacuum' (default) or 'reflective'
+The state of every iteration is the flux moments phi[K,2,L+1] at the LD nodes.
+
+Convergence test (Eq. iterate): the paper iterates while
+||phi_l^{m+1} - phi_l^m||_inf exceeds a tolerance without saying relative or
+absolute or which l; the reading used here is the relative change of the scalar
+flux, max|phi_0^{m+1} - phi_0^m| / max|phi_0^{m+1}| < tol.
+"""
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from . import quadrature as qd
+from . import transport as tr
+
+
+def tables(N, L):
+    """mu, w, D (L+1 x N), M (N x L+1) for an S_N set and scattering order L (Eqs. phi-mom, treq)."""
+    mu, w = qd.gauss_legendre(N)
+    return mu, w, qd.moment_operator(mu, w, L), qd.expansion_operator(mu, L)
+
+
+def moments(D, psi):
+    """phi[K,2,l] = sum_n D[l,n] psi[K,2,n] (Eq. phi-mom)."""
+    return np.einsum("ln,kan->kal", D, psi)
+
+
+def scattering_source(M, sigma_s, phi, Q=None):
+    """Nodal angular source q_n = sum_l M[n,l] (sigma_{s,l} phi_l + Q_l) (Eq. treq, S psi + q)."""
+    src = sigma_s[:, None, :] * phi
+    if Q is not None:
+        src = src + Q
+    return np.einsum("nl,kal->kan", M, src)
+
+
+def _streaming_inverse(prob, mu):
+    """Return a function q -> L_h^{-1} q (Eq. trsi left-hand side).
+
+    Vacuum: the upwind sweep. Reflective: a sparse LU of the global streaming
+    matrix (the sweep would need lagged boundary values there).
+    """
+    h, st = prob["h"], prob["sigma_t"]
+    if prob.get("bc", "vacuum") == "vacuum":
+        return lambda q: tr.sweep(mu, st, h, q)
+    K, N = h.size, mu.size
+    Kc = st[:, None, None] * np.eye(N)[None]
+    lu = spla.splu(tr.assemble(mu, h, Kc, bc=prob["bc"]))
+    return lambda q: lu.solve(tr.mass_weight(h, q).ravel()).reshape(K, 2, N)
+
+
+def fp_matrix(prob, mu, w, laplacian="mpd"):
+    """Sparse LD form of the FP operator F = mu d/dz + sigma_a - sigma_tr/2 A_FP (Eqs. fpop,
+    fp-mpd-oper, wd-eq-oper), with sigma_a = sigma_t - sigma_{s,0} and
+    sigma_tr = sigma_{s,0} - sigma_{s,1} (Sec. 2), same BCs as the transport problem
+    applied homogeneously to the correction."""
+    N = mu.size
+    A_fp = qd.angular_laplacian(mu, w, laplacian)
+    sa = prob["sigma_t"] - prob["sigma_s"][:, 0]
+    s1 = prob["sigma_s"][:, 1] if prob["sigma_s"].shape[1] > 1 else np.zeros_like(sa)
+    str_ = prob["sigma_s"][:, 0] - s1
+    Kc = sa[:, None, None] * np.eye(N)[None] - 0.5 * str_[:, None, None] * A_fp[None]
+    return tr.assemble(mu, prob["h"], Kc, bc=prob.get("bc", "vacuum"))
+
+
+def transport_matrix(prob, mu, w):
+    """Sparse LD form of L - S (Eq. trop) with S = M diag(sigma_s) D per cell."""
+    N, L = prob["N"], prob["L"]
+    _, _, D, M = tables(N, L)
+    Kc = prob["sigma_t"][:, None, None] * np.eye(N)[None] \
+        - np.einsum("nl,kl,lm->knm", M, prob["sigma_s"], D)
+    return tr.assemble(mu, prob["h"], Kc, bc=prob.get("bc", "vacuum"))
+
+
+def rel_change(phi_new, phi_old):
+    """Relative change of the scalar flux (reading of Eq. iterate, module docstring)."""
+    return np.max(np.abs(phi_new[..., 0] - phi_old[..., 0])) / np.max(np.abs(phi_new[..., 0]))
+
+
+def source_iteration(prob, tol=1e-10, max_it=100000, phi0=None, history=False):
+    """Source iteration L psi^{m+1} = S psi^m + q (Eq. trsi), on moments.
+
+    Returns (phi, iterations, list of relative changes).
+    Pinned by: the infinite-medium closed form phi_0^m = (S/sigma_t) sum_{k<m} c^k and
+    the spectral-radius bound max_l sigma_{s,l}/sigma_t (Sec. 2.1; P4, P11).
+    """
+    N, L = prob["N"], prob["L"]
+    mu, w, D, M = tables(N, L)
+    Linv = _streaming_inverse(prob, mu)
+    K = prob["h"].size
+    phi = np.zeros((K, 2, L + 1)) if phi0 is None else np.array(phi0, dtype=np.float64)
+    hist = []
+    for it in range(1, max_it + 1):
+        psi = Linv(scattering_source(M, prob["sigma_s"], phi, prob["Q"]))
+        phi_new = moments(D, psi)
+        e = rel_change(phi_new, phi)
+        hist.append(e)
+        phi = phi_new
+        if e < tol:
+            break
+    return (phi, it, hist) if history else (phi, it)
+
+
+def fpsa_source_iteration(prob, laplacian="mpd", tol=1e-10, max_it=10000, phi0=None,
+                          history=False, return_psi=False):
+    """FPSA source iteration (Eqs. predict, correct, iterate).
+
+    Predict:  L psi^{m+1/2} = S psi^m + q                        (sweep)
+    Correct:  psi^{m+1} = psi^{m+1/2} + F^{-1} S (psi^{m+1/2} - psi^m)
+    with F the LD / S_N FP operator using the MPD or WFD angular Laplacian,
+    factorized once by sparse LU (the paper factorizes the FP stiffness matrix
+    with an LU 'factorize' object, Sec. 4) and solved each iteration. Only the
+    moments l <= L of the corrected flux feed the next scattering source, so the
+    state carried is phi^{m+1} = phi^{m+1/2} + D F^{-1} S (psi^{m+1/2} - psi^m).
+    Returns (phi, iterations[, history][, psi]) where psi is the corrected angular
+    flux of the last iteration.
+    Pinned by: one-iteration convergence for P_L-equivalent moments with N = L+1
+    (Eq. fsa_pl_eq, P5); fixed point equal to the direct solve (P7); infinite-medium
+    one-step convergence (P4).
+    """
+    N, L = prob["N"], prob["L"]
+    mu, w, D, M = tables(N, L)
+    K = prob["h"].size
+    Linv = _streaming_inverse(prob, mu)
+    F = spla.splu(fp_matrix(prob, mu, w, laplacian))
+    phi = np.zeros((K, 2, L + 1)) if phi0 is None else np.array(phi0, dtype=np.float64)
+    hist = []
+    psi = None
+    for it in range(1, max_it + 1):
+        psi_half = Linv(scattering_source(M, prob["sigma_s"], phi, prob["Q"]))
+        phi_half = moments(D, psi_half)
+        r = scattering_source(M, prob["sigma_s"], phi_half - phi)      # S (psi^{m+1/2} - psi^m)
+        ups = F.solve(tr.mass_weight(prob["h"], r).ravel()).reshape(K, 2, N)
+        psi = psi_half + ups
+        phi_new = phi_half + moments(D, ups)
+        e = rel_change(phi_new, phi)
+        hist.append(e)
+        phi = phi_new
+        if e < tol:
+            break
+    out = (phi, it)
+    if history:
+        out = out + (hist,)
+    if return_psi:
+        out = out + (psi,)
+    return out
+
+
+def direct_solve(prob, return_psi=False):
+    """The discrete solution itself: (L_h - S_h) psi = m q by sparse LU (the fixed point that
+    SI and FPSA converge to; unique for sigma_a > 0)."""
+    N, L = prob["N"], prob["L"]
+    mu, w, D, M = tables(N, L)
+    K = prob["h"].size
+    A = transport_matrix(prob, mu, w)
+    b = tr.mass_weight(prob["h"], scattering_source(M, np.zeros_like(prob["sigma_s"]),
+                                                   np.zeros((K, 2, L + 1)), prob["Q"]))
+    psi = spla.splu(A).solve(b.ravel()).reshape(K, 2, N)
+    phi = moments(D, psi)
+    return (phi, psi) if return_psi else phi
