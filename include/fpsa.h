@@ -1,0 +1,141 @@
+/*
+ * fpsa.h -- C ABI of the GB300 FPSA source-iteration library (libfpsa.so).
+ *
+ * Computes the steady, mono-energetic 1D slab S_N transport problem of
+ * arXiv:1907.13013, Sec. 2 (Eq. treq with Eq. trans-equation-bc):
+ *
+ *   mu dpsi/dz + sigma_t psi = sum_{l<=L} (2l+1)/2 sigma_{s,l} P_l(mu) phi_l + q
+ *
+ * discretized with S_N Gauss-Legendre in angle and linear-discontinuous (LD)
+ * Galerkin finite elements (consistent mass, upwind edges) in space (Sec. 2.2),
+ * and solves it by source iteration (Eq. trsi) or by Fokker-Planck synthetic
+ * acceleration (Eqs. predict, correct, iterate) whose correction operator is the
+ * FP operator F = mu d/dz + sigma_a - sigma_tr/2 L_FP (Eq. fpop) with the MPD
+ * (Eq. fp-mpd) or WFD (Eq. w_wfd) angular Laplacian, sigma_a = sigma_t - sigma_{s,0}
+ * and sigma_tr = sigma_{s,0} - sigma_{s,1}.
+ *
+ * Conventions used by every entry point
+ *   - Ordinates mu_1 < ... < mu_N (Gauss-Legendre, weights sum to 2).
+ *   - A context holds B independent slab instances sharing (N, L); instance b
+ *     has K_b cells. Cells of all instances are concatenated instance-major:
+ *     global cell g in [0, sumK), instance b owning [off_b, off_b + K_b).
+ *   - Every instance is solved for R right-hand sides (sources) at once.
+ *   - Moments at the two LD nodes of a cell: node 0 = left edge, 1 = right edge.
+ *   - Layouts are row-major with the LAST index contiguous:
+ *       sigma_t [sumK]                 sigma_s [sumK][L+1]
+ *       q       [R][sumK][2][L+1]      phi     [R][sumK][2][L+1]
+ *     q holds source MOMENTS: the angular source is
+ *     q_n = sum_l (2l+1)/2 P_l(mu_n) q_l, so an isotropic scalar source S is q_0 = S.
+ *   - Boundary conditions: vacuum at both edges (Eq. trans-equation-bc with
+ *     psi_L = psi_R = 0).
+ *   - Ownership: the caller owns every pointer it passes; the library copies
+ *     inputs into device buffers it owns and writes results into the caller's
+ *     buffers before returning (the context stream is synchronised).
+ *   - Errors: every int-returning call returns FPSA_OK (0) or a negative code;
+ *     nothing throws across the ABI. fpsa_last_error() gives the message of the
+ *     last failing call on a context.
+ *   - Threading: one context must not be used from two threads at once.
+ */
+#ifndef FPSA_H
+#define FPSA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FPSA_OK          0
+#define FPSA_EINVAL     -1   /* bad argument (sizes, layout, cross sections) */
+#define FPSA_ENOMEM     -2   /* device allocation failed */
+#define FPSA_ENONFINITE -3   /* a NaN/Inf appeared in an input or iterate */
+#define FPSA_ENOTCONV   -4   /* max_iterations reached before tol */
+#define FPSA_EPIVOT     -5   /* FP block factorization: zero/non-finite pivot or growth above limit */
+#define FPSA_ETIMEOUT   -6   /* a bounded device wait ran out */
+#define FPSA_ECUDA      -7   /* a CUDA runtime call failed */
+#define FPSA_ENOTSUP    -8   /* configuration outside what this build supports */
+#define FPSA_ESTATE     -9   /* call order violated (e.g. solve before set_xs) */
+
+enum fpsa_laplacian { FPSA_LAPLACIAN_MPD = 0, FPSA_LAPLACIAN_WFD = 1 };
+enum fpsa_precision { FPSA_PRECISION_FP64 = 0, FPSA_PRECISION_MIXED = 1 };
+enum fpsa_method    { FPSA_METHOD_SI = 0, FPSA_METHOD_FPSA = 1 };
+enum fpsa_mem       { FPSA_MEM_HOST = 0, FPSA_MEM_DEVICE = 1 };
+
+typedef struct fpsa_ctx fpsa_ctx;
+
+typedef struct {
+    int32_t n_instances;      /* B >= 1 */
+    int32_t n_ordinates;      /* N: even, 2 <= N <= FPSA_MAX_ORDINATES */
+    int32_t n_moments;        /* L+1: 1 <= L+1 <= N */
+    int32_t n_rhs;            /* R >= 1 */
+    const int32_t *n_cells;   /* host [B]: K_b >= 1 */
+    const double *h;          /* host [sumK]: cell widths > 0 */
+    int32_t laplacian;        /* enum fpsa_laplacian */
+    int32_t precision;        /* enum fpsa_precision */
+    int32_t device;           /* CUDA device ordinal */
+    void *stream;             /* cudaStream_t the library launches on; NULL = legacy default */
+} fpsa_desc;
+
+typedef struct {
+    int32_t method;           /* enum fpsa_method */
+    int32_t max_iterations;   /* cap on transport sweeps (FP64) / refinement steps (MIXED) */
+    double tol;               /* stop when max|phi_0^{m+1}-phi_0^m| / max|phi_0^{m+1}| < tol,
+                                 the worst instance/right-hand side deciding (Eq. iterate) */
+    int32_t inner_iterations; /* MIXED: FP32 FPSA iterations per FP64 refinement step (0 = default 6) */
+    double inner_tol;         /* MIXED: inner relative-change target (0 = default 1e-5) */
+    int32_t check_every;      /* test convergence every this many iterations (0 = 1) */
+} fpsa_opts;
+
+typedef struct {
+    int32_t status;           /* same as the return value of fpsa_solve */
+    int32_t iterations;       /* FP64: FPSA/SI iterations; MIXED: total inner iterations */
+    int32_t outer_iterations; /* MIXED: FP64 refinement steps; FP64: = iterations */
+    int32_t sweeps;           /* transport sweeps launched (each covers all instances and rhs) */
+    double rel_change;        /* last tested relative change of phi_0 */
+    double setup_ms;          /* last fpsa_set_xs: upload + FP assembly + block factorization */
+    double solve_ms;          /* this fpsa_solve, wall clock on the host */
+    double cell_angles;       /* sum_b K_b * N * R * sweeps */
+    double pivot_growth;      /* max over FP blocks of max|A^{-1}| * max|A| (FP64 check) */
+} fpsa_stats;
+
+/* Largest N this build supports (FP block 2N x 2N must fit the factorization tile). */
+#define FPSA_MAX_ORDINATES 64
+
+/* Create a context: validates the descriptor, builds the S_N tables (mu_n, w_n,
+ * D = [w_n P_l(mu_n)], M = [(2l+1)/2 P_l(mu_n)], the MPD or WFD Laplacian;
+ * Sec. 2.2 Eqs. phi-mom, treq, fp-mpd, w_wfd), copies h and allocates every
+ * device buffer. *out is NULL on failure. Sets and keeps desc->device current. */
+int fpsa_create(fpsa_ctx **out, const fpsa_desc *desc);
+
+/* Load cross sections and sources (layouts above; mem = enum fpsa_mem says
+ * whether the three pointers are host or device memory), then assemble the LD
+ * FP operator per cell (2N x 2N diagonal blocks, N/2 x N/2 upwind couplings;
+ * Eqs. fpop, fp-mpd-oper, wd-eq-oper) and factor it by block cyclic reduction.
+ * Requires sigma_t > 0, 0 <= sigma_{s,0} <= sigma_t, finite values.
+ * Returns FPSA_EPIVOT if a block is singular or its growth check fails. */
+int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s,
+                const double *q, int32_t mem);
+
+/* Iterate to convergence (opts may be NULL: FPSA, tol 1e-10, 10000 iterations).
+ * phi: output [R][sumK][2][L+1]; phi0: optional initial moments, same layout
+ * (NULL = zero). Both pointers are of kind mem. stats may be NULL.
+ * Returns FPSA_ENOTCONV (with phi holding the last iterate) if max_iterations
+ * is reached. */
+int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *phi0,
+               int32_t mem, fpsa_stats *stats);
+
+/* Release every device buffer of the context (NULL is allowed). */
+void fpsa_destroy(fpsa_ctx *ctx);
+
+/* Static text for a status code. */
+const char *fpsa_strerror(int code);
+
+/* Message of the last failing call on ctx ("" if none); valid until the next call. */
+const char *fpsa_last_error(const fpsa_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPSA_H */

@@ -1,0 +1,192 @@
+"""Thin ctypes binding of libfpsa.so (argument marshalling only).
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+packs descriptors, passes host (numpy) or device (torch CUDA tensor) pointers
+and the current torch stream, and unpacks results. It raises if the library
+is missing: there is no CPU fallback.
+
+Names follow the C ABI in include/fpsa.h: fpsa_create, fpsa_set_xs,
+fpsa_solve, fpsa_destroy, fpsa_strerror, fpsa_last_error.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfpsa.so")
+
+OK, EINVAL, ENOMEM, ENONFINITE, ENOTCONV, EPIVOT, ETIMEOUT, ECUDA, ENOTSUP, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+LAPLACIAN = {"mpd": 0, "wfd": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+METHOD = {"si": 0, "fpsa": 1}
+MEM_HOST, MEM_DEVICE = 0, 1
+MAX_ORDINATES = 64
+
+
+class FpsaDesc(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int32), ("n_ordinates", ctypes.c_int32),
+                ("n_moments", ctypes.c_int32), ("n_rhs", ctypes.c_int32),
+                ("n_cells", ctypes.POINTER(ctypes.c_int32)), ("h", ctypes.POINTER(ctypes.c_double)),
+                ("laplacian", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class FpsaOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("inner_iterations", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("check_every", ctypes.c_int32)]
+
+
+class FpsaStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("outer_iterations", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("rel_change", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("cell_angles", ctypes.c_double),
+                ("pivot_growth", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error"]
+
+_lib = None
+
+
+def load():
+    """Load libfpsa.so once (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfpsa.so not built (run __graft_entry__.build()); no CPU fallback exists")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p
+    lib.fpsa_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(FpsaDesc)]
+    lib.fpsa_create.restype = ctypes.c_int
+    lib.fpsa_set_xs.argtypes = [vp, dp, dp, dp, i32]
+    lib.fpsa_set_xs.restype = ctypes.c_int
+    lib.fpsa_solve.argtypes = [vp, ctypes.POINTER(FpsaOpts), dp, dp, i32, ctypes.POINTER(FpsaStats)]
+    lib.fpsa_solve.restype = ctypes.c_int
+    lib.fpsa_destroy.argtypes = [vp]
+    lib.fpsa_destroy.restype = None
+    lib.fpsa_strerror.argtypes = [ctypes.c_int]
+    lib.fpsa_strerror.restype = ctypes.c_char_p
+    lib.fpsa_last_error.argtypes = [vp]
+    lib.fpsa_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class FpsaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (load().fpsa_strerror(code).decode(), code, msg))
+        self.code = code
+
+
+def _ptr(x):
+    """(pointer, mem kind, keepalive) of a numpy array (host) or torch CUDA tensor (device)."""
+    if isinstance(x, np.ndarray):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        return a.ctypes.data, MEM_HOST, a
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("device arrays must be contiguous float64 torch tensors")
+        return x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+    raise TypeError("expected numpy array or torch tensor")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+class Context:
+    """One fpsa_ctx: B slab instances sharing (N, L), ragged cell counts, R right-hand sides."""
+
+    def __init__(self, n_cells, h, N, L, n_rhs=1, laplacian="mpd", precision="fp64", device=0, stream=None):
+        lib = load()
+        self.n_cells = np.ascontiguousarray(np.atleast_1d(n_cells), dtype=np.int32)
+        self.h = np.ascontiguousarray(h, dtype=np.float64)
+        self.N, self.L, self.R = int(N), int(L), int(n_rhs)
+        self.B = int(self.n_cells.size)
+        self.sumK = int(self.n_cells.sum())
+        if self.h.size != self.sumK:
+            raise ValueError("h must hold sum(n_cells) widths")
+        self.stream = _stream_handle(stream)
+        d = FpsaDesc(self.B, self.N, self.L + 1, self.R,
+                     self.n_cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                     self.h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     LAPLACIAN[laplacian], PRECISION[precision], int(device), ctypes.c_void_p(self.stream))
+        self._h = ctypes.c_void_p()
+        rc = lib.fpsa_create(ctypes.byref(self._h), ctypes.byref(d))
+        if rc != OK:
+            raise FpsaError(rc, "fpsa_create")
+        self._lib = lib
+
+    def _check(self, rc, what):
+        if rc != OK:
+            raise FpsaError(rc, "%s: %s" % (what, self._lib.fpsa_last_error(self._h).decode()))
+
+    def set_xs(self, sigma_t, sigma_s, q):
+        """sigma_t [sumK], sigma_s [sumK][L+1], q [R][sumK][2][L+1] (numpy host or torch cuda float64)."""
+        ps = [_ptr(x) for x in (sigma_t, sigma_s, q)]
+        mems = {m for _, m, _ in ps}
+        if len(mems) != 1:
+            raise TypeError("sigma_t, sigma_s and q must all be host or all device")
+        self._check(self._lib.fpsa_set_xs(self._h, ps[0][0], ps[1][0], ps[2][0], mems.pop()), "fpsa_set_xs")
+
+    def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, out=None, phi0=None,
+              inner_iterations=0, inner_tol=0.0, check_every=1, raise_on_notconv=True):
+        """Returns (phi, stats dict). phi [R][sumK][2][L+1]: into `out` if given (numpy or torch
+        cuda), else a new numpy array."""
+        if out is None:
+            out = np.zeros((self.R, self.sumK, 2, self.L + 1))
+        po, mem, keep = _ptr(out)
+        if phi0 is not None:
+            p0, m0, keep0 = _ptr(phi0)
+            if m0 != mem:
+                raise TypeError("phi0 and out must be of the same memory kind")
+        else:
+            p0 = None
+        o = FpsaOpts(METHOD[method], int(max_iterations), float(tol), int(inner_iterations), float(inner_tol),
+                     int(check_every))
+        st = FpsaStats()
+        rc = self._lib.fpsa_solve(self._h, ctypes.byref(o), po, p0, mem, ctypes.byref(st))
+        if rc != OK and not (rc == ENOTCONV and not raise_on_notconv):
+            self._check(rc, "fpsa_solve")
+        if isinstance(out, np.ndarray) and keep is not out:
+            out[...] = keep
+        return out, st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fpsa_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def context_for(problems, n_rhs=None, **kw):
+    """Context + set_xs for a list of problem dicts (see inputs.py) sharing N and L."""
+    probs = problems if isinstance(problems, (list, tuple)) else [problems]
+    N, L = probs[0]["N"], probs[0]["L"]
+    K = [p["h"].size for p in probs]
+    h = np.concatenate([p["h"] for p in probs])
+    st = np.concatenate([p["sigma_t"] for p in probs])
+    ss = np.concatenate([p["sigma_s"] for p in probs])
+    Qs = [p["Q"] if p["Q"].ndim == 4 else p["Q"][None] for p in probs]
+    R = Qs[0].shape[0] if n_rhs is None else n_rhs
+    q = np.concatenate(Qs, axis=1)
+    ctx = Context(K, h, N, L, n_rhs=R, **kw)
+    ctx.set_xs(st, ss, q)
+    return ctx

@@ -1,0 +1,450 @@
+// C ABI and host driver of the FPSA library (declarations and contracts in include/fpsa.h).
+//
+// One FPSA source iteration (Eqs. predict, correct, iterate of arXiv:1907.13013)
+// is, per sweep, the launch sequence
+//   k_sweep            psi^{m+1/2} = L^{-1} q                      (LD upwind sweep)
+//   k_fp_rhs           phi^{m+1/2} = D psi^{m+1/2};  rhs = m (x) M Sigma (phi^{m+1/2} - phi^m)
+//   k_bcr_fwd x levels, roots, k_bcr_bwd x levels     upsilon = F^{-1} rhs
+//   k_update_scatter   phi^{m+1} = phi^{m+1/2} + D upsilon; q = M (Sigma phi^{m+1} + Q)
+// with the convergence maxima of Eq. iterate accumulated in k_update_scatter.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fpsa_internal.h"
+#include "kernels.cuh"
+
+using namespace fpsa;
+
+namespace {
+
+constexpr int kSweepThreads = 256;
+constexpr int kContractThreads = 256;
+constexpr int kInvertThreads = 512;
+
+template <typename T>
+struct PathBuffers {
+    T *DT = nullptr, *MT = nullptr;          // D^T [n][l], M^T [l][n]
+    T *sigma_s = nullptr;                    // [sumK][N] (zero for l >= L+1)
+    T *Q = nullptr;                          // [R][sumK][2][N]
+    T *coef = nullptr;                       // [sumK][6][N]
+    T *A = nullptr, *Bc = nullptr, *Cc = nullptr;
+    T *phi = nullptr, *phi_half = nullptr, *q = nullptr, *psi = nullptr, *rhs = nullptr;
+};
+
+}  // namespace
+
+struct fpsa_ctx {
+    Geometry geo;
+    Tables tab;
+    int laplacian = 0, precision = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool xs_ready = false;
+    double setup_ms = 0.0, pivot_growth = 0.0;
+    std::vector<void *> allocs;
+
+    int32_t *d_off = nullptr, *d_K = nullptr, *d_cell_inst = nullptr, *d_slot_base = nullptr;
+    double *d_mu = nullptr, *d_Afp = nullptr, *d_h = nullptr, *d_sigma_t = nullptr, *d_s0 = nullptr,
+           *d_s1 = nullptr;
+    std::vector<BcrItem *> d_levels;
+    BcrItem *d_roots = nullptr;
+    unsigned long long *d_conv = nullptr, *d_growth = nullptr;
+    int *d_status = nullptr;
+    double *d_result = nullptr;
+    double *h_result = nullptr;  // pinned
+
+    PathBuffers<double> p64;
+};
+
+namespace {
+
+int fail(fpsa_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FPSA_ENOMEM : FPSA_ECUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(fpsa_ctx *ctx, P **p, size_t count) {
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(P));
+    if (e != cudaSuccess) return e;
+    ctx->allocs.push_back(v);
+    *p = static_cast<P *>(v);
+    return cudaSuccess;
+}
+
+template <typename T>
+size_t contract_smem(int N) { return 2 * 2 * (size_t)kContractCells * N * sizeof(T); }
+
+template <typename T>
+size_t invert_smem(int N) {
+    const int n2 = 2 * N;
+    return ((size_t)n2 * (n2 + 1) + n2) * sizeof(T) + (size_t)n2 * sizeof(int);
+}
+
+template <typename T>
+int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p) {
+    const Geometry &g = ctx->geo;
+    const size_t N = g.N, ang = (size_t)g.R * g.sumK * 2 * N;
+    const int h2 = g.N / 2;
+    CK(dalloc(ctx, &p.DT, N * N));
+    CK(dalloc(ctx, &p.MT, N * N));
+    CK(dalloc(ctx, &p.sigma_s, (size_t)g.sumK * N));
+    CK(dalloc(ctx, &p.Q, ang));
+    CK(dalloc(ctx, &p.coef, (size_t)g.sumK * 6 * N));
+    CK(dalloc(ctx, &p.A, (size_t)g.sumK * 4 * N * N));
+    CK(dalloc(ctx, &p.Bc, (size_t)g.n_slots * h2 * h2));
+    CK(dalloc(ctx, &p.Cc, (size_t)g.n_slots * h2 * h2));
+    CK(dalloc(ctx, &p.phi, ang));
+    CK(dalloc(ctx, &p.phi_half, ang));
+    CK(dalloc(ctx, &p.q, ang));
+    CK(dalloc(ctx, &p.psi, ang));
+    CK(dalloc(ctx, &p.rhs, ang));
+    std::vector<T> DT(N * N), MT(N * N);
+    for (size_t l = 0; l < N; ++l)
+        for (size_t n = 0; n < N; ++n) {
+            DT[n * N + l] = (T)ctx->tab.D[l * N + n];
+            MT[l * N + n] = (T)ctx->tab.M[n * N + l];
+        }
+    CK(cudaMemcpy(p.DT, DT.data(), N * N * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p.MT, MT.data(), N * N * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaFuncSetAttribute(k_bcr_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)invert_smem<T>(g.N)));
+    return FPSA_OK;
+}
+
+// Upload per-path cross sections / sources (padded to N moments) and factor the FP operator.
+template <typename T>
+int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, const std::vector<double> &qm) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N, L1 = g.L1, n2 = 2 * N, h2 = N / 2;
+    cudaStream_t st = ctx->stream;
+    std::vector<T> sp((size_t)g.sumK * N, T(0));
+    for (int c = 0; c < g.sumK; ++c)
+        for (int l = 0; l < L1; ++l) sp[(size_t)c * N + l] = (T)ss[(size_t)c * L1 + l];
+    const size_t ncol = (size_t)g.R * g.sumK * 2;
+    std::vector<T> Qp(ncol * N, T(0));
+    for (size_t c = 0; c < ncol; ++c)
+        for (int l = 0; l < L1; ++l) Qp[c * N + l] = (T)qm[c * L1 + l];
+    CK(cudaMemcpyAsync(p.sigma_s, sp.data(), sp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p.Q, Qp.data(), Qp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    {
+        const size_t tot = (size_t)g.sumK * N;
+        k_sweep_coef<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->d_mu, ctx->d_h, ctx->d_sigma_t, N,
+                                                                        g.sumK, p.coef);
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemsetAsync(p.Bc, 0, (size_t)g.n_slots * h2 * h2 * sizeof(T), st));
+    CK(cudaMemsetAsync(p.Cc, 0, (size_t)g.n_slots * h2 * h2 * sizeof(T), st));
+    k_fp_assemble<T><<<g.sumK, 256, 0, st>>>(ctx->d_mu, ctx->d_Afp, ctx->d_h, ctx->d_sigma_t, ctx->d_s0, ctx->d_s1,
+                                             ctx->d_cell_inst, ctx->d_off, ctx->d_K, ctx->d_slot_base, N, p.A, p.Bc,
+                                             p.Cc);
+    CK(cudaGetLastError());
+    const size_t ism = invert_smem<T>(N);
+    for (int l = 0; l < g.n_levels; ++l) {
+        const int ni = (int)g.levels[l].size();
+        if (!ni) continue;
+        k_bcr_invert<T><<<ni, kInvertThreads, ism, st>>>(p.A, ctx->d_levels[l], n2, ctx->d_growth, ctx->d_status);
+        CK(cudaGetLastError());
+        k_bcr_schur<T><<<ni, 256, (size_t)h2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], N);
+        CK(cudaGetLastError());
+    }
+    k_bcr_invert<T><<<g.B, kInvertThreads, ism, st>>>(p.A, ctx->d_roots, n2, ctx->d_growth, ctx->d_status);
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
+template <typename T>
+int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N, n2 = 2 * N, h2 = N / 2;
+    cudaStream_t st = ctx->stream;
+    for (int l = 0; l < g.n_levels; ++l) {
+        const int ni = (int)g.levels[l].size();
+        if (!ni) continue;
+        k_bcr_fwd<T><<<dim3(ni, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
+                                                                      g.sumK);
+    }
+    k_bcr_fwd<T><<<dim3(g.B, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_roots, rhs, N, g.sumK);
+    for (int l = g.n_levels - 1; l >= 0; --l) {
+        const int ni = (int)g.levels[l].size();
+        if (!ni) continue;
+        k_bcr_bwd<T><<<dim3(ni, g.R), 128, 2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
+                                                                      g.sumK);
+    }
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
+int check_xs(fpsa_ctx *ctx, const double *st, const double *ss, const double *q) {
+    const Geometry &g = ctx->geo;
+    for (int c = 0; c < g.sumK; ++c) {
+        if (!std::isfinite(st[c]) || !(st[c] > 0.0))
+            return fail(ctx, FPSA_EINVAL, "sigma_t must be finite and > 0 (cell " + std::to_string(c) + ")");
+        for (int l = 0; l < g.L1; ++l)
+            if (!std::isfinite(ss[(size_t)c * g.L1 + l]))
+                return fail(ctx, FPSA_ENONFINITE, "non-finite sigma_s at cell " + std::to_string(c));
+        const double s0 = ss[(size_t)c * g.L1];
+        if (s0 < 0.0 || s0 > st[c])
+            return fail(ctx, FPSA_EINVAL, "need 0 <= sigma_s0 <= sigma_t (cell " + std::to_string(c) + ")");
+    }
+    const size_t nq = (size_t)g.R * g.sumK * 2 * g.L1;
+    for (size_t i = 0; i < nq; ++i)
+        if (!std::isfinite(q[i])) return fail(ctx, FPSA_ENONFINITE, "non-finite source moment");
+    return FPSA_OK;
+}
+
+template <typename T>
+int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const double *phi0, int mem, double *phi_out,
+               fpsa_stats &stats) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N, L1 = g.L1;
+    cudaStream_t st = ctx->stream;
+    const size_t ncol = (size_t)g.R * g.sumK * 2;
+    const size_t csm = contract_smem<T>(N);
+    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    const dim3 sgrid(N, g.B, g.R);
+    const bool fpsa = o.method == FPSA_METHOD_FPSA;
+
+    if (phi0) {
+        CK(cudaMemsetAsync(p.phi, 0, ncol * N * sizeof(T), st));
+        CK(cudaMemcpy2DAsync(p.phi, N * sizeof(T), phi0, L1 * sizeof(double), L1 * sizeof(double), ncol,
+                             mem == FPSA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemsetAsync(p.phi, 0, ncol * N * sizeof(T), st));
+    }
+    CK(cudaMemsetAsync(ctx->d_conv, 0, (size_t)g.R * g.B * 2 * sizeof(unsigned long long), st));
+    k_scatter<T><<<cgrid, kContractThreads, csm / 2, st>>>(p.phi, p.sigma_s, p.Q, p.MT, p.q, N, g.sumK);
+    CK(cudaGetLastError());
+    const int every = o.check_every > 0 ? o.check_every : 1;
+    int status = FPSA_ENOTCONV;
+    double e = INFINITY;
+    int it = 0;
+    for (it = 1; it <= o.max_iterations; ++it) {
+        k_sweep<T, kSweepThreads><<<sgrid, kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu, ctx->d_off, ctx->d_K,
+                                                                  N, g.sumK);
+        if (fpsa) {
+            k_fp_rhs<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, p.phi, p.phi_half, p.sigma_s, ctx->d_h, p.DT,
+                                                               p.MT, p.rhs, N, g.sumK);
+            int rc = bcr_solve(ctx, p, p.rhs);
+            if (rc) return rc;
+            k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.rhs, p.phi_half, p.phi, p.sigma_s, p.Q, p.DT,
+                                                                       p.MT, p.q, ctx->d_cell_inst, g.B, ctx->d_conv,
+                                                                       N, g.sumK);
+        } else {
+            k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const T *)nullptr, p.phi, p.sigma_s,
+                                                                       p.Q, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
+                                                                       ctx->d_conv, N, g.sumK);
+        }
+        CK(cudaGetLastError());
+        if (it % every == 0 || it == o.max_iterations) {
+            k_conv_finalize<<<1, 256, 0, st>>>(ctx->d_conv, g.R * g.B, ctx->d_result);
+            CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            e = ctx->h_result[0];
+            if (std::isnan(e)) {
+                status = fail(ctx, FPSA_ENONFINITE, "non-finite iterate at iteration " + std::to_string(it));
+                break;
+            }
+            if (e < o.tol) {
+                status = FPSA_OK;
+                break;
+            }
+        }
+    }
+    if (it > o.max_iterations) it = o.max_iterations;
+    stats.iterations = it;
+    stats.outer_iterations = it;
+    stats.sweeps = it;
+    stats.rel_change = e;
+    CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(T), L1 * sizeof(double), ncol,
+                         mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (status == FPSA_ENOTCONV)
+        fail(ctx, FPSA_ENOTCONV, "not converged after " + std::to_string(o.max_iterations) + " iterations");
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fpsa_strerror(int code) {
+    switch (code) {
+        case FPSA_OK: return "ok";
+        case FPSA_EINVAL: return "invalid argument";
+        case FPSA_ENOMEM: return "device out of memory";
+        case FPSA_ENONFINITE: return "non-finite value";
+        case FPSA_ENOTCONV: return "iteration did not converge";
+        case FPSA_EPIVOT: return "FP block factorization failed (pivot or growth)";
+        case FPSA_ETIMEOUT: return "bounded device wait timed out";
+        case FPSA_ECUDA: return "CUDA runtime error";
+        case FPSA_ENOTSUP: return "configuration not supported by this build";
+        case FPSA_ESTATE: return "call order violated";
+        default: return "unknown status";
+    }
+}
+
+const char *fpsa_last_error(const fpsa_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void fpsa_destroy(fpsa_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->h_result) cudaFreeHost(ctx->h_result);
+    delete ctx;
+}
+
+int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
+    if (!out) return FPSA_EINVAL;
+    *out = nullptr;
+    if (!d || !d->n_cells || !d->h) return FPSA_EINVAL;
+    if (d->n_instances < 1 || d->n_rhs < 1 || d->n_ordinates < 2 || d->n_ordinates % 2 ||
+        d->n_moments < 1 || d->n_moments > d->n_ordinates)
+        return FPSA_EINVAL;
+    if (d->laplacian != FPSA_LAPLACIAN_MPD && d->laplacian != FPSA_LAPLACIAN_WFD) return FPSA_EINVAL;
+    if (d->precision != FPSA_PRECISION_FP64 && d->precision != FPSA_PRECISION_MIXED) return FPSA_EINVAL;
+    if (d->n_ordinates > FPSA_MAX_ORDINATES) return FPSA_ENOTSUP;
+    if (d->precision == FPSA_PRECISION_MIXED) return FPSA_ENOTSUP;
+    long long sumK = 0;
+    for (int b = 0; b < d->n_instances; ++b) {
+        if (d->n_cells[b] < 1) return FPSA_EINVAL;
+        sumK += d->n_cells[b];
+    }
+    if (sumK > (1ll << 30)) return FPSA_EINVAL;
+    for (long long c = 0; c < sumK; ++c)
+        if (!(d->h[c] > 0.0) || !std::isfinite(d->h[c])) return FPSA_EINVAL;
+
+    fpsa_ctx *ctx = new fpsa_ctx();
+    ctx->laplacian = d->laplacian;
+    ctx->precision = d->precision;
+    ctx->device = d->device;
+    ctx->stream = static_cast<cudaStream_t>(d->stream);
+    auto bail = [&](int rc) {
+        fpsa_destroy(ctx);
+        return rc;
+    };
+    if (cudaSetDevice(d->device) != cudaSuccess) return bail(FPSA_ECUDA);
+    build_tables(d->n_ordinates, d->n_moments, d->laplacian, ctx->tab);
+    build_geometry(d->n_cells, d->n_instances, d->n_ordinates, d->n_moments, d->n_rhs, ctx->geo);
+    const Geometry &g = ctx->geo;
+    int rc = [&]() -> int {
+        CK(dalloc(ctx, &ctx->d_off, g.B));
+        CK(dalloc(ctx, &ctx->d_K, g.B));
+        CK(dalloc(ctx, &ctx->d_cell_inst, g.sumK));
+        CK(dalloc(ctx, &ctx->d_slot_base, g.sumK));
+        CK(dalloc(ctx, &ctx->d_mu, g.N));
+        CK(dalloc(ctx, &ctx->d_Afp, (size_t)g.N * g.N));
+        CK(dalloc(ctx, &ctx->d_h, g.sumK));
+        CK(dalloc(ctx, &ctx->d_sigma_t, g.sumK));
+        CK(dalloc(ctx, &ctx->d_s0, g.sumK));
+        CK(dalloc(ctx, &ctx->d_s1, g.sumK));
+        CK(dalloc(ctx, &ctx->d_conv, (size_t)g.R * g.B * 2));
+        CK(dalloc(ctx, &ctx->d_growth, 1));
+        CK(dalloc(ctx, &ctx->d_status, 1));
+        CK(dalloc(ctx, &ctx->d_result, 2));
+        CK(cudaMallocHost(&ctx->h_result, 2 * sizeof(double)));
+        CK(cudaMemcpy(ctx->d_off, g.off.data(), g.B * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_K, g.K.data(), g.B * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_cell_inst, g.cell_inst.data(), g.sumK * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_slot_base, g.slot_base.data(), g.sumK * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_mu, ctx->tab.mu.data(), g.N * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_Afp, ctx->tab.Afp.data(), (size_t)g.N * g.N * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_h, d->h, g.sumK * sizeof(double), cudaMemcpyHostToDevice));
+        ctx->d_levels.assign(g.n_levels, nullptr);
+        for (int l = 0; l < g.n_levels; ++l) {
+            CK(dalloc(ctx, &ctx->d_levels[l], g.levels[l].size()));
+            CK(cudaMemcpy(ctx->d_levels[l], g.levels[l].data(), g.levels[l].size() * sizeof(BcrItem),
+                          cudaMemcpyHostToDevice));
+        }
+        CK(dalloc(ctx, &ctx->d_roots, g.B));
+        CK(cudaMemcpy(ctx->d_roots, g.roots.data(), g.B * sizeof(BcrItem), cudaMemcpyHostToDevice));
+        return alloc_path(ctx, ctx->p64);
+    }();
+    if (rc != FPSA_OK) return bail(rc);
+    *out = ctx;
+    return FPSA_OK;
+}
+
+int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, const double *q, int32_t mem) {
+    if (!ctx) return FPSA_EINVAL;
+    if (!sigma_t || !sigma_s || !q) return fail(ctx, FPSA_EINVAL, "null input pointer");
+    if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
+    CK(cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    const Geometry &g = ctx->geo;
+    const size_t nss = (size_t)g.sumK * g.L1, nq = (size_t)g.R * g.sumK * 2 * g.L1;
+    std::vector<double> st(g.sumK), ss(nss), qm(nq);
+    const cudaMemcpyKind k = mem == FPSA_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpy(st.data(), sigma_t, g.sumK * sizeof(double), k));
+    CK(cudaMemcpy(ss.data(), sigma_s, nss * sizeof(double), k));
+    CK(cudaMemcpy(qm.data(), q, nq * sizeof(double), k));
+    ctx->xs_ready = false;
+    int rc = check_xs(ctx, st.data(), ss.data(), qm.data());
+    if (rc) return rc;
+    std::vector<double> s0(g.sumK), s1(g.sumK);
+    for (int c = 0; c < g.sumK; ++c) {
+        s0[c] = ss[(size_t)c * g.L1];
+        s1[c] = g.L1 > 1 ? ss[(size_t)c * g.L1 + 1] : 0.0;
+    }
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->d_sigma_t, st.data(), g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_s0, s0.data(), g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_s1, s1.data(), g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_growth, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+    rc = setup_path(ctx, ctx->p64, ss, qm);
+    if (rc) return rc;
+    unsigned long long growth = 0;
+    int status = 0;
+    CK(cudaMemcpyAsync(&growth, ctx->d_growth, sizeof(growth), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(status), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double gr;
+    std::memcpy(&gr, &growth, sizeof(gr));
+    ctx->pivot_growth = gr;
+    ctx->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (status || !std::isfinite(gr) || gr > 1e14)
+        return fail(ctx, FPSA_EPIVOT, "FP block factorization failed: growth " + std::to_string(gr));
+    ctx->xs_ready = true;
+    return FPSA_OK;
+}
+
+int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *phi0, int32_t mem,
+               fpsa_stats *stats) {
+    if (!ctx) return FPSA_EINVAL;
+    if (!phi) return fail(ctx, FPSA_EINVAL, "null phi");
+    if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
+    if (!ctx->xs_ready) return fail(ctx, FPSA_ESTATE, "fpsa_set_xs must succeed before fpsa_solve");
+    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-10, 0, 0.0, 1};
+    if (opts) o = *opts;
+    if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA) return fail(ctx, FPSA_EINVAL, "bad method");
+    if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol");
+    CK(cudaSetDevice(ctx->device));
+    fpsa_stats s{};
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s);
+    s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    s.status = rc;
+    s.setup_ms = ctx->setup_ms;
+    s.pivot_growth = ctx->pivot_growth;
+    s.cell_angles = (double)ctx->geo.sumK * ctx->geo.N * ctx->geo.R * s.sweeps;
+    if (stats) *stats = s;
+    return rc;
+}
+
+}  // extern "C"

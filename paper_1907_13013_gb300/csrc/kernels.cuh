@@ -1,0 +1,598 @@
+// Device kernels of the FPSA source iteration (arXiv:1907.13013), templated on
+// the arithmetic type T (double for the FP64 path, float for the inner solves of
+// the mixed-precision path).
+//
+// Data layout in HBM (last index contiguous):
+//   angular / nodal arrays   X[r][g][a][n]   r < R, g < sumK, a in {0=L,1=R}, n < N
+//   moment arrays            P[r][g][a][l]   l padded to N (l >= L+1 unused or 0)
+//   sweep coefficients       coef[g][6][n]
+//   FP blocks                A[g][2N][2N]    row-major, replaced in place by the
+//                                            TRANSPOSED inverse when g is eliminated
+//   upwind couplings         Bc/Cc[slot][N/2][N/2]
+// The 2N unknowns of a cell are [u_L(0..N-1), u_R(0..N-1)] with ordinates
+// ascending, so the index sets of the LD upwind coupling are
+//   L- = [0, N/2)  L+ = [N/2, N)  R- = [N, 3N/2)  R+ = [3N/2, 2N)
+// (L+ and R- receive inflow from the neighbours, R+ and L- are the outflows).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fpsa_internal.h"
+
+namespace fpsa {
+
+// ---------------------------------------------------------------------------
+// LD cell algebra (Sec. 2.2 reading: Galerkin LD, consistent mass, upwind).
+// For ordinate mu with nu = |mu|, the upwind node u (L for mu>0, R for mu<0)
+// and the downwind node d, one cell solves
+//   [[nu/2 + s h/3, nu/2 + s h/6], [-nu/2 + s h/6, nu/2 + s h/3]] [psi_u, psi_d]
+//       = m [q_u, q_d] + [nu psi_in, 0],    m = (h/6)[[2,1],[1,2]].
+// Its solution is affine in (q_u, q_d, psi_in):
+//   psi_u = G_uu q_u + G_ud q_d + a_u psi_in
+//   psi_d = G_du q_u + G_dd q_d + alpha psi_in
+// alpha = (6 - 2 tau)/(6 + 4 tau + tau^2), tau = s h / nu, is the cell
+// transmission (the [1/2] Pade approximant of exp(-tau)). The coefficients are
+// computed once per cross-section set in FP64 and stored as coef[g][k][n] with
+// k = 0 alpha, 1 a_u, 2 G_uu, 3 G_ud, 4 G_du, 5 G_dd.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sweep_coef(const double *__restrict__ mu, const double *__restrict__ h,
+                             const double *__restrict__ sigma_t, int N, int sumK, T *__restrict__ coef) {
+    size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (idx >= (size_t)sumK * N) return;
+    int g = (int)(idx / N), n = (int)(idx - (size_t)g * N);
+    double nu = fabs(mu[n]), hh = h[g], sh = sigma_t[g] * hh;
+    double T00 = 0.5 * nu + sh / 3.0, T01 = 0.5 * nu + sh / 6.0, T10 = -0.5 * nu + sh / 6.0, T11 = T00;
+    double id = 1.0 / (T00 * T11 - T01 * T10);
+    double I00 = T11 * id, I01 = -T01 * id, I10 = -T10 * id, I11 = T00 * id;
+    double m0 = hh / 3.0, m1 = hh / 6.0;
+    T *c = coef + (size_t)g * 6 * N + n;
+    c[0] = (T)(I10 * nu);
+    c[N] = (T)(I00 * nu);
+    c[2 * N] = (T)(I00 * m0 + I01 * m1);
+    c[3 * N] = (T)(I00 * m1 + I01 * m0);
+    c[4 * N] = (T)(I10 * m0 + I11 * m1);
+    c[5 * N] = (T)(I10 * m1 + I11 * m0);
+}
+
+// ---------------------------------------------------------------------------
+// Transport sweep L psi = q (Eq. trsi / Eq. predict), one block per
+// (ordinate, instance, rhs). The sequential recurrence over cells
+// x_{k+1} = alpha_k x_k + beta_k (x = outflow of cell k, beta_k its outflow
+// for zero inflow) is an affine map per cell; affine maps compose
+// associatively, so each thread composes the maps of a contiguous chunk of
+// cells (pass 1), the block scans the chunk maps (warp shuffles, then across
+// warps), and each thread re-sweeps its chunk from the exact inflow (pass 2).
+// Vacuum inflow at the domain edge.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Affine {
+    T a, b;  // x -> a x + b
+};
+
+template <typename T>
+__device__ __forceinline__ Affine<T> compose(Affine<T> first, Affine<T> then) {
+    return {then.a * first.a, then.a * first.b + then.b};
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__restrict__ psi,
+                                              const T *__restrict__ coef, const double *__restrict__ mu,
+                                              const int32_t *__restrict__ off, const int32_t *__restrict__ Kc,
+                                              int N, int sumK) {
+    __shared__ Affine<T> warp_tot[NT / 32];
+    const int n = blockIdx.x, b = blockIdx.y, r = blockIdx.z;
+    const int K = Kc[b], o = off[b];
+    const bool fwd = mu[n] > 0.0;
+    const int nu_ = fwd ? 0 : 1, nd_ = 1 - nu_;
+    const int chunk = (K + NT - 1) / NT;
+    const int p0 = min((int)threadIdx.x * chunk, K), p1 = min(p0 + chunk, K);
+    const size_t base = ((size_t)r * sumK + o) * 2 * N + n;
+    const T *qb = q + base;
+    T *pb = psi + base;
+    const T *cb = coef + (size_t)o * 6 * N + n;
+
+    Affine<T> m{T(1), T(0)};
+    for (int p = p0; p < p1; ++p) {
+        const int c = fwd ? p : K - 1 - p;
+        const T qu = qb[(size_t)(2 * c + nu_) * N], qd = qb[(size_t)(2 * c + nd_) * N];
+        const T *cc = cb + (size_t)c * 6 * N;
+        const T al = cc[0], gdu = cc[4 * N], gdd = cc[5 * N];
+        m.b = al * m.b + (gdu * qu + gdd * qd);
+        m.a = al * m.a;
+    }
+    // inclusive scan over the block (thread order = sweep order)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    Affine<T> inc = m;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T pa = __shfl_up_sync(0xffffffffu, inc.a, d);
+        T pbv = __shfl_up_sync(0xffffffffu, inc.b, d);
+        if (lane >= d) inc = compose(Affine<T>{pa, pbv}, inc);
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        Affine<T> t = (lane < NT / 32) ? warp_tot[lane] : Affine<T>{T(1), T(0)};
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            T pa = __shfl_up_sync(0xffffffffu, t.a, d);
+            T pbv = __shfl_up_sync(0xffffffffu, t.b, d);
+            if (lane >= d) t = compose(Affine<T>{pa, pbv}, t);
+        }
+        if (lane < NT / 32) warp_tot[lane] = t;  // inclusive prefix over warps
+    }
+    __syncthreads();
+    // exclusive prefix for this thread, applied to the vacuum inflow 0
+    T before_warp = (wid > 0) ? warp_tot[wid - 1].b : T(0);
+    T inc_b_full = inc.a * before_warp + inc.b;  // inclusive, thread-level
+    T x = __shfl_up_sync(0xffffffffu, inc_b_full, 1);
+    if (lane == 0) x = before_warp;
+
+    for (int p = p0; p < p1; ++p) {
+        const int c = fwd ? p : K - 1 - p;
+        const T qu = qb[(size_t)(2 * c + nu_) * N], qd = qb[(size_t)(2 * c + nd_) * N];
+        const T *cc = cb + (size_t)c * 6 * N;
+        const T al = cc[0], au = cc[N], guu = cc[2 * N], gud = cc[3 * N], gdu = cc[4 * N], gdd = cc[5 * N];
+        const T pu = guu * qu + gud * qd + au * x;
+        const T pd = gdu * qu + gdd * qd + al * x;
+        pb[(size_t)(2 * c + nu_) * N] = pu;
+        pb[(size_t)(2 * c + nd_) * N] = pd;
+        x = pd;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Angular contractions. Ys[c][o] = sum_k MatT[k][o] Xs[c][k] over the columns
+// c < ncols of a shared-memory tile; MatT is the transposed operator in global
+// memory (k-major, so consecutive threads read consecutive o).
+//   moments    phi_l = sum_n D[l][n] psi_n            (Eq. phi-mom)   MatT = D^T
+//   expansion  q_n = sum_l M[n][l] (sigma_{s,l} phi_l + Q_l)  (Eq. treq) MatT = M^T
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void block_contract(const T *Xs, int ldx, const T *__restrict__ MatT, int N, int ncols,
+                                               T *Ys, int ldy) {
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
+        const int c = idx / N, o = idx - c * N;
+        const T *x = Xs + c * ldx;
+        T acc = T(0);
+#pragma unroll 8
+        for (int k = 0; k < N; ++k) acc = fma(MatT[(size_t)k * N + o], x[k], acc);
+        Ys[c * ldy + o] = acc;
+    }
+}
+
+// Columns handled by one contraction block: CB cells x 2 nodes.
+constexpr int kContractCells = 8;
+
+// q = M (sigma_s phi + Q) for every column (Eq. treq: scattering + external source).
+template <typename T>
+__global__ void k_scatter(const T *__restrict__ phi, const T *__restrict__ sigma_s, const T *__restrict__ Qext,
+                          const T *__restrict__ MT, T *__restrict__ q, int N, int sumK) {
+    extern __shared__ unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);
+    const int r = blockIdx.y;
+    const int g0 = blockIdx.x * kContractCells;
+    const int ncell = min(kContractCells, sumK - g0);
+    const int ncols = 2 * ncell;
+    const size_t colbase = ((size_t)r * sumK + g0) * 2;
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
+        const int c = idx / N, l = idx - c * N;
+        const int g = g0 + c / 2;
+        const size_t e = (colbase + c) * N + l;
+        Xs[c * N + l] = sigma_s[(size_t)g * N + l] * phi[e] + Qext[e];
+    }
+    __syncthreads();
+    block_contract(Xs, N, MT, N, ncols, q + colbase * N, N);
+}
+
+// FPSA, after the sweep: phi_half = D psi_half; then the FP right-hand side
+// m (x) M diag(sigma_s) (phi_half - phi)  (Eq. correct: S (psi^{m+1/2} - psi^m),
+// mass-weighted for the LD system).
+template <typename T>
+__global__ void k_fp_rhs(const T *__restrict__ psi_half, const T *__restrict__ phi, T *__restrict__ phi_half,
+                         const T *__restrict__ sigma_s, const double *__restrict__ h, const T *__restrict__ DT,
+                         const T *__restrict__ MT, T *__restrict__ rhs, int N, int sumK) {
+    extern __shared__ unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);
+    T *Ys = Xs + 2 * kContractCells * N;
+    const int r = blockIdx.y;
+    const int g0 = blockIdx.x * kContractCells;
+    const int ncell = min(kContractCells, sumK - g0);
+    const int ncols = 2 * ncell;
+    const size_t colbase = ((size_t)r * sumK + g0) * 2;
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) Xs[idx] = psi_half[colbase * N + idx];
+    __syncthreads();
+    block_contract(Xs, N, DT, N, ncols, Ys, N);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
+        const int c = idx / N, l = idx - c * N;
+        const int g = g0 + c / 2;
+        const T ph = Ys[idx];
+        phi_half[colbase * N + idx] = ph;
+        Xs[idx] = sigma_s[(size_t)g * N + l] * (ph - phi[colbase * N + idx]);
+    }
+    __syncthreads();
+    block_contract(Xs, N, MT, N, ncols, Ys, N);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * N; idx += blockDim.x) {
+        const int cl = idx / N, n = idx - cl * N;
+        const T w = (T)(h[g0 + cl] / 6.0);
+        const T r0 = Ys[(2 * cl) * N + n], r1 = Ys[(2 * cl + 1) * N + n];
+        rhs[(colbase + 2 * cl) * N + n] = w * (T(2) * r0 + r1);
+        rhs[(colbase + 2 * cl + 1) * N + n] = w * (r0 + T(2) * r1);
+    }
+}
+
+// Order-preserving key of a non-negative double (NaN sorts above +Inf).
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    return (unsigned long long)__double_as_longlong(fabs(x));
+}
+
+// phi_new = (phi_base ? phi_base : 0) + D v ; convergence maxima; then
+// q = M (sigma_s phi_new + Q) for the next sweep.
+//   SI:   phi_base = NULL, v = psi (Eq. trsi)
+//   FPSA: phi_base = phi_half, v = FP correction upsilon (Eq. correct)
+// conv[(r*B + b)*2 + 0] = max |phi_0 new - old|, [..+1] = max |phi_0 new|.
+template <typename T>
+__global__ void k_update_scatter(const T *__restrict__ v, const T *__restrict__ phi_base, T *__restrict__ phi,
+                                 const T *__restrict__ sigma_s, const T *__restrict__ Qext,
+                                 const T *__restrict__ DT, const T *__restrict__ MT, T *__restrict__ q,
+                                 const int32_t *__restrict__ cell_inst, int B,
+                                 unsigned long long *__restrict__ conv, int N, int sumK) {
+    extern __shared__ unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);
+    T *Ys = Xs + 2 * kContractCells * N;
+    const int r = blockIdx.y;
+    const int g0 = blockIdx.x * kContractCells;
+    const int ncell = min(kContractCells, sumK - g0);
+    const int ncols = 2 * ncell;
+    const size_t colbase = ((size_t)r * sumK + g0) * 2;
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) Xs[idx] = v[colbase * N + idx];
+    __syncthreads();
+    block_contract(Xs, N, DT, N, ncols, Ys, N);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
+        const int c = idx / N, l = idx - c * N;
+        const int g = g0 + c / 2;
+        const size_t e = colbase * N + idx;
+        T pn = Ys[idx];
+        if (phi_base) pn += phi_base[e];
+        if (l == 0) {
+            const int slot = (r * B + cell_inst[g]) * 2;
+            atomicMax(conv + slot, dkey((double)pn - (double)phi[e]));
+            atomicMax(conv + slot + 1, dkey((double)pn));
+        }
+        phi[e] = pn;
+        Xs[idx] = sigma_s[(size_t)g * N + l] * pn + Qext[e];
+    }
+    __syncthreads();
+    block_contract(Xs, N, MT, N, ncols, q + colbase * N, N);
+}
+
+// Worst relative change over (rhs, instance); resets the accumulators.
+// out[0] = max_rb conv_d / conv_a (NaN if any value was non-finite).
+__global__ void k_conv_finalize(unsigned long long *conv, int nrb, double *out) {
+    __shared__ double red[256];
+    double worst = 0.0;
+    bool bad = false;
+    for (int i = threadIdx.x; i < nrb; i += blockDim.x) {
+        double d = __longlong_as_double((long long)conv[2 * i]);
+        double a = __longlong_as_double((long long)conv[2 * i + 1]);
+        if (!isfinite(d) || !isfinite(a)) bad = true;
+        double e = (a > 0.0) ? d / a : (d > 0.0 ? INFINITY : 0.0);
+        worst = fmax(worst, e);
+        conv[2 * i] = 0ull;
+        conv[2 * i + 1] = 0ull;
+    }
+    red[threadIdx.x] = bad ? NAN : worst;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            double x = red[threadIdx.x], y = red[threadIdx.x + s];
+            red[threadIdx.x] = (isnan(x) || isnan(y)) ? NAN : fmax(x, y);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// ---------------------------------------------------------------------------
+// FP operator, LD in space (Eqs. fpop, fp-mpd-oper, wd-eq-oper):
+//   mu d/dz + K_g,  K_g = sigma_a I - sigma_tr/2 A_FP,
+// cell block A_g[a*N+n][b*N+m] = G(mu_n)_ab delta_nm + m_ab K_g[n][m] with
+// G(mu) = [[mu/2 - mu[mu<0], mu/2], [-mu/2, -mu/2 + mu[mu>0]]], m = (h/6)[[2,1],[1,2]].
+// Upwind couplings at level 0: B_g[p][p] = -mu_{N/2+p} (row L+ of g, column
+// R+ of g-1), C_g[p][p] = mu_p (row R- of g, column L- of g+1).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fp_assemble(const double *__restrict__ mu, const double *__restrict__ Afp,
+                              const double *__restrict__ h, const double *__restrict__ sigma_t,
+                              const double *__restrict__ sigma_s0, const double *__restrict__ sigma_s1,
+                              const int32_t *__restrict__ cell_inst, const int32_t *__restrict__ off,
+                              const int32_t *__restrict__ Kc, const int32_t *__restrict__ slot_base, int N,
+                              T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc) {
+    const int g = blockIdx.x;
+    const int n2 = 2 * N, h2 = N / 2;
+    const double hh = h[g];
+    const double sa = sigma_t[g] - sigma_s0[g];
+    const double str = sigma_s0[g] - sigma_s1[g];
+    T *Ag = A + (size_t)g * n2 * n2;
+    for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+        const int row = idx / n2, col = idx - row * n2;
+        const int a = row / N, n = row - a * N, bb = col / N, m = col - bb * N;
+        const double mass = hh / 6.0 * (a == bb ? 2.0 : 1.0);
+        double v = mass * ((n == m ? sa : 0.0) - 0.5 * str * Afp[(size_t)n * N + m]);
+        if (n == m) {
+            const double x = mu[n];
+            const double pos = x > 0.0 ? 1.0 : 0.0, neg = 1.0 - pos;
+            const double G = (a == 0) ? (bb == 0 ? 0.5 * x - x * neg : 0.5 * x)
+                                      : (bb == 0 ? -0.5 * x : -0.5 * x + x * pos);
+            v += G;
+        }
+        Ag[idx] = (T)v;
+    }
+    const int b = cell_inst[g];
+    const int local = g - off[b];
+    T *Bg = Bc + (size_t)slot_base[g] * h2 * h2;
+    T *Cg = Cc + (size_t)slot_base[g] * h2 * h2;
+    for (int idx = threadIdx.x; idx < h2 * h2; idx += blockDim.x) {
+        const int p = idx / h2, qq = idx - p * h2;
+        Bg[idx] = (p == qq && local > 0) ? (T)(-mu[h2 + p]) : T(0);
+        Cg[idx] = (p == qq && local < Kc[b] - 1) ? (T)(mu[p]) : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block cyclic reduction, factorization. Gauss-Jordan inversion with partial
+// pivoting of the eliminated cells' 2N x 2N blocks, in shared memory; the
+// inverse is written back transposed. Growth check (always in FP64):
+// max|A| * max|A^{-1}| per block, max-reduced into *growth; a zero or
+// non-finite pivot sets *status = 1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ items, int n2,
+                             unsigned long long *__restrict__ growth, int *__restrict__ status) {
+    extern __shared__ unsigned char smem_raw[];
+    const int ld = n2 + 1;
+    T *a = reinterpret_cast<T *>(smem_raw);
+    T *colk = a + (size_t)n2 * ld;
+    int *perm = reinterpret_cast<int *>(colk + n2);
+    __shared__ double s_amax;
+    __shared__ int s_piv;
+    __shared__ T s_pval;
+    const BcrItem it = items[blockIdx.x];
+    T *Ag = A + (size_t)it.cell * n2 * n2;
+    double amax = 0.0;
+    for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+        const int i = idx / n2, j = idx - i * n2;
+        const T v = Ag[idx];
+        a[i * ld + j] = v;
+        amax = fmax(amax, fabs((double)v));
+    }
+    // block max of |A|
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (threadIdx.x == 0) s_amax = 0.0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)&s_amax, dkey(amax));
+    __syncthreads();
+    bool bad = false;
+    for (int k = 0; k < n2; ++k) {
+        // pivot search in column k, rows k..n2-1 (warp 0)
+        if (threadIdx.x < 32) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + threadIdx.x; i < n2; i += 32) {
+                const double v = fabs((double)a[i * ld + k]);
+                if (v > best) { best = v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (threadIdx.x == 0) { s_piv = bi; perm[k] = bi; }
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != k)
+            for (int j = threadIdx.x; j < n2; j += blockDim.x) {
+                const T t = a[k * ld + j];
+                a[k * ld + j] = a[p * ld + j];
+                a[p * ld + j] = t;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) s_pval = a[k * ld + k];
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) colk[i] = a[i * ld + k];
+        __syncthreads();
+        const T pv = s_pval;
+        if (pv == T(0) || !isfinite((double)pv)) bad = true;
+        const T inv = T(1) / pv;
+        // scale pivot row; column k of the pivot row becomes 1/pv
+        for (int j = threadIdx.x; j < n2; j += blockDim.x) a[k * ld + j] = (j == k) ? inv : a[k * ld + j] * inv;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+            const int i = idx / n2, j = idx - i * n2;
+            if (i == k) continue;
+            const T f = colk[i];
+            if (j == k) a[i * ld + j] = -f * inv;
+            else a[i * ld + j] = fma(-f, a[k * ld + j], a[i * ld + j]);
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int k = n2 - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k)
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const T t = a[i * ld + k];
+                a[i * ld + k] = a[i * ld + p];
+                a[i * ld + p] = t;
+            }
+        __syncthreads();
+    }
+    double ainv = 0.0;
+    for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+        const int c = idx / n2, rr = idx - c * n2;  // write transposed: Ag[c][r] = inv[r][c]
+        const T v = a[rr * ld + c];
+        Ag[idx] = v;
+        ainv = fmax(ainv, fabs((double)v));
+        if (!isfinite((double)v)) bad = true;
+    }
+    for (int o = 16; o > 0; o >>= 1) ainv = fmax(ainv, __shfl_xor_sync(0xffffffffu, ainv, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(growth, dkey(ainv * s_amax));
+    if (bad) atomicExch(status, 1);
+}
+
+// C[p][q] -= / = sum_k X(p,k) Y(k,q) for h2 x h2 operands addressed by strides.
+template <typename T>
+__device__ __forceinline__ void tile_mm(T *out, int ldo, bool accumulate_neg, const T *X, int xr, int xc,
+                                        const T *Y, int yr, int yc, int h2) {
+    for (int idx = threadIdx.x; idx < h2 * h2; idx += blockDim.x) {
+        const int p = idx / h2, qq = idx - p * h2;
+        T acc = T(0);
+        for (int k = 0; k < h2; ++k) acc = fma(X[(size_t)p * xr + (size_t)k * xc], Y[(size_t)k * yr + (size_t)qq * yc], acc);
+        if (accumulate_neg) out[(size_t)p * ldo + qq] -= acc;
+        else out[(size_t)p * ldo + qq] = acc;
+    }
+}
+
+// Schur updates of the kept neighbours of each eliminated cell i at level l
+// (s = 2^l), using only the N/2-wide coupling blocks:
+//   right j = i+s:  A_j[L+,L-] -= B_j Ainv_i[R+,R-] C_i
+//                   B_j' = -B_j Ainv_i[R+,L+] B_i
+//   left  j = i-s:  A_j[R-,R+] -= C_j Ainv_i[L-,L+] B_i
+//                   C_j' = -C_j Ainv_i[L-,R-] C_i   (0 if i has no right neighbour)
+template <typename T>
+__global__ void k_bcr_schur(T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc,
+                            const BcrItem *__restrict__ items, int N) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+    T *X = reinterpret_cast<T *>(smem_raw);
+    const BcrItem it = items[blockIdx.x];
+    const T *Ai = A + (size_t)it.cell * n2 * n2;  // transposed inverse: Ainv[r][c] = Ai[c*n2 + r]
+    const int Lm = 0, Lp = h2, Rm = N, Rp = N + h2;
+    const T *Bi = Bc + (size_t)it.s_cell * hh;
+    const T *Ci = Cc + (size_t)it.s_cell * hh;
+    // Ainv[r0 + p][c0 + k] = Ai[(c0 + k) * n2 + r0 + p]: row stride 1, col stride n2
+    if (it.right >= 0) {
+        const T *Bj = Bc + (size_t)it.s_right * hh;
+        T *Aj = A + (size_t)it.right * n2 * n2;
+        tile_mm(X, h2, false, Bj, h2, 1, Ai + (size_t)Rm * n2 + Rp, 1, n2, h2);   // X = B_j Ainv[R+,R-]
+        __syncthreads();
+        tile_mm(Aj + (size_t)Lp * n2 + Lm, n2, true, X, h2, 1, Ci, h2, 1, h2);    // A_j[L+,L-] -= X C_i
+        __syncthreads();
+        tile_mm(X, h2, false, Bj, h2, 1, Ai + (size_t)Lp * n2 + Rp, 1, n2, h2);   // X = B_j Ainv[R+,L+]
+        __syncthreads();
+        T *Bn = Bc + (size_t)it.s_right_next * hh;
+        tile_mm(Bn, h2, false, X, h2, 1, Bi, h2, 1, h2);                          // B_j' = X B_i
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) Bn[idx] = -Bn[idx];
+        __syncthreads();
+    }
+    if (it.left >= 0) {
+        const T *Cj = Cc + (size_t)it.s_left * hh;
+        T *Aj = A + (size_t)it.left * n2 * n2;
+        tile_mm(X, h2, false, Cj, h2, 1, Ai + (size_t)Lp * n2 + Lm, 1, n2, h2);   // X = C_j Ainv[L-,L+]
+        __syncthreads();
+        tile_mm(Aj + (size_t)Rm * n2 + Rp, n2, true, X, h2, 1, Bi, h2, 1, h2);    // A_j[R-,R+] -= X B_i
+        __syncthreads();
+        T *Cn = Cc + (size_t)it.s_left_next * hh;
+        if (it.right >= 0) {
+            tile_mm(X, h2, false, Cj, h2, 1, Ai + (size_t)Rm * n2 + Lm, 1, n2, h2);  // X = C_j Ainv[L-,R-]
+            __syncthreads();
+            tile_mm(Cn, h2, false, X, h2, 1, Ci, h2, 1, h2);                         // C_j' = X C_i
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) Cn[idx] = -Cn[idx];
+        } else {
+            for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) Cn[idx] = T(0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block cyclic reduction, solve F u = rhs for every rhs, in place.
+// Forward (level l, eliminated i): y_i = Ainv_i r_i; r_{i+s}[L+] -= B_{i+s} y_i[R+];
+// r_{i-s}[R-] -= C_{i-s} y_i[L-]. Roots: u = Ainv r.
+// Backward (level l descending): u_i = y_i - Ainv_i[:,L+] B_i u_{i-s}[R+]
+//                                          - Ainv_i[:,R-] C_i u_{i+s}[L-].
+// One block per (item, rhs); every write touches a disjoint sub-vector.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_bcr_fwd(const T *__restrict__ A, const T *__restrict__ Bc, const T *__restrict__ Cc,
+                          const BcrItem *__restrict__ items, T *__restrict__ rhs, int N, int sumK) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+    T *rs = reinterpret_cast<T *>(smem_raw);
+    T *ys = rs + n2;
+    const BcrItem it = items[blockIdx.x];
+    const int r = blockIdx.y;
+    T *ri = rhs + ((size_t)r * sumK + it.cell) * n2;
+    const T *Ai = A + (size_t)it.cell * n2 * n2;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) rs[i] = ri[i];
+    __syncthreads();
+    for (int row = threadIdx.x; row < n2; row += blockDim.x) {
+        T acc = T(0);
+        for (int k = 0; k < n2; ++k) acc = fma(Ai[(size_t)k * n2 + row], rs[k], acc);
+        ys[row] = acc;
+        ri[row] = acc;
+    }
+    __syncthreads();
+    if (it.right >= 0) {
+        const T *Bj = Bc + (size_t)it.s_right * hh;
+        T *rj = rhs + ((size_t)r * sumK + it.right) * n2 + h2;  // L+
+        for (int p = threadIdx.x; p < h2; p += blockDim.x) {
+            T acc = T(0);
+            for (int k = 0; k < h2; ++k) acc = fma(Bj[p * h2 + k], ys[N + h2 + k], acc);
+            rj[p] -= acc;
+        }
+    }
+    if (it.left >= 0) {
+        const T *Cj = Cc + (size_t)it.s_left * hh;
+        T *rj = rhs + ((size_t)r * sumK + it.left) * n2 + N;  // R-
+        for (int p = threadIdx.x; p < h2; p += blockDim.x) {
+            T acc = T(0);
+            for (int k = 0; k < h2; ++k) acc = fma(Cj[p * h2 + k], ys[k], acc);
+            rj[p] -= acc;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_bcr_bwd(const T *__restrict__ A, const T *__restrict__ Bc, const T *__restrict__ Cc,
+                          const BcrItem *__restrict__ items, T *__restrict__ rhs, int N, int sumK) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+    T *g1 = reinterpret_cast<T *>(smem_raw);
+    T *g2 = g1 + h2;
+    const BcrItem it = items[blockIdx.x];
+    const int r = blockIdx.y;
+    T *ri = rhs + ((size_t)r * sumK + it.cell) * n2;
+    const T *Ai = A + (size_t)it.cell * n2 * n2;
+    const T *Bi = Bc + (size_t)it.s_cell * hh;
+    const T *Ci = Cc + (size_t)it.s_cell * hh;
+    const T *ul = rhs + ((size_t)r * sumK + it.left) * n2 + N + h2;  // u_left[R+]
+    for (int p = threadIdx.x; p < h2; p += blockDim.x) {
+        T acc = T(0);
+        for (int k = 0; k < h2; ++k) acc = fma(Bi[p * h2 + k], ul[k], acc);
+        g1[p] = acc;
+        T acc2 = T(0);
+        if (it.right >= 0) {
+            const T *ur = rhs + ((size_t)r * sumK + it.right) * n2;  // u_right[L-]
+            for (int k = 0; k < h2; ++k) acc2 = fma(Ci[p * h2 + k], ur[k], acc2);
+        }
+        g2[p] = acc2;
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < n2; row += blockDim.x) {
+        T acc = ri[row];
+        for (int p = 0; p < h2; ++p) {
+            acc = fma(-Ai[(size_t)(h2 + p) * n2 + row], g1[p], acc);
+            acc = fma(-Ai[(size_t)(N + p) * n2 + row], g2[p], acc);
+        }
+        ri[row] = acc;
+    }
+}
+
+}  // namespace fpsa

@@ -1,0 +1,64 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every symbol the
+header declares, and rejects bad descriptors without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1907_13013_gb300 import binding
+    return binding.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fpsa.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(fpsa_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_strerror_texts(lib):
+    from paper_1907_13013_gb300 import binding
+    for code in (binding.OK, binding.EINVAL, binding.ENOTCONV, binding.EPIVOT, binding.ENOTSUP):
+        assert lib.fpsa_strerror(code)
+    assert lib.fpsa_last_error(None) == b""
+
+
+def test_create_rejects_bad_descriptors_before_any_cuda_call(lib):
+    from paper_1907_13013_gb300 import binding
+    K = np.array([4], dtype=np.int32)
+    h = np.full(4, 0.25)
+
+    def create(**kw):
+        args = dict(n_instances=1, n_ordinates=8, n_moments=8, n_rhs=1, laplacian=0, precision=0)
+        args.update(kw)
+        d = binding.FpsaDesc(args["n_instances"], args["n_ordinates"], args["n_moments"], args["n_rhs"],
+                             K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                             h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             args["laplacian"], args["precision"], 0, None)
+        out = ctypes.c_void_p()
+        return lib.fpsa_create(ctypes.byref(out), ctypes.byref(d)), out
+
+    for bad in (dict(n_ordinates=7), dict(n_ordinates=0), dict(n_moments=9), dict(n_moments=0),
+                dict(n_rhs=0), dict(n_instances=0), dict(laplacian=5), dict(precision=7)):
+        rc, out = create(**bad)
+        assert rc == binding.EINVAL and not out.value, bad
+    rc, out = create(n_ordinates=2 * binding.MAX_ORDINATES, n_moments=2)
+    assert rc == binding.ENOTSUP and not out.value

@@ -1,0 +1,142 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerance: converged scalar flux within 1e-9 relative (max-norm, relative to
+max|phi_0|) of the oracle; both sides iterate to a relative change of 1e-13 so
+the iteration error is far below the bound. Moments l >= 1 are compared with the
+same absolute scale.
+"""
+import numpy as np
+import pytest
+
+from oracle import iterations as oit
+from paper_1907_13013_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def binding():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__ as g
+    g.build()
+    from paper_1907_13013_gb300 import binding as b
+    return b
+
+
+def relerr(phi, ref):
+    return np.abs(phi - ref).max() / np.abs(ref[..., 0]).max()
+
+
+def oracle(p, method, lap="mpd", tol=1e-13, max_it=5000):
+    if method == "si":
+        return oit.source_iteration(p, tol=tol, max_it=max_it)
+    return oit.fpsa_source_iteration(p, lap, tol=tol, max_it=max_it)
+
+
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+def test_plain_hg_slab_fpsa(binding, lap):
+    p = inputs.plain_hg_slab()
+    ctx = binding.context_for(p, laplacian=lap)
+    phi, st = ctx.solve("fpsa", tol=1e-13, max_iterations=500)
+    ref, n = oracle(p, "fpsa", lap)
+    assert relerr(phi[0], ref) < TOL
+    assert abs(st["iterations"] - n) <= 1
+    # direct discrete solution (the fixed point itself)
+    assert relerr(phi[0], oit.direct_solve(p)) < TOL
+
+
+def test_plain_hg_slab_si_iterates_match(binding):
+    # identical iterate counts: both sides run exactly 40 SI iterations from zero
+    p = inputs.plain_hg_slab()
+    ctx = binding.context_for(p)
+    phi, st = ctx.solve("si", tol=0.0, max_iterations=40, raise_on_notconv=False)
+    ref, _ = oit.source_iteration(p, tol=0.0, max_it=40)
+    assert st["iterations"] == 40
+    assert relerr(phi[0], ref) < 1e-12
+
+
+@pytest.mark.parametrize("N,K,seed,kernel", [(2, 5, 0, "hg"), (4, 1, 1, "hg"), (8, 2, 2, "srk"),
+                                             (8, 3, 3, "hg"), (16, 33, 4, "srk"), (32, 64, 5, "hg"),
+                                             (64, 97, 6, "srk")])
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+def test_random_slabs(binding, N, K, seed, kernel, lap):
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel=kernel, thick=(1, 300), c=(0.5, 0.999))
+    ctx = binding.context_for(p, laplacian=lap)
+    phi, st = ctx.solve("fpsa", tol=1e-13, max_iterations=2000)
+    ref, n = oracle(p, "fpsa", lap)
+    assert relerr(phi[0], ref) < TOL, (relerr(phi[0], ref), st)
+
+
+def test_truncated_expansion_L_below_N_minus_1(binding):
+    p = inputs.random_slab(40, 16, 5, seed=7, kernel="hg")
+    ctx = binding.context_for(p)
+    phi, st = ctx.solve("fpsa", tol=1e-13, max_iterations=2000)
+    ref, n = oracle(p, "fpsa")
+    assert phi.shape == (1, 40, 2, 6)
+    assert relerr(phi[0], ref) < TOL
+
+
+def test_batch_ragged_instances_and_rhs(binding):
+    # several instances of different cell counts and R = 3 right-hand sides in one context
+    R = 3
+    probs = [inputs.random_slab(K, 16, 15, seed=20 + i, kernel="srk", nrhs=R) for i, K in enumerate([1, 7, 64, 33, 2])]
+    ctx = binding.context_for(probs)
+    phi, st = ctx.solve("fpsa", tol=1e-13, max_iterations=2000)
+    off = 0
+    for p in probs:
+        K = p["h"].size
+        for r in range(R):
+            pr = dict(p, Q=p["Q"][r])
+            ref, _ = oracle(pr, "fpsa")
+            assert relerr(phi[r, off:off + K], ref) < TOL
+        off += K
+
+
+def test_pl_equivalent_one_iteration(binding):
+    # Eq. fsa_pl_eq: P_L-equivalent moments with N = L+1 converge in one FPSA iteration (MPD)
+    p = inputs.pl_equivalent_slab(50, 16, 3)
+    ctx = binding.context_for(p, laplacian="mpd")
+    phi, st = ctx.solve("fpsa", tol=0.0, max_iterations=1, raise_on_notconv=False)
+    assert relerr(phi[0], oit.direct_solve(p)) < 1e-10
+
+
+def test_device_pointers_and_phi0(binding):
+    import torch
+    p = inputs.random_slab(30, 8, 7, seed=8)
+    ctx = binding.context_for(p)
+    dev = torch.device("cuda:0")
+    st_ = torch.tensor(p["sigma_t"], device=dev)
+    ss = torch.tensor(p["sigma_s"], device=dev)
+    q = torch.tensor(p["Q"][None], device=dev)
+    ctx.set_xs(st_, ss, q)
+    out = torch.zeros((1, 30, 2, 8), dtype=torch.float64, device=dev)
+    ctx.solve("fpsa", tol=1e-13, out=out)
+    ref, _ = oracle(p, "fpsa")
+    assert relerr(out.cpu().numpy()[0], ref) < TOL
+    # restarting from the converged moments converges at once (resume = pass back the iterate)
+    out2 = torch.zeros_like(out)
+    _, st = ctx.solve("fpsa", tol=1e-11, out=out2, phi0=out.clone())
+    assert st["iterations"] <= 2
+
+
+def test_error_paths(binding):
+    p = inputs.random_slab(10, 8, 7, seed=9)
+    ctx = binding.Context([10], p["h"], 8, 7)
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.solve()
+    assert e.value.code == binding.ESTATE
+    bad = p["sigma_t"].copy(); bad[3] = -1.0
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.set_xs(bad, p["sigma_s"], p["Q"][None])
+    assert e.value.code == binding.EINVAL
+    nan = p["Q"][None].copy(); nan[0, 2, 1, 0] = np.nan
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.set_xs(p["sigma_t"], p["sigma_s"], nan)
+    assert e.value.code == binding.ENONFINITE
+    ctx.set_xs(p["sigma_t"], p["sigma_s"], p["Q"][None])
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.solve("si", tol=1e-14, max_iterations=3)
+    assert e.value.code == binding.ENOTCONV
