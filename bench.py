@@ -1,0 +1,334 @@
+"""Benchmark: converged slab S_N solves/s (FPSA source iteration) on the precision workload.
+
+Workload (one step = one pass of the whole path over one problem):
+  1 cm slab, 2000 LD cells, S64 Gauss-Legendre, screened-Rutherford scattering
+  (eta = 1e-5) expanded to L = 63, sigma_s0 = 1000/cm, sigma_a = 0.01/cm,
+  isotropic unit source on z < 0.5, vacuum edges; synthetic, seeded inputs.
+  A step is fpsa_set_xs (upload, sweep coefficients, FP block assembly, block
+  cyclic-reduction factorization) followed by fpsa_solve to a relative change of
+  phi_0 below 1e-10 (FPSA source iteration).
+
+  value : solves/s with inputs already resident in device memory (torch CUDA
+          tensors passed to the C ABI), device-timed with CUDA events on the
+          library's stream.
+  e2e   : the same step through the same C ABI with HOST numpy inputs/outputs, so
+          the host->device input copies and the device->host flux copy are inside
+          the timed region.
+  The factor storage of one step (2000 x 128 x 128 FP64 = 262 MB) exceeds the
+  L2 (126 MB), so each step streams its working set from HBM.
+
+Multi-GPU (torchrun): every rank solves its own replica of the problem (the
+workload does not shard); value = solves of all ranks / max rank time.
+
+--impl reference runs the FP64 CPU oracle (the only other place this file runs
+oracle code) on rank 0 on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, sigma_s0=1000, sigma_a=0.01, Q=1 on z<0.5, vacuum"
+METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
+TOL = 1e-10
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def read_golden(name):
+    path = os.path.join(ROOT, "tests", "golden", name)
+    vals, its10 = [], None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                if "relative change 1e-10" in line:
+                    its10 = int(line.rsplit(":", 1)[1])
+                continue
+            vals.append(float(line))
+    return np.array(vals), its10
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import iterations as oit
+    from paper_1907_13013_gb300 import inputs
+    p = inputs.precision_srk_slab()
+    _, n_it = read_golden("precision_srk_slab_fpsa_mpd_phi0.txt")
+    sample_its = 3
+
+    def step():
+        t0 = time.perf_counter()
+        # FP operator assembly + sparse LU (the setup), then `sample_its` FPSA iterations
+        _, n = oit.fpsa_source_iteration(p, "mpd", tol=0.0, max_it=sample_its)
+        t_all = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        _, n = oit.fpsa_source_iteration(p, "mpd", tol=0.0, max_it=sample_its + 2)
+        t_more = time.perf_counter() - t1
+        per_it = max((t_more - t_all) / 2.0, 0.0)
+        setup = max(t_all - sample_its * per_it, 0.0)
+        return setup + n_it * per_it
+
+    for _ in range(args.warmup):
+        step()
+    est = [step() for _ in range(args.steps)]
+    s_per_solve = float(np.mean(est))
+    v = 1.0 / s_per_solve
+    sample = ("per step: oracle FP setup + %d and %d FPSA iterations, extrapolated to the oracle's %d "
+              "iterations to 1e-10 (mean of %d steps)" % (sample_its, sample_its + 2, n_it, args.steps))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_per_solve,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64", "laplacian": "mpd"},
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": v, "unit": "solves/s"},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline_sample():
+    """One full oracle solve of the workload (about 10-30 s of single-threaded CPU work)."""
+    from oracle import iterations as oit
+    from paper_1907_13013_gb300 import inputs
+    p = inputs.precision_srk_slab()
+    t0 = time.perf_counter()
+    _, n = oit.fpsa_source_iteration(p, "mpd", tol=TOL)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "one complete FP64 oracle FPSA-SI (MPD) solve of the workload, %d iterations, %.1f s" % (n, dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--laplacian", default="mpd", choices=["mpd", "wfd"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1907_13013_gb300 import binding, inputs
+
+    p = inputs.precision_srk_slab()
+    K, N, L = p["h"].size, p["N"], p["L"]
+    stream = torch.cuda.current_stream()
+    ctx = binding.Context([K], p["h"], N, L, laplacian=args.laplacian, precision=args.precision,
+                          device=local, stream=stream.cuda_stream)
+    d_st = torch.tensor(p["sigma_t"], device=dev)
+    d_ss = torch.tensor(p["sigma_s"], device=dev)
+    d_q = torch.tensor(p["Q"][None], device=dev)
+    d_phi = torch.zeros((1, K, 2, L + 1), dtype=torch.float64, device=dev)
+    h_st = torch.tensor(p["sigma_t"]).pin_memory().numpy()
+    h_ss = torch.tensor(p["sigma_s"]).pin_memory().numpy()
+    h_q = torch.tensor(p["Q"][None]).pin_memory().numpy()
+    h_phi = torch.zeros((1, K, 2, L + 1), dtype=torch.float64).pin_memory().numpy()
+    stats = {}
+
+    def step_device():
+        ctx.set_xs(d_st, d_ss, d_q)
+        _, s = ctx.solve("fpsa", tol=TOL, out=d_phi)
+        stats.update(s)
+
+    def step_host():
+        ctx.set_xs(h_st, h_ss, h_q)
+        _, s = ctx.solve("fpsa", tol=TOL, out=h_phi)
+        stats.update(s)
+
+    def timed(fn, k):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step_device()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile_enable(False)  # reset launch counters, no events
+    ms = timed(step_device, args.steps)
+    prof_counts = ctx.profile_read()
+    clocks = sampler.stop()
+    launches = sum(v["launches"] for v in prof_counts.values())
+    dev_stats = dict(stats)
+    # end to end: host inputs / outputs through the same C ABI
+    for _ in range(1):
+        step_host()
+    ms_e2e = timed(step_host, args.steps)
+    # per-kernel durations: the same steps again with CUDA events around every launch
+    ctx.profile_enable(True)
+    ms_prof = timed(step_device, args.steps)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+
+    # parity of the benchmarked result against the stored oracle flux
+    ref, its_ref = read_golden("precision_srk_slab_fpsa_%s_phi0.txt" % args.laplacian)
+    phi0 = d_phi[0, :, :, 0].cpu().numpy().ravel()
+    rel_err = float(np.abs(phi0 - ref).max() / np.abs(ref).max())
+
+    # roofline of the dominant kernel class
+    n2 = 2 * N
+    lev_items = K - 1  # every cell but the root is eliminated at exactly one level
+    phases = {k: v for k, v in prof.items() if v["timed"]}
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    inv_flops = 2.0 * n2 ** 3 * K  # Gauss-Jordan: ~n^3 multiply-adds per block, K blocks per step
+    sweeps = dev_stats["sweeps"]
+    solve_bytes_per_sweep = 8.0 * (lev_items * (n2 * n2 + n2 * N) + n2 * n2)  # A^{-1} reads (fwd + bwd)
+    roof = None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    if dom == "bcr_invert":
+        per_launch_ms = phases[dom]["ms"] / phases[dom]["timed"]
+        launches_per_step = phases[dom]["timed"] / args.steps
+        achieved = inv_flops / launches_per_step / (per_launch_ms * 1e-3) / 1e12
+        peak = 1.25  # FP64 nominal (no FP64 figure in the measured peaks)
+        roof = {"kernel": "k_bcr_invert<double>", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300); not in MEASURED_PEAKS.json"}
+    elif dom == "bcr_solve":
+        per_launch_ms = phases[dom]["ms"] / phases[dom]["timed"]
+        launches_per_step = phases[dom]["timed"] / args.steps
+        byt = solve_bytes_per_sweep * sweeps / launches_per_step
+        achieved = byt / (per_launch_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "k_bcr_fwd/k_bcr_bwd<double>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None}
+    else:
+        per_launch_ms = phases[dom]["ms"] / phases[dom]["timed"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None}
+    roof["avg_launch_ms"] = per_launch_ms
+
+    value = world * args.steps / (ms * 1e-3)
+    h2d = 8 * (K + K * (L + 1) + 2 * K * (L + 1))
+    d2h = 8 * 2 * K * (L + 1)
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "laplacian": args.laplacian,
+                   "tol": TOL, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set (262 MB FP64 factors) larger than L2; no flush"},
+        "cell_angles_per_s": dev_stats["cell_angles"] * world * args.steps / (ms * 1e-3),
+        "iterations": dev_stats["iterations"], "oracle_iterations_1e-10": its_ref,
+        "setup_ms": dev_stats["setup_ms"], "solve_ms": dev_stats["solve_ms"],
+        "max_rel_err_vs_oracle": rel_err,
+        "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "solves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "profile": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["timed"] / args.steps}
+                    for k, v in phases.items()},
+        "profiled_ms_per_step": ms_prof / args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -99,6 +99,32 @@ typedef struct {
     double pivot_growth;      /* max over FP blocks of max|A^{-1}| * max|A| (FP64 check) */
 } fpsa_stats;
 
+/* Kernel classes for the built-in profiler. */
+enum fpsa_phase {
+    FPSA_PHASE_SWEEP = 0,       /* LD transport sweep */
+    FPSA_PHASE_CONTRACT = 1,    /* moment / scattering-source contractions (+ fused updates) */
+    FPSA_PHASE_BCR_SOLVE = 2,   /* block cyclic reduction forward / backward solve */
+    FPSA_PHASE_BCR_INVERT = 3,  /* block inversion of eliminated cells (factorization) */
+    FPSA_PHASE_BCR_SCHUR = 4,   /* Schur updates of kept cells (factorization) */
+    FPSA_PHASE_ASSEMBLE = 5,    /* FP block assembly and sweep coefficients */
+    FPSA_PHASE_CONVERGENCE = 6, /* convergence reduction */
+    FPSA_PHASE_RESIDUAL = 7,    /* FP64 refinement residual and update (MIXED) */
+    FPSA_N_PHASES = 8
+};
+
+typedef struct {
+    int64_t launches[FPSA_N_PHASES];  /* kernel launches since the last reset (always counted) */
+    int64_t timed[FPSA_N_PHASES];     /* launches bracketed by CUDA events while profiling was on */
+    double ms[FPSA_N_PHASES];         /* summed event time of the timed launches */
+} fpsa_profile;
+
+/* Reset the counters; on != 0 additionally brackets every kernel launch with a
+ * pair of CUDA events on the context stream (adds host-side launch overhead). */
+int fpsa_profile_enable(fpsa_ctx *ctx, int32_t on);
+
+/* Synchronise the context stream and return the counters since the last reset. */
+int fpsa_profile_read(fpsa_ctx *ctx, fpsa_profile *out);
+
 /* Largest N this build supports (FP block 2N x 2N must fit the factorization tile). */
 #define FPSA_MAX_ORDINATES 64
 

@@ -50,7 +50,19 @@ class FpsaStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error"]
+PHASES = ["sweep", "contract", "bcr_solve", "bcr_invert", "bcr_schur", "assemble", "convergence", "residual"]
+
+
+class FpsaProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("timed", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8)]
+
+    def as_dict(self):
+        return {ph: {"launches": int(self.launches[i]), "timed": int(self.timed[i]), "ms": float(self.ms[i])}
+                for i, ph in enumerate(PHASES)}
+
+
+EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error",
+           "fpsa_profile_enable", "fpsa_profile_read"]
 
 _lib = None
 
@@ -76,6 +88,10 @@ def load():
     lib.fpsa_strerror.restype = ctypes.c_char_p
     lib.fpsa_last_error.argtypes = [vp]
     lib.fpsa_last_error.restype = ctypes.c_char_p
+    lib.fpsa_profile_enable.argtypes = [vp, i32]
+    lib.fpsa_profile_enable.restype = ctypes.c_int
+    lib.fpsa_profile_read.argtypes = [vp, ctypes.POINTER(FpsaProfile)]
+    lib.fpsa_profile_read.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -163,6 +179,16 @@ class Context:
         if isinstance(out, np.ndarray) and keep is not out:
             out[...] = keep
         return out, st.as_dict()
+
+    def profile_enable(self, on=True):
+        """Reset the launch counters; with on, bracket every launch with CUDA events."""
+        self._check(self._lib.fpsa_profile_enable(self._h, 1 if on else 0), "fpsa_profile_enable")
+
+    def profile_read(self):
+        """Per kernel class: launches, timed launches and summed event milliseconds."""
+        p = FpsaProfile()
+        self._check(self._lib.fpsa_profile_read(self._h, ctypes.byref(p)), "fpsa_profile_read")
+        return p.as_dict()
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

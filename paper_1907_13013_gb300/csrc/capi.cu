@@ -59,9 +59,39 @@ struct fpsa_ctx {
     double *h_result = nullptr;  // pinned
 
     PathBuffers<double> p64;
+
+    // built-in profiler: launch counters (always) and event pairs (when on)
+    bool prof_on = false;
+    int64_t launches[FPSA_N_PHASES] = {};
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_rec;  // (phase, index of start event)
+    size_t ev_used = 0;
 };
 
 namespace {
+
+// Launch bracket: counts every launch of a kernel class and, while profiling is
+// on, records a CUDA event pair around it on the context stream.
+struct Launch {
+    fpsa_ctx *c;
+    int phase;
+    Launch(fpsa_ctx *ctx, int ph) : c(ctx), phase(ph) {
+        c->launches[ph]++;
+        if (!c->prof_on) return;
+        if (c->ev_used + 2 > c->ev_pool.size())
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                c->ev_pool.push_back(e);
+            }
+        c->ev_rec.push_back({ph, (int)c->ev_used});
+        cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+        c->ev_used += 2;
+    }
+    ~Launch() {
+        if (c->prof_on) cudaEventRecord(c->ev_pool[c->ev_rec.back().second + 1], c->stream);
+    }
+};
 
 int fail(fpsa_ctx *c, int code, const std::string &msg) {
     if (c) c->err = msg;
@@ -143,26 +173,41 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
     CK(cudaMemcpyAsync(p.Q, Qp.data(), Qp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     {
         const size_t tot = (size_t)g.sumK * N;
-        k_sweep_coef<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->d_mu, ctx->d_h, ctx->d_sigma_t, N,
-                                                                        g.sumK, p.coef);
+        {
+            Launch L_(ctx, FPSA_PHASE_ASSEMBLE);
+            k_sweep_coef<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->d_mu, ctx->d_h, ctx->d_sigma_t, N,
+                                                                            g.sumK, p.coef);
+        }
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(p.Bc, 0, (size_t)g.n_slots * h2 * h2 * sizeof(T), st));
     CK(cudaMemsetAsync(p.Cc, 0, (size_t)g.n_slots * h2 * h2 * sizeof(T), st));
-    k_fp_assemble<T><<<g.sumK, 256, 0, st>>>(ctx->d_mu, ctx->d_Afp, ctx->d_h, ctx->d_sigma_t, ctx->d_s0, ctx->d_s1,
-                                             ctx->d_cell_inst, ctx->d_off, ctx->d_K, ctx->d_slot_base, N, p.A, p.Bc,
-                                             p.Cc);
+    {
+        Launch L_(ctx, FPSA_PHASE_ASSEMBLE);
+        k_fp_assemble<T><<<g.sumK, 256, 0, st>>>(ctx->d_mu, ctx->d_Afp, ctx->d_h, ctx->d_sigma_t, ctx->d_s0, ctx->d_s1,
+                                                 ctx->d_cell_inst, ctx->d_off, ctx->d_K, ctx->d_slot_base, N, p.A, p.Bc,
+                                                 p.Cc);
+    }
     CK(cudaGetLastError());
     const size_t ism = invert_smem<T>(N);
     for (int l = 0; l < g.n_levels; ++l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
-        k_bcr_invert<T><<<ni, kInvertThreads, ism, st>>>(p.A, ctx->d_levels[l], n2, ctx->d_growth, ctx->d_status);
+        {
+            Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+            k_bcr_invert<T><<<ni, kInvertThreads, ism, st>>>(p.A, ctx->d_levels[l], n2, ctx->d_growth, ctx->d_status);
+        }
         CK(cudaGetLastError());
-        k_bcr_schur<T><<<ni, 256, (size_t)h2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], N);
+        {
+            Launch L_(ctx, FPSA_PHASE_BCR_SCHUR);
+            k_bcr_schur<T><<<ni, 256, (size_t)h2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], N);
+        }
         CK(cudaGetLastError());
     }
-    k_bcr_invert<T><<<g.B, kInvertThreads, ism, st>>>(p.A, ctx->d_roots, n2, ctx->d_growth, ctx->d_status);
+    {
+        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+        k_bcr_invert<T><<<g.B, kInvertThreads, ism, st>>>(p.A, ctx->d_roots, n2, ctx->d_growth, ctx->d_status);
+    }
     CK(cudaGetLastError());
     return FPSA_OK;
 }
@@ -175,15 +220,24 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     for (int l = 0; l < g.n_levels; ++l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
-        k_bcr_fwd<T><<<dim3(ni, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
-                                                                      g.sumK);
+        {
+            Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
+            k_bcr_fwd<T><<<dim3(ni, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
+                                                                          g.sumK);
+        }
     }
-    k_bcr_fwd<T><<<dim3(g.B, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_roots, rhs, N, g.sumK);
+    {
+        Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
+        k_bcr_fwd<T><<<dim3(g.B, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_roots, rhs, N, g.sumK);
+    }
     for (int l = g.n_levels - 1; l >= 0; --l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
-        k_bcr_bwd<T><<<dim3(ni, g.R), 128, 2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
-                                                                      g.sumK);
+        {
+            Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
+            k_bcr_bwd<T><<<dim3(ni, g.R), 128, 2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
+                                                                          g.sumK);
+        }
     }
     CK(cudaGetLastError());
     return FPSA_OK;
@@ -227,31 +281,49 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
         CK(cudaMemsetAsync(p.phi, 0, ncol * N * sizeof(T), st));
     }
     CK(cudaMemsetAsync(ctx->d_conv, 0, (size_t)g.R * g.B * 2 * sizeof(unsigned long long), st));
-    k_scatter<T><<<cgrid, kContractThreads, csm / 2, st>>>(p.phi, p.sigma_s, p.Q, p.MT, p.q, N, g.sumK);
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);
+        k_scatter<T><<<cgrid, kContractThreads, csm / 2, st>>>(p.phi, p.sigma_s, p.Q, p.MT, p.q, N, g.sumK);
+    }
     CK(cudaGetLastError());
     const int every = o.check_every > 0 ? o.check_every : 1;
     int status = FPSA_ENOTCONV;
     double e = INFINITY;
     int it = 0;
     for (it = 1; it <= o.max_iterations; ++it) {
-        k_sweep<T, kSweepThreads><<<sgrid, kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu, ctx->d_off, ctx->d_K,
-                                                                  N, g.sumK);
+        {
+            Launch L_(ctx, FPSA_PHASE_SWEEP);
+            k_sweep<T, kSweepThreads><<<sgrid, kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu, ctx->d_off, ctx->d_K,
+                                                                      N, g.sumK);
+        }
         if (fpsa) {
-            k_fp_rhs<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, p.phi, p.phi_half, p.sigma_s, ctx->d_h, p.DT,
-                                                               p.MT, p.rhs, N, g.sumK);
+            {
+                Launch L_(ctx, FPSA_PHASE_CONTRACT);
+                k_fp_rhs<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, p.phi, p.phi_half, p.sigma_s, ctx->d_h, p.DT,
+                                                                   p.MT, p.rhs, N, g.sumK);
+            }
             int rc = bcr_solve(ctx, p, p.rhs);
             if (rc) return rc;
-            k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.rhs, p.phi_half, p.phi, p.sigma_s, p.Q, p.DT,
-                                                                       p.MT, p.q, ctx->d_cell_inst, g.B, ctx->d_conv,
-                                                                       N, g.sumK);
+            {
+                Launch L_(ctx, FPSA_PHASE_CONTRACT);
+                k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.rhs, p.phi_half, p.phi, p.sigma_s, p.Q, p.DT,
+                                                                           p.MT, p.q, ctx->d_cell_inst, g.B, ctx->d_conv,
+                                                                           N, g.sumK);
+            }
         } else {
-            k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const T *)nullptr, p.phi, p.sigma_s,
-                                                                       p.Q, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
-                                                                       ctx->d_conv, N, g.sumK);
+            {
+                Launch L_(ctx, FPSA_PHASE_CONTRACT);
+                k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const T *)nullptr, p.phi, p.sigma_s,
+                                                                           p.Q, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
+                                                                           ctx->d_conv, N, g.sumK);
+            }
         }
         CK(cudaGetLastError());
         if (it % every == 0 || it == o.max_iterations) {
-            k_conv_finalize<<<1, 256, 0, st>>>(ctx->d_conv, g.R * g.B, ctx->d_result);
+            {
+                Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
+                k_conv_finalize<<<1, 256, 0, st>>>(ctx->d_conv, g.R * g.B, ctx->d_result);
+            }
             CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             e = ctx->h_result[0];
@@ -305,6 +377,7 @@ void fpsa_destroy(fpsa_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (void *p : ctx->allocs) cudaFree(p);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
     delete ctx;
 }
@@ -421,6 +494,32 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     if (status || !std::isfinite(gr) || gr > 1e14)
         return fail(ctx, FPSA_EPIVOT, "FP block factorization failed: growth " + std::to_string(gr));
     ctx->xs_ready = true;
+    return FPSA_OK;
+}
+
+int fpsa_profile_enable(fpsa_ctx *ctx, int32_t on) {
+    if (!ctx) return FPSA_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < FPSA_N_PHASES; ++k) ctx->launches[k] = 0;
+    ctx->ev_rec.clear();
+    ctx->ev_used = 0;
+    ctx->prof_on = on != 0;
+    return FPSA_OK;
+}
+
+int fpsa_profile_read(fpsa_ctx *ctx, fpsa_profile *out) {
+    if (!ctx || !out) return FPSA_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memset(out, 0, sizeof(*out));
+    for (int k = 0; k < FPSA_N_PHASES; ++k) out->launches[k] = ctx->launches[k];
+    for (const auto &r : ctx->ev_rec) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev_pool[r.second], ctx->ev_pool[r.second + 1]));
+        out->ms[r.first] += ms;
+        out->timed[r.first] += 1;
+    }
     return FPSA_OK;
 }
 

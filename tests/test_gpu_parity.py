@@ -140,3 +140,33 @@ def test_error_paths(binding):
     with pytest.raises(binding.FpsaError) as e:
         ctx.solve("si", tol=1e-14, max_iterations=3)
     assert e.value.code == binding.ENOTCONV
+
+
+def read_golden(name):
+    import os
+    vals, its = [], {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            if line.startswith("#"):
+                if "iterations to relative change" in line:
+                    key = line.split("change")[1].split(":")[0].strip().split()[0]
+                    its[key] = int(line.rsplit(":", 1)[1])
+                continue
+            vals.append(float(line))
+    return np.array(vals), its
+
+
+@pytest.mark.parametrize("name,factory", [("plain_hg_slab", inputs.plain_hg_slab),
+                                          ("precision_srk_slab", inputs.precision_srk_slab)])
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+def test_full_size_against_golden(binding, name, factory, lap):
+    # Full-size workloads in the benchmark's launch configuration, against the stored oracle flux.
+    p = factory()
+    ref, its = read_golden("%s_fpsa_%s_phi0.txt" % (name, lap))
+    ctx = binding.context_for(p, laplacian=lap)
+    phi, st = ctx.solve("fpsa", tol=1e-10)
+    assert abs(st["iterations"] - its["1e-10"]) <= 1, (st, its)
+    phi0 = phi[0, :, :, 0].ravel()
+    assert np.abs(phi0 - ref).max() / np.abs(ref).max() < TOL
+    phi, st = ctx.solve("fpsa", tol=1e-13)
+    assert np.abs(phi[0, :, :, 0].ravel() - ref).max() / np.abs(ref).max() < 1e-11
