@@ -62,7 +62,8 @@ class FpsaProfile(ctypes.Structure):
 
 
 EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error",
-           "fpsa_profile_enable", "fpsa_profile_read"]
+           "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc"]
+NOALLOC_MAX_CELL_ANGLES = 131072
 
 _lib = None
 
@@ -92,6 +93,8 @@ def load():
     lib.fpsa_profile_enable.restype = ctypes.c_int
     lib.fpsa_profile_read.argtypes = [vp, ctypes.POINTER(FpsaProfile)]
     lib.fpsa_profile_read.restype = ctypes.c_int
+    lib.fpsa_sweep_noalloc.argtypes = [i32, i32, dp, dp, dp, dp, vp]
+    lib.fpsa_sweep_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -200,6 +203,23 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def sweep_noalloc(N, h, sigma_t, q, psi, stream=None):
+    """One LD sweep psi = L^{-1} q of a single slab through fpsa_sweep_noalloc, the entry point
+    that allocates no device memory (for callers that cannot call cudaMalloc). h, sigma_t [K],
+    q, psi [K][2][N] are contiguous float64 CUDA tensors; the work is enqueued on `stream`
+    (default: torch's current stream) and not synchronised."""
+    import torch
+    for x in (h, sigma_t, q, psi):
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise TypeError("sweep_noalloc takes contiguous float64 CUDA tensors")
+    K = int(h.numel())
+    rc = load().fpsa_sweep_noalloc(int(N), K, h.data_ptr(), sigma_t.data_ptr(), q.data_ptr(), psi.data_ptr(),
+                                   ctypes.c_void_p(_stream_handle(stream)))
+    if rc != OK:
+        raise FpsaError(rc, "fpsa_sweep_noalloc (N=%d, K=%d)" % (N, K))
+    return psi
 
 
 def context_for(problems, n_rhs=None, **kw):

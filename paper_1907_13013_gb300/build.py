@@ -6,7 +6,7 @@ import subprocess
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libfpsa.so")
-SOURCES = ["capi.cu", "tables.cpp", "geometry.cpp"]
+SOURCES = ["capi.cu", "tables.cpp", "geometry.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -226,7 +226,7 @@ __global__ void k_fp_rhs(const T *__restrict__ psi_half, const T *__restrict__ p
 }
 
 // Order-preserving key of a non-negative double (NaN sorts above +Inf).
-__device__ __forceinline__ unsigned long long dkey(double x) {
+static __device__ __forceinline__ unsigned long long dkey(double x) {
     return (unsigned long long)__double_as_longlong(fabs(x));
 }
 
@@ -273,7 +273,7 @@ __global__ void k_update_scatter(const T *__restrict__ v, const T *__restrict__ 
 
 // Worst relative change over (rhs, instance); resets the accumulators.
 // out[0] = max_rb conv_d / conv_a (NaN if any value was non-finite).
-__global__ void k_conv_finalize(unsigned long long *conv, int nrb, double *out) {
+static __global__ void k_conv_finalize(unsigned long long *conv, int nrb, double *out) {
     __shared__ double red[256];
     double worst = 0.0;
     bool bad = false;
