@@ -171,7 +171,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--laplacian", default="mpd", choices=["mpd", "wfd"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

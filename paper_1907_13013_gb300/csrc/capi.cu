@@ -34,6 +34,7 @@ struct PathBuffers {
     T *coef = nullptr;                       // [sumK][6][N]
     T *A = nullptr, *Bc = nullptr, *Cc = nullptr;
     T *phi = nullptr, *phi_half = nullptr, *q = nullptr, *psi = nullptr, *rhs = nullptr;
+    T *qang = nullptr;                       // MIXED inner path: nodal residual source [R][sumK][2][N]
 };
 
 }  // namespace
@@ -58,7 +59,8 @@ struct fpsa_ctx {
     double *d_result = nullptr;
     double *h_result = nullptr;  // pinned
 
-    PathBuffers<double> p64;
+    PathBuffers<double> p64;  // FP64 path; for MIXED: FP64 tables, psi (refined iterate), phi
+    PathBuffers<float> p32;   // MIXED: the FP32 inner FPSA solve
 
     // built-in profiler: launch counters (always) and event pairs (when on)
     bool prof_on = false;
@@ -125,24 +127,32 @@ size_t invert_smem(int N) {
     return ((size_t)n2 * (n2 + 1) + n2) * sizeof(T) + (size_t)n2 * sizeof(int);
 }
 
+// full: every buffer of an FPSA iteration in precision T. Otherwise only the tables,
+// cross sections, sources and the psi / phi state (the FP64 side of MIXED).
 template <typename T>
-int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p) {
+int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     const Geometry &g = ctx->geo;
     const size_t N = g.N, ang = (size_t)g.R * g.sumK * 2 * N;
     const int h2 = g.N / 2;
     CK(dalloc(ctx, &p.DT, N * N));
     CK(dalloc(ctx, &p.MT, N * N));
     CK(dalloc(ctx, &p.sigma_s, (size_t)g.sumK * N));
-    CK(dalloc(ctx, &p.Q, ang));
-    CK(dalloc(ctx, &p.coef, (size_t)g.sumK * 6 * N));
-    CK(dalloc(ctx, &p.A, (size_t)g.sumK * 4 * N * N));
-    CK(dalloc(ctx, &p.Bc, (size_t)g.n_slots * h2 * h2));
-    CK(dalloc(ctx, &p.Cc, (size_t)g.n_slots * h2 * h2));
     CK(dalloc(ctx, &p.phi, ang));
-    CK(dalloc(ctx, &p.phi_half, ang));
-    CK(dalloc(ctx, &p.q, ang));
     CK(dalloc(ctx, &p.psi, ang));
-    CK(dalloc(ctx, &p.rhs, ang));
+    if (full) {
+        CK(dalloc(ctx, &p.coef, (size_t)g.sumK * 6 * N));
+        CK(dalloc(ctx, &p.A, (size_t)g.sumK * 4 * N * N));
+        CK(dalloc(ctx, &p.Bc, (size_t)g.n_slots * h2 * h2));
+        CK(dalloc(ctx, &p.Cc, (size_t)g.n_slots * h2 * h2));
+        CK(dalloc(ctx, &p.phi_half, ang));
+        CK(dalloc(ctx, &p.q, ang));
+        CK(dalloc(ctx, &p.rhs, ang));
+    }
+    if (full && ctx->precision == FPSA_PRECISION_MIXED) {
+        CK(dalloc(ctx, &p.qang, ang));
+    } else {
+        CK(dalloc(ctx, &p.Q, ang));
+    }
     std::vector<T> DT(N * N), MT(N * N);
     for (size_t l = 0; l < N; ++l)
         for (size_t n = 0; n < N; ++n) {
@@ -156,9 +166,11 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p) {
     return FPSA_OK;
 }
 
-// Upload per-path cross sections / sources (padded to N moments) and factor the FP operator.
+// Upload per-path cross sections / sources (padded to N moments); with full, also the
+// sweep coefficients, the FP operator assembly and its block factorization.
 template <typename T>
-int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, const std::vector<double> &qm) {
+int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, const std::vector<double> &qm,
+               bool full) {
     const Geometry &g = ctx->geo;
     const int N = g.N, L1 = g.L1, n2 = 2 * N, h2 = N / 2;
     cudaStream_t st = ctx->stream;
@@ -170,7 +182,10 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
     for (size_t c = 0; c < ncol; ++c)
         for (int l = 0; l < L1; ++l) Qp[c * N + l] = (T)qm[c * L1 + l];
     CK(cudaMemcpyAsync(p.sigma_s, sp.data(), sp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(p.Q, Qp.data(), Qp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    if (p.Q) CK(cudaMemcpyAsync(p.Q, Qp.data(), Qp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    // the pageable staging vectors must outlive the asynchronous copies
+    CK(cudaStreamSynchronize(st));
+    if (!full) return FPSA_OK;
     {
         const size_t tot = (size_t)g.sumK * N;
         {
@@ -350,6 +365,113 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
     return status;
 }
 
+// MIXED: FP64 iterative refinement on the GPU around FP32 FPSA inner solves.
+//   outer k:  phi = D psi64, convergence test of phi_0 against the previous outer
+//             iterate (Eq. iterate), residual source dq (FP64, stored FP32)
+//   inner:    `inner` FPSA iterations (Eqs. predict, correct) on L dpsi = S dpsi + dq
+//             from dpsi = 0, all in FP32: sweep, contractions, BCR solve
+//   update:   psi64 += psi_half + upsilon of the last inner iteration (FP64)
+int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N, L1 = g.L1;
+    cudaStream_t st = ctx->stream;
+    PathBuffers<double> &p = ctx->p64;
+    PathBuffers<float> &f = ctx->p32;
+    const size_t ncol = (size_t)g.R * g.sumK * 2, nang = ncol * N;
+    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    const dim3 sgrid(N, g.B, g.R);
+    const int inner = o.inner_iterations > 0 ? o.inner_iterations : 6;
+    const bool fpsa = o.method == FPSA_METHOD_FPSA;
+
+    CK(cudaMemsetAsync(p.phi, 0, nang * sizeof(double), st));
+    if (phi0) {
+        CK(cudaMemcpy2DAsync(p.phi, N * sizeof(double), phi0, L1 * sizeof(double), L1 * sizeof(double), ncol,
+                             mem == FPSA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+        Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+        k_expand<double><<<cgrid, kContractThreads, contract_smem<double>(N) / 2, st>>>(p.phi, p.MT, p.psi, N, g.sumK);
+    } else {
+        CK(cudaMemsetAsync(p.psi, 0, nang * sizeof(double), st));
+    }
+    CK(cudaMemsetAsync(ctx->d_conv, 0, (size_t)g.R * g.B * 2 * sizeof(unsigned long long), st));
+    int status = FPSA_ENOTCONV;
+    double e = INFINITY;
+    int outer = 0, sweeps = 0;
+    for (outer = 1; outer <= o.max_iterations + 1; ++outer) {
+        {
+            Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+            k_mixed_residual<<<cgrid, kContractThreads, contract_smem<double>(N), st>>>(
+                p.psi, p.phi, p.sigma_s, p.Q, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst,
+                ctx->d_off, ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK);
+        }
+        {
+            Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
+            k_conv_finalize<<<1, 256, 0, st>>>(ctx->d_conv, g.R * g.B, ctx->d_result);
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        e = ctx->h_result[0];
+        if (std::isnan(e)) {
+            status = fail(ctx, FPSA_ENONFINITE, "non-finite iterate at refinement step " + std::to_string(outer));
+            break;
+        }
+        if ((outer > 1 || phi0) && e < o.tol) {
+            status = FPSA_OK;
+            break;
+        }
+        if (outer > o.max_iterations) break;
+        // inner FP32 solve of the correction from zero
+        CK(cudaMemsetAsync(f.phi, 0, nang * sizeof(float), st));
+        CK(cudaMemcpyAsync(f.q, f.qang, nang * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        for (int j = 1; j <= inner; ++j) {
+            {
+                Launch L_(ctx, FPSA_PHASE_SWEEP);
+                k_sweep<float, kSweepThreads><<<sgrid, kSweepThreads, 0, st>>>(f.q, f.psi, f.coef, ctx->d_mu,
+                                                                               ctx->d_off, ctx->d_K, N, g.sumK);
+            }
+            ++sweeps;
+            const float *vin = f.psi, *base = nullptr;
+            if (fpsa) {
+                {
+                    Launch L_(ctx, FPSA_PHASE_CONTRACT);
+                    k_fp_rhs<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
+                        f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h, f.DT, f.MT, f.rhs, N, g.sumK);
+                }
+                int rc = bcr_solve(ctx, f, f.rhs);
+                if (rc) return rc;
+                vin = f.rhs;
+                base = f.phi_half;
+            }
+            if (j < inner) {
+                Launch L_(ctx, FPSA_PHASE_CONTRACT);
+                k_update_scatter<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
+                    vin, base, f.phi, f.sigma_s, (const float *)nullptr, f.DT, f.MT, f.q, ctx->d_cell_inst, g.B,
+                    (unsigned long long *)nullptr, N, g.sumK, f.qang);
+            }
+        }
+        {
+            Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+            if (fpsa) {
+                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, f.rhs, nang);
+            } else {
+                CK(cudaMemsetAsync(f.rhs, 0, nang * sizeof(float), st));
+                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, f.rhs, nang);
+            }
+        }
+        CK(cudaGetLastError());
+    }
+    stats.iterations = sweeps;
+    stats.outer_iterations = std::min(outer, o.max_iterations + 1);
+    stats.sweeps = sweeps;
+    stats.rel_change = e;
+    CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(double), L1 * sizeof(double), ncol,
+                         mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (status == FPSA_ENOTCONV)
+        fail(ctx, FPSA_ENOTCONV, "not converged after " + std::to_string(o.max_iterations) + " refinement steps");
+    return status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -392,7 +514,6 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
     if (d->laplacian != FPSA_LAPLACIAN_MPD && d->laplacian != FPSA_LAPLACIAN_WFD) return FPSA_EINVAL;
     if (d->precision != FPSA_PRECISION_FP64 && d->precision != FPSA_PRECISION_MIXED) return FPSA_EINVAL;
     if (d->n_ordinates > FPSA_MAX_ORDINATES) return FPSA_ENOTSUP;
-    if (d->precision == FPSA_PRECISION_MIXED) return FPSA_ENOTSUP;
     long long sumK = 0;
     for (int b = 0; b < d->n_instances; ++b) {
         if (d->n_cells[b] < 1) return FPSA_EINVAL;
@@ -446,7 +567,10 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         }
         CK(dalloc(ctx, &ctx->d_roots, g.B));
         CK(cudaMemcpy(ctx->d_roots, g.roots.data(), g.B * sizeof(BcrItem), cudaMemcpyHostToDevice));
-        return alloc_path(ctx, ctx->p64);
+        if (ctx->precision == FPSA_PRECISION_FP64) return alloc_path(ctx, ctx->p64, true);
+        int r2 = alloc_path(ctx, ctx->p64, false);
+        if (r2) return r2;
+        return alloc_path(ctx, ctx->p32, true);
     }();
     if (rc != FPSA_OK) return bail(rc);
     *out = ctx;
@@ -480,7 +604,12 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     CK(cudaMemcpyAsync(ctx->d_s1, s1.data(), g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->d_growth, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
-    rc = setup_path(ctx, ctx->p64, ss, qm);
+    if (ctx->precision == FPSA_PRECISION_FP64) {
+        rc = setup_path(ctx, ctx->p64, ss, qm, true);
+    } else {
+        rc = setup_path(ctx, ctx->p64, ss, qm, false);
+        if (!rc) rc = setup_path(ctx, ctx->p32, ss, qm, true);
+    }
     if (rc) return rc;
     unsigned long long growth = 0;
     int status = 0;
@@ -536,7 +665,8 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
     CK(cudaSetDevice(ctx->device));
     fpsa_stats s{};
     const auto t0 = std::chrono::steady_clock::now();
-    int rc = solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s);
+    int rc = ctx->precision == FPSA_PRECISION_FP64 ? solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s)
+                                                   : solve_mixed(ctx, o, phi0, mem, phi, s);
     s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     s.status = rc;
     s.setup_ms = ctx->setup_ms;

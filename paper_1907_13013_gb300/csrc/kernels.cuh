@@ -152,11 +152,11 @@ __global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__rest
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void block_contract(const T *Xs, int ldx, const T *__restrict__ MatT, int N, int ncols,
-                                               T *Ys, int ldy) {
+                                               T *Ys, int ldy, const T *__restrict__ add = nullptr) {
     for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
         const int c = idx / N, o = idx - c * N;
         const T *x = Xs + c * ldx;
-        T acc = T(0);
+        T acc = add ? add[(size_t)c * ldy + o] : T(0);
 #pragma unroll 8
         for (int k = 0; k < N; ++k) acc = fma(MatT[(size_t)k * N + o], x[k], acc);
         Ys[c * ldy + o] = acc;
@@ -166,10 +166,12 @@ __device__ __forceinline__ void block_contract(const T *Xs, int ldx, const T *__
 // Columns handled by one contraction block: CB cells x 2 nodes.
 constexpr int kContractCells = 8;
 
-// q = M (sigma_s phi + Q) for every column (Eq. treq: scattering + external source).
+// q = M (sigma_s phi + Q) + q_ang for every column (Eq. treq: scattering + external
+// source given as moments Q and/or as nodal angular values q_ang; either may be NULL).
 template <typename T>
 __global__ void k_scatter(const T *__restrict__ phi, const T *__restrict__ sigma_s, const T *__restrict__ Qext,
-                          const T *__restrict__ MT, T *__restrict__ q, int N, int sumK) {
+                          const T *__restrict__ MT, T *__restrict__ q, int N, int sumK,
+                          const T *__restrict__ Qang = nullptr) {
     extern __shared__ unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);
     const int r = blockIdx.y;
@@ -181,10 +183,10 @@ __global__ void k_scatter(const T *__restrict__ phi, const T *__restrict__ sigma
         const int c = idx / N, l = idx - c * N;
         const int g = g0 + c / 2;
         const size_t e = (colbase + c) * N + l;
-        Xs[c * N + l] = sigma_s[(size_t)g * N + l] * phi[e] + Qext[e];
+        Xs[c * N + l] = sigma_s[(size_t)g * N + l] * phi[e] + (Qext ? Qext[e] : T(0));
     }
     __syncthreads();
-    block_contract(Xs, N, MT, N, ncols, q + colbase * N, N);
+    block_contract(Xs, N, MT, N, ncols, q + colbase * N, N, Qang ? Qang + colbase * N : nullptr);
 }
 
 // FPSA, after the sweep: phi_half = D psi_half; then the FP right-hand side
@@ -230,8 +232,8 @@ static __device__ __forceinline__ unsigned long long dkey(double x) {
     return (unsigned long long)__double_as_longlong(fabs(x));
 }
 
-// phi_new = (phi_base ? phi_base : 0) + D v ; convergence maxima; then
-// q = M (sigma_s phi_new + Q) for the next sweep.
+// phi_new = (phi_base ? phi_base : 0) + D v ; convergence maxima (if conv); then
+// q = M (sigma_s phi_new + Q) + q_ang for the next sweep (Q, q_ang nullable).
 //   SI:   phi_base = NULL, v = psi (Eq. trsi)
 //   FPSA: phi_base = phi_half, v = FP correction upsilon (Eq. correct)
 // conv[(r*B + b)*2 + 0] = max |phi_0 new - old|, [..+1] = max |phi_0 new|.
@@ -240,7 +242,8 @@ __global__ void k_update_scatter(const T *__restrict__ v, const T *__restrict__ 
                                  const T *__restrict__ sigma_s, const T *__restrict__ Qext,
                                  const T *__restrict__ DT, const T *__restrict__ MT, T *__restrict__ q,
                                  const int32_t *__restrict__ cell_inst, int B,
-                                 unsigned long long *__restrict__ conv, int N, int sumK) {
+                                 unsigned long long *__restrict__ conv, int N, int sumK,
+                                 const T *__restrict__ Qang = nullptr) {
     extern __shared__ unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);
     T *Ys = Xs + 2 * kContractCells * N;
@@ -259,16 +262,107 @@ __global__ void k_update_scatter(const T *__restrict__ v, const T *__restrict__ 
         const size_t e = colbase * N + idx;
         T pn = Ys[idx];
         if (phi_base) pn += phi_base[e];
-        if (l == 0) {
+        if (l == 0 && conv) {
             const int slot = (r * B + cell_inst[g]) * 2;
             atomicMax(conv + slot, dkey((double)pn - (double)phi[e]));
             atomicMax(conv + slot + 1, dkey((double)pn));
         }
         phi[e] = pn;
+        Xs[idx] = sigma_s[(size_t)g * N + l] * pn + (Qext ? Qext[e] : T(0));
+    }
+    __syncthreads();
+    block_contract(Xs, N, MT, N, ncols, q + colbase * N, N, Qang ? Qang + colbase * N : nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision: FP64 iterative refinement around FP32 FPSA inner solves.
+// Residual of the discrete transport system (L_h - S_h) psi = m q (Eq. trop in
+// LD form), in the nodal form the sweep consumes, per cell and ordinate:
+//   dq = s - sigma_t psi - m^{-1} (G(mu) psi - |mu| psi_in e_up),
+//   s  = M (Sigma phi + Q),  phi = D psi,
+// so that the correction equation is L dpsi = S dpsi + dq with vacuum inflow.
+// Also: phi (FP64) is stored and its l = 0 change against the previous outer
+// iterate is max-reduced into conv (Eq. iterate on the refined iterates).
+// ---------------------------------------------------------------------------
+static __global__ void k_mixed_residual(const double *__restrict__ psi, double *__restrict__ phi,
+                                 const double *__restrict__ sigma_s, const double *__restrict__ Qext,
+                                 const double *__restrict__ DT, const double *__restrict__ MT,
+                                 const double *__restrict__ sigma_t, const double *__restrict__ h,
+                                 const double *__restrict__ mu, const int32_t *__restrict__ cell_inst,
+                                 const int32_t *__restrict__ off, const int32_t *__restrict__ Kc, int B,
+                                 unsigned long long *__restrict__ conv, float *__restrict__ dq, int N, int sumK) {
+    extern __shared__ unsigned char smem_raw[];
+    double *Xs = reinterpret_cast<double *>(smem_raw);
+    double *Ys = Xs + 2 * kContractCells * N;
+    const int r = blockIdx.y;
+    const int g0 = blockIdx.x * kContractCells;
+    const int ncell = min(kContractCells, sumK - g0);
+    const int ncols = 2 * ncell;
+    const size_t colbase = ((size_t)r * sumK + g0) * 2;
+    const double *psr = psi + (size_t)r * sumK * 2 * N;  // this rhs
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) Xs[idx] = psi[colbase * N + idx];
+    __syncthreads();
+    block_contract(Xs, N, DT, N, ncols, Ys, N);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
+        const int c = idx / N, l = idx - c * N;
+        const int g = g0 + c / 2;
+        const size_t e = colbase * N + idx;
+        const double pn = Ys[idx];
+        if (l == 0) {
+            const int slot = (r * B + cell_inst[g]) * 2;
+            atomicMax(conv + slot, dkey(pn - phi[e]));
+            atomicMax(conv + slot + 1, dkey(pn));
+        }
+        phi[e] = pn;
         Xs[idx] = sigma_s[(size_t)g * N + l] * pn + Qext[e];
     }
     __syncthreads();
-    block_contract(Xs, N, MT, N, ncols, q + colbase * N, N);
+    block_contract(Xs, N, MT, N, ncols, Ys, N);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncell * N; idx += blockDim.x) {
+        const int cl = idx / N, n = idx - cl * N;
+        const int g = g0 + cl;
+        const int b = cell_inst[g], loc = g - off[b];
+        const double m = mu[n], hh = h[g], st = sigma_t[g];
+        const double pL = psr[((size_t)2 * g) * N + n], pR = psr[((size_t)2 * g + 1) * N + n];
+        double tL, tR;
+        if (m > 0.0) {
+            const double pin = loc > 0 ? psr[((size_t)2 * (g - 1) + 1) * N + n] : 0.0;
+            tL = 0.5 * m * (pL + pR) - m * pin;
+            tR = 0.5 * m * (pR - pL);
+        } else {
+            const double pin = loc < Kc[b] - 1 ? psr[((size_t)2 * (g + 1)) * N + n] : 0.0;
+            tL = 0.5 * m * (pR - pL);
+            tR = -0.5 * m * (pL + pR) + m * pin;  // -|mu| psi_in with mu < 0
+        }
+        const double w = 2.0 / hh;
+        const double sL = Ys[(2 * cl) * N + n], sR = Ys[(2 * cl + 1) * N + n];
+        dq[(colbase + 2 * cl) * N + n] = (float)(sL - st * pL - w * (2.0 * tL - tR));
+        dq[(colbase + 2 * cl + 1) * N + n] = (float)(sR - st * pR - w * (2.0 * tR - tL));
+    }
+}
+
+// psi64 += dpsi, dpsi = psi_half + upsilon of the last inner FPSA iteration (Eq. correct).
+static __global__ void k_mixed_accumulate(double *__restrict__ psi, const float *__restrict__ psi_half,
+                                   const float *__restrict__ ups, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        psi[i] += (double)psi_half[i] + (double)ups[i];
+}
+
+// x (moments, padded to N) -> nodal angular values M x, used to turn a moment
+// initial guess into an angular one.
+template <typename T>
+__global__ void k_expand(const T *__restrict__ x, const T *__restrict__ MT, T *__restrict__ out, int N, int sumK) {
+    extern __shared__ unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);
+    const int r = blockIdx.y;
+    const int g0 = blockIdx.x * kContractCells;
+    const int ncols = 2 * min(kContractCells, sumK - g0);
+    const size_t colbase = ((size_t)r * sumK + g0) * 2;
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) Xs[idx] = x[colbase * N + idx];
+    __syncthreads();
+    block_contract(Xs, N, MT, N, ncols, out + colbase * N, N);
 }
 
 // Worst relative change over (rhs, instance); resets the accumulators.

@@ -170,3 +170,45 @@ def test_full_size_against_golden(binding, name, factory, lap):
     assert np.abs(phi0 - ref).max() / np.abs(ref).max() < TOL
     phi, st = ctx.solve("fpsa", tol=1e-13)
     assert np.abs(phi[0, :, :, 0].ravel() - ref).max() / np.abs(ref).max() < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision: FP32 sweeps / contractions / BCR inside FP64 refinement.
+# The converged flux must still be within 1e-9 of the FP64 oracle.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,K,seed,kernel", [(2, 5, 0, "hg"), (8, 3, 3, "hg"), (16, 33, 4, "srk"),
+                                             (32, 64, 5, "hg"), (64, 97, 6, "srk")])
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+def test_mixed_random_slabs(binding, N, K, seed, kernel, lap):
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel=kernel, thick=(1, 300), c=(0.5, 0.999))
+    ctx = binding.context_for(p, laplacian=lap, precision="mixed")
+    phi, st = ctx.solve("fpsa", tol=1e-12, max_iterations=100)
+    ref, n = oracle(p, "fpsa", lap)
+    assert relerr(phi[0], ref) < TOL, (relerr(phi[0], ref), st)
+
+
+def test_mixed_batch_and_si(binding):
+    R = 2
+    probs = [inputs.random_slab(K, 8, 7, seed=40 + i, kernel="hg", c=(0.3, 0.8), nrhs=R) for i, K in enumerate([1, 9, 40])]
+    for method in ("fpsa", "si"):
+        ctx = binding.context_for(probs, precision="mixed")
+        phi, st = ctx.solve(method, tol=1e-12, max_iterations=200, inner_iterations=8)
+        off = 0
+        for p in probs:
+            K = p["h"].size
+            for r in range(R):
+                ref = oit.direct_solve(dict(p, Q=p["Q"][r]))
+                assert relerr(phi[r, off:off + K], ref) < TOL, (method, relerr(phi[r, off:off + K], ref))
+            off += K
+
+
+@pytest.mark.parametrize("name,factory", [("plain_hg_slab", inputs.plain_hg_slab),
+                                          ("precision_srk_slab", inputs.precision_srk_slab)])
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+def test_mixed_full_size_against_golden(binding, name, factory, lap):
+    p = factory()
+    ref, its = read_golden("%s_fpsa_%s_phi0.txt" % (name, lap))
+    ctx = binding.context_for(p, laplacian=lap, precision="mixed")
+    phi, st = ctx.solve("fpsa", tol=1e-10, max_iterations=50)
+    err = np.abs(phi[0, :, :, 0].ravel() - ref).max() / np.abs(ref).max()
+    assert err < TOL, (err, st)
