@@ -4,7 +4,7 @@
 // is, per sweep, the launch sequence
 //   k_sweep            psi^{m+1/2} = L^{-1} q                      (LD upwind sweep)
 //   k_fp_rhs           phi^{m+1/2} = D psi^{m+1/2};  rhs = m (x) M Sigma (phi^{m+1/2} - phi^m)
-//   k_bcr_fwd x levels, roots, k_bcr_bwd x levels     upsilon = F^{-1} rhs
+//   k_bcr_solve_coop   upsilon = F^{-1} rhs (all reduction levels in one cooperative launch)
 //   k_update_scatter   phi^{m+1} = phi^{m+1/2} + D upsilon; q = M (Sigma phi^{m+1} + Q)
 // with the convergence maxima of Eq. iterate accumulated in k_update_scatter.
 #include <algorithm>
@@ -25,6 +25,7 @@ namespace {
 constexpr int kSweepThreads = 256;
 constexpr int kContractThreads = 256;
 constexpr int kInvertThreads = 512;
+constexpr int kSolveThreads = 256;  // one (item, rhs) unit per block
 
 template <typename T>
 struct PathBuffers {
@@ -35,6 +36,7 @@ struct PathBuffers {
     T *A = nullptr, *Bc = nullptr, *Cc = nullptr;
     T *phi = nullptr, *phi_half = nullptr, *q = nullptr, *psi = nullptr, *rhs = nullptr;
     T *qang = nullptr;                       // MIXED inner path: nodal residual source [R][sumK][2][N]
+    T *ybuf = nullptr;                       // BCR solve: intermediate y, then the solution [R][sumK][2N]
 };
 
 }  // namespace
@@ -54,6 +56,9 @@ struct fpsa_ctx {
            *d_s1 = nullptr;
     std::vector<BcrItem *> d_levels;
     BcrItem *d_roots = nullptr;
+    BcrItem *d_items_all = nullptr;  // levels concatenated, then roots (cooperative solve)
+    LevelTable lvt[2] = {};          // per element type (row slicing depends on the vector width)
+    int coop_grid[2] = {0, 0};       // cooperative BCR solve grid for float [0] / double [1]
     unsigned long long *d_conv = nullptr, *d_growth = nullptr;
     int *d_status = nullptr;
     double *d_result = nullptr;
@@ -121,6 +126,12 @@ cudaError_t dalloc(fpsa_ctx *ctx, P **p, size_t count) {
 template <typename T>
 size_t contract_smem(int N) { return 2 * 2 * (size_t)kContractCells * N * sizeof(T); }
 
+// shared scratch of the cooperative BCR solve (one unit per block)
+template <typename T>
+size_t solve_smem(int N) {
+    return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V) * sizeof(T);
+}
+
 template <typename T>
 size_t invert_smem(int N) {
     const int n2 = 2 * N;
@@ -147,6 +158,7 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         CK(dalloc(ctx, &p.phi_half, ang));
         CK(dalloc(ctx, &p.q, ang));
         CK(dalloc(ctx, &p.rhs, ang));
+        CK(dalloc(ctx, &p.ybuf, ang));
     }
     if (full && ctx->precision == FPSA_PRECISION_MIXED) {
         CK(dalloc(ctx, &p.qang, ang));
@@ -205,13 +217,22 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
     }
     CK(cudaGetLastError());
     const size_t ism = invert_smem<T>(N);
+    // register-tiled inversion where a 16-warp tile layout exists, else the shared-memory one
+    auto invert = [&](const BcrItem *items, int ni) {
+        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+        if (n2 == 128)
+            k_bcr_invert_reg<T, 128><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+        else if (n2 == 64)
+            k_bcr_invert_reg<T, 64><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+        else if (n2 == 32)
+            k_bcr_invert_reg<T, 32><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+        else
+            k_bcr_invert<T><<<ni, kInvertThreads, ism, st>>>(p.A, items, n2, ctx->d_growth, ctx->d_status);
+    };
     for (int l = 0; l < g.n_levels; ++l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
-        {
-            Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
-            k_bcr_invert<T><<<ni, kInvertThreads, ism, st>>>(p.A, ctx->d_levels[l], n2, ctx->d_growth, ctx->d_status);
-        }
+        invert(ctx->d_levels[l], ni);
         CK(cudaGetLastError());
         {
             Launch L_(ctx, FPSA_PHASE_BCR_SCHUR);
@@ -219,42 +240,27 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
         }
         CK(cudaGetLastError());
     }
-    {
-        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
-        k_bcr_invert<T><<<g.B, kInvertThreads, ism, st>>>(p.A, ctx->d_roots, n2, ctx->d_growth, ctx->d_status);
-    }
+    invert(ctx->d_roots, g.B);
     CK(cudaGetLastError());
     return FPSA_OK;
 }
 
+// F u = rhs by block cyclic reduction over the stored factors: one cooperative
+// launch (forward levels, roots, backward levels); the solution is left in p.ybuf.
 template <typename T>
 int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     const Geometry &g = ctx->geo;
-    const int N = g.N, n2 = 2 * N, h2 = N / 2;
-    cudaStream_t st = ctx->stream;
-    for (int l = 0; l < g.n_levels; ++l) {
-        const int ni = (int)g.levels[l].size();
-        if (!ni) continue;
-        {
-            Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
-            k_bcr_fwd<T><<<dim3(ni, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
-                                                                          g.sumK);
-        }
-    }
-    {
-        Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
-        k_bcr_fwd<T><<<dim3(g.B, g.R), 128, 2 * n2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_roots, rhs, N, g.sumK);
-    }
-    for (int l = g.n_levels - 1; l >= 0; --l) {
-        const int ni = (int)g.levels[l].size();
-        if (!ni) continue;
-        {
-            Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
-            k_bcr_bwd<T><<<dim3(ni, g.R), 128, 2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], rhs, N,
-                                                                          g.sumK);
-        }
-    }
-    CK(cudaGetLastError());
+    int N = g.N, sumK = g.sumK, R = g.R;
+    const BcrItem *items = ctx->d_items_all;
+    LevelTable lv = ctx->lvt[sizeof(T) == 8 ? 1 : 0];
+    const T *A = p.A, *Bc = p.Bc, *Cc = p.Cc;
+    T *Y = p.ybuf;
+    void *args[] = {(void *)&A, (void *)&Bc, (void *)&Cc, (void *)&items, (void *)&lv, (void *)&rhs,
+                    (void *)&Y, (void *)&N, (void *)&sumK, (void *)&R};
+    const int grid = ctx->coop_grid[sizeof(T) == 8 ? 1 : 0];
+    Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
+    CK(cudaLaunchCooperativeKernel((const void *)k_bcr_solve_coop<T, kSolveThreads>, dim3(grid), dim3(kSolveThreads),
+                                   args, solve_smem<T>(N), ctx->stream));
     return FPSA_OK;
 }
 
@@ -321,7 +327,7 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
             if (rc) return rc;
             {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.rhs, p.phi_half, p.phi, p.sigma_s, p.Q, p.DT,
+                k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.ybuf, p.phi_half, p.phi, p.sigma_s, p.Q, p.DT,
                                                                            p.MT, p.q, ctx->d_cell_inst, g.B, ctx->d_conv,
                                                                            N, g.sumK);
             }
@@ -439,7 +445,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
                 }
                 int rc = bcr_solve(ctx, f, f.rhs);
                 if (rc) return rc;
-                vin = f.rhs;
+                vin = f.ybuf;
                 base = f.phi_half;
             }
             if (j < inner) {
@@ -452,7 +458,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         {
             Launch L_(ctx, FPSA_PHASE_RESIDUAL);
             if (fpsa) {
-                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, f.rhs, nang);
+                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, f.ybuf, nang);
             } else {
                 CK(cudaMemsetAsync(f.rhs, 0, nang * sizeof(float), st));
                 k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, f.rhs, nang);
@@ -567,6 +573,46 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         }
         CK(dalloc(ctx, &ctx->d_roots, g.B));
         CK(cudaMemcpy(ctx->d_roots, g.roots.data(), g.B * sizeof(BcrItem), cudaMemcpyHostToDevice));
+        {
+            std::vector<BcrItem> all;
+            for (int l = 0; l < g.n_levels; ++l) all.insert(all.end(), g.levels[l].begin(), g.levels[l].end());
+            all.insert(all.end(), g.roots.begin(), g.roots.end());
+            CK(dalloc(ctx, &ctx->d_items_all, all.size()));
+            CK(cudaMemcpy(ctx->d_items_all, all.data(), all.size() * sizeof(BcrItem), cudaMemcpyHostToDevice));
+            int nsm = 0, per_sm = 0;
+            CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+            CK(cudaFuncSetAttribute(k_bcr_solve_coop<float, kSolveThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)solve_smem<float>(g.N)));
+            CK(cudaFuncSetAttribute(k_bcr_solve_coop<double, kSolveThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)solve_smem<double>(g.N)));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcr_solve_coop<float, kSolveThreads>, kSolveThreads,
+                                                             solve_smem<float>(g.N)));
+            ctx->coop_grid[0] = std::max(1, std::min(per_sm, 4)) * nsm;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcr_solve_coop<double, kSolveThreads>, kSolveThreads,
+                                                             solve_smem<double>(g.N)));
+            ctx->coop_grid[1] = std::max(1, std::min(per_sm, 4)) * nsm;
+            // Row slices per item: split an item's 2N rows (in vectors of V) into S in {1, 2, 4}
+            // slices (quadrant-aligned) of >= 2 vectors while the level's units still fit in
+            // one pass of the grid.
+            for (int e = 0; e < 2; ++e) {
+                const int V = e ? VecOf<double>::V : VecOf<float>::V;
+                const int vecs = 2 * g.N / V;
+                LevelTable &lv = ctx->lvt[e];
+                lv.n_levels = g.n_levels;
+                lv.n_roots = g.B;
+                int off = 0;
+                for (int l = 0; l <= g.n_levels; ++l) {
+                    const int items = l < g.n_levels ? (int)g.levels[l].size() : g.B;
+                    lv.off[l] = off;
+                    off += items;
+                    int S = 1;
+                    while (2 * S <= 4 && vecs % (2 * S) == 0 && vecs / (2 * S) >= 2 &&
+                           (long long)items * g.R * 2 * S <= ctx->coop_grid[e])
+                        S *= 2;
+                    lv.slices[l] = S;
+                }
+            }
+        }
         if (ctx->precision == FPSA_PRECISION_FP64) return alloc_path(ctx, ctx->p64, true);
         int r2 = alloc_path(ctx, ctx->p64, false);
         if (r2) return r2;

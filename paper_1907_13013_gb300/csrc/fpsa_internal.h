@@ -33,6 +33,9 @@ struct BcrItem {
     int32_t s_left_next;   // slot(left, l+1)
     int32_t s_right;       // slot(right, l)
     int32_t s_right_next;  // slot(right, l+1)
+    int32_t local;         // cell index within its instance
+    int32_t K_inst;        // cells of the instance
+    int32_t level;         // level the cell is eliminated at (roots: the instance's level count)
 };
 
 // Device-side geometry of the batch.

@@ -64,6 +64,9 @@ void build_geometry(const int32_t *K, int B, int N, int L1, int R, Geometry &g) 
                 it.s_left_next = g.slot_base[it.left] + l + 1;
                 it.s_right = it.right >= 0 ? g.slot_base[it.right] + l : -1;
                 it.s_right_next = it.right >= 0 ? g.slot_base[it.right] + l + 1 : -1;
+                it.local = i;
+                it.K_inst = K[b];
+                it.level = l;
                 g.levels[l].push_back(it);
             }
         }
@@ -75,6 +78,9 @@ void build_geometry(const int32_t *K, int B, int N, int L1, int R, Geometry &g) 
         it.left = it.right = -1;
         it.s_cell = g.slot_base[it.cell] + levels_for(K[b]);
         it.s_left = it.s_left_next = it.s_right = it.s_right_next = -1;
+        it.local = 0;
+        it.K_inst = K[b];
+        it.level = levels_for(K[b]);
         g.roots.push_back(it);
     }
 }

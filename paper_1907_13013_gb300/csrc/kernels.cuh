@@ -15,10 +15,13 @@
 // (L+ and R- receive inflow from the neighbours, R+ and L- are the outflows).
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "fpsa_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace fpsa {
 
@@ -539,6 +542,141 @@ __global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ item
     if (bad) atomicExch(status, 1);
 }
 
+// Register-tiled Gauss-Jordan inversion for n2 = 2N in {32, 64, 128}: 16 warps;
+// warp w owns the columns w + 16 j (j < n2/16), lane t the rows t + 32 i
+// (i < n2/32), so every thread holds an (n2/32) x (n2/16) tile in registers and
+// column k lives in one warp. Pivoting is implicit: step k picks, among rows not
+// yet used, the row p_k of largest |a[p][k]| (partial pivoting without moving
+// rows). The in-place update is the usual one with row p_k as pivot row; at the
+// end the array X holds A^{-1}[r][c] = X[p_r][q_c] with q the inverse of p
+// (row p_k carries step k's identity column). Written back transposed.
+template <typename T, int N2>
+__global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const BcrItem *__restrict__ items,
+                                                        unsigned long long *__restrict__ growth,
+                                                        int *__restrict__ status) {
+    constexpr int RI = N2 / 32, CJ = N2 / 16;
+    __shared__ T colbuf[2][N2], rowbuf[2][N2];
+    __shared__ int s_p[2], used[N2], perm[N2], iperm[N2];
+    __shared__ T s_inv[2];
+    __shared__ double s_red[16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const BcrItem it = items[blockIdx.x];
+    T *Ag = A + (size_t)it.cell * N2 * N2;
+    T x[RI][CJ];
+    double amax = 0.0;
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+            x[i][j] = Ag[(size_t)(lane + 32 * i) * N2 + w + 16 * j];
+            amax = fmax(amax, fabs((double)x[i][j]));
+        }
+    for (int r = threadIdx.x; r < N2; r += blockDim.x) used[r] = 0;
+    bool bad = false;
+    __syncthreads();
+    for (int k = 0; k < N2; ++k) {
+        const int b = k & 1;
+        const int jk = k >> 4;  // column k is x[.][jk] of warp k % 16
+        if (w == (k & 15)) {
+            T best = T(-1);
+            int bi = N2;
+            T colv[RI];
+#pragma unroll
+            for (int i = 0; i < RI; ++i) {
+#pragma unroll
+                for (int j = 0; j < CJ; ++j)
+                    if (j == jk) colv[i] = x[i][j];
+                const int row = lane + 32 * i;
+                colbuf[b][row] = colv[i];
+                const T v = fabs(colv[i]);
+                if (!used[row] && v > best) { best = v; bi = row; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                s_p[b] = bi;
+                used[bi] = 1;
+                perm[k] = bi;
+                iperm[bi] = k;
+            }
+        }
+        __syncthreads();
+        const int p = s_p[b];
+        const T pv = colbuf[b][p];
+        if (pv == T(0) || !isfinite(pv)) bad = true;
+        const T inv = T(1) / pv;
+        const int ip = p >> 5;
+        if (lane == (p & 31)) {
+#pragma unroll
+            for (int i = 0; i < RI; ++i)
+                if (i == ip)
+#pragma unroll
+                    for (int j = 0; j < CJ; ++j) {
+                        const int col = w + 16 * j;
+                        rowbuf[b][col] = (col == k) ? inv : x[i][j] * inv;
+                    }
+        }
+        __syncthreads();
+        T f[RI], rv[CJ];
+#pragma unroll
+        for (int i = 0; i < RI; ++i) f[i] = colbuf[b][lane + 32 * i];
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) rv[j] = rowbuf[b][w + 16 * j];
+        if (w == (k & 15)) {
+            // this warp owns column k: its old value is replaced, not updated
+#pragma unroll
+            for (int j = 0; j < CJ; ++j)
+                if (j == jk)
+#pragma unroll
+                    for (int i = 0; i < RI; ++i) x[i][j] = T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < RI; ++i)
+#pragma unroll
+            for (int j = 0; j < CJ; ++j) x[i][j] = fma(-f[i], rv[j], x[i][j]);
+        if (lane == (p & 31)) {
+            // the pivot row becomes the scaled row (its f is the pivot itself)
+#pragma unroll
+            for (int i = 0; i < RI; ++i)
+                if (i == ip)
+#pragma unroll
+                    for (int j = 0; j < CJ; ++j) x[i][j] = rv[j];
+        }
+    }
+    __syncthreads();
+    // Thread holds X[row][col] = A^{-1}[r][c] with perm[r] = row (r = iperm[row]) and
+    // iperm[c] = col (c = perm[col]); written transposed, Ag[c][r].
+    double ainv = 0.0;
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+            const int row = lane + 32 * i, col = w + 16 * j;
+            const int r = iperm[row], c = perm[col];
+            Ag[(size_t)c * N2 + r] = x[i][j];
+            ainv = fmax(ainv, fabs((double)x[i][j]));
+            if (!isfinite((double)x[i][j])) bad = true;
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        ainv = fmax(ainv, __shfl_xor_sync(0xffffffffu, ainv, o));
+    }
+    if (lane == 0) s_red[w] = amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < 16; ++i) m = fmax(m, s_red[i]);
+        s_red[0] = m;
+    }
+    __syncthreads();
+    if (lane == 0) atomicMax(growth, dkey(ainv * s_red[0]));
+    if (bad) atomicExch(status, 1);
+}
+
 // C[p][q] -= / = sum_k X(p,k) Y(k,q) for h2 x h2 operands addressed by strides.
 template <typename T>
 __device__ __forceinline__ void tile_mm(T *out, int ldo, bool accumulate_neg, const T *X, int xr, int xc,
@@ -613,79 +751,221 @@ __global__ void k_bcr_schur(T *__restrict__ A, T *__restrict__ Bc, T *__restrict
 //                                          - Ainv_i[:,R-] C_i u_{i+s}[L-].
 // One block per (item, rhs); every write touches a disjoint sub-vector.
 // ---------------------------------------------------------------------------
+// Row-sliced BCR solve units (push style). One BLOCK of NT threads handles one
+// (item, rhs, row slice) unit; a level's units spread over all blocks, and at the
+// upper levels (few items) an item's 2N rows are split into S in {1, 2, 4}
+// slices so that several SMs share one matrix-vector product. With S <= 4 every
+// slice boundary is a quadrant boundary (L-, L+, R-, R+ are N/2 rows each).
+//   forward (item i at level l, s = 2^l, or a root):
+//     y_i = A_i^{-1} r_i                                (rows of this slice) -> Y
+//     the slice holding y_i[R+] pushes  r_{i+s}[L+] -= B_{i+s} y_i[R+]
+//     the slice holding y_i[L-] pushes  r_{i-s}[R-] -= C_{i-s} y_i[L-]
+//   backward (item i at level l, descending; u of the kept neighbours is final):
+//     u_i = y_i - A_i^{-1}[:, L+] B_i u_{i-s}[R+] - A_i^{-1}[:, R-] C_i u_{i+s}[L-]
+// r_i is complete when item i's level runs (its pushes came from lower levels);
+// every pushed-to sub-vector has exactly one writer per level, so nothing races.
+// rhs and Y are written by other blocks between grid-wide barriers and are read
+// with L1-bypassing loads. The solution is left in Y.
 template <typename T>
-__global__ void k_bcr_fwd(const T *__restrict__ A, const T *__restrict__ Bc, const T *__restrict__ Cc,
-                          const BcrItem *__restrict__ items, T *__restrict__ rhs, int N, int sumK) {
-    extern __shared__ unsigned char smem_raw[];
-    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
-    T *rs = reinterpret_cast<T *>(smem_raw);
-    T *ys = rs + n2;
-    const BcrItem it = items[blockIdx.x];
-    const int r = blockIdx.y;
-    T *ri = rhs + ((size_t)r * sumK + it.cell) * n2;
-    const T *Ai = A + (size_t)it.cell * n2 * n2;
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) rs[i] = ri[i];
-    __syncthreads();
-    for (int row = threadIdx.x; row < n2; row += blockDim.x) {
+struct VecOf;
+template <>
+struct VecOf<float> {
+    using type = float4;
+    static constexpr int V = 4;
+};
+template <>
+struct VecOf<double> {
+    using type = double2;
+    static constexpr int V = 2;
+};
+
+// shared scratch (values of T) of one solve block
+__host__ __device__ constexpr int bcr_unit_smem_values(int N, int NT, int V) { return 4 * N + NT * V + 2 * N; }
+
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// part[ks][row] = sum over the k of slice ks of Mt[col(k)][row0 + row] * coef[k],
+// rows [row0, row0 + nr), col(k) = col_off0 + k for k < col_split else col_off1 + k - col_split.
+// Returns the number of k-slices.
+template <typename T, int NT>
+__device__ __forceinline__ int sliced_matvec(const T *__restrict__ Mt, int n2, int row0, int nr, int nk,
+                                             int col_split, int col_off0, int col_off1, const T *coef, T *part) {
+    using VT = typename VecOf<T>::type;
+    constexpr int V = VecOf<T>::V;
+    const int RG = nr / V;
+    int KS = NT / RG;
+    if (KS > nk) KS = nk;
+    if (KS < 1) KS = 1;
+    const int kl = (nk + KS - 1) / KS;
+    for (int t = threadIdx.x; t < RG * KS; t += NT) {
+        const int rg = t % RG, ks = t / RG;
+        const int k0 = ks * kl, k1 = min(nk, k0 + kl);
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = T(0);
+#pragma unroll 16
+        for (int k = k0; k < k1; ++k) {
+            const int col = (k < col_split) ? col_off0 + k : col_off1 + (k - col_split);
+            const VT a = __ldg(reinterpret_cast<const VT *>(Mt + (size_t)col * n2 + row0) + rg);
+            const T c = coef[k];
+            if constexpr (V == 4) {
+                acc[0] = fma(a.x, c, acc[0]); acc[1] = fma(a.y, c, acc[1]);
+                acc[2] = fma(a.z, c, acc[2]); acc[3] = fma(a.w, c, acc[3]);
+            } else {
+                acc[0] = fma(a.x, c, acc[0]); acc[1] = fma(a.y, c, acc[1]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) part[ks * nr + rg * V + v] = acc[v];
+    }
+    return KS;
+}
+
+// Up to two h2 x h2 coupling products at once, all NT threads: rows (side, p) of
+// M_side (row-major), a group of G threads per row, each reading a contiguous
+// k-range; the group's partial sums meet by shuffles. Every matrix load of the
+// block is issued before any product is formed. out_side[p] = sum_k M_side[p][k] v_side[k].
+template <typename T, int NT>
+__device__ __forceinline__ void coupling_products(const T *__restrict__ M0, const T *v0, T *out0,
+                                                  const T *__restrict__ M1, const T *v1, T *out1, int h2) {
+    const int nrows = (M0 ? h2 : 0) + (M1 ? h2 : 0);
+    if (nrows == 0) return;
+    int G = 1;
+    while (G < 32 && G * 2 * nrows <= NT && G * 2 <= h2) G *= 2;
+    const int kl = (h2 + G - 1) / G;
+    for (int t = threadIdx.x; t < ((nrows * G + 31) & ~31); t += NT) {  // whole warps for the shuffles
+        const int row = t / G, gq = t % G;
+        const bool live = row < nrows;
+        const bool second = live && (!M0 || row >= h2);
+        const int p = second ? row - (M0 ? h2 : 0) : row;
+        const T *M = second ? M1 : M0;
+        const T *v = second ? v1 : v0;
         T acc = T(0);
-        for (int k = 0; k < n2; ++k) acc = fma(Ai[(size_t)k * n2 + row], rs[k], acc);
-        ys[row] = acc;
-        ri[row] = acc;
-    }
-    __syncthreads();
-    if (it.right >= 0) {
-        const T *Bj = Bc + (size_t)it.s_right * hh;
-        T *rj = rhs + ((size_t)r * sumK + it.right) * n2 + h2;  // L+
-        for (int p = threadIdx.x; p < h2; p += blockDim.x) {
-            T acc = T(0);
-            for (int k = 0; k < h2; ++k) acc = fma(Bj[p * h2 + k], ys[N + h2 + k], acc);
-            rj[p] -= acc;
+        if (live) {
+            const int k0 = gq * kl, k1 = min(h2, k0 + kl);
+#pragma unroll 8
+            for (int k = k0; k < k1; ++k) acc = fma(__ldg(M + (size_t)p * h2 + k), v[k], acc);
         }
-    }
-    if (it.left >= 0) {
-        const T *Cj = Cc + (size_t)it.s_left * hh;
-        T *rj = rhs + ((size_t)r * sumK + it.left) * n2 + N;  // R-
-        for (int p = threadIdx.x; p < h2; p += blockDim.x) {
-            T acc = T(0);
-            for (int k = 0; k < h2; ++k) acc = fma(Cj[p * h2 + k], ys[k], acc);
-            rj[p] -= acc;
-        }
+        acc = group_sum(acc, G);
+        if (live && gq == 0) (second ? out1 : out0)[p] = acc;
     }
 }
 
-template <typename T>
-__global__ void k_bcr_bwd(const T *__restrict__ A, const T *__restrict__ Bc, const T *__restrict__ Cc,
-                          const BcrItem *__restrict__ items, T *__restrict__ rhs, int N, int sumK) {
-    extern __shared__ unsigned char smem_raw[];
+template <typename T, int NT>
+__device__ __forceinline__ void bcr_fwd_unit(const T *__restrict__ A, const T *__restrict__ Bc,
+                                             const T *__restrict__ Cc, const BcrItem &it, int r, int sl, int S,
+                                             T *rhs, T *Y, int N, int sumK, T *sm) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
-    T *g1 = reinterpret_cast<T *>(smem_raw);
-    T *g2 = g1 + h2;
-    const BcrItem it = items[blockIdx.x];
-    const int r = blockIdx.y;
-    T *ri = rhs + ((size_t)r * sumK + it.cell) * n2;
+    T *rs = sm, *ys = sm + n2, *pr = sm + 2 * n2, *part = sm + 3 * n2;  // pr: pushed products (N)
+    const size_t rb = (size_t)r * sumK;
+    const T *ri = rhs + (rb + it.cell) * n2;
+    for (int i = threadIdx.x; i < n2; i += NT) rs[i] = __ldcg(ri + i);
+    __syncthreads();
+    const int nr = n2 / S, row0 = sl * nr;
     const T *Ai = A + (size_t)it.cell * n2 * n2;
-    const T *Bi = Bc + (size_t)it.s_cell * hh;
-    const T *Ci = Cc + (size_t)it.s_cell * hh;
-    const T *ul = rhs + ((size_t)r * sumK + it.left) * n2 + N + h2;  // u_left[R+]
-    for (int p = threadIdx.x; p < h2; p += blockDim.x) {
-        T acc = T(0);
-        for (int k = 0; k < h2; ++k) acc = fma(Bi[p * h2 + k], ul[k], acc);
-        g1[p] = acc;
-        T acc2 = T(0);
-        if (it.right >= 0) {
-            const T *ur = rhs + ((size_t)r * sumK + it.right) * n2;  // u_right[L-]
-            for (int k = 0; k < h2; ++k) acc2 = fma(Ci[p * h2 + k], ur[k], acc2);
-        }
-        g2[p] = acc2;
+    const int KS = sliced_matvec<T, NT>(Ai, n2, row0, nr, n2, n2, 0, 0, rs, part);
+    __syncthreads();
+    T *yi = Y + (rb + it.cell) * n2;
+    for (int row = threadIdx.x; row < nr; row += NT) {
+        T y = T(0);
+        for (int s = 0; s < KS; ++s) y += part[s * nr + row];
+        ys[row0 + row] = y;
+        yi[row0 + row] = y;
     }
     __syncthreads();
-    for (int row = threadIdx.x; row < n2; row += blockDim.x) {
-        T acc = ri[row];
-        for (int p = 0; p < h2; ++p) {
-            acc = fma(-Ai[(size_t)(h2 + p) * n2 + row], g1[p], acc);
-            acc = fma(-Ai[(size_t)(N + p) * n2 + row], g2[p], acc);
+    const bool push_right = it.right >= 0 && row0 + nr == n2;  // this slice holds R+
+    const bool push_left = it.left >= 0 && row0 == 0;          // this slice holds L-
+    coupling_products<T, NT>(push_right ? Bc + (size_t)it.s_right * hh : nullptr, ys + N + h2, pr,
+                             push_left ? Cc + (size_t)it.s_left * hh : nullptr, ys, pr + h2, h2);
+    __syncthreads();
+    for (int p = threadIdx.x; p < N; p += NT) {
+        if (p < h2 && push_right) {
+            T *rj = rhs + (rb + it.right) * n2 + h2 + p;  // L+
+            *rj = __ldcg(rj) - pr[p];
         }
-        ri[row] = acc;
+        if (p >= h2 && push_left) {
+            T *rj = rhs + (rb + it.left) * n2 + N + (p - h2);  // R-
+            *rj = __ldcg(rj) - pr[p];
+        }
+    }
+    __syncthreads();  // scratch reuse by the block's next unit
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void bcr_bwd_unit(const T *__restrict__ A, const T *__restrict__ Bc,
+                                             const T *__restrict__ Cc, const BcrItem &it, int r, int sl, int S,
+                                             T *Y, int N, int sumK, T *sm) {
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+    T *gv = sm, *g = sm + N, *part = sm + 2 * N;  // gv = [u_left[R+], u_right[L-]], g = [B_i gv0, C_i gv1]
+    const size_t rb = (size_t)r * sumK;
+    for (int idx = threadIdx.x; idx < N; idx += NT) {
+        T v = T(0);
+        if (idx < h2) v = __ldcg(Y + (rb + it.left) * n2 + N + h2 + idx);
+        else if (it.right >= 0) v = __ldcg(Y + (rb + it.right) * n2 + (idx - h2));
+        gv[idx] = v;
+    }
+    __syncthreads();
+    coupling_products<T, NT>(Bc + (size_t)it.s_cell * hh, gv, g, it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr,
+                             gv + h2, g + h2, h2);
+    if (it.right < 0)
+        for (int p = threadIdx.x; p < h2; p += NT) g[h2 + p] = T(0);
+    __syncthreads();
+    const int nr = n2 / S, row0 = sl * nr;
+    const T *Ai = A + (size_t)it.cell * n2 * n2;
+    const int KS = sliced_matvec<T, NT>(Ai, n2, row0, nr, N, h2, h2, N, g, part);
+    __syncthreads();
+    T *ui = Y + (rb + it.cell) * n2 + row0;
+    for (int row = threadIdx.x; row < nr; row += NT) {
+        T s = T(0);
+        for (int q = 0; q < KS; ++q) s += part[q * nr + row];
+        ui[row] = __ldcg(ui + row) - s;
+    }
+    __syncthreads();
+}
+
+// Item ranges of every reduction level in one concatenated item array:
+// level l owns items [off[l], off[l+1]); roots follow at [off[n_levels], off[n_levels] + n_roots).
+// slices[l] = row slices per item at level l (index n_levels: the roots).
+constexpr int kMaxLevels = 32;
+struct LevelTable {
+    int32_t off[kMaxLevels + 2];
+    int32_t slices[kMaxLevels + 2];
+    int32_t n_levels, n_roots;
+};
+
+// The whole BCR solve in one cooperative launch: forward levels, roots, backward
+// levels, separated by grid-wide barriers (all blocks are co-resident by the
+// cooperative launch, so every barrier completes). Blocks take
+// (item, rhs, slice) units block-stride within a level. Solution left in Y.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, const T *__restrict__ Bc,
+                                                       const T *__restrict__ Cc, const BcrItem *__restrict__ items,
+                                                       LevelTable lv, T *rhs, T *Y, int N, int sumK, int R) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    cg::grid_group grid = cg::this_grid();
+    for (int l = 0; l <= lv.n_levels; ++l) {  // level n_levels = the roots
+        const int base = lv.off[l], S = lv.slices[l];
+        const int nitems = (l < lv.n_levels) ? lv.off[l + 1] - base : lv.n_roots;
+        const int nw = nitems * R * S;
+        for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+            const int sl = w % S, rr = (w / S) % R, item = w / (S * R);
+            bcr_fwd_unit<T, NT>(A, Bc, Cc, items[base + item], rr, sl, S, rhs, Y, N, sumK, sm);
+        }
+        if (l < lv.n_levels) grid.sync();
+    }
+    for (int l = lv.n_levels - 1; l >= 0; --l) {
+        grid.sync();
+        const int base = lv.off[l], S = lv.slices[l];
+        const int nw = (lv.off[l + 1] - base) * R * S;
+        for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+            const int sl = w % S, rr = (w / S) % R, item = w / (S * R);
+            bcr_bwd_unit<T, NT>(A, Bc, Cc, items[base + item], rr, sl, S, Y, N, sumK, sm);
+        }
     }
 }
 
