@@ -21,12 +21,14 @@ anisotropic scattering using the Fokker-Planck equation" (arXiv:1907.13013):
   (Eqs. trop, fpop, fp-mpd-oper, wd-eq-oper).
 - ``iterations``  -- source iteration (Eq. trsi), FPSA predict / correct /
   iterate (Eqs. predict, correct, iterate) with the FP operator solved by sparse
-  LU as in Sec. 4, the direct solve of the discrete system, and the adjoint
-  (implicit differentiation of the converged fixed point).
+  LU as in Sec. 4, and the direct solve of the discrete system.
+- ``adjoint``     -- sensitivities of the exit current (or of a linear functional
+  of the flux moments) to every per-cell sigma_t and sigma_s,l, by implicit
+  differentiation of the discrete solution (sparse LU of A^T).
 
 Parity status of every function is stated in its docstring; every function here
 is pinned by at least one test in ``tests/test_oracle_*.py`` against a closed
 form, an invariant, a special case or brute force.
 """
 
-from . import quadrature, transport, iterations  # noqa: F401
+from . import quadrature, transport, iterations, adjoint  # noqa: F401
