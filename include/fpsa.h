@@ -151,6 +151,31 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s,
 int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *phi0,
                int32_t mem, fpsa_stats *stats);
 
+/* Sensitivities of an objective J of the converged solution with respect to every
+ * per-cell sigma_t and sigma_s,l, by implicit differentiation of the discrete
+ * fixed point (the paper has no adjoint; the system is Eq. trop in LD / S_N form,
+ * A psi = b with A = L_h - S_h). No iteration history is used: A^T lambda = dJ/dpsi
+ * is solved through the identity A^T = W Pi A Pi W^{-1} (W = diag(w_n) per node,
+ * Pi = ordinate reversal; the transposed upwind sweep of mu is the sweep of -mu and
+ * S, MPD and WFD are w-self-adjoint and reversal-symmetric), i.e. as the forward
+ * FPSA iteration A x = Pi W^{-1} dJ/dpsi with the same factors (reverse-direction
+ * sweeps and transposed FP corrections in the original ordinates), then
+ *   dJ/dsigma_t,g   = -sum_{a,b} m_ab sum_{l<N} (2l+1)/2 (-1)^l x_{l,a} phi_{l,b}
+ *   dJ/dsigma_s,l,g = +sum_{a,b} m_ab (2l+1)/2 (-1)^l x_{l,a} phi_{l,b}
+ * with m = (h_g/6)[[2,1],[1,2]], summed over right-hand sides.
+ * Requires the last fpsa_solve since fpsa_set_xs to have returned FPSA_OK
+ * (FPSA_ESTATE otherwise); its moments are kept by the context.
+ *   opts:        iteration settings of the adjoint solve (NULL: FPSA, tol 1e-12)
+ *   dJ_dphi:     NULL -> J = sum over rhs and instances of the right-boundary exit
+ *                current sum_{mu_n>0} w_n mu_n psi_n(z_1); else the vector-Jacobian
+ *                product with dJ_dphi [R][sumK][2][L+1]
+ *   dJ_dsigma_t: output [sumK]; dJ_dsigma_s: output [sumK][L+1]
+ *   J:           optional output [R][B], the exit currents of the forward solution
+ * All array pointers are of kind mem. Returns FPSA_ENOTCONV if the adjoint solve
+ * does not converge. */
+int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, double *dJ_dsigma_t,
+                 double *dJ_dsigma_s, double *J, int32_t mem, fpsa_stats *stats);
+
 /* Release every device buffer of the context (NULL is allowed). */
 void fpsa_destroy(fpsa_ctx *ctx);
 

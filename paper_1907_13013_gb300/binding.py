@@ -62,7 +62,7 @@ class FpsaProfile(ctypes.Structure):
 
 
 EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error",
-           "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc"]
+           "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc", "fpsa_adjoint"]
 NOALLOC_MAX_CELL_ANGLES = 131072
 
 _lib = None
@@ -93,6 +93,8 @@ def load():
     lib.fpsa_profile_enable.restype = ctypes.c_int
     lib.fpsa_profile_read.argtypes = [vp, ctypes.POINTER(FpsaProfile)]
     lib.fpsa_profile_read.restype = ctypes.c_int
+    lib.fpsa_adjoint.argtypes = [vp, ctypes.POINTER(FpsaOpts), dp, dp, dp, dp, i32, ctypes.POINTER(FpsaStats)]
+    lib.fpsa_adjoint.restype = ctypes.c_int
     lib.fpsa_sweep_noalloc.argtypes = [i32, i32, dp, dp, dp, dp, vp]
     lib.fpsa_sweep_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -183,6 +185,40 @@ class Context:
             out[...] = keep
         return out, st.as_dict()
 
+    def adjoint(self, dJ_dphi=None, method="fpsa", tol=1e-12, max_iterations=10000, out_sigma_t=None,
+                out_sigma_s=None, inner_iterations=0, check_every=1):
+        """Gradients of J with respect to sigma_t [sumK] and sigma_s [sumK][L+1] at the last
+        converged solve (fpsa_adjoint). dJ_dphi None: J = exit current through the right edge,
+        summed over instances and rhs; else the vector-Jacobian product with dJ_dphi
+        [R][sumK][2][L+1]. Returns (dJ_dsigma_t, dJ_dsigma_s, J [R][B] or None, stats)."""
+        dev = out_sigma_t is not None and not isinstance(out_sigma_t, np.ndarray)
+        if out_sigma_t is None:
+            out_sigma_t = np.zeros(self.sumK)
+        if out_sigma_s is None:
+            out_sigma_s = (np.zeros((self.sumK, self.L + 1)) if isinstance(out_sigma_t, np.ndarray)
+                           else out_sigma_t.new_zeros((self.sumK, self.L + 1)))
+        pt, mem, kt = _ptr(out_sigma_t)
+        ps, ms, ks = _ptr(out_sigma_s)
+        pg = None
+        if dJ_dphi is not None:
+            pg, mg, kg = _ptr(dJ_dphi)
+            if mg != mem:
+                raise TypeError("dJ_dphi and the outputs must be of the same memory kind")
+        J = None
+        pj = None
+        if mem == MEM_HOST:
+            J = np.zeros((self.R, self.B))
+            pj = J.ctypes.data
+        o = FpsaOpts(METHOD[method], int(max_iterations), float(tol), int(inner_iterations), 0.0, int(check_every))
+        st = FpsaStats()
+        rc = self._lib.fpsa_adjoint(self._h, ctypes.byref(o), pg, pt, ps, pj, mem, ctypes.byref(st))
+        self._check(rc, "fpsa_adjoint")
+        if isinstance(out_sigma_t, np.ndarray) and kt is not out_sigma_t:
+            out_sigma_t[...] = kt
+        if isinstance(out_sigma_s, np.ndarray) and ks is not out_sigma_s:
+            out_sigma_s[...] = ks
+        return out_sigma_t, out_sigma_s, (J if dJ_dphi is None else None), st.as_dict()
+
     def profile_enable(self, on=True):
         """Reset the launch counters; with on, bracket every launch with CUDA events."""
         self._check(self._lib.fpsa_profile_enable(self._h, 1 if on else 0), "fpsa_profile_enable")
@@ -236,3 +272,56 @@ def context_for(problems, n_rhs=None, **kw):
     ctx = Context(K, h, N, L, n_rhs=R, **kw)
     ctx.set_xs(st, ss, q)
     return ctx
+
+
+class FPSASolve:
+    """torch.autograd.Function wrapper: phi = solve(sigma_t, sigma_s, q) on a Context, with
+    backward = fpsa_adjoint (implicit differentiation of the converged fixed point; no
+    iteration history is stored). Inputs are contiguous float64 CUDA tensors:
+    sigma_t [sumK], sigma_s [sumK][L+1], q [R][sumK][2][L+1]; returns phi [R][sumK][2][L+1].
+    Gradients flow to sigma_t and sigma_s (q is treated as a constant)."""
+
+    _fn = None
+
+    @classmethod
+    def function(cls):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(actx, fctx, sigma_t, sigma_s, q, tol, max_iterations):
+                    fctx.set_xs(sigma_t.detach(), sigma_s.detach(), q.detach())
+                    phi = torch.empty((fctx.R, fctx.sumK, 2, fctx.L + 1), dtype=torch.float64, device=sigma_t.device)
+                    fctx.solve("fpsa", tol=tol, max_iterations=max_iterations, out=phi)
+                    fctx._generation = getattr(fctx, "_generation", 0) + 1
+                    actx.fctx = fctx
+                    actx.gen = fctx._generation
+                    actx.tol, actx.max_iterations = tol, max_iterations
+                    actx.save_for_backward(sigma_t.detach(), sigma_s.detach(), q.detach())
+                    return phi
+
+                @staticmethod
+                def backward(actx, grad_phi):
+                    fctx = actx.fctx
+                    sigma_t, sigma_s, q = actx.saved_tensors
+                    if getattr(fctx, "_generation", 0) != actx.gen:
+                        # the context has solved something else since: restore this forward state
+                        fctx.set_xs(sigma_t, sigma_s, q)
+                        fctx.solve("fpsa", tol=actx.tol, max_iterations=actx.max_iterations,
+                                   out=torch.empty((fctx.R, fctx.sumK, 2, fctx.L + 1), dtype=torch.float64,
+                                                   device=sigma_t.device))
+                        fctx._generation += 1
+                        actx.gen = fctx._generation
+                    d_st = torch.empty_like(sigma_t)
+                    d_ss = torch.empty_like(sigma_s)
+                    fctx.adjoint(dJ_dphi=grad_phi.contiguous(), tol=min(actx.tol, 1e-12), out_sigma_t=d_st,
+                                 out_sigma_s=d_ss)
+                    return None, d_st, d_ss, None, None, None
+
+            cls._fn = _F
+        return cls._fn
+
+    @classmethod
+    def apply(cls, fctx, sigma_t, sigma_s, q, tol=1e-12, max_iterations=10000):
+        return cls.function().apply(fctx, sigma_t, sigma_s, q, tol, max_iterations)

@@ -64,6 +64,12 @@ struct fpsa_ctx {
     double *d_result = nullptr;
     double *h_result = nullptr;  // pinned
 
+    // adjoint
+    bool fwd_ready = false;      // d_phi_fwd holds the last converged forward moments
+    double *d_phi_fwd = nullptr, *d_adj_src = nullptr, *d_gphi = nullptr;  // [R][sumK][2][N]
+    double *d_Pm = nullptr, *d_cJ = nullptr;                              // (-1)^l P_l(mu_n), exit-current weights
+    double *d_J = nullptr, *d_grad_t = nullptr, *d_grad_s = nullptr;
+
     PathBuffers<double> p64;  // FP64 path; for MIXED: FP64 tables, psi (refined iterate), phi
     PathBuffers<float> p32;   // MIXED: the FP32 inner FPSA solve
 
@@ -283,8 +289,10 @@ int check_xs(fpsa_ctx *ctx, const double *st, const double *ss, const double *q)
 }
 
 template <typename T>
+// Qm: source moments (may be NULL), Qa: nodal angular source (may be NULL).
+// phi_out may be NULL (the iterate stays in p.phi).
 int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const double *phi0, int mem, double *phi_out,
-               fpsa_stats &stats) {
+               fpsa_stats &stats, const T *Qm, const T *Qa) {
     const Geometry &g = ctx->geo;
     const int N = g.N, L1 = g.L1;
     cudaStream_t st = ctx->stream;
@@ -304,7 +312,7 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
     CK(cudaMemsetAsync(ctx->d_conv, 0, (size_t)g.R * g.B * 2 * sizeof(unsigned long long), st));
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_scatter<T><<<cgrid, kContractThreads, csm / 2, st>>>(p.phi, p.sigma_s, p.Q, p.MT, p.q, N, g.sumK);
+        k_scatter<T><<<cgrid, kContractThreads, csm / 2, st>>>(p.phi, p.sigma_s, Qm, p.MT, p.q, N, g.sumK, Qa);
     }
     CK(cudaGetLastError());
     const int every = o.check_every > 0 ? o.check_every : 1;
@@ -327,16 +335,16 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
             if (rc) return rc;
             {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.ybuf, p.phi_half, p.phi, p.sigma_s, p.Q, p.DT,
+                k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.ybuf, p.phi_half, p.phi, p.sigma_s, Qm, p.DT,
                                                                            p.MT, p.q, ctx->d_cell_inst, g.B, ctx->d_conv,
-                                                                           N, g.sumK);
+                                                                           N, g.sumK, Qa);
             }
         } else {
             {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
                 k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const T *)nullptr, p.phi, p.sigma_s,
-                                                                           p.Q, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
-                                                                           ctx->d_conv, N, g.sumK);
+                                                                           Qm, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
+                                                                           ctx->d_conv, N, g.sumK, Qa);
             }
         }
         CK(cudaGetLastError());
@@ -363,8 +371,9 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
     stats.outer_iterations = it;
     stats.sweeps = it;
     stats.rel_change = e;
-    CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(T), L1 * sizeof(double), ncol,
-                         mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    if (phi_out)
+        CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(T), L1 * sizeof(double), ncol,
+                             mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     if (status == FPSA_ENOTCONV)
         fail(ctx, FPSA_ENOTCONV, "not converged after " + std::to_string(o.max_iterations) + " iterations");
@@ -377,7 +386,8 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
 //   inner:    `inner` FPSA iterations (Eqs. predict, correct) on L dpsi = S dpsi + dq
 //             from dpsi = 0, all in FP32: sweep, contractions, BCR solve
 //   update:   psi64 += psi_half + upsilon of the last inner iteration (FP64)
-int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats) {
+int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats,
+                const double *Qm, const double *Qa) {
     const Geometry &g = ctx->geo;
     const int N = g.N, L1 = g.L1;
     cudaStream_t st = ctx->stream;
@@ -406,8 +416,8 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         {
             Launch L_(ctx, FPSA_PHASE_RESIDUAL);
             k_mixed_residual<<<cgrid, kContractThreads, contract_smem<double>(N), st>>>(
-                p.psi, p.phi, p.sigma_s, p.Q, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst,
-                ctx->d_off, ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK);
+                p.psi, p.phi, p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst,
+                ctx->d_off, ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa);
         }
         {
             Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
@@ -470,8 +480,9 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     stats.outer_iterations = std::min(outer, o.max_iterations + 1);
     stats.sweeps = sweeps;
     stats.rel_change = e;
-    CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(double), L1 * sizeof(double), ncol,
-                         mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    if (phi_out)
+        CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(double), L1 * sizeof(double), ncol,
+                             mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     if (status == FPSA_ENOTCONV)
         fail(ctx, FPSA_ENOTCONV, "not converged after " + std::to_string(o.max_iterations) + " refinement steps");
@@ -574,6 +585,27 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         CK(dalloc(ctx, &ctx->d_roots, g.B));
         CK(cudaMemcpy(ctx->d_roots, g.roots.data(), g.B * sizeof(BcrItem), cudaMemcpyHostToDevice));
         {
+            const size_t nang = (size_t)g.R * g.sumK * 2 * g.N;
+            CK(dalloc(ctx, &ctx->d_phi_fwd, nang));
+            CK(dalloc(ctx, &ctx->d_adj_src, nang));
+            CK(dalloc(ctx, &ctx->d_gphi, nang));
+            CK(dalloc(ctx, &ctx->d_Pm, (size_t)g.N * g.N));
+            CK(dalloc(ctx, &ctx->d_cJ, g.N));
+            CK(dalloc(ctx, &ctx->d_J, (size_t)g.R * g.B));
+            CK(dalloc(ctx, &ctx->d_grad_t, g.sumK));
+            CK(dalloc(ctx, &ctx->d_grad_s, (size_t)g.sumK * g.L1));
+            // P_l(mu_n) = D[l][n] / w_n
+            std::vector<double> Pm((size_t)g.N * g.N), cJ(g.N, 0.0);
+            for (int n = 0; n < g.N; ++n)
+                for (int l = 0; l < g.N; ++l) {
+                    const double P = ctx->tab.D[(size_t)l * g.N + n] / ctx->tab.w[n];
+                    Pm[(size_t)n * g.N + l] = (l & 1) ? -P : P;
+                    if (ctx->tab.mu[n] > 0.0) cJ[l] += ctx->tab.w[n] * ctx->tab.mu[n] * (l + 0.5) * P;
+                }
+            CK(cudaMemcpy(ctx->d_Pm, Pm.data(), Pm.size() * sizeof(double), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(ctx->d_cJ, cJ.data(), cJ.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        {
             std::vector<BcrItem> all;
             for (int l = 0; l < g.n_levels; ++l) all.insert(all.end(), g.levels[l].begin(), g.levels[l].end());
             all.insert(all.end(), g.roots.begin(), g.roots.end());
@@ -637,6 +669,7 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     CK(cudaMemcpy(ss.data(), sigma_s, nss * sizeof(double), k));
     CK(cudaMemcpy(qm.data(), q, nq * sizeof(double), k));
     ctx->xs_ready = false;
+    ctx->fwd_ready = false;
     int rc = check_xs(ctx, st.data(), ss.data(), qm.data());
     if (rc) return rc;
     std::vector<double> s0(g.sumK), s1(g.sumK);
@@ -711,8 +744,17 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
     CK(cudaSetDevice(ctx->device));
     fpsa_stats s{};
     const auto t0 = std::chrono::steady_clock::now();
-    int rc = ctx->precision == FPSA_PRECISION_FP64 ? solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s)
-                                                   : solve_mixed(ctx, o, phi0, mem, phi, s);
+    ctx->fwd_ready = false;
+    int rc = ctx->precision == FPSA_PRECISION_FP64
+                 ? solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s, (const double *)ctx->p64.Q, (const double *)nullptr)
+                 : solve_mixed(ctx, o, phi0, mem, phi, s, ctx->p64.Q, nullptr);
+    if (rc == FPSA_OK) {
+        // keep the converged moments (all N) for fpsa_adjoint
+        const size_t nang = (size_t)ctx->geo.R * ctx->geo.sumK * 2 * ctx->geo.N;
+        CK(cudaMemcpyAsync(ctx->d_phi_fwd, ctx->p64.phi, nang * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->fwd_ready = true;
+    }
     s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     s.status = rc;
     s.setup_ms = ctx->setup_ms;
@@ -720,6 +762,67 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
     s.cell_angles = (double)ctx->geo.sumK * ctx->geo.N * ctx->geo.R * s.sweeps;
     if (stats) *stats = s;
     return rc;
+}
+
+int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, double *dJ_dsigma_t,
+                 double *dJ_dsigma_s, double *J, int32_t mem, fpsa_stats *stats) {
+    if (!ctx) return FPSA_EINVAL;
+    if (!dJ_dsigma_t || !dJ_dsigma_s) return fail(ctx, FPSA_EINVAL, "null gradient output");
+    if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
+    if (!ctx->fwd_ready) return fail(ctx, FPSA_ESTATE, "fpsa_adjoint needs a converged fpsa_solve since the last fpsa_set_xs");
+    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-12, 0, 0.0, 1};
+    if (opts) o = *opts;
+    if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA) return fail(ctx, FPSA_EINVAL, "bad method");
+    if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol");
+    CK(cudaSetDevice(ctx->device));
+    const Geometry &g = ctx->geo;
+    const int N = g.N, L1 = g.L1;
+    const size_t ncol = (size_t)g.R * g.sumK * 2, nang = ncol * N;
+    cudaStream_t st = ctx->stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    const cudaMemcpyKind h2d = mem == FPSA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind d2h = mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (dJ_dphi) {
+        CK(cudaMemsetAsync(ctx->d_gphi, 0, nang * sizeof(double), st));
+        CK(cudaMemcpy2DAsync(ctx->d_gphi, N * sizeof(double), dJ_dphi, L1 * sizeof(double), L1 * sizeof(double), ncol,
+                             h2d, st));
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+        k_adjoint_source<<<4 * 152, 256, 0, st>>>(dJ_dphi ? ctx->d_gphi : nullptr, ctx->d_Pm, ctx->d_mu, ctx->d_h,
+                                                  ctx->d_cell_inst, ctx->d_off, ctx->d_K, N, g.sumK, g.R,
+                                                  ctx->d_adj_src);
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+        k_exit_current<<<dim3(g.B, g.R), 32, 0, st>>>(ctx->d_phi_fwd, ctx->d_cJ, ctx->d_off, ctx->d_K, N, g.sumK, g.B,
+                                                       ctx->d_J);
+    }
+    CK(cudaGetLastError());
+    fpsa_stats s{};
+    // A x = Pi W^{-1} dJ/dpsi with the forward machinery and factors
+    int rc = ctx->precision == FPSA_PRECISION_FP64
+                 ? solve_fp64(ctx, ctx->p64, o, nullptr, mem, nullptr, s, (const double *)nullptr,
+                              (const double *)ctx->d_adj_src)
+                 : solve_mixed(ctx, o, nullptr, mem, nullptr, s, nullptr, ctx->d_adj_src);
+    if (rc != FPSA_OK) return rc;
+    {
+        Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+        k_adjoint_grad<<<g.sumK, 128, 0, st>>>(ctx->d_phi_fwd, ctx->p64.phi, ctx->d_h, N, L1, g.sumK, g.R,
+                                               ctx->d_grad_t, ctx->d_grad_s);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dJ_dsigma_t, ctx->d_grad_t, g.sumK * sizeof(double), d2h, st));
+    CK(cudaMemcpyAsync(dJ_dsigma_s, ctx->d_grad_s, (size_t)g.sumK * L1 * sizeof(double), d2h, st));
+    if (J) CK(cudaMemcpyAsync(J, ctx->d_J, (size_t)g.R * g.B * sizeof(double), d2h, st));
+    CK(cudaStreamSynchronize(st));
+    s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    s.status = rc;
+    s.setup_ms = ctx->setup_ms;
+    s.pivot_growth = ctx->pivot_growth;
+    s.cell_angles = (double)g.sumK * g.N * g.R * s.sweeps;
+    if (stats) *stats = s;
+    return FPSA_OK;
 }
 
 }  // extern "C"

@@ -283,7 +283,8 @@ __global__ void k_update_scatter(const T *__restrict__ v, const T *__restrict__ 
 // LD form), in the nodal form the sweep consumes, per cell and ordinate:
 //   dq = s - sigma_t psi - m^{-1} (G(mu) psi - |mu| psi_in e_up),
 //   s  = M (Sigma phi + Q),  phi = D psi,
-// so that the correction equation is L dpsi = S dpsi + dq with vacuum inflow.
+// so that the correction equation is L dpsi = S dpsi + dq with vacuum inflow
+// (the source is q = M Q + q_ang; either part may be NULL).
 // Also: phi (FP64) is stored and its l = 0 change against the previous outer
 // iterate is max-reduced into conv (Eq. iterate on the refined iterates).
 // ---------------------------------------------------------------------------
@@ -293,7 +294,8 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
                                  const double *__restrict__ sigma_t, const double *__restrict__ h,
                                  const double *__restrict__ mu, const int32_t *__restrict__ cell_inst,
                                  const int32_t *__restrict__ off, const int32_t *__restrict__ Kc, int B,
-                                 unsigned long long *__restrict__ conv, float *__restrict__ dq, int N, int sumK) {
+                                 unsigned long long *__restrict__ conv, float *__restrict__ dq, int N, int sumK,
+                                 const double *__restrict__ Qang) {
     extern __shared__ unsigned char smem_raw[];
     double *Xs = reinterpret_cast<double *>(smem_raw);
     double *Ys = Xs + 2 * kContractCells * N;
@@ -318,10 +320,10 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
             atomicMax(conv + slot + 1, dkey(pn));
         }
         phi[e] = pn;
-        Xs[idx] = sigma_s[(size_t)g * N + l] * pn + Qext[e];
+        Xs[idx] = sigma_s[(size_t)g * N + l] * pn + (Qext ? Qext[e] : 0.0);
     }
     __syncthreads();
-    block_contract(Xs, N, MT, N, ncols, Ys, N);
+    block_contract(Xs, N, MT, N, ncols, Ys, N, Qang ? Qang + colbase * N : nullptr);
     __syncthreads();
     for (int idx = threadIdx.x; idx < ncell * N; idx += blockDim.x) {
         const int cl = idx / N, n = idx - cl * N;
@@ -966,6 +968,98 @@ __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, 
             const int sl = w % S, rr = (w / S) % R, item = w / (S * R);
             bcr_bwd_unit<T, NT>(A, Bc, Cc, items[base + item], rr, sl, S, Y, N, sumK, sm);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint (implicit differentiation of the converged discrete solution; the
+// paper has no adjoint). The LD / S_N matrix A = L_h - S_h satisfies
+// A^T = W Pi A Pi W^{-1} (W = diag(w_n) per node, Pi reverses the ordinates:
+// the transposed upwind streaming of mu is the streaming of -mu, and S, the MPD
+// and the WFD operators are w-self-adjoint and reversal-symmetric), so
+// A^T lambda = s is solved as the forward system A x = Pi W^{-1} s with the
+// same FPSA iteration and factors, lambda = W Pi x.
+// Mirrored adjoint source as a nodal source of the sweep (b = m (x) q):
+//   exit current (g == NULL): s_{K,R,n} = w_n mu_n for mu_n > 0, so
+//     (Pi W^{-1} s) is |mu_n| at the last cell's right node for mu_n < 0;
+//   moment functional <g, phi>: s = D^T g, so
+//     (Pi W^{-1} s)_{a,n} = sum_l (-1)^l P_l(mu_n) g_{a,l}.
+// q = m^{-1} (Pi W^{-1} s) per cell, m^{-1} = (2/h)[[2,-1],[-1,2]].
+// Pm[n][l] = (-1)^l P_l(mu_n).
+// ---------------------------------------------------------------------------
+static __global__ void k_adjoint_source(const double *__restrict__ g, const double *__restrict__ Pm,
+                                        const double *__restrict__ mu, const double *__restrict__ h,
+                                        const int32_t *__restrict__ cell_inst, const int32_t *__restrict__ off,
+                                        const int32_t *__restrict__ Kc, int N, int sumK, int R,
+                                        double *__restrict__ q) {
+    const size_t tot = (size_t)R * sumK * N;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
+        const int n = (int)(idx % N);
+        const size_t rg = idx / N;  // r * sumK + cell
+        const int cell = (int)(rg % sumK);
+        double sL = 0.0, sR = 0.0;
+        if (g) {
+            const double *gL = g + (rg * 2) * N, *gR = gL + N;
+            for (int l = 0; l < N; ++l) {
+                const double p = Pm[(size_t)n * N + l];
+                sL = fma(p, gL[l], sL);
+                sR = fma(p, gR[l], sR);
+            }
+        } else {
+            const int b = cell_inst[cell];
+            if (cell == off[b] + Kc[b] - 1 && mu[n] < 0.0) sR = -mu[n];
+        }
+        const double w = 2.0 / h[cell];
+        q[(rg * 2) * N + n] = w * (2.0 * sL - sR);
+        q[(rg * 2 + 1) * N + n] = w * (2.0 * sR - sL);
+    }
+}
+
+// Right-boundary exit current per (rhs, instance) from the forward moments:
+// J = sum_{mu_n > 0} w_n mu_n psi_{K,R,n} = sum_l cJ[l] phi_{K,R,l}, cJ[l] =
+// sum_{mu_n > 0} w_n mu_n (2l+1)/2 P_l(mu_n) (psi = M phi with all N moments).
+static __global__ void k_exit_current(const double *__restrict__ phi, const double *__restrict__ cJ,
+                                      const int32_t *__restrict__ off, const int32_t *__restrict__ Kc, int N,
+                                      int sumK, int B, double *__restrict__ J) {
+    const int b = blockIdx.x, r = blockIdx.y;
+    const int cell = off[b] + Kc[b] - 1;
+    const double *p = phi + (((size_t)r * sumK + cell) * 2 + 1) * N;
+    double acc = 0.0;
+    for (int l = threadIdx.x; l < N; l += 32) acc = fma(cJ[l], p[l], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) J[(size_t)r * B + b] = acc;
+}
+
+// Gradients from the forward moments phi and the mirrored adjoint moments x
+// (both with all N moments), summed over right-hand sides:
+//   t_l = (h/6) sum_r (2 x_L phi_L + x_L phi_R + x_R phi_L + 2 x_R phi_R)_l (2l+1)/2 (-1)^l
+//   dJ/dsigma_s,l = t_l (l < L+1),   dJ/dsigma_t = -sum_{l<N} t_l
+static __global__ void k_adjoint_grad(const double *__restrict__ phi, const double *__restrict__ x,
+                                      const double *__restrict__ h, int N, int L1, int sumK, int R,
+                                      double *__restrict__ d_st, double *__restrict__ d_ss) {
+    __shared__ double red[32];
+    const int g = blockIdx.x;
+    double tsum = 0.0;
+    for (int l = threadIdx.x; l < N; l += blockDim.x) {
+        double t = 0.0;
+        for (int r = 0; r < R; ++r) {
+            const size_t e = (((size_t)r * sumK + g) * 2) * N + l;
+            const double xL = x[e], xR = x[e + N], pL = phi[e], pR = phi[e + N];
+            t += 2.0 * xL * pL + xL * pR + xR * pL + 2.0 * xR * pR;
+        }
+        t *= h[g] / 6.0 * (l + 0.5) * ((l & 1) ? -1.0 : 1.0);
+        if (l < L1) d_ss[(size_t)g * L1 + l] = t;
+        tsum += t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        d_st[g] = -s;
     }
 }
 

@@ -212,3 +212,84 @@ def test_mixed_full_size_against_golden(binding, name, factory, lap):
     phi, st = ctx.solve("fpsa", tol=1e-10, max_iterations=50)
     err = np.abs(phi[0, :, :, 0].ravel() - ref).max() / np.abs(ref).max()
     assert err < TOL, (err, st)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint: gradients of the exit current / of a moment functional with respect to
+# every per-cell sigma_t and sigma_s,l, against the oracle adjoint (sparse LU of A^T).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("objective", ["exit", "vjp"])
+@pytest.mark.parametrize("N,K,seed,kernel", [(8, 13, 1, "srk"), (16, 40, 2, "hg"), (64, 60, 3, "srk")])
+def test_adjoint_against_oracle(binding, precision, objective, N, K, seed, kernel):
+    from oracle import adjoint as oadj
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel=kernel, thick=(1, 200), c=(0.6, 0.99))
+    g = np.random.default_rng(seed).standard_normal((K, 2, N)) if objective == "vjp" else None
+    J, d_st, d_ss, _, _ = oadj.gradients(p, g)
+    ctx = binding.context_for(p, precision=precision)
+    ctx.solve("fpsa", tol=1e-13, max_iterations=500)
+    gt, gs, Jg, st = ctx.adjoint(dJ_dphi=None if g is None else g[None], tol=1e-13)
+    if g is None:
+        assert abs(Jg[0, 0] - J) < 1e-10 * abs(J)
+    assert np.abs(gt - d_st).max() < 1e-8 * np.abs(d_st).max()
+    assert np.abs(gs - d_ss).max() < 1e-8 * np.abs(d_ss).max()
+
+
+def test_adjoint_central_differences_and_batch(binding):
+    # two instances x two rhs: gradients are summed over rhs, instances are independent
+    R = 2
+    probs = [inputs.random_slab(K, 16, 15, seed=50 + i, kernel="srk", thick=(2, 100), c=(0.8, 0.99), nrhs=R)
+             for i, K in enumerate([30, 17])]
+    ctx = binding.context_for(probs)
+    ctx.solve("fpsa", tol=1e-13)
+    gt, gs, J, _ = ctx.adjoint(tol=1e-13)
+    st = np.concatenate([p["sigma_t"] for p in probs])
+    ss = np.concatenate([p["sigma_s"] for p in probs])
+    q = np.concatenate([p["Q"] for p in probs], axis=1)
+
+    def Jtot(st_, ss_):
+        ctx.set_xs(st_, ss_, q)
+        ctx.solve("fpsa", tol=1e-14, max_iterations=2000)
+        return ctx.adjoint(tol=1e-6)[2].sum()
+
+    assert J.shape == (R, 2)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(st.size, 5, replace=False):
+        d = 1e-6 * st[i]
+        a = st.copy(); a[i] += d
+        b = st.copy(); b[i] -= d
+        fd = (Jtot(a, ss) - Jtot(b, ss)) / (2 * d)
+        assert abs(fd - gt[i]) < 1e-4 * np.abs(gt).max()
+        l = int(rng.integers(0, 16))
+        d = 1e-6 * max(abs(ss[i, l]), 1e-2)
+        a = ss.copy(); a[i, l] += d
+        b = ss.copy(); b[i, l] -= d
+        fd = (Jtot(st, a) - Jtot(st, b)) / (2 * d)
+        assert abs(fd - gs[i, l]) < 1e-4 * np.abs(gs).max()
+
+
+def test_autograd_function(binding):
+    import torch
+    from oracle import adjoint as oadj
+    p = inputs.random_slab(25, 16, 15, seed=77, kernel="hg", thick=(1, 50), c=(0.7, 0.98))
+    dev = torch.device("cuda:0")
+    ctx = binding.Context([25], p["h"], 16, 15)
+    st = torch.tensor(p["sigma_t"], device=dev, requires_grad=True)
+    ss = torch.tensor(p["sigma_s"], device=dev, requires_grad=True)
+    q = torch.tensor(p["Q"][None], device=dev)
+    w = torch.tensor(np.random.default_rng(3).standard_normal((1, 25, 2, 16)), device=dev)
+    phi = binding.FPSASolve.apply(ctx, st, ss, q, 1e-13)
+    loss = (phi * w).sum()
+    loss.backward()
+    J, d_st, d_ss, _, _ = oadj.gradients(p, w[0].cpu().numpy())
+    assert abs(loss.item() - J) < 1e-9 * abs(J)
+    assert np.abs(st.grad.cpu().numpy() - d_st).max() < 1e-8 * np.abs(d_st).max()
+    assert np.abs(ss.grad.cpu().numpy() - d_ss).max() < 1e-8 * np.abs(d_ss).max()
+
+
+def test_adjoint_requires_forward(binding):
+    p = inputs.random_slab(10, 8, 7, seed=9)
+    ctx = binding.context_for(p)
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.adjoint()
+    assert e.value.code == binding.ESTATE
