@@ -85,6 +85,9 @@ typedef struct {
     int32_t inner_iterations; /* MIXED: FP32 FPSA iterations per FP64 refinement step (0 = default 6) */
     double inner_tol;         /* MIXED: inner relative-change target (0 = default 1e-5) */
     int32_t check_every;      /* test convergence every this many iterations (0 = 1) */
+    int32_t contraction;      /* MIXED inner contractions: 0 = auto (tensor cores when N is a
+                                 multiple of 16 and <= 128), 1 = SIMT FP32, 2 = tensor cores
+                                 (tcgen05, split BF16 x3; FPSA_ENOTSUP if N does not qualify) */
 } fpsa_opts;
 
 typedef struct {

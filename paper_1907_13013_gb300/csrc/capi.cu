@@ -17,6 +17,7 @@
 
 #include "fpsa_internal.h"
 #include "kernels.cuh"
+#include "tc_contract.cuh"
 
 using namespace fpsa;
 
@@ -72,6 +73,11 @@ struct fpsa_ctx {
 
     PathBuffers<double> p64;  // FP64 path; for MIXED: FP64 tables, psi (refined iterate), phi
     PathBuffers<float> p32;   // MIXED: the FP32 inner FPSA solve
+    // tensor-core contractions of the FP32 inner solve
+    bool tc_able = false;               // N multiple of 16, 16 <= N <= 128
+    unsigned char *d_tc_ops = nullptr;  // D_hi, D_lo, M_hi, M_lo (BF16, core-matrix layout)
+    int *d_tc_err = nullptr, *h_flag = nullptr;
+    int tc_grid = 0;
 
     // built-in profiler: launch counters (always) and event pairs (when on)
     bool prof_on = false;
@@ -181,6 +187,41 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     CK(cudaMemcpy(p.MT, MT.data(), N * N * sizeof(T), cudaMemcpyHostToDevice));
     CK(cudaFuncSetAttribute(k_bcr_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)invert_smem<T>(g.N)));
+    return FPSA_OK;
+}
+
+// Tensor-core operands of the FP32 inner contractions: D and M (as FP32 values)
+// split into BF16 hi / lo, stored as the B operands of Out = X Op^T in the
+// K-major core-matrix layout (Op_D[l][n] = D[l][n], Op_M[n][l] = M[n][l]).
+int setup_tc(fpsa_ctx *ctx) {
+    const int N = ctx->geo.N;
+    CK(dalloc(ctx, &ctx->d_tc_err, 1));
+    CK(cudaMallocHost(&ctx->h_flag, sizeof(int)));
+    CK(cudaMemset(ctx->d_tc_err, 0, sizeof(int)));
+    ctx->tc_able = (N % 16 == 0) && N >= 16 && N <= 128;
+    if (!ctx->tc_able) return FPSA_OK;
+    const size_t nn = (size_t)N * N;
+    std::vector<__nv_bfloat16> ops(4 * nn);
+    for (int o = 0; o < N; ++o)
+        for (int k = 0; k < N; ++k) {
+            const size_t off = tc::kmajor_offset(o, k, N) / 2;
+            const float d = (float)ctx->tab.D[(size_t)o * N + k];
+            const float m = (float)ctx->tab.M[(size_t)o * N + k];
+            const __nv_bfloat16 dh = __float2bfloat16_rn(d), mh = __float2bfloat16_rn(m);
+            ops[off] = dh;
+            ops[nn + off] = __float2bfloat16_rn(d - __bfloat162float(dh));
+            ops[2 * nn + off] = mh;
+            ops[3 * nn + off] = __float2bfloat16_rn(m - __bfloat162float(mh));
+        }
+    CK(dalloc(ctx, &ctx->d_tc_ops, 4 * nn * sizeof(__nv_bfloat16)));
+    CK(cudaMemcpy(ctx->d_tc_ops, ops.data(), ops.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+    const int smem = (int)tc::Plan::make(N).total;
+    CK(cudaFuncSetAttribute(k_tc_fp_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_tc_update_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int nsm = 0, per_sm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_update_scatter, 128, smem));
+    ctx->tc_grid = std::max(1, std::min(per_sm, 2)) * nsm;
     return FPSA_OK;
 }
 
@@ -398,6 +439,14 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     const dim3 sgrid(N, g.B, g.R);
     const int inner = o.inner_iterations > 0 ? o.inner_iterations : 6;
     const bool fpsa = o.method == FPSA_METHOD_FPSA;
+    if (o.contraction == 2 && !ctx->tc_able)
+        return fail(ctx, FPSA_ENOTSUP, "tensor-core contractions need N a multiple of 16 and <= 128");
+    const bool use_tc = ctx->tc_able && o.contraction != 1;
+    const TcOps tcops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
+    const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
+    const int tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
+    const size_t tc_smem = tc::Plan::make(N).total;
+    if (use_tc) CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
 
     CK(cudaMemsetAsync(p.phi, 0, nang * sizeof(double), st));
     if (phi0) {
@@ -425,8 +474,13 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (use_tc) CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         e = ctx->h_result[0];
+        if (use_tc && *ctx->h_flag) {
+            status = fail(ctx, FPSA_ETIMEOUT, "a tensor-core contraction wait ran out");
+            break;
+        }
         if (std::isnan(e)) {
             status = fail(ctx, FPSA_ENONFINITE, "non-finite iterate at refinement step " + std::to_string(outer));
             break;
@@ -450,8 +504,12 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             if (fpsa) {
                 {
                     Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                    k_fp_rhs<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
-                        f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h, f.DT, f.MT, f.rhs, N, g.sumK);
+                    if (use_tc)
+                        k_tc_fp_rhs<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h,
+                                                                     tcops, f.rhs, N, g.sumK, g.R, ctx->d_tc_err);
+                    else
+                        k_fp_rhs<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
+                            f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h, f.DT, f.MT, f.rhs, N, g.sumK);
                 }
                 int rc = bcr_solve(ctx, f, f.rhs);
                 if (rc) return rc;
@@ -460,9 +518,13 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             }
             if (j < inner) {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                k_update_scatter<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
-                    vin, base, f.phi, f.sigma_s, (const float *)nullptr, f.DT, f.MT, f.q, ctx->d_cell_inst, g.B,
-                    (unsigned long long *)nullptr, N, g.sumK, f.qang);
+                if (use_tc)
+                    k_tc_update_scatter<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops, f.q,
+                                                                         f.qang, N, g.sumK, g.R, ctx->d_tc_err);
+                else
+                    k_update_scatter<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
+                        vin, base, f.phi, f.sigma_s, (const float *)nullptr, f.DT, f.MT, f.q, ctx->d_cell_inst, g.B,
+                        (unsigned long long *)nullptr, N, g.sumK, f.qang);
             }
         }
         {
@@ -518,6 +580,7 @@ void fpsa_destroy(fpsa_ctx *ctx) {
     for (void *p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
+    if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
     delete ctx;
 }
 
@@ -648,7 +711,9 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         if (ctx->precision == FPSA_PRECISION_FP64) return alloc_path(ctx, ctx->p64, true);
         int r2 = alloc_path(ctx, ctx->p64, false);
         if (r2) return r2;
-        return alloc_path(ctx, ctx->p32, true);
+        r2 = alloc_path(ctx, ctx->p32, true);
+        if (r2) return r2;
+        return setup_tc(ctx);
     }();
     if (rc != FPSA_OK) return bail(rc);
     *out = ctx;
@@ -737,7 +802,7 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
     if (!phi) return fail(ctx, FPSA_EINVAL, "null phi");
     if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
     if (!ctx->xs_ready) return fail(ctx, FPSA_ESTATE, "fpsa_set_xs must succeed before fpsa_solve");
-    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-10, 0, 0.0, 1};
+    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-10, 0, 0.0, 1, 0};
     if (opts) o = *opts;
     if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA) return fail(ctx, FPSA_EINVAL, "bad method");
     if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol");
@@ -770,7 +835,7 @@ int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, do
     if (!dJ_dsigma_t || !dJ_dsigma_s) return fail(ctx, FPSA_EINVAL, "null gradient output");
     if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
     if (!ctx->fwd_ready) return fail(ctx, FPSA_ESTATE, "fpsa_adjoint needs a converged fpsa_solve since the last fpsa_set_xs");
-    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-12, 0, 0.0, 1};
+    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-12, 0, 0.0, 1, 0};
     if (opts) o = *opts;
     if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA) return fail(ctx, FPSA_EINVAL, "bad method");
     if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol");

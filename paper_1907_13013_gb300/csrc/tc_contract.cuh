@@ -1,0 +1,412 @@
+// Tensor-core (tcgen05) angular contractions for the FP32 inner solves of the
+// mixed-precision path (sm_100a / sm_103a, inline PTX).
+//
+// A contraction over a tile of 128 columns (64 cells x 2 LD nodes) is the GEMM
+//   Out[c][o] = sum_k X[c][k] Op[o][k],   c < 128, o, k < N,
+// with Op = D (phi = D psi, Eq. phi-mom) or Op = M (q = M src, Eq. treq).
+// Precision: split BF16 with three products. x = x_hi + x_lo with
+// x_hi = bf16(x), x_lo = bf16(x - x_hi) (likewise for Op), and
+//   x Op ~= x_hi Op_hi + x_hi Op_lo + x_lo Op_hi
+// accumulated in FP32 in tensor memory (the dropped x_lo Op_lo term is ~2^-16
+// relative). One elected thread issues tcgen05.mma (M = 128, N = N, K = 16 per
+// instruction, cta_group::1, kind::f16, A and B both BF16); completion is
+// signalled through an mbarrier by tcgen05.commit; the four warps read their 32
+// accumulator lanes back with tcgen05.ld.
+//
+// Shared-memory operand layout (no swizzle, K-major): an R x K BF16 operand is a
+// grid of 8 x 8 "core matrices" (8 rows of 16 bytes, 128 contiguous bytes);
+// element (row, k) sits at byte
+//   ((row / 8) * (K / 8) + k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2,
+// so core matrices adjacent in K are 128 B apart (leading byte offset) and
+// adjacent 8-row groups K * 16 B apart (stride byte offset). A K-step of 16
+// starts 256 B further. The constant operands (D, M) are stored in global memory
+// already split and in this layout and are staged with one bulk asynchronous
+// copy (cp.async.bulk, the TMA engine) per CTA.
+//
+// Every wait on an mbarrier is bounded; on timeout the kernel records an error
+// flag, releases its tensor memory and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace fpsa {
+namespace tc {
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // give up a wait after 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity to complete, for at most kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > kWaitNs) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 1D bulk asynchronous copy global -> shared, completing on an mbarrier (16-byte
+// aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {  // whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // whole warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start address, leading / stride byte offsets,
+// descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
+// both operands K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, k) in the K-major no-swizzle layout with K columns
+__host__ __device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int K) {
+    return (uint32_t)((((row >> 3) * (K >> 3) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Shared-memory plan of one contraction CTA for N (multiple of 16, <= 256):
+//   opD_hi, opD_lo, opM_hi, opM_lo: N x N BF16 each (constant operands)
+//   x_hi, x_lo:                     128 x N BF16 each (the column tile)
+//   bars: 2 mbarriers (bulk copy, MMA), tmem slot
+struct Plan {
+    uint32_t op_bytes, x_bytes, total;
+    __host__ __device__ static Plan make(int N) {
+        Plan p;
+        p.op_bytes = (uint32_t)N * N * 2;
+        p.x_bytes = 128u * N * 2;
+        p.total = 4 * p.op_bytes + 2 * p.x_bytes + 64;
+        return p;
+    }
+};
+
+__host__ __device__ constexpr uint32_t tmem_cols_for(int N) { return N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u)); }
+
+// Issue Out = X Op over K = N for the tile in x_hi / x_lo against op_hi / op_lo
+// (three products per K-step), then commit to bar. Called by one thread.
+__device__ __forceinline__ void issue_split_gemm(uint32_t tmem, const unsigned char *x_hi, const unsigned char *x_lo,
+                                                 const unsigned char *op_hi, const unsigned char *op_lo, int N,
+                                                 uint64_t *bar) {
+    const uint32_t idesc = idesc_bf16(128, N);
+    const uint32_t sbo = (uint32_t)N * 16;  // (K / 8) core matrices of 128 B per 8-row group
+    const uint32_t xh = smem_u32(x_hi), xl = smem_u32(x_lo), oh = smem_u32(op_hi), ol = smem_u32(op_lo);
+    for (int s = 0; s < N / 16; ++s) {
+        const uint32_t ko = 256u * s;
+        const uint64_t a_hi = smem_desc(xh + ko, 128, sbo), a_lo = smem_desc(xl + ko, 128, sbo);
+        const uint64_t b_hi = smem_desc(oh + ko, 128, sbo), b_lo = smem_desc(ol + ko, 128, sbo);
+        mma_bf16(tmem, a_hi, b_hi, idesc, s > 0 ? 1u : 0u);
+        mma_bf16(tmem, a_hi, b_lo, idesc, 1u);
+        mma_bf16(tmem, a_lo, b_hi, idesc, 1u);
+    }
+    mma_commit(bar);
+}
+
+// Write 16 FP32 values of tile row c, columns k0..k0+15 (k0 a multiple of 8), into
+// x_hi / x_lo: two 16-byte stores per half (one core-matrix row each).
+__device__ __forceinline__ void store_split_row16(unsigned char *x_hi, unsigned char *x_lo, int c, int k0,
+                                                  const float *v, int N) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) split_bf16(v[8 * half + i], h[i], l[i]);
+        const uint32_t off = kmajor_offset(c, k0 + 8 * half, N);
+        *reinterpret_cast<uint4 *>(x_hi + off) = *reinterpret_cast<const uint4 *>(h);
+        *reinterpret_cast<uint4 *>(x_lo + off) = *reinterpret_cast<const uint4 *>(l);
+    }
+}
+
+// 16 consecutive floats from 16-byte aligned global memory (or zeros).
+__device__ __forceinline__ void load16(const float *p, bool live, float *v) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 x = live ? __ldg(reinterpret_cast<const float4 *>(p) + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+    }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Fused FPSA contraction kernels on tensor cores (FP32 data), persistent over
+// 128-column tiles. Columns are (cell, node) pairs of one rhs: column index
+// j = 2 g + a within rhs r. 128 threads: thread t owns tile row t.
+//   k_tc_fp_rhs:        phi_half = D psi;  rhs = m (x) M Sigma (phi_half - phi)
+//   k_tc_update_scatter: phi = phi_base + D v;  q = M (Sigma phi) + q_ang
+// err is set to 1 if an mbarrier wait ran out (the kernel then stops).
+// ---------------------------------------------------------------------------
+struct TcOps {
+    const unsigned char *D;  // D_hi then D_lo, N x N BF16 each, K-major core-matrix layout
+    const unsigned char *M;  // M_hi then M_lo
+};
+
+// Common prologue: smem carve-up, TMEM allocation, operand staging. Returns false on timeout.
+struct TcCta {
+    unsigned char *opD_hi, *opD_lo, *opM_hi, *opM_lo, *x_hi, *x_lo;
+    uint64_t *bar_copy, *bar_mma;
+    uint32_t *tmem_slot;
+    uint32_t tmem;
+    uint32_t mma_phase;
+};
+
+__device__ __forceinline__ bool tc_cta_setup(TcCta &s, unsigned char *smem, const TcOps &ops, int N, int *err) {
+    const tc::Plan pl = tc::Plan::make(N);
+    s.opD_hi = smem;
+    s.opD_lo = smem + pl.op_bytes;
+    s.opM_hi = smem + 2 * pl.op_bytes;
+    s.opM_lo = smem + 3 * pl.op_bytes;
+    s.x_hi = smem + 4 * pl.op_bytes;
+    s.x_lo = s.x_hi + pl.x_bytes;
+    unsigned char *tail = s.x_lo + pl.x_bytes;
+    s.bar_copy = reinterpret_cast<uint64_t *>(tail);
+    s.bar_mma = s.bar_copy + 1;
+    s.tmem_slot = reinterpret_cast<uint32_t *>(s.bar_mma + 1);
+    s.mma_phase = 0;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(s.bar_copy, 1);
+        tc::mbar_init(s.bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(s.tmem_slot, tc::tmem_cols_for(N));
+        tc::tmem_relinquish();
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    s.tmem = *s.tmem_slot;
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(s.bar_copy, 4 * pl.op_bytes);
+        tc::bulk_copy_g2s(s.opD_hi, ops.D, 2 * pl.op_bytes, s.bar_copy);
+        tc::bulk_copy_g2s(s.opM_hi, ops.M, 2 * pl.op_bytes, s.bar_copy);
+    }
+    const bool ok = tc::mbar_wait(s.bar_copy, 0);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    return ok;
+}
+
+__device__ __forceinline__ void tc_cta_teardown(TcCta &s, int N) {
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(s.tmem, tc::tmem_cols_for(N));
+}
+
+// Run one split GEMM on the tile already in x_hi / x_lo against (op_hi, op_lo);
+// afterwards the accumulator lanes are ready for tcgen05.ld. Returns false on timeout.
+__device__ __forceinline__ bool tc_gemm(TcCta &s, const unsigned char *op_hi, const unsigned char *op_lo, int N,
+                                        int *err) {
+    tc::fence_async_smem();  // the tile's st.shared must be visible to the tensor core
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::tc_fence_after();
+        tc::issue_split_gemm(s.tmem, s.x_hi, s.x_lo, op_hi, op_lo, N, s.bar_mma);
+    }
+    const bool ok = tc::mbar_wait(s.bar_mma, s.mma_phase);
+    s.mma_phase ^= 1u;
+    tc::tc_fence_after();
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    return ok;
+}
+
+__global__ void __launch_bounds__(128) k_tc_fp_rhs(const float *__restrict__ psi_half, const float *__restrict__ phi,
+                                                   float *__restrict__ phi_half, const float *__restrict__ sigma_s,
+                                                   const double *__restrict__ h, TcOps ops,
+                                                   float *__restrict__ rhs, int N, int sumK, int R, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcCta s;
+    const bool ok0 = tc_cta_setup(s, smem_tc, ops, N, err);
+    const int t = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    bool ok = ok0;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int j = j0 + t;  // this thread's column
+        const bool live = j < 2 * sumK;
+        const size_t col = (size_t)r * sumK * 2 + j;
+        // A = psi columns
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float v[16];
+            tc::load16(psi_half + col * N + k0, live, v);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        if (!(ok = tc_gemm(s, s.opD_hi, s.opD_lo, N, err))) break;
+        // phi_half = D psi; next A = Sigma (phi_half - phi)
+        const int g = j >> 1;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (live) {
+                    phi_half[col * N + k0 + i] = a[i];
+                    v[i] = sigma_s[(size_t)g * N + k0 + i] * (a[i] - phi[col * N + k0 + i]);
+                } else {
+                    v[i] = 0.f;
+                }
+            }
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        if (!(ok = tc_gemm(s, s.opM_hi, s.opM_lo, N, err))) break;
+        // rhs = m (x) r: node partner is the adjacent lane (column j ^ 1)
+        const float w = live ? (float)(h[g] / 6.0) : 0.f;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);  // r at the other node
+                if (live) rhs[col * N + k0 + i] = w * (2.f * a[i] + other);
+            }
+        }
+    }
+    tc_cta_teardown(s, N);
+}
+
+__global__ void __launch_bounds__(128) k_tc_update_scatter(const float *__restrict__ v_in,
+                                                           const float *__restrict__ phi_base,
+                                                           float *__restrict__ phi, const float *__restrict__ sigma_s,
+                                                           TcOps ops, float *__restrict__ q,
+                                                           const float *__restrict__ qang, int N, int sumK, int R,
+                                                           int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcCta s;
+    const bool ok0 = tc_cta_setup(s, smem_tc, ops, N, err);
+    const int t = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    bool ok = ok0;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int j = j0 + t;
+        const bool live = j < 2 * sumK;
+        const size_t col = (size_t)r * sumK * 2 + j;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float v[16];
+            tc::load16(v_in + col * N + k0, live, v);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        if (!(ok = tc_gemm(s, s.opD_hi, s.opD_lo, N, err))) break;
+        const int g = j >> 1;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (live) {
+                    const float pn = a[i] + (phi_base ? phi_base[col * N + k0 + i] : 0.f);
+                    phi[col * N + k0 + i] = pn;
+                    v[i] = sigma_s[(size_t)g * N + k0 + i] * pn;
+                } else {
+                    v[i] = 0.f;
+                }
+            }
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        if (!(ok = tc_gemm(s, s.opM_hi, s.opM_lo, N, err))) break;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (live) q[col * N + k0 + i] = a[i] + (qang ? qang[col * N + k0 + i] : 0.f);
+        }
+    }
+    tc_cta_teardown(s, N);
+}
+
+}  // namespace fpsa

@@ -293,3 +293,39 @@ def test_adjoint_requires_forward(binding):
     with pytest.raises(binding.FpsaError) as e:
         ctx.adjoint()
     assert e.value.code == binding.ESTATE
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core (tcgen05, split BF16 x3) contractions in the FP32 inner solves.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,K,seed", [(16, 70, 11), (32, 65, 12), (64, 150, 13)])
+@pytest.mark.parametrize("contraction", ["tensor", "simt"])
+def test_mixed_contraction_engines(binding, N, K, seed, contraction):
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel="srk", thick=(1, 300), c=(0.5, 0.999))
+    ctx = binding.context_for(p, precision="mixed")
+    phi, st = ctx.solve("fpsa", tol=1e-12, max_iterations=100, contraction=contraction)
+    ref, n = oracle(p, "fpsa")
+    assert relerr(phi[0], ref) < TOL, (relerr(phi[0], ref), st)
+
+
+def test_tensor_contraction_refused_when_N_does_not_qualify(binding):
+    p = inputs.random_slab(10, 8, 7, seed=14)
+    ctx = binding.context_for(p, precision="mixed")
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.solve("fpsa", tol=1e-12, contraction="tensor")
+    assert e.value.code == binding.ENOTSUP
+
+
+def test_tensor_contraction_batch_rhs_ragged_tail(binding):
+    # 3 instances x 2 rhs, 2*sumK = 2*(61+3+70) = 268 columns: tiles straddle instances and end ragged
+    R = 2
+    probs = [inputs.random_slab(K, 32, 31, seed=60 + i, kernel="hg", nrhs=R) for i, K in enumerate([61, 3, 70])]
+    ctx = binding.context_for(probs, precision="mixed")
+    phi, st = ctx.solve("fpsa", tol=1e-12, max_iterations=100, contraction="tensor")
+    off = 0
+    for p in probs:
+        K = p["h"].size
+        for r in range(R):
+            ref = oit.direct_solve(dict(p, Q=p["Q"][r]))
+            assert relerr(phi[r, off:off + K], ref) < TOL
+        off += K
