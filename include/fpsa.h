@@ -128,8 +128,8 @@ int fpsa_profile_enable(fpsa_ctx *ctx, int32_t on);
 /* Synchronise the context stream and return the counters since the last reset. */
 int fpsa_profile_read(fpsa_ctx *ctx, fpsa_profile *out);
 
-/* Largest N this build supports (FP block 2N x 2N must fit the factorization tile). */
-#define FPSA_MAX_ORDINATES 64
+/* Largest N this build supports. */
+#define FPSA_MAX_ORDINATES 256
 
 /* Create a context: validates the descriptor, builds the S_N tables (mu_n, w_n,
  * D = [w_n P_l(mu_n)], M = [(2l+1)/2 P_l(mu_n)], the MPD or WFD Laplacian;
@@ -185,7 +185,9 @@ void fpsa_destroy(fpsa_ctx *ctx);
 /* Static text for a status code. */
 const char *fpsa_strerror(int code);
 
-/* Message of the last failing call on ctx ("" if none); valid until the next call. */
+/* Message of the last failing call on ctx ("" if none); valid until the next call.
+ * With ctx == NULL: why the last fpsa_create on this thread failed in a CUDA call
+ * ("" after a successful create or an argument error). */
 const char *fpsa_last_error(const fpsa_ctx *ctx);
 
 /* ---------------------------------------------------------------------------

@@ -23,7 +23,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 METHOD = {"si": 0, "fpsa": 1}
 CONTRACTION = {"auto": 0, "simt": 1, "tensor": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
-MAX_ORDINATES = 64
+MAX_ORDINATES = 256
 
 
 class FpsaDesc(ctypes.Structure):
@@ -148,7 +148,7 @@ class Context:
         self._h = ctypes.c_void_p()
         rc = lib.fpsa_create(ctypes.byref(self._h), ctypes.byref(d))
         if rc != OK:
-            raise FpsaError(rc, "fpsa_create")
+            raise FpsaError(rc, "fpsa_create: " + lib.fpsa_last_error(None).decode())
         self._lib = lib
 
     def _check(self, rc, what):

@@ -18,6 +18,7 @@
 #include "fpsa_internal.h"
 #include "kernels.cuh"
 #include "tc_contract.cuh"
+#include "bcr_large.cuh"
 
 using namespace fpsa;
 
@@ -38,6 +39,9 @@ struct PathBuffers {
     T *phi = nullptr, *phi_half = nullptr, *q = nullptr, *psi = nullptr, *rhs = nullptr;
     T *qang = nullptr;                       // MIXED inner path: nodal residual source [R][sumK][2][N]
     T *ybuf = nullptr;                       // BCR solve: intermediate y, then the solution [R][sumK][2N]
+    // recursive block inversion (2N too large for one CTA): per-depth scratch X, Y
+    std::vector<T *> inv_scratch;
+    double *inv_amax = nullptr;
 };
 
 }  // namespace
@@ -88,6 +92,8 @@ struct fpsa_ctx {
 };
 
 namespace {
+
+thread_local std::string g_create_error;  // why the last fpsa_create on this thread failed
 
 // Launch bracket: counts every launch of a kernel class and, while profiling is
 // on, records a CUDA event pair around it on the context stream.
@@ -152,6 +158,15 @@ size_t invert_smem(int N) {
 
 // full: every buffer of an FPSA iteration in precision T. Otherwise only the tables,
 // cross sections, sources and the psi / phi state (the FP64 side of MIXED).
+// usable dynamic shared memory per CTA (227 KB opt-in, less room for static shared memory)
+constexpr size_t kSmemLimit = 227 * 1024 - 1024;
+
+// Can one CTA invert an n x n block (registers for n in {32, 64, 128}, else shared memory)?
+template <typename T>
+bool cta_invertible(int n) {
+    return n == 32 || n == 64 || n == 128 || invert_smem<T>(n / 2) <= kSmemLimit;
+}
+
 template <typename T>
 int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     const Geometry &g = ctx->geo;
@@ -171,6 +186,27 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         CK(dalloc(ctx, &p.q, ang));
         CK(dalloc(ctx, &p.rhs, ang));
         CK(dalloc(ctx, &p.ybuf, ang));
+        // scratch of the recursive block inversion: X and Y per recursion depth
+        for (int n = 2 * g.N; !cta_invertible<T>(n); n /= 2) {
+            T *s = nullptr;
+            CK(dalloc(ctx, &s, (size_t)2 * kLargeChunk * (n / 2) * (n / 2)));
+            p.inv_scratch.push_back(s);
+        }
+        if (!p.inv_scratch.empty()) {
+            CK(dalloc(ctx, &p.inv_amax, kLargeChunk));
+            CK(cudaFuncSetAttribute(k_binv_smem_rm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        }
+        CK(cudaFuncSetAttribute(k_bcr_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)h2 * h2 * sizeof(T))));
+    }
+    {
+        const int cs = (int)contract_smem<T>(g.N);
+        CK(cudaFuncSetAttribute(k_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        CK(cudaFuncSetAttribute(k_fp_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        CK(cudaFuncSetAttribute(k_update_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        CK(cudaFuncSetAttribute(k_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        if (sizeof(T) == 8)
+            CK(cudaFuncSetAttribute(k_mixed_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
     }
     if (full && ctx->precision == FPSA_PRECISION_MIXED) {
         CK(dalloc(ctx, &p.qang, ang));
@@ -185,8 +221,74 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         }
     CK(cudaMemcpy(p.DT, DT.data(), N * N * sizeof(T), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p.MT, MT.data(), N * N * sizeof(T), cudaMemcpyHostToDevice));
-    CK(cudaFuncSetAttribute(k_bcr_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)invert_smem<T>(g.N)));
+    if (invert_smem<T>(g.N) <= kSmemLimit)
+        CK(cudaFuncSetAttribute(k_bcr_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)invert_smem<T>(g.N)));
+    return FPSA_OK;
+}
+
+// In-place inverse (row-major) of the n x n blocks M of a batch of ne items,
+// recursing by block Schur complements down to CTA-sized blocks.
+template <typename T>
+int invert_inplace(fpsa_ctx *ctx, PathBuffers<T> &p, BMat<T> M, int n, const BcrItem *items, int ne, int depth) {
+    cudaStream_t st = ctx->stream;
+    if (n == 128) {
+        k_binv_reg_rm<T, 128><<<ne, 512, 0, st>>>(M, items, ctx->d_status);
+    } else if (n == 64) {
+        k_binv_reg_rm<T, 64><<<ne, 512, 0, st>>>(M, items, ctx->d_status);
+    } else if (n == 32) {
+        k_binv_reg_rm<T, 32><<<ne, 512, 0, st>>>(M, items, ctx->d_status);
+    } else if (invert_smem<T>(n / 2) <= kSmemLimit) {
+        k_binv_smem_rm<T><<<ne, kInvertThreads, invert_smem<T>(n / 2), st>>>(M, n, items, ctx->d_status);
+    } else {
+        const int h = n / 2;
+        if (depth >= (int)p.inv_scratch.size()) return fail(ctx, FPSA_ENOTSUP, "block inversion scratch missing");
+        const BMat<T> A11 = M.sub(0, 0), A12 = M.sub(0, h), A21 = M.sub(h, 0), A22 = M.sub(h, h);
+        T *s = p.inv_scratch[depth];
+        const BMat<T> X{s, (long long)h * h, h, 0}, Y{s + (size_t)kLargeChunk * h * h, (long long)h * h, h, 0};
+        const dim3 gg((h + 63) / 64, (h + 63) / 64, ne);
+        int rc = invert_inplace(ctx, p, A11, h, items, ne, depth + 1);  // A11 <- P
+        if (rc) return rc;
+        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(1), A11, A12, T(0), X, items);    // X = P A12
+        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(1), A21, A11, T(0), Y, items);    // Y = A21 P
+        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), A21, X, T(1), A22, items);   // A22 <- S = A22 - A21 X
+        rc = invert_inplace(ctx, p, A22, h, items, ne, depth + 1);            // A22 <- Q = S^{-1}
+        if (rc) return rc;
+        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), X, A22, T(0), A12, items);   // A12 <- -X Q
+        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), A22, Y, T(0), A21, items);   // A21 <- -Q Y
+        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), X, A21, T(1), A11, items);   // A11 <- P - X A21
+    }
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
+// Invert the eliminated blocks of `items` (ni of them) in place, transposed, with
+// the FP64 growth check: one CTA per block when it fits, else the recursive path.
+template <typename T>
+int invert_level(fpsa_ctx *ctx, PathBuffers<T> &p, const BcrItem *items, int ni) {
+    const int n2 = 2 * ctx->geo.N;
+    cudaStream_t st = ctx->stream;
+    Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+    if (n2 == 128) {
+        k_bcr_invert_reg<T, 128><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+    } else if (n2 == 64) {
+        k_bcr_invert_reg<T, 64><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+    } else if (n2 == 32) {
+        k_bcr_invert_reg<T, 32><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+    } else if (cta_invertible<T>(n2)) {
+        k_bcr_invert<T><<<ni, kInvertThreads, invert_smem<T>(ctx->geo.N), st>>>(p.A, items, n2, ctx->d_growth,
+                                                                               ctx->d_status);
+    } else {
+        const BMat<T> M{p.A, (long long)n2 * n2, n2, 1};
+        for (int c0 = 0; c0 < ni; c0 += kLargeChunk) {
+            const int ne = std::min(kLargeChunk, ni - c0);
+            k_bamax<T><<<ne, 256, 0, st>>>(M, n2, items + c0, p.inv_amax);
+            int rc = invert_inplace(ctx, p, M, n2, items + c0, ne, 0);
+            if (rc) return rc;
+            k_btranspose<T><<<ne, 256, 0, st>>>(M, n2, items + c0, p.inv_amax, ctx->d_growth, ctx->d_status);
+        }
+    }
+    CK(cudaGetLastError());
     return FPSA_OK;
 }
 
@@ -263,23 +365,11 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
                                                  p.Cc);
     }
     CK(cudaGetLastError());
-    const size_t ism = invert_smem<T>(N);
-    // register-tiled inversion where a 16-warp tile layout exists, else the shared-memory one
-    auto invert = [&](const BcrItem *items, int ni) {
-        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
-        if (n2 == 128)
-            k_bcr_invert_reg<T, 128><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
-        else if (n2 == 64)
-            k_bcr_invert_reg<T, 64><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
-        else if (n2 == 32)
-            k_bcr_invert_reg<T, 32><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
-        else
-            k_bcr_invert<T><<<ni, kInvertThreads, ism, st>>>(p.A, items, n2, ctx->d_growth, ctx->d_status);
-    };
     for (int l = 0; l < g.n_levels; ++l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
-        invert(ctx->d_levels[l], ni);
+        int rc = invert_level(ctx, p, ctx->d_levels[l], ni);
+        if (rc) return rc;
         CK(cudaGetLastError());
         {
             Launch L_(ctx, FPSA_PHASE_BCR_SCHUR);
@@ -287,7 +377,10 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
         }
         CK(cudaGetLastError());
     }
-    invert(ctx->d_roots, g.B);
+    {
+        int rc = invert_level(ctx, p, ctx->d_roots, g.B);
+        if (rc) return rc;
+    }
     CK(cudaGetLastError());
     return FPSA_OK;
 }
@@ -571,7 +664,7 @@ const char *fpsa_strerror(int code) {
     }
 }
 
-const char *fpsa_last_error(const fpsa_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+const char *fpsa_last_error(const fpsa_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 void fpsa_destroy(fpsa_ctx *ctx) {
     if (!ctx) return;
@@ -715,7 +808,11 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         if (r2) return r2;
         return setup_tc(ctx);
     }();
-    if (rc != FPSA_OK) return bail(rc);
+    if (rc != FPSA_OK) {
+        g_create_error = ctx->err;
+        return bail(rc);
+    }
+    g_create_error.clear();
     *out = ctx;
     return FPSA_OK;
 }

@@ -450,9 +450,13 @@ __global__ void k_fp_assemble(const double *__restrict__ mu, const double *__res
 // max|A| * max|A^{-1}| per block, max-reduced into *growth; a zero or
 // non-finite pivot sets *status = 1.
 // ---------------------------------------------------------------------------
+// Body shared by the in-place kernel below and the strided sub-block variant:
+// src / dst are n2 x n2 row-major with leading dimensions lds / ldd (they may be
+// the same memory); the inverse is written transposed (dst[c][r]) when tout.
+// growth may be NULL (no growth report).
 template <typename T>
-__global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ items, int n2,
-                             unsigned long long *__restrict__ growth, int *__restrict__ status) {
+__device__ __forceinline__ void gj_smem_body(const T *src, int lds, T *dst, int ldd, bool tout, int n2,
+                                             unsigned long long *__restrict__ growth, int *__restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
     const int ld = n2 + 1;
     T *a = reinterpret_cast<T *>(smem_raw);
@@ -461,12 +465,10 @@ __global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ item
     __shared__ double s_amax;
     __shared__ int s_piv;
     __shared__ T s_pval;
-    const BcrItem it = items[blockIdx.x];
-    T *Ag = A + (size_t)it.cell * n2 * n2;
     double amax = 0.0;
     for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
         const int i = idx / n2, j = idx - i * n2;
-        const T v = Ag[idx];
+        const T v = src[(size_t)i * lds + j];
         a[i * ld + j] = v;
         amax = fmax(amax, fabs((double)v));
     }
@@ -533,15 +535,24 @@ __global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ item
     }
     double ainv = 0.0;
     for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
-        const int c = idx / n2, rr = idx - c * n2;  // write transposed: Ag[c][r] = inv[r][c]
+        const int c = idx / n2, rr = idx - c * n2;  // inv[rr][c]
         const T v = a[rr * ld + c];
-        Ag[idx] = v;
+        if (tout) dst[(size_t)c * ldd + rr] = v;
+        else dst[(size_t)rr * ldd + c] = v;
         ainv = fmax(ainv, fabs((double)v));
         if (!isfinite((double)v)) bad = true;
     }
     for (int o = 16; o > 0; o >>= 1) ainv = fmax(ainv, __shfl_xor_sync(0xffffffffu, ainv, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(growth, dkey(ainv * s_amax));
+    if (growth && (threadIdx.x & 31) == 0) atomicMax(growth, dkey(ainv * s_amax));
     if (bad) atomicExch(status, 1);
+}
+
+// In place, inverse written back transposed (the layout the BCR solve reads).
+template <typename T>
+__global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ items, int n2,
+                             unsigned long long *__restrict__ growth, int *__restrict__ status) {
+    T *Ag = A + (size_t)items[blockIdx.x].cell * n2 * n2;
+    gj_smem_body(Ag, n2, Ag, n2, true, n2, growth, status);
 }
 
 // Register-tiled Gauss-Jordan inversion for n2 = 2N in {32, 64, 128}: 16 warps;
@@ -552,25 +563,24 @@ __global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ item
 // rows). The in-place update is the usual one with row p_k as pivot row; at the
 // end the array X holds A^{-1}[r][c] = X[p_r][q_c] with q the inverse of p
 // (row p_k carries step k's identity column). Written back transposed.
+// Body shared by the in-place kernel and the strided sub-block variant: src / dst
+// are N2 x N2 row-major with leading dimensions lds / ldd; transposed output when
+// tout; growth may be NULL.
 template <typename T, int N2>
-__global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const BcrItem *__restrict__ items,
-                                                        unsigned long long *__restrict__ growth,
-                                                        int *__restrict__ status) {
+__device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int ldd, bool tout,
+                                            unsigned long long *__restrict__ growth, int *__restrict__ status) {
     constexpr int RI = N2 / 32, CJ = N2 / 16;
     __shared__ T colbuf[2][N2], rowbuf[2][N2];
     __shared__ int s_p[2], used[N2], perm[N2], iperm[N2];
-    __shared__ T s_inv[2];
     __shared__ double s_red[16];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const BcrItem it = items[blockIdx.x];
-    T *Ag = A + (size_t)it.cell * N2 * N2;
     T x[RI][CJ];
     double amax = 0.0;
 #pragma unroll
     for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int j = 0; j < CJ; ++j) {
-            x[i][j] = Ag[(size_t)(lane + 32 * i) * N2 + w + 16 * j];
+            x[i][j] = src[(size_t)(lane + 32 * i) * lds + w + 16 * j];
             amax = fmax(amax, fabs((double)x[i][j]));
         }
     for (int r = threadIdx.x; r < N2; r += blockDim.x) used[r] = 0;
@@ -659,7 +669,8 @@ __global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const
         for (int j = 0; j < CJ; ++j) {
             const int row = lane + 32 * i, col = w + 16 * j;
             const int r = iperm[row], c = perm[col];
-            Ag[(size_t)c * N2 + r] = x[i][j];
+            if (tout) dst[(size_t)c * ldd + r] = x[i][j];
+            else dst[(size_t)r * ldd + c] = x[i][j];
             ainv = fmax(ainv, fabs((double)x[i][j]));
             if (!isfinite((double)x[i][j])) bad = true;
         }
@@ -675,8 +686,16 @@ __global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const
         s_red[0] = m;
     }
     __syncthreads();
-    if (lane == 0) atomicMax(growth, dkey(ainv * s_red[0]));
+    if (growth && lane == 0) atomicMax(growth, dkey(ainv * s_red[0]));
     if (bad) atomicExch(status, 1);
+}
+
+template <typename T, int N2>
+__global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const BcrItem *__restrict__ items,
+                                                        unsigned long long *__restrict__ growth,
+                                                        int *__restrict__ status) {
+    T *Ag = A + (size_t)items[blockIdx.x].cell * N2 * N2;
+    gj_reg_body<T, N2>(Ag, N2, Ag, N2, true, growth, status);
 }
 
 // C[p][q] -= / = sum_k X(p,k) Y(k,q) for h2 x h2 operands addressed by strides.

@@ -329,3 +329,19 @@ def test_tensor_contraction_batch_rhs_ragged_tail(binding):
             ref = oit.direct_solve(dict(p, Q=p["Q"][r]))
             assert relerr(phi[r, off:off + K], ref) < TOL
         off += K
+
+
+# ---------------------------------------------------------------------------
+# Large angular orders: 2N > 128 uses the recursive block-Schur inversion
+# (N = 96: one Schur level with shared-memory Gauss-Jordan leaves; N = 128, 256:
+# register Gauss-Jordan leaves of 128), N = 80 the one-CTA shared-memory inversion.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,K,seed", [(80, 9, 21), (96, 10, 22), (128, 12, 23), (256, 5, 24)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_N(binding, N, K, seed, precision):
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel="srk", thick=(5, 500), c=(0.8, 0.999))
+    ctx = binding.context_for(p, precision=precision)
+    phi, st = ctx.solve("fpsa", tol=1e-12, max_iterations=200)
+    ref = oit.direct_solve(p)
+    assert relerr(phi[0], ref) < TOL, (relerr(phi[0], ref), st)
+    assert st["pivot_growth"] < 1e8
