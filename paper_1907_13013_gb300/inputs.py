@@ -143,3 +143,27 @@ def batch_slabs(B, seed, N_choices=(16, 32, 64, 128), K_range=(100, 5000)):
         p = slab(K, N, L, 1.0, st[reg], ss, 1.0)
         out.append(p)
     return out
+
+
+def differentiation_slab(K=1000, N=128, L=127, eta=1e-6, sigma_s0=1000.0, sigma_a=0.01, noise=0.05, seed=0):
+    """Differentiation workload: 1 cm, K cells, S_N, screened Rutherford (eta) to L moments,
+    base sigma_s0 = 1000/cm, sigma_a = 0.01/cm, isotropic unit source, vacuum; per-cell
+    seeded lognormal noise: sigma_a,i = sigma_a exp(noise z_i), sigma_s,l,i = sigma_s,l exp(noise z'_i)
+    (one z' per cell for all l, so each cell keeps a valid kernel shape), sigma_t,i = sigma_a,i + sigma_s0,i."""
+    rng = np.random.default_rng(SEED_BASE + 4 + seed)
+    z = rng.standard_normal(K)
+    zp = rng.standard_normal(K)
+    sa = sigma_a * np.exp(noise * z)
+    ss = (sigma_s0 * srk_moments(eta, L))[None, :] * np.exp(noise * zp)[:, None]
+    return slab(K, N, L, 1.0, sa + ss[:, 0], ss, 1.0)
+
+
+def scale_slab(K=20000, N=256, L=255, g=0.99, c=0.9999, sigma_t=100.0, nrhs=64, seed=0):
+    """Scale workload: 1 cm, K cells, S_N, HG g to L moments, sigma_t = 100/cm, c = 0.9999,
+    nrhs seeded nonnegative isotropic sources Q ~ U[0, 1) per (rhs, cell), vacuum."""
+    rng = np.random.default_rng(SEED_BASE + 5 + seed)
+    p = slab(K, N, L, 1.0, sigma_t, c * sigma_t * hg_moments(g, L), 0.0)
+    Q = np.zeros((nrhs, K, 2, L + 1))
+    Q[..., 0] = rng.uniform(0.0, 1.0, (nrhs, K))[:, :, None]
+    p["Q"] = Q
+    return p

@@ -345,3 +345,67 @@ def test_large_N(binding, N, K, seed, precision):
     ref = oit.direct_solve(p)
     assert relerr(phi[0], ref) < TOL, (relerr(phi[0], ref), st)
     assert st["pivot_growth"] < 1e8
+
+
+# ---------------------------------------------------------------------------
+# Differentiation workload (K = 1000, S128, SRK eta = 1e-6, +-5% lognormal noise):
+# full-size GPU adjoint against central differences on 20 seeded cells (step 1e-6
+# relative, both perturbed solves to a relative change of 1e-13), and mixed vs FP64
+# gradients; oracle
+# adjoint parity on a reduced slab built with the same recipe.
+# ---------------------------------------------------------------------------
+def exit_current_weights(N):
+    from oracle import quadrature as qd
+    mu, w = qd.gauss_legendre(N)
+    M = qd.expansion_operator(mu, N - 1)
+    pos = mu > 0
+    return (w[pos] * mu[pos]) @ M[pos]
+
+
+def test_differentiation_workload_oracle_parity_reduced(binding):
+    from oracle import adjoint as oadj
+    p = inputs.differentiation_slab(K=40)
+    J, d_st, d_ss, _, _ = oadj.gradients(p)
+    for precision in ("fp64", "mixed"):
+        ctx = binding.context_for(p, precision=precision)
+        ctx.solve("fpsa", tol=1e-13, max_iterations=500)
+        gt, gs, Jg, _ = ctx.adjoint(tol=1e-13)
+        assert abs(Jg[0, 0] - J) < 1e-9 * abs(J)
+        assert np.abs(gt - d_st).max() < 1e-6 * np.abs(d_st).max()
+        assert np.abs(gs - d_ss).max() < 1e-6 * np.abs(d_ss).max()
+
+
+def test_differentiation_workload_full_size_central_differences(binding):
+    p = inputs.differentiation_slab()
+    K, N, L = p["h"].size, p["N"], p["L"]
+    cJ = exit_current_weights(N)
+    ctx = binding.context_for(p, precision="fp64")
+    ctx.solve("fpsa", tol=1e-13, max_iterations=1000)
+    gt, gs, Jg, st = ctx.adjoint(tol=1e-13, max_iterations=1000)
+    ctxm = binding.context_for(p, precision="mixed")
+    ctxm.solve("fpsa", tol=1e-13, max_iterations=300)
+    gtm, gsm, _, _ = ctxm.adjoint(tol=1e-13, max_iterations=300)
+    assert np.abs(gtm - gt).max() < 1e-6 * np.abs(gt).max()
+    assert np.abs(gsm - gs).max() < 1e-6 * np.abs(gs).max()
+    q = p["Q"][None]
+
+    def J(st_, ss_):
+        ctx.set_xs(st_, ss_, q)
+        phi, _ = ctx.solve("fpsa", tol=1e-13, max_iterations=1000)
+        return float(phi[0, K - 1, 1] @ cJ)
+
+    assert abs(J(p["sigma_t"], p["sigma_s"]) - Jg[0, 0]) < 1e-12 * abs(Jg[0, 0])
+    rng = np.random.default_rng(2026)
+    cells = rng.choice(K, 20, replace=False)
+    for i in cells:
+        d = 1e-6 * p["sigma_t"][i]
+        a = p["sigma_t"].copy(); a[i] += d
+        b = p["sigma_t"].copy(); b[i] -= d
+        fd = (J(a, p["sigma_s"]) - J(b, p["sigma_s"])) / (2 * d)
+        assert abs(fd - gt[i]) < 1e-4 * np.abs(gt).max(), (i, fd, gt[i])
+        l = int(rng.integers(0, L + 1))
+        d = 1e-6 * abs(p["sigma_s"][i, l])
+        a = p["sigma_s"].copy(); a[i, l] += d
+        b = p["sigma_s"].copy(); b[i, l] -= d
+        fd = (J(p["sigma_t"], a) - J(p["sigma_t"], b)) / (2 * d)
+        assert abs(fd - gs[i, l]) < 1e-4 * np.abs(gs).max(), (i, l, fd, gs[i, l])
