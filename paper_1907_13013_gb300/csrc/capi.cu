@@ -144,10 +144,23 @@ cudaError_t dalloc(fpsa_ctx *ctx, P **p, size_t count) {
 template <typename T>
 size_t contract_smem(int N) { return 2 * 2 * (size_t)kContractCells * N * sizeof(T); }
 
+// right-hand sides per BCR solve unit
+int solve_rc(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
+
 // shared scratch of the cooperative BCR solve (one unit per block)
 template <typename T>
-size_t solve_smem(int N) {
-    return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V) * sizeof(T);
+size_t solve_smem(int N, int RC) {
+    return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V, RC) * sizeof(T);
+}
+
+template <typename T>
+const void *coop_kernel(int RC) {
+    switch (RC) {
+        case 8: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 8>;
+        case 4: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 4>;
+        case 2: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 2>;
+        default: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 1>;
+    }
 }
 
 template <typename T>
@@ -399,8 +412,9 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
                     (void *)&Y, (void *)&N, (void *)&sumK, (void *)&R};
     const int grid = ctx->coop_grid[sizeof(T) == 8 ? 1 : 0];
     Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
-    CK(cudaLaunchCooperativeKernel((const void *)k_bcr_solve_coop<T, kSolveThreads>, dim3(grid), dim3(kSolveThreads),
-                                   args, solve_smem<T>(N), ctx->stream));
+    const int RC = solve_rc(R);
+    CK(cudaLaunchCooperativeKernel(coop_kernel<T>(RC), dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC),
+                                   ctx->stream));
     return FPSA_OK;
 }
 
@@ -769,15 +783,16 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             CK(cudaMemcpy(ctx->d_items_all, all.data(), all.size() * sizeof(BcrItem), cudaMemcpyHostToDevice));
             int nsm = 0, per_sm = 0;
             CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-            CK(cudaFuncSetAttribute(k_bcr_solve_coop<float, kSolveThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)solve_smem<float>(g.N)));
-            CK(cudaFuncSetAttribute(k_bcr_solve_coop<double, kSolveThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)solve_smem<double>(g.N)));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcr_solve_coop<float, kSolveThreads>, kSolveThreads,
-                                                             solve_smem<float>(g.N)));
+            const int RC = solve_rc(g.R);
+            CK(cudaFuncSetAttribute(coop_kernel<float>(RC), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)solve_smem<float>(g.N, RC)));
+            CK(cudaFuncSetAttribute(coop_kernel<double>(RC), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)solve_smem<double>(g.N, RC)));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<float>(RC), kSolveThreads,
+                                                             solve_smem<float>(g.N, RC)));
             ctx->coop_grid[0] = std::max(1, std::min(per_sm, 4)) * nsm;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcr_solve_coop<double, kSolveThreads>, kSolveThreads,
-                                                             solve_smem<double>(g.N)));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<double>(RC), kSolveThreads,
+                                                             solve_smem<double>(g.N, RC)));
             ctx->coop_grid[1] = std::max(1, std::min(per_sm, 4)) * nsm;
             // Row slices per item: split an item's 2N rows (in vectors of V) into S in {1, 2, 4}
             // slices (quadrant-aligned) of >= 2 vectors while the level's units still fit in
@@ -794,8 +809,9 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
                     lv.off[l] = off;
                     off += items;
                     int S = 1;
+                    const int nchunk = (g.R + RC - 1) / RC;
                     while (2 * S <= 4 && vecs % (2 * S) == 0 && vecs / (2 * S) >= 2 &&
-                           (long long)items * g.R * 2 * S <= ctx->coop_grid[e])
+                           (long long)items * nchunk * 2 * S <= ctx->coop_grid[e])
                         S *= 2;
                     lv.slices[l] = S;
                 }

@@ -800,8 +800,10 @@ struct VecOf<double> {
     static constexpr int V = 2;
 };
 
-// shared scratch (values of T) of one solve block
-__host__ __device__ constexpr int bcr_unit_smem_values(int N, int NT, int V) { return 4 * N + NT * V + 2 * N; }
+// shared scratch (values of T) of one solve block handling RC right-hand sides
+__host__ __device__ constexpr int bcr_unit_smem_values(int N, int NT, int V, int RC) {
+    return RC * (2 * N) + RC * (2 * N) + RC * N + NT * V * RC;
+}
 
 template <typename T>
 __device__ __forceinline__ T group_sum(T v, int G) {
@@ -809,12 +811,15 @@ __device__ __forceinline__ T group_sum(T v, int G) {
     return v;
 }
 
-// part[ks][row] = sum over the k of slice ks of Mt[col(k)][row0 + row] * coef[k],
+// For RC right-hand sides at once (coef[rc][k], row stride cstride):
+// part[ks][rc][row] = sum over the k of slice ks of Mt[col(k)][row0 + row] * coef[rc][k],
 // rows [row0, row0 + nr), col(k) = col_off0 + k for k < col_split else col_off1 + k - col_split.
+// Each A^{-1} vector is loaded once and used for all RC right-hand sides.
 // Returns the number of k-slices.
-template <typename T, int NT>
+template <typename T, int NT, int RC>
 __device__ __forceinline__ int sliced_matvec(const T *__restrict__ Mt, int n2, int row0, int nr, int nk,
-                                             int col_split, int col_off0, int col_off1, const T *coef, T *part) {
+                                             int col_split, int col_off0, int col_off1, const T *coef, int cstride,
+                                             T *part) {
     using VT = typename VecOf<T>::type;
     constexpr int V = VecOf<T>::V;
     const int RG = nr / V;
@@ -825,34 +830,42 @@ __device__ __forceinline__ int sliced_matvec(const T *__restrict__ Mt, int n2, i
     for (int t = threadIdx.x; t < RG * KS; t += NT) {
         const int rg = t % RG, ks = t / RG;
         const int k0 = ks * kl, k1 = min(nk, k0 + kl);
-        T acc[V];
+        T acc[RC][V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = T(0);
-#pragma unroll 16
+        for (int rc = 0; rc < RC; ++rc)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[rc][v] = T(0);
+#pragma unroll 8
         for (int k = k0; k < k1; ++k) {
             const int col = (k < col_split) ? col_off0 + k : col_off1 + (k - col_split);
             const VT a = __ldg(reinterpret_cast<const VT *>(Mt + (size_t)col * n2 + row0) + rg);
-            const T c = coef[k];
-            if constexpr (V == 4) {
-                acc[0] = fma(a.x, c, acc[0]); acc[1] = fma(a.y, c, acc[1]);
-                acc[2] = fma(a.z, c, acc[2]); acc[3] = fma(a.w, c, acc[3]);
-            } else {
-                acc[0] = fma(a.x, c, acc[0]); acc[1] = fma(a.y, c, acc[1]);
+#pragma unroll
+            for (int rc = 0; rc < RC; ++rc) {
+                const T c = coef[rc * cstride + k];
+                if constexpr (V == 4) {
+                    acc[rc][0] = fma(a.x, c, acc[rc][0]); acc[rc][1] = fma(a.y, c, acc[rc][1]);
+                    acc[rc][2] = fma(a.z, c, acc[rc][2]); acc[rc][3] = fma(a.w, c, acc[rc][3]);
+                } else {
+                    acc[rc][0] = fma(a.x, c, acc[rc][0]); acc[rc][1] = fma(a.y, c, acc[rc][1]);
+                }
             }
         }
 #pragma unroll
-        for (int v = 0; v < V; ++v) part[ks * nr + rg * V + v] = acc[v];
+        for (int rc = 0; rc < RC; ++rc)
+#pragma unroll
+            for (int v = 0; v < V; ++v) part[(ks * RC + rc) * nr + rg * V + v] = acc[rc][v];
     }
     return KS;
 }
 
-// Up to two h2 x h2 coupling products at once, all NT threads: rows (side, p) of
-// M_side (row-major), a group of G threads per row, each reading a contiguous
-// k-range; the group's partial sums meet by shuffles. Every matrix load of the
-// block is issued before any product is formed. out_side[p] = sum_k M_side[p][k] v_side[k].
-template <typename T, int NT>
+// Up to two h2 x h2 coupling products for RC vectors at once, all NT threads:
+// rows (side, p) of M_side (row-major), a group of G threads per row, each
+// reading a contiguous k-range once for all RC vectors; partial sums meet by
+// shuffles. out_side[rc * ostride + p] = sum_k M_side[p][k] v_side[rc * vstride + k].
+template <typename T, int NT, int RC>
 __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, const T *v0, T *out0,
-                                                  const T *__restrict__ M1, const T *v1, T *out1, int h2) {
+                                                  const T *__restrict__ M1, const T *v1, T *out1, int h2,
+                                                  int vstride, int ostride) {
     const int nrows = (M0 ? h2 : 0) + (M1 ? h2 : 0);
     if (nrows == 0) return;
     int G = 1;
@@ -865,85 +878,104 @@ __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, cons
         const int p = second ? row - (M0 ? h2 : 0) : row;
         const T *M = second ? M1 : M0;
         const T *v = second ? v1 : v0;
-        T acc = T(0);
+        T acc[RC];
+#pragma unroll
+        for (int rc = 0; rc < RC; ++rc) acc[rc] = T(0);
         if (live) {
             const int k0 = gq * kl, k1 = min(h2, k0 + kl);
-#pragma unroll 8
-            for (int k = k0; k < k1; ++k) acc = fma(__ldg(M + (size_t)p * h2 + k), v[k], acc);
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) {
+                const T m = __ldg(M + (size_t)p * h2 + k);
+#pragma unroll
+                for (int rc = 0; rc < RC; ++rc) acc[rc] = fma(m, v[rc * vstride + k], acc[rc]);
+            }
         }
-        acc = group_sum(acc, G);
-        if (live && gq == 0) (second ? out1 : out0)[p] = acc;
+#pragma unroll
+        for (int rc = 0; rc < RC; ++rc) {
+            const T s = group_sum(acc[rc], G);
+            if (live && gq == 0) (second ? out1 : out0)[rc * ostride + p] = s;
+        }
     }
 }
 
-template <typename T, int NT>
+// Units cover RC consecutive right-hand sides r0 .. r0 + nrc - 1 (nrc <= RC).
+template <typename T, int NT, int RC>
 __device__ __forceinline__ void bcr_fwd_unit(const T *__restrict__ A, const T *__restrict__ Bc,
-                                             const T *__restrict__ Cc, const BcrItem &it, int r, int sl, int S,
-                                             T *rhs, T *Y, int N, int sumK, T *sm) {
+                                             const T *__restrict__ Cc, const BcrItem &it, int r0, int nrc, int sl,
+                                             int S, T *rhs, T *Y, int N, int sumK, T *sm) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
-    T *rs = sm, *ys = sm + n2, *pr = sm + 2 * n2, *part = sm + 3 * n2;  // pr: pushed products (N)
-    const size_t rb = (size_t)r * sumK;
-    const T *ri = rhs + (rb + it.cell) * n2;
-    for (int i = threadIdx.x; i < n2; i += NT) rs[i] = __ldcg(ri + i);
+    T *rs = sm, *ys = sm + RC * n2, *pr = ys + RC * n2, *part = pr + RC * N;  // pr: pushed products
+    const size_t rstride = (size_t)sumK * n2;  // between right-hand sides
+    for (int i = threadIdx.x; i < RC * n2; i += NT) {
+        const int rc = i / n2, k = i - rc * n2;
+        rs[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
+    }
     __syncthreads();
     const int nr = n2 / S, row0 = sl * nr;
     const T *Ai = A + (size_t)it.cell * n2 * n2;
-    const int KS = sliced_matvec<T, NT>(Ai, n2, row0, nr, n2, n2, 0, 0, rs, part);
+    const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, n2, n2, 0, 0, rs, n2, part);
     __syncthreads();
-    T *yi = Y + (rb + it.cell) * n2;
-    for (int row = threadIdx.x; row < nr; row += NT) {
+    for (int idx = threadIdx.x; idx < RC * nr; idx += NT) {
+        const int rc = idx / nr, row = idx - rc * nr;
         T y = T(0);
-        for (int s = 0; s < KS; ++s) y += part[s * nr + row];
-        ys[row0 + row] = y;
-        yi[row0 + row] = y;
+        for (int s = 0; s < KS; ++s) y += part[(s * RC + rc) * nr + row];
+        ys[rc * n2 + row0 + row] = y;
+        if (rc < nrc) Y[(size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row] = y;
     }
     __syncthreads();
     const bool push_right = it.right >= 0 && row0 + nr == n2;  // this slice holds R+
     const bool push_left = it.left >= 0 && row0 == 0;          // this slice holds L-
-    coupling_products<T, NT>(push_right ? Bc + (size_t)it.s_right * hh : nullptr, ys + N + h2, pr,
-                             push_left ? Cc + (size_t)it.s_left * hh : nullptr, ys, pr + h2, h2);
+    coupling_products<T, NT, RC>(push_right ? Bc + (size_t)it.s_right * hh : nullptr, ys + N + h2, pr,
+                                 push_left ? Cc + (size_t)it.s_left * hh : nullptr, ys, pr + h2, h2, n2, N);
     __syncthreads();
-    for (int p = threadIdx.x; p < N; p += NT) {
+    for (int idx = threadIdx.x; idx < nrc * N; idx += NT) {
+        const int rc = idx / N, p = idx - rc * N;
+        T *base = rhs + (size_t)(r0 + rc) * rstride;
         if (p < h2 && push_right) {
-            T *rj = rhs + (rb + it.right) * n2 + h2 + p;  // L+
-            *rj = __ldcg(rj) - pr[p];
+            T *rj = base + (size_t)it.right * n2 + h2 + p;  // L+
+            *rj = __ldcg(rj) - pr[rc * N + p];
         }
         if (p >= h2 && push_left) {
-            T *rj = rhs + (rb + it.left) * n2 + N + (p - h2);  // R-
-            *rj = __ldcg(rj) - pr[p];
+            T *rj = base + (size_t)it.left * n2 + N + (p - h2);  // R-
+            *rj = __ldcg(rj) - pr[rc * N + p];
         }
     }
     __syncthreads();  // scratch reuse by the block's next unit
 }
 
-template <typename T, int NT>
+template <typename T, int NT, int RC>
 __device__ __forceinline__ void bcr_bwd_unit(const T *__restrict__ A, const T *__restrict__ Bc,
-                                             const T *__restrict__ Cc, const BcrItem &it, int r, int sl, int S,
-                                             T *Y, int N, int sumK, T *sm) {
+                                             const T *__restrict__ Cc, const BcrItem &it, int r0, int nrc, int sl,
+                                             int S, T *Y, int N, int sumK, T *sm) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
-    T *gv = sm, *g = sm + N, *part = sm + 2 * N;  // gv = [u_left[R+], u_right[L-]], g = [B_i gv0, C_i gv1]
-    const size_t rb = (size_t)r * sumK;
-    for (int idx = threadIdx.x; idx < N; idx += NT) {
+    T *gv = sm, *g = sm + RC * N, *part = g + RC * N;  // gv[rc] = [u_left[R+], u_right[L-]]
+    const size_t rstride = (size_t)sumK * n2;
+    for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
+        const int rc = idx / N, k = idx - rc * N;
         T v = T(0);
-        if (idx < h2) v = __ldcg(Y + (rb + it.left) * n2 + N + h2 + idx);
-        else if (it.right >= 0) v = __ldcg(Y + (rb + it.right) * n2 + (idx - h2));
+        if (rc < nrc) {
+            const T *base = Y + (size_t)(r0 + rc) * rstride;
+            if (k < h2) v = __ldcg(base + (size_t)it.left * n2 + N + h2 + k);
+            else if (it.right >= 0) v = __ldcg(base + (size_t)it.right * n2 + (k - h2));
+        }
         gv[idx] = v;
     }
     __syncthreads();
-    coupling_products<T, NT>(Bc + (size_t)it.s_cell * hh, gv, g, it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr,
-                             gv + h2, g + h2, h2);
+    coupling_products<T, NT, RC>(Bc + (size_t)it.s_cell * hh, gv, g,
+                                 it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr, gv + h2, g + h2, h2, N, N);
     if (it.right < 0)
-        for (int p = threadIdx.x; p < h2; p += NT) g[h2 + p] = T(0);
+        for (int idx = threadIdx.x; idx < RC * h2; idx += NT) g[(idx / h2) * N + h2 + idx % h2] = T(0);
     __syncthreads();
     const int nr = n2 / S, row0 = sl * nr;
     const T *Ai = A + (size_t)it.cell * n2 * n2;
-    const int KS = sliced_matvec<T, NT>(Ai, n2, row0, nr, N, h2, h2, N, g, part);
+    const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, N, h2, h2, N, g, N, part);
     __syncthreads();
-    T *ui = Y + (rb + it.cell) * n2 + row0;
-    for (int row = threadIdx.x; row < nr; row += NT) {
+    for (int idx = threadIdx.x; idx < nrc * nr; idx += NT) {
+        const int rc = idx / nr, row = idx - rc * nr;
         T s = T(0);
-        for (int q = 0; q < KS; ++q) s += part[q * nr + row];
-        ui[row] = __ldcg(ui + row) - s;
+        for (int q = 0; q < KS; ++q) s += part[(q * RC + rc) * nr + row];
+        T *ui = Y + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row;
+        *ui = __ldcg(ui) - s;
     }
     __syncthreads();
 }
@@ -961,31 +993,35 @@ struct LevelTable {
 // The whole BCR solve in one cooperative launch: forward levels, roots, backward
 // levels, separated by grid-wide barriers (all blocks are co-resident by the
 // cooperative launch, so every barrier completes). Blocks take
-// (item, rhs, slice) units block-stride within a level. Solution left in Y.
-template <typename T, int NT>
+// (item, right-hand-side chunk of RC, row slice) units block-stride within a level.
+// Solution left in Y.
+template <typename T, int NT, int RC>
 __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, const T *__restrict__ Bc,
                                                        const T *__restrict__ Cc, const BcrItem *__restrict__ items,
                                                        LevelTable lv, T *rhs, T *Y, int N, int sumK, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     cg::grid_group grid = cg::this_grid();
+    const int nchunk = (R + RC - 1) / RC;
     for (int l = 0; l <= lv.n_levels; ++l) {  // level n_levels = the roots
         const int base = lv.off[l], S = lv.slices[l];
         const int nitems = (l < lv.n_levels) ? lv.off[l + 1] - base : lv.n_roots;
-        const int nw = nitems * R * S;
+        const int nw = nitems * nchunk * S;
         for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-            const int sl = w % S, rr = (w / S) % R, item = w / (S * R);
-            bcr_fwd_unit<T, NT>(A, Bc, Cc, items[base + item], rr, sl, S, rhs, Y, N, sumK, sm);
+            const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
+            const int r0 = ch * RC;
+            bcr_fwd_unit<T, NT, RC>(A, Bc, Cc, items[base + item], r0, min(RC, R - r0), sl, S, rhs, Y, N, sumK, sm);
         }
         if (l < lv.n_levels) grid.sync();
     }
     for (int l = lv.n_levels - 1; l >= 0; --l) {
         grid.sync();
         const int base = lv.off[l], S = lv.slices[l];
-        const int nw = (lv.off[l + 1] - base) * R * S;
+        const int nw = (lv.off[l + 1] - base) * nchunk * S;
         for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-            const int sl = w % S, rr = (w / S) % R, item = w / (S * R);
-            bcr_bwd_unit<T, NT>(A, Bc, Cc, items[base + item], rr, sl, S, Y, N, sumK, sm);
+            const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
+            const int r0 = ch * RC;
+            bcr_bwd_unit<T, NT, RC>(A, Bc, Cc, items[base + item], r0, min(RC, R - r0), sl, S, Y, N, sumK, sm);
         }
     }
 }

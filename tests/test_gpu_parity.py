@@ -409,3 +409,44 @@ def test_differentiation_workload_full_size_central_differences(binding):
         b = p["sigma_s"].copy(); b[i, l] -= d
         fd = (J(p["sigma_t"], a) - J(p["sigma_t"], b)) / (2 * d)
         assert abs(fd - gs[i, l]) < 1e-4 * np.abs(gs).max(), (i, l, fd, gs[i, l])
+
+
+# ---------------------------------------------------------------------------
+# Scale workload (K = 20000, S256, L = 255, HG g = 0.99, c = 0.9999, 64 rhs):
+# full size in mixed precision, checked by particle balance per right-hand side
+# (emission = absorption + leakage, exact for the LD solution); oracle parity on a
+# reduced slab built with the same recipe.
+# ---------------------------------------------------------------------------
+def balance_defect(p, phi, r):
+    from oracle import quadrature as qd
+    N, L = p["N"], p["L"]
+    mu, w = qd.gauss_legendre(N)
+    M = qd.expansion_operator(mu, L)
+    pos, neg = mu > 0, mu < 0
+    jr = (w[pos] * mu[pos]) @ (M[pos] @ phi[r, -1, 1])
+    jl = (w[neg] * -mu[neg]) @ (M[neg] @ phi[r, 0, 0])
+    h = p["h"]
+    Q = p["Q"][r]
+    sa = p["sigma_t"] - p["sigma_s"][:, 0]
+    emission = np.sum(h * (Q[:, 0, 0] + Q[:, 1, 0]) / 2)
+    absorption = np.sum(sa * h * (phi[r, :, 0, 0] + phi[r, :, 1, 0]) / 2)
+    return abs(emission - absorption - jl - jr) / emission
+
+
+def test_scale_workload_reduced_oracle_parity(binding):
+    p = inputs.scale_slab(K=24, nrhs=3)
+    ctx = binding.context_for(p, precision="mixed")
+    phi, st = ctx.solve("fpsa", tol=1e-12, max_iterations=200)
+    for r in range(3):
+        ref = oit.direct_solve(dict(p, Q=p["Q"][r]))
+        assert relerr(phi[r], ref) < TOL
+        assert balance_defect(p, phi, r) < 1e-9
+
+
+def test_scale_workload_full_size(binding):
+    p = inputs.scale_slab()
+    ctx = binding.context_for(p, precision="mixed")
+    phi, st = ctx.solve("fpsa", tol=1e-10, max_iterations=200)
+    assert st["status"] == 0 and np.all(np.isfinite(phi))
+    for r in (0, 17, 63):
+        assert balance_defect(p, phi, r) < 1e-7, (r, balance_defect(p, phi, r), st)
