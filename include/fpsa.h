@@ -82,7 +82,7 @@ typedef struct {
     int32_t max_iterations;   /* cap on transport sweeps (FP64) / refinement steps (MIXED) */
     double tol;               /* stop when max|phi_0^{m+1}-phi_0^m| / max|phi_0^{m+1}| < tol,
                                  the worst instance/right-hand side deciding (Eq. iterate) */
-    int32_t inner_iterations; /* MIXED: FP32 FPSA iterations per FP64 refinement step (0 = default 6) */
+    int32_t inner_iterations; /* MIXED: FP32 FPSA iterations per FP64 refinement step (0 = default 4) */
     double inner_tol;         /* MIXED: inner relative-change target (0 = default 1e-5) */
     int32_t check_every;      /* test convergence every this many iterations (0 = 1) */
     int32_t contraction;      /* MIXED inner contractions: 0 = auto (tensor cores when N is a

@@ -144,6 +144,13 @@ cudaError_t dalloc(fpsa_ctx *ctx, P **p, size_t count) {
 template <typename T>
 size_t contract_smem(int N) { return 2 * 2 * (size_t)kContractCells * N * sizeof(T); }
 
+// shared memory of the Schur update kernel: X and two staged operands, (N/2)^2 each,
+// or X alone when staging does not fit
+template <typename T>
+bool schur_staged(int N) { return (size_t)3 * (N / 2) * (N / 2) * sizeof(T) <= 227 * 1024 - 1024; }
+template <typename T>
+size_t schur_smem(int N) { return (size_t)(schur_staged<T>(N) ? 3 : 1) * (N / 2) * (N / 2) * sizeof(T); }
+
 // right-hand sides per BCR solve unit
 int solve_rc(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
 
@@ -174,7 +181,10 @@ size_t invert_smem(int N) {
 // usable dynamic shared memory per CTA (227 KB opt-in, less room for static shared memory)
 constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 
-// Can one CTA invert an n x n block (registers for n in {32, 64, 128}, else shared memory)?
+// Does one CTA invert an n x n block directly (registers for n in {32, 64, 128},
+// else shared memory)? (Routing 128 x 128 FP32 blocks through one block-Schur
+// level with 64 x 64 leaves was measured slower: the elimination steps are
+// latency bound, so halving their length does not pay for the extra GEMMs.)
 template <typename T>
 bool cta_invertible(int n) {
     return n == 32 || n == 64 || n == 128 || invert_smem<T>(n / 2) <= kSmemLimit;
@@ -209,8 +219,7 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
             CK(dalloc(ctx, &p.inv_amax, kLargeChunk));
             CK(cudaFuncSetAttribute(k_binv_smem_rm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
         }
-        CK(cudaFuncSetAttribute(k_bcr_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((size_t)h2 * h2 * sizeof(T))));
+        CK(cudaFuncSetAttribute(k_bcr_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_smem<T>(g.N)));
     }
     {
         const int cs = (int)contract_smem<T>(g.N);
@@ -282,7 +291,7 @@ int invert_level(fpsa_ctx *ctx, PathBuffers<T> &p, const BcrItem *items, int ni)
     const int n2 = 2 * ctx->geo.N;
     cudaStream_t st = ctx->stream;
     Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
-    if (n2 == 128) {
+    if (n2 == 128 && cta_invertible<T>(128)) {
         k_bcr_invert_reg<T, 128><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
     } else if (n2 == 64) {
         k_bcr_invert_reg<T, 64><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
@@ -386,7 +395,8 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
         CK(cudaGetLastError());
         {
             Launch L_(ctx, FPSA_PHASE_BCR_SCHUR);
-            k_bcr_schur<T><<<ni, 256, (size_t)h2 * h2 * sizeof(T), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], N);
+            k_bcr_schur<T><<<ni, 256, schur_smem<T>(N), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], N,
+                                                              schur_staged<T>(N) ? 1 : 0);
         }
         CK(cudaGetLastError());
     }
@@ -544,7 +554,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     const size_t ncol = (size_t)g.R * g.sumK * 2, nang = ncol * N;
     const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
     const dim3 sgrid(N, g.B, g.R);
-    const int inner = o.inner_iterations > 0 ? o.inner_iterations : 6;
+    const int inner = o.inner_iterations > 0 ? o.inner_iterations : 4;
     const bool fpsa = o.method == FPSA_METHOD_FPSA;
     if (o.contraction == 2 && !ctx->tc_able)
         return fail(ctx, FPSA_ENOTSUP, "tensor-core contractions need N a multiple of 16 and <= 128");

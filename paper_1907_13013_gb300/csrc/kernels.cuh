@@ -698,17 +698,62 @@ __global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const
     gj_reg_body<T, N2>(Ag, N2, Ag, N2, true, growth, status);
 }
 
-// C[p][q] -= / = sum_k X(p,k) Y(k,q) for h2 x h2 operands addressed by strides.
+// out (+)= X Y for h2 x h2 operands through shared memory: both operands are
+// staged with coalesced loads (the index that is contiguous in memory runs
+// fastest across threads), then every thread forms a 2 x 2 register tile.
+// buf holds 2 h2^2 values. mode: 0 store, 1 subtract from out, 2 store negated.
+// With buf == NULL (blocks too large to stage) the operands are read from global
+// memory directly, one output per thread.
 template <typename T>
-__device__ __forceinline__ void tile_mm(T *out, int ldo, bool accumulate_neg, const T *X, int xr, int xc,
-                                        const T *Y, int yr, int yc, int h2) {
-    for (int idx = threadIdx.x; idx < h2 * h2; idx += blockDim.x) {
-        const int p = idx / h2, qq = idx - p * h2;
-        T acc = T(0);
-        for (int k = 0; k < h2; ++k) acc = fma(X[(size_t)p * xr + (size_t)k * xc], Y[(size_t)k * yr + (size_t)qq * yc], acc);
-        if (accumulate_neg) out[(size_t)p * ldo + qq] -= acc;
-        else out[(size_t)p * ldo + qq] = acc;
+__device__ __forceinline__ void smem_mm(T *out, int ldo, int mode, const T *X, int xr, int xc, const T *Y, int yr,
+                                        int yc, int h2, T *buf) {
+    const int hh = h2 * h2;
+    if (!buf) {
+        for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) {
+            const int p = idx / h2, q = idx - p * h2;
+            T acc = T(0);
+            for (int kk = 0; kk < h2; ++kk)
+                acc = fma(X[(size_t)p * xr + (size_t)kk * xc], Y[(size_t)kk * yr + (size_t)q * yc], acc);
+            T *o = out + (size_t)p * ldo + q;
+            if (mode == 1) *o -= acc;
+            else if (mode == 2) *o = -acc;
+            else *o = acc;
+        }
+        __syncthreads();
+        return;
     }
+    T *Xs = buf, *Ys = buf + h2 * h2;  // Xs[p][k], Ys[k][q]
+    for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) {
+        int p, kk;
+        if (xr == 1) { p = idx % h2; kk = idx / h2; } else { kk = idx % h2; p = idx / h2; }
+        Xs[p * h2 + kk] = X[(size_t)p * xr + (size_t)kk * xc];
+        int k2, q;
+        if (yr == 1) { k2 = idx % h2; q = idx / h2; } else { q = idx % h2; k2 = idx / h2; }
+        Ys[k2 * h2 + q] = Y[(size_t)k2 * yr + (size_t)q * yc];
+    }
+    __syncthreads();
+    const int half = (h2 + 1) / 2;
+    for (int t = threadIdx.x; t < half * half; t += blockDim.x) {
+        const int p0 = 2 * (t / half), q0 = 2 * (t % half);
+        T a00 = T(0), a01 = T(0), a10 = T(0), a11 = T(0);
+        const bool p1 = p0 + 1 < h2, q1 = q0 + 1 < h2;
+        for (int kk = 0; kk < h2; ++kk) {
+            const T x0 = Xs[p0 * h2 + kk], x1 = p1 ? Xs[(p0 + 1) * h2 + kk] : T(0);
+            const T y0 = Ys[kk * h2 + q0], y1 = q1 ? Ys[kk * h2 + q0 + 1] : T(0);
+            a00 = fma(x0, y0, a00); a01 = fma(x0, y1, a01);
+            a10 = fma(x1, y0, a10); a11 = fma(x1, y1, a11);
+        }
+        const T v[4] = {a00, a01, a10, a11};
+        for (int e = 0; e < 4; ++e) {
+            const int p = p0 + (e >> 1), q = q0 + (e & 1);
+            if (p >= h2 || q >= h2) continue;
+            T *o = out + (size_t)p * ldo + q;
+            if (mode == 1) *o -= v[e];
+            else if (mode == 2) *o = -v[e];
+            else *o = v[e];
+        }
+    }
+    __syncthreads();
 }
 
 // Schur updates of the kept neighbours of each eliminated cell i at level l
@@ -717,12 +762,15 @@ __device__ __forceinline__ void tile_mm(T *out, int ldo, bool accumulate_neg, co
 //                   B_j' = -B_j Ainv_i[R+,L+] B_i
 //   left  j = i-s:  A_j[R-,R+] -= C_j Ainv_i[L-,L+] B_i
 //                   C_j' = -C_j Ainv_i[L-,R-] C_i   (0 if i has no right neighbour)
+// Shared memory: 3 (N/2)^2 values (the product X and the staging buffer) when
+// staged, else (N/2)^2 (X only; operands read from global memory).
 template <typename T>
 __global__ void k_bcr_schur(T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc,
-                            const BcrItem *__restrict__ items, int N) {
+                            const BcrItem *__restrict__ items, int N, int staged) {
     extern __shared__ unsigned char smem_raw[];
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
     T *X = reinterpret_cast<T *>(smem_raw);
+    T *buf = staged ? X + hh : nullptr;
     const BcrItem it = items[blockIdx.x];
     const T *Ai = A + (size_t)it.cell * n2 * n2;  // transposed inverse: Ainv[r][c] = Ai[c*n2 + r]
     const int Lm = 0, Lp = h2, Rm = N, Rp = N + h2;
@@ -732,32 +780,20 @@ __global__ void k_bcr_schur(T *__restrict__ A, T *__restrict__ Bc, T *__restrict
     if (it.right >= 0) {
         const T *Bj = Bc + (size_t)it.s_right * hh;
         T *Aj = A + (size_t)it.right * n2 * n2;
-        tile_mm(X, h2, false, Bj, h2, 1, Ai + (size_t)Rm * n2 + Rp, 1, n2, h2);   // X = B_j Ainv[R+,R-]
-        __syncthreads();
-        tile_mm(Aj + (size_t)Lp * n2 + Lm, n2, true, X, h2, 1, Ci, h2, 1, h2);    // A_j[L+,L-] -= X C_i
-        __syncthreads();
-        tile_mm(X, h2, false, Bj, h2, 1, Ai + (size_t)Lp * n2 + Rp, 1, n2, h2);   // X = B_j Ainv[R+,L+]
-        __syncthreads();
-        T *Bn = Bc + (size_t)it.s_right_next * hh;
-        tile_mm(Bn, h2, false, X, h2, 1, Bi, h2, 1, h2);                          // B_j' = X B_i
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) Bn[idx] = -Bn[idx];
-        __syncthreads();
+        smem_mm(X, h2, 0, Bj, h2, 1, Ai + (size_t)Rm * n2 + Rp, 1, n2, h2, buf);   // X = B_j Ainv[R+,R-]
+        smem_mm(Aj + (size_t)Lp * n2 + Lm, n2, 1, X, h2, 1, Ci, h2, 1, h2, buf);    // A_j[L+,L-] -= X C_i
+        smem_mm(X, h2, 0, Bj, h2, 1, Ai + (size_t)Lp * n2 + Rp, 1, n2, h2, buf);   // X = B_j Ainv[R+,L+]
+        smem_mm(Bc + (size_t)it.s_right_next * hh, h2, 2, X, h2, 1, Bi, h2, 1, h2, buf);  // B_j' = -X B_i
     }
     if (it.left >= 0) {
         const T *Cj = Cc + (size_t)it.s_left * hh;
         T *Aj = A + (size_t)it.left * n2 * n2;
-        tile_mm(X, h2, false, Cj, h2, 1, Ai + (size_t)Lp * n2 + Lm, 1, n2, h2);   // X = C_j Ainv[L-,L+]
-        __syncthreads();
-        tile_mm(Aj + (size_t)Rm * n2 + Rp, n2, true, X, h2, 1, Bi, h2, 1, h2);    // A_j[R-,R+] -= X B_i
-        __syncthreads();
+        smem_mm(X, h2, 0, Cj, h2, 1, Ai + (size_t)Lp * n2 + Lm, 1, n2, h2, buf);   // X = C_j Ainv[L-,L+]
+        smem_mm(Aj + (size_t)Rm * n2 + Rp, n2, 1, X, h2, 1, Bi, h2, 1, h2, buf);    // A_j[R-,R+] -= X B_i
         T *Cn = Cc + (size_t)it.s_left_next * hh;
         if (it.right >= 0) {
-            tile_mm(X, h2, false, Cj, h2, 1, Ai + (size_t)Rm * n2 + Lm, 1, n2, h2);  // X = C_j Ainv[L-,R-]
-            __syncthreads();
-            tile_mm(Cn, h2, false, X, h2, 1, Ci, h2, 1, h2);                         // C_j' = X C_i
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) Cn[idx] = -Cn[idx];
+            smem_mm(X, h2, 0, Cj, h2, 1, Ai + (size_t)Rm * n2 + Lm, 1, n2, h2, buf);  // X = C_j Ainv[L-,R-]
+            smem_mm(Cn, h2, 2, X, h2, 1, Ci, h2, 1, h2, buf);                         // C_j' = -X C_i
         } else {
             for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) Cn[idx] = T(0);
         }
@@ -995,6 +1031,39 @@ struct LevelTable {
 // cooperative launch, so every barrier completes). Blocks take
 // (item, right-hand-side chunk of RC, row slice) units block-stride within a level.
 // Solution left in Y.
+// L2 prefetch of the data a forward (bwd = false) or backward unit will read:
+// its A^{-1} row slice (all 2N columns forward, the N inflow columns backward;
+// one 128-byte line per column for slices of <= 128 bytes) and its coupling blocks.
+template <typename T>
+__device__ __forceinline__ void prefetch_unit(const T *A, const T *Bc, const T *Cc, const BcrItem &it, int sl, int S,
+                                              int N, bool bwd) {
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+    const int nr = n2 / S, row0 = sl * nr;
+    const int lines_per_col = (int)((nr * sizeof(T) + 127) / 128);
+    const int ncols = bwd ? N : n2;
+    const T *Ai = A + (size_t)it.cell * n2 * n2;
+    for (int idx = threadIdx.x; idx < ncols * lines_per_col; idx += blockDim.x) {
+        const int kk = idx / lines_per_col, ln = idx - kk * lines_per_col;
+        const int col = bwd ? (kk < h2 ? h2 + kk : N + (kk - h2)) : kk;
+        const char *p = reinterpret_cast<const char *>(Ai + (size_t)col * n2 + row0) + 128 * ln;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+    const int cl = (int)((hh * sizeof(T) + 127) / 128);
+    const T *blk[2] = {bwd ? Bc + (size_t)it.s_cell * hh : (it.right >= 0 ? Bc + (size_t)it.s_right * hh : nullptr),
+                       bwd ? (it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr)
+                           : (it.left >= 0 ? Cc + (size_t)it.s_left * hh : nullptr)};
+    for (int idx = threadIdx.x; idx < 2 * cl; idx += blockDim.x) {
+        const T *b = blk[idx / cl];
+        if (b) asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(b) + 128 * (idx % cl)));
+    }
+}
+
+// The whole BCR solve in one cooperative launch: forward levels, roots, backward
+// levels, separated by grid-wide barriers (all blocks are co-resident by the
+// cooperative launch, so every barrier completes). Blocks take
+// (item, right-hand-side chunk of RC, row slice) units block-stride within a level;
+// before working on a level each block asks L2 for the data of its units of the
+// next level, so that level's factor reads hit L2. Solution left in Y.
 template <typename T, int NT, int RC>
 __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, const T *__restrict__ Bc,
                                                        const T *__restrict__ Cc, const BcrItem *__restrict__ items,
@@ -1003,10 +1072,20 @@ __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, 
     T *sm = reinterpret_cast<T *>(smem_raw);
     cg::grid_group grid = cg::this_grid();
     const int nchunk = (R + RC - 1) / RC;
+    auto level_units = [&](int l) {
+        const int nitems = (l < lv.n_levels) ? lv.off[l + 1] - lv.off[l] : lv.n_roots;
+        return nitems * nchunk * lv.slices[l];
+    };
+    auto prefetch_level = [&](int l, bool bwd) {
+        if (l < 0 || l > lv.n_levels) return;
+        const int S = lv.slices[l], nw = level_units(l);
+        for (int w = blockIdx.x; w < nw; w += gridDim.x)
+            prefetch_unit(A, Bc, Cc, items[lv.off[l] + w / (S * nchunk)], w % S, S, N, bwd);
+    };
     for (int l = 0; l <= lv.n_levels; ++l) {  // level n_levels = the roots
+        prefetch_level(l + 1, false);
         const int base = lv.off[l], S = lv.slices[l];
-        const int nitems = (l < lv.n_levels) ? lv.off[l + 1] - base : lv.n_roots;
-        const int nw = nitems * nchunk * S;
+        const int nw = level_units(l);
         for (int w = blockIdx.x; w < nw; w += gridDim.x) {
             const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
             const int r0 = ch * RC;
@@ -1016,6 +1095,7 @@ __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, 
     }
     for (int l = lv.n_levels - 1; l >= 0; --l) {
         grid.sync();
+        prefetch_level(l - 1, true);
         const int base = lv.off[l], S = lv.slices[l];
         const int nw = (lv.off[l + 1] - base) * nchunk * S;
         for (int w = blockIdx.x; w < nw; w += gridDim.x) {
