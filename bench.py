@@ -6,7 +6,10 @@ Workload (one step = one pass of the whole path over one problem):
   isotropic unit source on z < 0.5, vacuum edges; synthetic, seeded inputs.
   A step is fpsa_set_xs (upload, sweep coefficients, FP block assembly, block
   cyclic-reduction factorization) followed by fpsa_solve to a relative change of
-  phi_0 below 1e-10 (FPSA source iteration).
+  phi_0 below 1e-10 (FPSA source iteration). Default: mixed precision (FP32 inner
+  FPSA solves with tensor-core contractions inside FP64 refinement) and the WFD
+  angular Laplacian; the same workload with MPD and with the plain FP64 path is
+  reported under "secondary".
 
   value : solves/s with inputs already resident in device memory (torch CUDA
           tensors passed to the C ABI), device-timed with CUDA events on the
@@ -39,6 +42,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, sigma_s0=1000, sigma_a=0.01, Q=1 on z<0.5, vacuum"
 METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
 TOL = 1e-10
+# per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload
+NCU_TRAFFIC = {("k_bcr_solve_coop", "mixed"): 232.8e6}
 
 
 def dist_env():
@@ -62,7 +67,7 @@ def read_golden(name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -76,7 +81,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -122,16 +127,16 @@ def run_reference(args):
     from oracle import iterations as oit
     from paper_1907_13013_gb300 import inputs
     p = inputs.precision_srk_slab()
-    _, n_it = read_golden("precision_srk_slab_fpsa_mpd_phi0.txt")
+    _, n_it = read_golden("precision_srk_slab_fpsa_%s_phi0.txt" % args.laplacian)
     sample_its = 3
 
     def step():
         t0 = time.perf_counter()
         # FP operator assembly + sparse LU (the setup), then `sample_its` FPSA iterations
-        _, n = oit.fpsa_source_iteration(p, "mpd", tol=0.0, max_it=sample_its)
+        _, n = oit.fpsa_source_iteration(p, args.laplacian, tol=0.0, max_it=sample_its)
         t_all = time.perf_counter() - t0
         t1 = time.perf_counter()
-        _, n = oit.fpsa_source_iteration(p, "mpd", tol=0.0, max_it=sample_its + 2)
+        _, n = oit.fpsa_source_iteration(p, args.laplacian, tol=0.0, max_it=sample_its + 2)
         t_more = time.perf_counter() - t1
         per_it = max((t_more - t_all) / 2.0, 0.0)
         setup = max(t_all - sample_its * per_it, 0.0)
@@ -147,32 +152,34 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_per_solve,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64", "laplacian": "mpd"},
+           "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64", "laplacian": args.laplacian},
            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": v, "unit": "solves/s"},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline_sample():
+def cpu_baseline_sample(laplacian):
     """One full oracle solve of the workload (about 10-30 s of single-threaded CPU work)."""
     from oracle import iterations as oit
     from paper_1907_13013_gb300 import inputs
     p = inputs.precision_srk_slab()
     t0 = time.perf_counter()
-    _, n = oit.fpsa_source_iteration(p, "mpd", tol=TOL)
+    _, n = oit.fpsa_source_iteration(p, laplacian, tol=TOL)
     dt = time.perf_counter() - t0
     return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": "one complete FP64 oracle FPSA-SI (MPD) solve of the workload, %d iterations, %.1f s" % (n, dt)}
+            "sample": "one complete FP64 oracle FPSA-SI (%s) solve of the workload, %d iterations, %.1f s"
+                      % (laplacian.upper(), n, dt)}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--laplacian", default="mpd", choices=["mpd", "wfd"])
+    ap.add_argument("--laplacian", default="wfd", choices=["mpd", "wfd"])
+    ap.add_argument("--no-secondary", action="store_true", help="skip the MPD and FP64 comparison runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -261,41 +268,65 @@ def main():
     phi0 = d_phi[0, :, :, 0].cpu().numpy().ravel()
     rel_err = float(np.abs(phi0 - ref).max() / np.abs(ref).max())
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class (algorithmic bytes / FLOPs per launch)
+    esize = 4 if args.precision == "mixed" else 8
     n2 = 2 * N
-    lev_items = K - 1  # every cell but the root is eliminated at exactly one level
     phases = {k: v for k, v in prof.items() if v["timed"]}
     dom = max(phases, key=lambda k: phases[k]["ms"])
-    inv_flops = 2.0 * n2 ** 3 * K  # Gauss-Jordan: ~n^3 multiply-adds per block, K blocks per step
-    sweeps = dev_stats["sweeps"]
-    solve_bytes_per_sweep = 8.0 * (lev_items * (n2 * n2 + n2 * N) + n2 * n2)  # A^{-1} reads (fwd + bwd)
-    roof = None
+    per_launch_ms = phases[dom]["ms"] / phases[dom]["timed"]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    if dom == "bcr_invert":
-        per_launch_ms = phases[dom]["ms"] / phases[dom]["timed"]
-        launches_per_step = phases[dom]["timed"] / args.steps
-        achieved = inv_flops / launches_per_step / (per_launch_ms * 1e-3) / 1e12
-        peak = 1.25  # FP64 nominal (no FP64 figure in the measured peaks)
-        roof = {"kernel": "k_bcr_invert<double>", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300); not in MEASURED_PEAKS.json"}
-    elif dom == "bcr_solve":
-        per_launch_ms = phases[dom]["ms"] / phases[dom]["timed"]
-        launches_per_step = phases[dom]["timed"] / args.steps
-        byt = solve_bytes_per_sweep * sweeps / launches_per_step
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if dom == "bcr_solve":
+        # forward: every eliminated cell and the root read their full (2N)^2 inverse;
+        # backward: the 2N x N inflow columns; plus the N/2 x N/2 couplings (2 per cell)
+        byt = esize * (K * n2 * n2 + (K - 1) * n2 * N + 2 * (K - 1) * (N // 2) ** 2)
         achieved = byt / (per_launch_ms * 1e-3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "k_bcr_fwd/k_bcr_bwd<double>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None}
+        # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel for this
+        # workload (FP32), from profiles/k_bcr_solve_coop_precision_srk_slab.md
+        traffic = NCU_TRAFFIC.get(("k_bcr_solve_coop", args.precision))
+        roof = {"kernel": "k_bcr_solve_coop", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "algorithmic_bytes": byt}
+    elif dom == "bcr_invert":
+        flops = 2.0 * n2 ** 3 * K / 12.0  # per launch: K blocks over 12 launches on average
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        peak = 74.0 if esize == 4 else 1.20  # FMA-chain probe on this GB300 (not in MEASURED_PEAKS.json)
+        roof = {"kernel": "k_bcr_invert_reg", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP32 / FP64 FMA-chain probe on GB300 (74 / 1.20 TFLOP/s)"}
     else:
-        per_launch_ms = phases[dom]["ms"] / phases[dom]["timed"]
-        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": None}
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
     roof["avg_launch_ms"] = per_launch_ms
+    roof["peak_source"] = roof.get("peak_source", "MEASURED_PEAKS.json hbm_gbs (STREAM-style copy, burst)")
+
+    secondary = {}
+    if not args.no_secondary:
+        for name, lap, prec in (("mpd", "mpd", args.precision), ("fp64", args.laplacian, "fp64")):
+            if (lap, prec) == (args.laplacian, args.precision):
+                continue
+            c2 = binding.Context([K], p["h"], N, L, laplacian=lap, precision=prec, device=local,
+                                 stream=stream.cuda_stream)
+            st2 = {}
+
+            def step2():
+                c2.set_xs(d_st, d_ss, d_q)
+                _, s = c2.solve("fpsa", tol=TOL, out=d_phi)
+                st2.update(s)
+
+            for _ in range(2):
+                step2()
+            ms2 = timed(step2, 3)
+            ref2, _ = read_golden("precision_srk_slab_fpsa_%s_phi0.txt" % lap)
+            err2 = float(np.abs(d_phi[0, :, :, 0].cpu().numpy().ravel() - ref2).max() / np.abs(ref2).max())
+            secondary[name] = {"laplacian": lap, "precision": prec, "value": world * 3 / (ms2 * 1e-3),
+                               "unit": "solves/s", "ms_per_step": ms2 / 3, "iterations": st2["iterations"],
+                               "setup_ms": st2["setup_ms"], "solve_ms": st2["solve_ms"],
+                               "max_rel_err_vs_oracle": err2}
+            c2.close()
 
     value = world * args.steps / (ms * 1e-3)
     h2d = 8 * (K + K * (L + 1) + 2 * K * (L + 1))
@@ -303,7 +334,7 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64 (bf16x3 tensor-core contractions)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "laplacian": args.laplacian,
                    "tol": TOL, "parallelism": "replicas" if world > 1 else "single",
@@ -320,9 +351,10 @@ def main():
                     for k, v in phases.items()},
         "profiled_ms_per_step": ms_prof / args.steps,
         "clocks": clocks,
+        "secondary": secondary,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_sample()
+        out["cpu_baseline"] = cpu_baseline_sample(args.laplacian)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
