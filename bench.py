@@ -53,6 +53,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms, device=None):
+    """Max of a per-rank time over all ranks (torch.distributed, any backend); identity
+    when no process group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps_per_rank, max_ms):
+    """Weak scaling with one replica per rank: units of all ranks / slowest rank's time."""
+    return world * steps_per_rank / (max_ms * 1e-3)
+
+
 def read_golden(name):
     path = os.path.join(ROOT, "tests", "golden", name)
     vals, its10 = [], None
@@ -236,12 +253,7 @@ def main():
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dev)
 
     for _ in range(args.warmup):
         step_device()
@@ -322,13 +334,13 @@ def main():
             ms2 = timed(step2, 3)
             ref2, _ = read_golden("precision_srk_slab_fpsa_%s_phi0.txt" % lap)
             err2 = float(np.abs(d_phi[0, :, :, 0].cpu().numpy().ravel() - ref2).max() / np.abs(ref2).max())
-            secondary[name] = {"laplacian": lap, "precision": prec, "value": world * 3 / (ms2 * 1e-3),
+            secondary[name] = {"laplacian": lap, "precision": prec, "value": whole_job_rate(world, 3, ms2),
                                "unit": "solves/s", "ms_per_step": ms2 / 3, "iterations": st2["iterations"],
                                "setup_ms": st2["setup_ms"], "solve_ms": st2["solve_ms"],
                                "max_rel_err_vs_oracle": err2}
             c2.close()
 
-    value = world * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, args.steps, ms)
     h2d = 8 * (K + K * (L + 1) + 2 * K * (L + 1))
     d2h = 8 * 2 * K * (L + 1)
     out = {
@@ -343,7 +355,7 @@ def main():
         "iterations": dev_stats["iterations"], "oracle_iterations_1e-10": its_ref,
         "setup_ms": dev_stats["setup_ms"], "solve_ms": dev_stats["solve_ms"],
         "max_rel_err_vs_oracle": rel_err,
-        "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "solves/s",
+        "e2e": {"value": whole_job_rate(world, args.steps, ms_e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof,
