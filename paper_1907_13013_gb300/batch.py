@@ -1,0 +1,87 @@
+"""Batched solves of many independent slabs of uneven cell counts and angular orders.
+
+Slabs sharing (N, L) are solved together by one fpsa context (every kernel launch
+covers all of them: ragged cell counts are handled inside the kernels through
+per-instance offsets). Groups with different (N, L) run concurrently, each on its
+own CUDA stream from its own host thread (the ctypes calls release the GIL). A
+group whose factor storage would exceed the memory budget is split into waves,
+packed greedily so that each wave's block-inverse storage stays within budget.
+All arithmetic happens in the library; this module only partitions the work.
+"""
+
+import concurrent.futures as cf
+
+import numpy as np
+
+from . import binding
+
+
+def factor_bytes(K, N, precision):
+    """Device bytes dominated by the FP blocks (2N x 2N per cell) and the per-level couplings."""
+    es = 4 if precision == "mixed" else 8
+    return es * K * (4 * N * N + 2 * 2 * (N // 2) ** 2) + 64 * es * K * N
+
+
+def plan_waves(problems, budget_bytes, precision):
+    """Group problem indices by (N, L), then split each group into waves within budget.
+    Returns a list of (N, L, [indices]) in an order that starts the largest work first."""
+    groups = {}
+    for i, p in enumerate(problems):
+        groups.setdefault((p["N"], p["L"]), []).append(i)
+    waves = []
+    for (N, L), idx in groups.items():
+        idx = sorted(idx, key=lambda i: -problems[i]["h"].size)
+        cur, used = [], 0
+        for i in idx:
+            b = factor_bytes(problems[i]["h"].size, N, precision)
+            if cur and used + b > budget_bytes:
+                waves.append((N, L, cur))
+                cur, used = [], 0
+            cur.append(i)
+            used += b
+        if cur:
+            waves.append((N, L, cur))
+    waves.sort(key=lambda w: -sum(problems[i]["h"].size for i in w[2]) * w[0] ** 2)
+    return waves
+
+
+class BatchSolver:
+    """Solve a list of problem dicts (see inputs.py; single right-hand side each)."""
+
+    def __init__(self, problems, precision="mixed", laplacian="wfd", budget_bytes=32 << 30, device=0,
+                 max_streams=4):
+        self.problems = list(problems)
+        self.precision, self.laplacian = precision, laplacian
+        self.device = device
+        self.waves = plan_waves(self.problems, budget_bytes, precision)
+        self.max_streams = max_streams
+
+    def _run_wave(self, wave, solve_kw):
+        import torch
+        N, L, idx = wave
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(device=self.device)
+        probs = [self.problems[i] for i in idx]
+        with torch.cuda.stream(stream):
+            ctx = binding.context_for(probs, laplacian=self.laplacian, precision=self.precision,
+                                      device=self.device, stream=stream.cuda_stream)
+            phi, st = ctx.solve(**solve_kw)
+            ctx.close()
+        out, off = {}, 0
+        for i, p in zip(idx, probs):
+            K = p["h"].size
+            out[i] = phi[0, off:off + K]
+            off += K
+        return out, dict(st, N=N, instances=len(idx), cells=int(sum(p["h"].size for p in probs)))
+
+    def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, **kw):
+        """Returns (list of phi [K][2][L+1] per problem, list of per-wave stats)."""
+        solve_kw = dict(method=method, tol=tol, max_iterations=max_iterations, **kw)
+        results = [None] * len(self.problems)
+        stats = []
+        with cf.ThreadPoolExecutor(max_workers=self.max_streams) as ex:
+            for out, st in ex.map(lambda w: self._run_wave(w, solve_kw), self.waves):
+                for i, phi in out.items():
+                    results[i] = phi
+                stats.append(st)
+        return results, stats

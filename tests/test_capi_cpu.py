@@ -62,3 +62,17 @@ def test_create_rejects_bad_descriptors_before_any_cuda_call(lib):
         assert rc == binding.EINVAL and not out.value, bad
     rc, out = create(n_ordinates=2 * binding.MAX_ORDINATES, n_moments=2)
     assert rc == binding.ENOTSUP and not out.value
+
+
+def test_batch_wave_planning():
+    # host logic of the batch driver: grouping by (N, L) and memory-bounded waves
+    from paper_1907_13013_gb300 import batch, inputs
+    probs = inputs.batch_slabs(40, seed=2, K_range=(100, 5000))
+    budget = 2 << 30
+    waves = batch.plan_waves(probs, budget, "mixed")
+    seen = sorted(i for _, _, idx in waves for i in idx)
+    assert seen == list(range(len(probs)))
+    for N, L, idx in waves:
+        assert all(probs[i]["N"] == N and probs[i]["L"] == L for i in idx)
+        total = sum(batch.factor_bytes(probs[i]["h"].size, N, "mixed") for i in idx)
+        assert total <= budget or len(idx) == 1

@@ -450,3 +450,21 @@ def test_scale_workload_full_size(binding):
     assert st["status"] == 0 and np.all(np.isfinite(phi))
     for r in (0, 17, 63):
         assert balance_defect(p, phi, r) < 1e-7, (r, balance_defect(p, phi, r), st)
+
+
+# ---------------------------------------------------------------------------
+# Batching workload (the recipe of inputs.batch_slabs at reduced sizes): uneven K
+# and N in {16, 32, 64, 128}, grouped by N into contexts on concurrent streams.
+# ---------------------------------------------------------------------------
+def test_batching_workload_reduced(binding):
+    from paper_1907_13013_gb300 import batch
+    probs = inputs.batch_slabs(48, seed=1, K_range=(20, 160))
+    solver = batch.BatchSolver(probs, precision="mixed", laplacian="wfd", budget_bytes=64 << 20)
+    assert len(solver.waves) > 4  # the small budget forces several waves per group
+    phis, stats = solver.solve(tol=1e-12, max_iterations=200)
+    assert sum(s["instances"] for s in stats) == len(probs)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(probs), 8, replace=False):
+        p = probs[i]
+        ref = oit.direct_solve(p)
+        assert relerr(phis[i], ref) < TOL, (i, p["N"], p["h"].size)
