@@ -59,7 +59,7 @@ extern "C" {
 
 enum fpsa_laplacian { FPSA_LAPLACIAN_MPD = 0, FPSA_LAPLACIAN_WFD = 1 };
 enum fpsa_precision { FPSA_PRECISION_FP64 = 0, FPSA_PRECISION_MIXED = 1 };
-enum fpsa_method    { FPSA_METHOD_SI = 0, FPSA_METHOD_FPSA = 1 };
+enum fpsa_method    { FPSA_METHOD_SI = 0, FPSA_METHOD_FPSA = 1, FPSA_METHOD_GMRES = 2 };
 enum fpsa_mem       { FPSA_MEM_HOST = 0, FPSA_MEM_DEVICE = 1 };
 
 typedef struct fpsa_ctx fpsa_ctx;
@@ -80,14 +80,17 @@ typedef struct {
 typedef struct {
     int32_t method;           /* enum fpsa_method */
     int32_t max_iterations;   /* cap on transport sweeps (FP64) / refinement steps (MIXED) */
-    double tol;               /* stop when max|phi_0^{m+1}-phi_0^m| / max|phi_0^{m+1}| < tol,
-                                 the worst instance/right-hand side deciding (Eq. iterate) */
+    double tol;               /* SI / FPSA: stop when max|phi_0^{m+1}-phi_0^m| / max|phi_0^{m+1}| < tol,
+                                 the worst instance/right-hand side deciding (Eq. iterate);
+                                 GMRES: stop when every (rhs, instance) system has
+                                 ||b - (I-T) phi||_2 / ||b||_2 < tol on the moments */
     int32_t inner_iterations; /* MIXED: FP32 FPSA iterations per FP64 refinement step (0 = default 4) */
     double inner_tol;         /* MIXED: inner relative-change target (0 = default 1e-5) */
     int32_t check_every;      /* test convergence every this many iterations (0 = 1) */
     int32_t contraction;      /* MIXED inner contractions: 0 = auto (tensor cores when N is a
                                  multiple of 16 and <= 128), 1 = SIMT FP32, 2 = tensor cores
                                  (tcgen05, split BF16 x3; FPSA_ENOTSUP if N does not qualify) */
+    int32_t restart;          /* GMRES restart length m (0 = 30) */
 } fpsa_opts;
 
 typedef struct {
@@ -147,6 +150,11 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s,
                 const double *q, int32_t mem);
 
 /* Iterate to convergence (opts may be NULL: FPSA, tol 1e-10, 10000 iterations).
+ * Methods: source iteration (Eq. trsi); FPSA source iteration (Eqs. predict,
+ * correct, iterate); GMRES(m) on the moment equation (I - T) phi = b with right
+ * preconditioning by the FP correction, (I - T)(I + C) u = b, phi = (I + C) u,
+ * T = D L^{-1} M Sigma, C = D F^{-1} (m (x) M Sigma) (Sec. 4's FPSA-preconditioned
+ * GMRES; FP64 precision only, FPSA_ENOTSUP with MIXED).
  * phi: output [R][sumK][2][L+1]; phi0: optional initial moments, same layout
  * (NULL = zero). Both pointers are of kind mem. stats may be NULL.
  * Returns FPSA_ENOTCONV (with phi holding the last iterate) if max_iterations

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libfpsa.so")
 OK, EINVAL, ENOMEM, ENONFINITE, ENOTCONV, EPIVOT, ETIMEOUT, ECUDA, ENOTSUP, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 LAPLACIAN = {"mpd": 0, "wfd": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
-METHOD = {"si": 0, "fpsa": 1}
+METHOD = {"si": 0, "fpsa": 1, "gmres": 2}
 CONTRACTION = {"auto": 0, "simt": 1, "tensor": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
 MAX_ORDINATES = 256
@@ -37,7 +37,7 @@ class FpsaDesc(ctypes.Structure):
 class FpsaOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("inner_iterations", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("check_every", ctypes.c_int32), ("contraction", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("contraction", ctypes.c_int32), ("restart", ctypes.c_int32)]
 
 
 class FpsaStats(ctypes.Structure):
@@ -164,7 +164,8 @@ class Context:
         self._check(self._lib.fpsa_set_xs(self._h, ps[0][0], ps[1][0], ps[2][0], mems.pop()), "fpsa_set_xs")
 
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, out=None, phi0=None,
-              inner_iterations=0, inner_tol=0.0, check_every=1, raise_on_notconv=True, contraction="auto"):
+              inner_iterations=0, inner_tol=0.0, check_every=1, raise_on_notconv=True, contraction="auto",
+              restart=0):
         """Returns (phi, stats dict). phi [R][sumK][2][L+1]: into `out` if given (numpy or torch
         cuda), else a new numpy array."""
         if out is None:
@@ -177,7 +178,7 @@ class Context:
         else:
             p0 = None
         o = FpsaOpts(METHOD[method], int(max_iterations), float(tol), int(inner_iterations), float(inner_tol),
-                     int(check_every), CONTRACTION[contraction])
+                     int(check_every), CONTRACTION[contraction], int(restart))
         st = FpsaStats()
         rc = self._lib.fpsa_solve(self._h, ctypes.byref(o), po, p0, mem, ctypes.byref(st))
         if rc != OK and not (rc == ENOTCONV and not raise_on_notconv):
@@ -211,7 +212,7 @@ class Context:
             J = np.zeros((self.R, self.B))
             pj = J.ctypes.data
         o = FpsaOpts(METHOD[method], int(max_iterations), float(tol), int(inner_iterations), 0.0, int(check_every),
-                     CONTRACTION[contraction])
+                     CONTRACTION[contraction], 0)
         st = FpsaStats()
         rc = self._lib.fpsa_adjoint(self._h, ctypes.byref(o), pg, pt, ps, pj, mem, ctypes.byref(st))
         self._check(rc, "fpsa_adjoint")

@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -19,6 +21,7 @@
 #include "kernels.cuh"
 #include "tc_contract.cuh"
 #include "bcr_large.cuh"
+#include "gmres.cuh"
 
 using namespace fpsa;
 
@@ -75,6 +78,14 @@ struct fpsa_ctx {
     double *d_Pm = nullptr, *d_cJ = nullptr;                              // (-1)^l P_l(mu_n), exit-current weights
     double *d_J = nullptr, *d_grad_t = nullptr, *d_grad_s = nullptr;
 
+    // GMRES (FP64 path): Krylov basis and work vectors, allocated at first use
+    int gm_restart = 0;
+    double *gm_V = nullptr, *gm_u = nullptr, *gm_w = nullptr, *gm_b = nullptr;
+    double *gm_partial = nullptr, *gm_dots = nullptr, *gm_coef = nullptr, *gm_alpha = nullptr;
+    long long *gm_seg_begin = nullptr, *gm_seg_end = nullptr;
+    int32_t *gm_col_sys = nullptr;
+    int gm_nchunks = 0;
+
     PathBuffers<double> p64;  // FP64 path; for MIXED: FP64 tables, psi (refined iterate), phi
     PathBuffers<float> p32;   // MIXED: the FP32 inner FPSA solve
     // tensor-core contractions of the FP32 inner solve
@@ -94,6 +105,23 @@ struct fpsa_ctx {
 namespace {
 
 thread_local std::string g_create_error;  // why the last fpsa_create on this thread failed
+
+// The dynamic shared-memory limit of a kernel is process-wide state, while
+// contexts with different N (possibly on different host threads) need different
+// sizes: only ever raise it, under a lock, so no context lowers another's.
+std::mutex g_attr_mutex;
+std::map<std::pair<const void *, int>, int> g_attr_max;
+
+cudaError_t raise_smem_limit(const void *func, int bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    int &cur = g_attr_max[{func, dev}];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 // Launch bracket: counts every launch of a kernel class and, while profiling is
 // on, records a CUDA event pair around it on the context stream.
@@ -217,18 +245,20 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         }
         if (!p.inv_scratch.empty()) {
             CK(dalloc(ctx, &p.inv_amax, kLargeChunk));
-            CK(cudaFuncSetAttribute(k_binv_smem_rm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+            CK(raise_smem_limit((const void *)k_binv_smem_rm<T>, (int)kSmemLimit));
         }
-        CK(cudaFuncSetAttribute(k_bcr_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_smem<T>(g.N)));
+        CK(raise_smem_limit((const void *)k_bcr_schur<T>, (int)schur_smem<T>(g.N)));
     }
     {
         const int cs = (int)contract_smem<T>(g.N);
-        CK(cudaFuncSetAttribute(k_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
-        CK(cudaFuncSetAttribute(k_fp_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
-        CK(cudaFuncSetAttribute(k_update_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
-        CK(cudaFuncSetAttribute(k_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        CK(raise_smem_limit((const void *)k_scatter<T>, cs));
+        CK(raise_smem_limit((const void *)k_fp_rhs<T>, cs));
+        CK(raise_smem_limit((const void *)k_update_scatter<T>, cs));
+        CK(raise_smem_limit((const void *)k_expand<T>, cs));
+        CK(raise_smem_limit((const void *)k_fp_rhs_moments<T>, cs));
+        CK(raise_smem_limit((const void *)k_moments_axpy<T>, cs));
         if (sizeof(T) == 8)
-            CK(cudaFuncSetAttribute(k_mixed_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+            CK(raise_smem_limit((const void *)k_mixed_residual, cs));
     }
     if (full && ctx->precision == FPSA_PRECISION_MIXED) {
         CK(dalloc(ctx, &p.qang, ang));
@@ -244,8 +274,7 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     CK(cudaMemcpy(p.DT, DT.data(), N * N * sizeof(T), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p.MT, MT.data(), N * N * sizeof(T), cudaMemcpyHostToDevice));
     if (invert_smem<T>(g.N) <= kSmemLimit)
-        CK(cudaFuncSetAttribute(k_bcr_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)invert_smem<T>(g.N)));
+        CK(raise_smem_limit((const void *)k_bcr_invert<T>, (int)invert_smem<T>(g.N)));
     return FPSA_OK;
 }
 
@@ -340,8 +369,8 @@ int setup_tc(fpsa_ctx *ctx) {
     CK(dalloc(ctx, &ctx->d_tc_ops, 4 * nn * sizeof(__nv_bfloat16)));
     CK(cudaMemcpy(ctx->d_tc_ops, ops.data(), ops.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
     const int smem = (int)tc::Plan::make(N).total;
-    CK(cudaFuncSetAttribute(k_tc_fp_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CK(cudaFuncSetAttribute(k_tc_update_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(raise_smem_limit((const void *)k_tc_fp_rhs, smem));
+    CK(raise_smem_limit((const void *)k_tc_update_scatter, smem));
     int nsm = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_update_scatter, 128, smem));
@@ -668,6 +697,294 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     return status;
 }
 
+
+// Lazily allocate the GMRES work space for restart length m.
+int gmres_alloc(fpsa_ctx *ctx, int m) {
+    if (ctx->gm_restart >= m) return FPSA_OK;
+    const Geometry &g = ctx->geo;
+    const size_t n = (size_t)g.R * g.sumK * 2 * g.N;
+    const int nsys = g.R * g.B;
+    if (ctx->gm_V) {  // grow: release the old basis (the allocations list keeps the pointer)
+        CK(cudaFree(ctx->gm_V));
+        ctx->allocs.erase(std::find(ctx->allocs.begin(), ctx->allocs.end(), (void *)ctx->gm_V));
+        ctx->gm_V = nullptr;
+    }
+    CK(dalloc(ctx, &ctx->gm_V, (size_t)(m + 1) * n));
+    if (!ctx->gm_u) {
+        CK(dalloc(ctx, &ctx->gm_u, n));
+        CK(dalloc(ctx, &ctx->gm_w, n));
+        CK(dalloc(ctx, &ctx->gm_b, n));
+        CK(dalloc(ctx, &ctx->gm_seg_begin, nsys));
+        CK(dalloc(ctx, &ctx->gm_seg_end, nsys));
+        CK(dalloc(ctx, &ctx->gm_col_sys, (size_t)g.R * g.sumK * 2));
+        std::vector<long long> sb(nsys), se(nsys);
+        std::vector<int32_t> cs((size_t)g.R * g.sumK * 2);
+        long long maxlen = 0;
+        for (int r = 0; r < g.R; ++r)
+            for (int b = 0; b < g.B; ++b) {
+                const int s = r * g.B + b;
+                sb[s] = ((long long)r * g.sumK + g.off[b]) * 2 * g.N;
+                se[s] = sb[s] + (long long)g.K[b] * 2 * g.N;
+                maxlen = std::max(maxlen, se[s] - sb[s]);
+                for (int c = 0; c < g.K[b]; ++c)
+                    for (int a = 0; a < 2; ++a) cs[((size_t)r * g.sumK + g.off[b] + c) * 2 + a] = s;
+            }
+        CK(cudaMemcpy(ctx->gm_seg_begin, sb.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->gm_seg_end, se.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->gm_col_sys, cs.data(), cs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        ctx->gm_nchunks = (int)((maxlen + kDotChunk - 1) / kDotChunk);
+    }
+    if (ctx->gm_partial) {
+        for (double *q : {ctx->gm_partial, ctx->gm_dots, ctx->gm_coef, ctx->gm_alpha}) {
+            CK(cudaFree(q));
+            ctx->allocs.erase(std::find(ctx->allocs.begin(), ctx->allocs.end(), (void *)q));
+        }
+    }
+    CK(dalloc(ctx, &ctx->gm_partial, (size_t)nsys * ctx->gm_nchunks * (m + 1)));
+    CK(dalloc(ctx, &ctx->gm_dots, (size_t)nsys * (m + 1)));
+    CK(dalloc(ctx, &ctx->gm_coef, (size_t)nsys * (m + 1)));
+    CK(dalloc(ctx, &ctx->gm_alpha, nsys));
+    ctx->gm_restart = m;
+    return FPSA_OK;
+}
+
+// out[s][i] = <V_i, w>_s for i < nv, all systems s; result copied to host hdots.
+int gm_dots(fpsa_ctx *ctx, const double *V, int nv, const double *w, std::vector<double> &hdots) {
+    const Geometry &g = ctx->geo;
+    const int nsys = g.R * g.B;
+    const size_t n = (size_t)g.R * g.sumK * 2 * g.N;
+    cudaStream_t st = ctx->stream;
+    {
+        Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
+        k_seg_dots<double><<<dim3(ctx->gm_nchunks, nsys), 256, 0, st>>>(V, n, nv, w, ctx->gm_seg_begin,
+                                                                      ctx->gm_seg_end, ctx->gm_nchunks,
+                                                                      ctx->gm_partial);
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
+        k_seg_dots_finish<<<(nsys * nv + 255) / 256, 256, 0, st>>>(ctx->gm_partial, nsys, ctx->gm_nchunks, nv,
+                                                                    ctx->gm_dots);
+    }
+    CK(cudaGetLastError());
+    hdots.resize((size_t)nsys * nv);
+    CK(cudaMemcpyAsync(hdots.data(), ctx->gm_dots, hdots.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return FPSA_OK;
+}
+
+// y = alpha_s y + sum_i coef[s][i] V_i (alpha NULL: y = sum ...), coefficients from the host.
+int gm_combine(fpsa_ctx *ctx, double *y, const std::vector<double> *alpha, const double *V, int nv,
+               const std::vector<double> &coef) {
+    const Geometry &g = ctx->geo;
+    const size_t n = (size_t)g.R * g.sumK * 2 * g.N;
+    cudaStream_t st = ctx->stream;
+    if (nv) CK(cudaMemcpyAsync(ctx->gm_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (alpha)
+        CK(cudaMemcpyAsync(ctx->gm_alpha, alpha->data(), alpha->size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    {
+        Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
+        k_seg_combine<double><<<4 * 152, 256, 0, st>>>(y, alpha ? ctx->gm_alpha : nullptr, V, n, nv, ctx->gm_coef,
+                                                       ctx->gm_col_sys, g.N, n);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));  // the host vectors are reused right away
+    return FPSA_OK;
+}
+
+// out = (I - T)(I + C) v  (FP64 path buffers; out may not alias v)
+int gm_apply(fpsa_ctx *ctx, PathBuffers<double> &p, const double *v, double *out) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N;
+    cudaStream_t st = ctx->stream;
+    const size_t csm = contract_smem<double>(N);
+    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);
+        k_fp_rhs_moments<double><<<cgrid, kContractThreads, csm, st>>>(v, p.sigma_s, ctx->d_h, p.MT, p.rhs, N, g.sumK);
+    }
+    int rc = bcr_solve(ctx, p, p.rhs);
+    if (rc) return rc;
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);  // out = z = v + D upsilon;  q = M Sigma z
+        k_update_scatter<double><<<cgrid, kContractThreads, csm, st>>>(
+            p.ybuf, v, out, p.sigma_s, (const double *)nullptr, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
+            (unsigned long long *)nullptr, N, g.sumK, (const double *)nullptr);
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_SWEEP);
+        k_sweep<double, kSweepThreads><<<dim3(N, g.B, g.R), kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu,
+                                                                                  ctx->d_off, ctx->d_K, N, g.sumK);
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);  // out = z - D psi
+        k_moments_axpy<double><<<cgrid, kContractThreads, csm, st>>>(p.psi, out, -1.0, p.DT, out, N, g.sumK);
+    }
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
+// GMRES(m) with right FPSA preconditioning, FP64, batched over (rhs, instance) systems.
+int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats,
+                const double *Qm, const double *Qa) {
+    PathBuffers<double> &p = ctx->p64;
+    const Geometry &g = ctx->geo;
+    const int N = g.N, L1 = g.L1, nsys = g.R * g.B;
+    const int m = o.restart > 0 ? o.restart : 30;
+    const size_t n = (size_t)g.R * g.sumK * 2 * N, ncol = (size_t)g.R * g.sumK * 2;
+    cudaStream_t st = ctx->stream;
+    if (phi0) return fail(ctx, FPSA_ENOTSUP, "GMRES starts from zero (phi0 not supported)");
+    int rc = gmres_alloc(ctx, m);
+    if (rc) return rc;
+    const size_t csm = contract_smem<double>(N);
+    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    // b = D L^{-1} (M Q + q_ang)
+    CK(cudaMemsetAsync(ctx->gm_u, 0, n * sizeof(double), st));
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);
+        k_scatter<double><<<cgrid, kContractThreads, csm / 2, st>>>(ctx->gm_u, p.sigma_s, Qm, p.MT, p.q, N, g.sumK, Qa);
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_SWEEP);
+        k_sweep<double, kSweepThreads><<<dim3(N, g.B, g.R), kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu,
+                                                                                  ctx->d_off, ctx->d_K, N, g.sumK);
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);
+        k_moments_axpy<double><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const double *)nullptr, 1.0, p.DT,
+                                                                     ctx->gm_b, N, g.sumK);
+    }
+    CK(cudaGetLastError());
+    std::vector<double> dots, bnorm(nsys), coef, alpha(nsys);
+    rc = gm_dots(ctx, ctx->gm_b, 1, ctx->gm_b, dots);
+    if (rc) return rc;
+    for (int s = 0; s < nsys; ++s) bnorm[s] = std::sqrt(dots[s]);
+    int it = 0, sweeps = 1, status = FPSA_ENOTCONV;
+    double worst = INFINITY;
+    double *V = ctx->gm_V;
+    while (it < o.max_iterations) {
+        // r = b - A' u  (u = 0 on the first cycle)
+        if (it == 0) {
+            CK(cudaMemcpyAsync(V, ctx->gm_b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        } else {
+            rc = gm_apply(ctx, p, ctx->gm_u, ctx->gm_w);
+            if (rc) return rc;
+            ++sweeps;
+            std::vector<double> one(nsys, -1.0), c1(nsys, 1.0);
+            CK(cudaMemcpyAsync(V, ctx->gm_b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            rc = gm_combine(ctx, V, &c1, ctx->gm_w, 1, one);  // V_0 = b - A' u
+            if (rc) return rc;
+        }
+        rc = gm_dots(ctx, V, 1, V, dots);
+        if (rc) return rc;
+        std::vector<double> beta(nsys);
+        worst = 0.0;
+        for (int s = 0; s < nsys; ++s) {
+            beta[s] = std::sqrt(dots[s]);
+            worst = std::max(worst, bnorm[s] > 0 ? beta[s] / bnorm[s] : 0.0);
+            alpha[s] = beta[s] > 0 ? 1.0 / beta[s] : 0.0;
+        }
+        if (!std::isfinite(worst)) return fail(ctx, FPSA_ENONFINITE, "non-finite GMRES residual");
+        if (worst < o.tol) { status = FPSA_OK; break; }
+        rc = gm_combine(ctx, V, &alpha, V, 0, coef);  // V_0 = r / beta
+        if (rc) return rc;
+        // Arnoldi with classical Gram-Schmidt applied twice, Givens rotations per system
+        std::vector<double> H((size_t)nsys * (m + 1) * m, 0.0), cs((size_t)nsys * m), sn((size_t)nsys * m),
+            gvec((size_t)nsys * (m + 1), 0.0);
+        for (int s = 0; s < nsys; ++s) gvec[(size_t)s * (m + 1)] = beta[s];
+        auto Hs = [&](int s, int i, int j) -> double & { return H[((size_t)s * (m + 1) + i) * m + j]; };
+        int j = 0, jdone = 0;
+        for (j = 0; j < m && it < o.max_iterations; ++j) {
+            double *Vj = V + (size_t)j * n, *w = ctx->gm_w;
+            rc = gm_apply(ctx, p, Vj, w);
+            if (rc) return rc;
+            ++sweeps;
+            std::vector<double> hsum((size_t)nsys * (j + 1), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                rc = gm_dots(ctx, V, j + 1, w, dots);
+                if (rc) return rc;
+                std::vector<double> neg(dots.size());
+                for (size_t q = 0; q < dots.size(); ++q) {
+                    neg[q] = -dots[q];
+                    hsum[q] += dots[q];
+                }
+                std::vector<double> c1(nsys, 1.0);
+                rc = gm_combine(ctx, w, &c1, V, j + 1, neg);
+                if (rc) return rc;
+            }
+            rc = gm_dots(ctx, w, 1, w, dots);
+            if (rc) return rc;
+            worst = 0.0;
+            for (int s = 0; s < nsys; ++s) {
+                const double hnext = std::sqrt(dots[s]);
+                for (int i = 0; i <= j; ++i) Hs(s, i, j) = hsum[(size_t)s * (j + 1) + i];
+                for (int i = 0; i < j; ++i) {
+                    const double c = cs[(size_t)s * m + i], sv = sn[(size_t)s * m + i];
+                    const double t = c * Hs(s, i, j) + sv * Hs(s, i + 1, j);
+                    Hs(s, i + 1, j) = -sv * Hs(s, i, j) + c * Hs(s, i + 1, j);
+                    Hs(s, i, j) = t;
+                }
+                const double den = std::hypot(Hs(s, j, j), hnext);
+                const double c = den > 0 ? Hs(s, j, j) / den : 1.0, sv = den > 0 ? hnext / den : 0.0;
+                cs[(size_t)s * m + j] = c;
+                sn[(size_t)s * m + j] = sv;
+                Hs(s, j, j) = den;
+                double *gs = &gvec[(size_t)s * (m + 1)];
+                gs[j + 1] = -sv * gs[j];
+                gs[j] = c * gs[j];
+                worst = std::max(worst, bnorm[s] > 0 ? std::fabs(gs[j + 1]) / bnorm[s] : 0.0);
+                alpha[s] = hnext > 0 ? 1.0 / hnext : 0.0;
+            }
+            ++it;
+            jdone = j + 1;
+            if (!std::isfinite(worst)) return fail(ctx, FPSA_ENONFINITE, "non-finite GMRES residual");
+            if (worst < o.tol) break;
+            if (j + 1 < m) {  // V_{j+1} = w / h_{j+1,j}
+                CK(cudaMemcpyAsync(V + (size_t)(j + 1) * n, w, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                rc = gm_combine(ctx, V + (size_t)(j + 1) * n, &alpha, V, 0, coef);
+                if (rc) return rc;
+            }
+        }
+        // u += sum_i y_i V_i, y from the triangular least-squares system per system
+        std::vector<double> y((size_t)nsys * jdone, 0.0);
+        for (int s = 0; s < nsys; ++s)
+            for (int i = jdone - 1; i >= 0; --i) {
+                double acc = gvec[(size_t)s * (m + 1) + i];
+                for (int k2 = i + 1; k2 < jdone; ++k2) acc -= Hs(s, i, k2) * y[(size_t)s * jdone + k2];
+                y[(size_t)s * jdone + i] = Hs(s, i, i) != 0.0 ? acc / Hs(s, i, i) : 0.0;
+            }
+        std::vector<double> c1(nsys, 1.0);
+        rc = gm_combine(ctx, ctx->gm_u, &c1, V, jdone, y);
+        if (rc) return rc;
+        if (worst < o.tol) { status = FPSA_OK; break; }
+    }
+    // phi = (I + C) u
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);
+        k_fp_rhs_moments<double><<<cgrid, kContractThreads, csm, st>>>(ctx->gm_u, p.sigma_s, ctx->d_h, p.MT, p.rhs, N,
+                                                                      g.sumK);
+    }
+    rc = bcr_solve(ctx, p, p.rhs);
+    if (rc) return rc;
+    {
+        Launch L_(ctx, FPSA_PHASE_CONTRACT);
+        k_update_scatter<double><<<cgrid, kContractThreads, csm, st>>>(
+            p.ybuf, ctx->gm_u, p.phi, p.sigma_s, (const double *)nullptr, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
+            (unsigned long long *)nullptr, N, g.sumK, (const double *)nullptr);
+    }
+    CK(cudaGetLastError());
+    stats.iterations = it;
+    stats.outer_iterations = it;
+    stats.sweeps = sweeps;
+    stats.rel_change = worst;
+    if (phi_out)
+        CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(double), L1 * sizeof(double), ncol,
+                             mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (status == FPSA_ENOTCONV)
+        fail(ctx, FPSA_ENOTCONV, "GMRES not converged after " + std::to_string(it) + " iterations");
+    return status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -794,10 +1111,8 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             int nsm = 0, per_sm = 0;
             CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
             const int RC = solve_rc(g.R);
-            CK(cudaFuncSetAttribute(coop_kernel<float>(RC), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)solve_smem<float>(g.N, RC)));
-            CK(cudaFuncSetAttribute(coop_kernel<double>(RC), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)solve_smem<double>(g.N, RC)));
+            CK(raise_smem_limit((const void *)coop_kernel<float>(RC), (int)solve_smem<float>(g.N, RC)));
+            CK(raise_smem_limit((const void *)coop_kernel<double>(RC), (int)solve_smem<double>(g.N, RC)));
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<float>(RC), kSolveThreads,
                                                              solve_smem<float>(g.N, RC)));
             ctx->coop_grid[0] = std::max(1, std::min(per_sm, 4)) * nsm;
@@ -925,15 +1240,20 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
     if (!phi) return fail(ctx, FPSA_EINVAL, "null phi");
     if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
     if (!ctx->xs_ready) return fail(ctx, FPSA_ESTATE, "fpsa_set_xs must succeed before fpsa_solve");
-    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-10, 0, 0.0, 1, 0};
+    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-10, 0, 0.0, 1, 0, 0};
     if (opts) o = *opts;
-    if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA) return fail(ctx, FPSA_EINVAL, "bad method");
-    if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol");
+    if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA && o.method != FPSA_METHOD_GMRES)
+        return fail(ctx, FPSA_EINVAL, "bad method");
+    if (o.max_iterations < 1 || !(o.tol >= 0.0) || o.restart < 0) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol / restart");
+    if (o.method == FPSA_METHOD_GMRES && ctx->precision != FPSA_PRECISION_FP64)
+        return fail(ctx, FPSA_ENOTSUP, "GMRES is available in FP64 precision");
     CK(cudaSetDevice(ctx->device));
     fpsa_stats s{};
     const auto t0 = std::chrono::steady_clock::now();
     ctx->fwd_ready = false;
-    int rc = ctx->precision == FPSA_PRECISION_FP64
+    int rc = o.method == FPSA_METHOD_GMRES
+                 ? solve_gmres(ctx, o, phi0, mem, phi, s, ctx->p64.Q, nullptr)
+                 : ctx->precision == FPSA_PRECISION_FP64
                  ? solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s, (const double *)ctx->p64.Q, (const double *)nullptr)
                  : solve_mixed(ctx, o, phi0, mem, phi, s, ctx->p64.Q, nullptr);
     if (rc == FPSA_OK) {
@@ -958,9 +1278,12 @@ int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, do
     if (!dJ_dsigma_t || !dJ_dsigma_s) return fail(ctx, FPSA_EINVAL, "null gradient output");
     if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
     if (!ctx->fwd_ready) return fail(ctx, FPSA_ESTATE, "fpsa_adjoint needs a converged fpsa_solve since the last fpsa_set_xs");
-    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-12, 0, 0.0, 1, 0};
+    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-12, 0, 0.0, 1, 0, 0};
     if (opts) o = *opts;
-    if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA) return fail(ctx, FPSA_EINVAL, "bad method");
+    if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA && o.method != FPSA_METHOD_GMRES)
+        return fail(ctx, FPSA_EINVAL, "bad method");
+    if (o.method == FPSA_METHOD_GMRES && ctx->precision != FPSA_PRECISION_FP64)
+        return fail(ctx, FPSA_ENOTSUP, "GMRES is available in FP64 precision");
     if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol");
     CK(cudaSetDevice(ctx->device));
     const Geometry &g = ctx->geo;
@@ -989,7 +1312,9 @@ int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, do
     CK(cudaGetLastError());
     fpsa_stats s{};
     // A x = Pi W^{-1} dJ/dpsi with the forward machinery and factors
-    int rc = ctx->precision == FPSA_PRECISION_FP64
+    int rc = o.method == FPSA_METHOD_GMRES
+                 ? solve_gmres(ctx, o, nullptr, mem, nullptr, s, nullptr, ctx->d_adj_src)
+                 : ctx->precision == FPSA_PRECISION_FP64
                  ? solve_fp64(ctx, ctx->p64, o, nullptr, mem, nullptr, s, (const double *)nullptr,
                               (const double *)ctx->d_adj_src)
                  : solve_mixed(ctx, o, nullptr, mem, nullptr, s, nullptr, ctx->d_adj_src);

@@ -468,3 +468,42 @@ def test_batching_workload_reduced(binding):
         p = probs[i]
         ref = oit.direct_solve(p)
         assert relerr(phis[i], ref) < TOL, (i, p["N"], p["h"].size)
+
+
+# ---------------------------------------------------------------------------
+# FPSA-preconditioned GMRES(m) (FP64), against the oracle's GMRES and direct solve.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+@pytest.mark.parametrize("N,K,seed,restart", [(8, 30, 71, 30), (16, 60, 72, 5), (64, 40, 73, 30)])
+def test_gmres_against_oracle(binding, lap, N, K, seed, restart):
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel="srk", thick=(5, 300), c=(0.9, 0.999))
+    ctx = binding.context_for(p, laplacian=lap)
+    phi, st = ctx.solve("gmres", tol=1e-12, max_iterations=500, restart=restart)
+    ref = oit.direct_solve(p)
+    assert relerr(phi[0], ref) < TOL
+    _, n_or = oit.fpsa_gmres(p, lap, restart=restart, tol=1e-12)
+    assert abs(st["iterations"] - n_or) <= 2, (st["iterations"], n_or)
+
+
+def test_gmres_batch_systems_and_adjoint(binding):
+    R = 2
+    probs = [inputs.random_slab(K, 16, 15, seed=80 + i, kernel="hg", c=(0.8, 0.99), nrhs=R) for i, K in enumerate([25, 9])]
+    ctx = binding.context_for(probs)
+    phi, st = ctx.solve("gmres", tol=1e-12, max_iterations=300)
+    off = 0
+    for p in probs:
+        K = p["h"].size
+        for r in range(R):
+            assert relerr(phi[r, off:off + K], oit.direct_solve(dict(p, Q=p["Q"][r]))) < TOL
+        off += K
+    gt, gs, J, _ = ctx.adjoint(method="gmres", tol=1e-13)   # adjoint solve by GMRES too
+    gt2, gs2, _, _ = ctx.adjoint(method="fpsa", tol=1e-13)
+    assert np.abs(gt - gt2).max() < 1e-8 * np.abs(gt2).max()
+
+
+def test_gmres_precision_rules(binding):
+    p = inputs.random_slab(10, 8, 7, seed=90)
+    ctx = binding.context_for(p, precision="mixed")
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.solve("gmres", tol=1e-10)
+    assert e.value.code == binding.ENOTSUP
