@@ -8,7 +8,10 @@ A slab problem is a dict with
   Q[K,2,L+1]      external source as Legendre moments at the two LD nodes; the
                   angular source is q_n = sum_l (2l+1)/2 P_l(mu_n) Q_l, so an
                   isotropic scalar source of strength S has Q_0 = S (q_n = S/2)
-  bc              'vacuum' (default) or 'reflective'
+  bc              'vacuum' (default), 'reflective', or a (left, right) pair of them
+  psi_inc         optional (2, N) incoming angular flux at the vacuum edges (row 0:
+                  left edge, read for mu > 0; row 1: right edge, read for mu < 0);
+                  absent = no incoming flux (Eq. trans-equation-bc)
 The state of every iteration is the flux moments phi[K,2,L+1] at the LD nodes.
 
 Convergence test (Eq. iterate): the paper iterates while
@@ -44,18 +47,31 @@ def scattering_source(M, sigma_s, phi, Q=None):
 
 
 def _streaming_inverse(prob, mu):
-    """Return a function q -> L_h^{-1} q (Eq. trsi left-hand side).
+    """Return a function (q, incident) -> L_h^{-1} q (Eq. trsi left-hand side) with
+    the problem's incoming boundary fluxes when incident is True (the source
+    sweeps) and none when False (sweeps of an error or Krylov vector).
 
-    Vacuum: the upwind sweep. Reflective: a sparse LU of the global streaming
-    matrix (the sweep would need lagged boundary values there).
+    Both edges vacuum: the upwind sweep. A reflective edge: a sparse LU of the
+    global streaming matrix (the sweep would need lagged boundary values there).
     """
     h, st = prob["h"], prob["sigma_t"]
-    if prob.get("bc", "vacuum") == "vacuum":
-        return lambda q: tr.sweep(mu, st, h, q)
+    bc = tr.bc_sides(prob.get("bc", "vacuum"))
+    inc = prob.get("psi_inc")
     K, N = h.size, mu.size
+    if bc == ("vacuum", "vacuum"):
+        def sweep(q, incident=False):
+            if incident and inc is not None:
+                return tr.sweep(mu, st, h, q, psi_in_left=inc[0], psi_in_right=inc[1])
+            return tr.sweep(mu, st, h, q)
+        return sweep
     Kc = st[:, None, None] * np.eye(N)[None]
-    lu = spla.splu(tr.assemble(mu, h, Kc, bc=prob["bc"]))
-    return lambda q: lu.solve(tr.mass_weight(h, q).ravel()).reshape(K, 2, N)
+    lu = spla.splu(tr.assemble(mu, h, Kc, bc=bc))
+    src = tr.incident_source(mu, K, inc, bc)
+
+    def solve(q, incident=False):
+        rhs = tr.mass_weight(h, q) + (src if incident else 0.0)
+        return lu.solve(rhs.ravel()).reshape(K, 2, N)
+    return solve
 
 
 def fp_matrix(prob, mu, w, laplacian="mpd"):
@@ -100,7 +116,7 @@ def source_iteration(prob, tol=1e-10, max_it=100000, phi0=None, history=False):
     phi = np.zeros((K, 2, L + 1)) if phi0 is None else np.array(phi0, dtype=np.float64)
     hist = []
     for it in range(1, max_it + 1):
-        psi = Linv(scattering_source(M, prob["sigma_s"], phi, prob["Q"]))
+        psi = Linv(scattering_source(M, prob["sigma_s"], phi, prob["Q"]), incident=True)
         phi_new = moments(D, psi)
         e = rel_change(phi_new, phi)
         hist.append(e)
@@ -136,7 +152,7 @@ def fpsa_source_iteration(prob, laplacian="mpd", tol=1e-10, max_it=10000, phi0=N
     hist = []
     psi = None
     for it in range(1, max_it + 1):
-        psi_half = Linv(scattering_source(M, prob["sigma_s"], phi, prob["Q"]))
+        psi_half = Linv(scattering_source(M, prob["sigma_s"], phi, prob["Q"]), incident=True)
         phi_half = moments(D, psi_half)
         r = scattering_source(M, prob["sigma_s"], phi_half - phi)      # S (psi^{m+1/2} - psi^m)
         ups = F.solve(tr.mass_weight(prob["h"], r).ravel()).reshape(K, 2, N)
@@ -156,14 +172,15 @@ def fpsa_source_iteration(prob, laplacian="mpd", tol=1e-10, max_it=10000, phi0=N
 
 
 def direct_solve(prob, return_psi=False):
-    """The discrete solution itself: (L_h - S_h) psi = m q by sparse LU (the fixed point that
-    SI and FPSA converge to; unique for sigma_a > 0)."""
+    """The discrete solution itself: (L_h - S_h) psi = m q + (incoming boundary fluxes) by
+    sparse LU (the fixed point that SI and FPSA converge to; unique for sigma_a > 0)."""
     N, L = prob["N"], prob["L"]
     mu, w, D, M = tables(N, L)
     K = prob["h"].size
     A = transport_matrix(prob, mu, w)
     b = tr.mass_weight(prob["h"], scattering_source(M, np.zeros_like(prob["sigma_s"]),
-                                                   np.zeros((K, 2, L + 1)), prob["Q"]))
+                                                   np.zeros((K, 2, L + 1)), prob["Q"])) \
+        + tr.incident_source(mu, K, prob.get("psi_inc"), prob.get("bc", "vacuum"))
     psi = spla.splu(A).solve(b.ravel()).reshape(K, 2, N)
     phi = moments(D, psi)
     return (phi, psi) if return_psi else phi
@@ -203,7 +220,7 @@ def fpsa_gmres(prob, laplacian="mpd", restart=30, tol=1e-10, max_it=10000, histo
         z = u + C(u)
         return z - T(z)
 
-    b = moments(D, Linv(scattering_source(M, np.zeros_like(ss), np.zeros(shape), prob["Q"])))
+    b = moments(D, Linv(scattering_source(M, np.zeros_like(ss), np.zeros(shape), prob["Q"]), incident=True))
     bnorm = np.linalg.norm(b)
     u = np.zeros(shape)
     hist = []

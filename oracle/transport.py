@@ -86,14 +86,28 @@ def sweep(mu, sigma_t, h, q, psi_in_left=None, psi_in_right=None):
     return psi
 
 
+def bc_sides(bc):
+    """(left, right) edge conditions from 'vacuum', 'reflective' or a pair of them."""
+    if isinstance(bc, str):
+        bc = (bc, bc)
+    left, right = bc
+    for side in (left, right):
+        if side not in ("vacuum", "reflective"):
+            raise ValueError(f"unknown boundary condition {side!r}")
+    return left, right
+
+
 def assemble(mu, h, Kcell, bc="vacuum"):
     """Global sparse matrix of  mu d/dz + K  in LD (module docstring), shape (2KN, 2KN).
 
-    Kcell: per-cell angular matrices, shape (K, N, N). bc: 'vacuum' (no incoming
-    flux; Eq. trans-equation-bc with psi_L = psi_R = 0) or 'reflective'
-    (incoming psi(mu) = outgoing psi(-mu) at both edges; not in the paper, used
-    only to realise infinite-medium special cases in the tests).
+    Kcell: per-cell angular matrices, shape (K, N, N). bc (per edge, see
+    ``bc_sides``): 'vacuum' (the incoming flux is a given boundary value, which
+    belongs to the right-hand side -- zero in Eq. trans-equation-bc; a beam sets
+    one ordinate, see ``incident_source``) or 'reflective' (incoming psi(mu) =
+    outgoing psi(-mu) at that edge: the infinite-medium and symmetric-slab special
+    cases of the tests and the mirrored half-slab).
     """
+    left, right = bc_sides(bc)
     K, N, _ = Kcell.shape
     rows, cols, vals = [], [], []
 
@@ -119,17 +133,50 @@ def assemble(mu, h, Kcell, bc="vacuum"):
             if mu[n] > 0:
                 if i > 0:
                     rows.append([idx(i, 0, n)]); cols.append([idx(i - 1, 1, n)]); vals.append([-mu[n]])
-                elif bc == "reflective":
+                elif left == "reflective":
                     rows.append([idx(0, 0, n)]); cols.append([idx(0, 0, N - 1 - n)]); vals.append([-mu[n]])
             else:
                 if i < K - 1:
                     rows.append([idx(i, 1, n)]); cols.append([idx(i + 1, 0, n)]); vals.append([mu[n]])
-                elif bc == "reflective":
+                elif right == "reflective":
                     rows.append([idx(K - 1, 1, n)]); cols.append([idx(K - 1, 1, N - 1 - n)]); vals.append([mu[n]])
     A = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(2 * K * N, 2 * K * N))
     A.sum_duplicates()
     return A
+
+
+def incident_source(mu, K, psi_inc, bc="vacuum"):
+    """Right-hand-side contribution of given incoming boundary fluxes, shape (K, 2, N).
+
+    psi_inc: shape (2, N), the incoming angular flux at the left edge (row 0,
+    read for mu_n > 0) and at the right edge (row 1, read for mu_n < 0). In the
+    cell equations of the module docstring the inflow enters as |mu| psi_in at
+    the upwind node of the boundary cell. Reflective edges take no given inflow.
+    """
+    left, right = bc_sides(bc)
+    N = mu.size
+    out = np.zeros((K, 2, N))
+    if psi_inc is None:
+        return out
+    psi_inc = np.asarray(psi_inc, dtype=np.float64)
+    pos, neg = mu > 0, mu < 0
+    if left == "vacuum":
+        out[0, 0, pos] = mu[pos] * psi_inc[0, pos]
+    if right == "vacuum":
+        out[K - 1, 1, neg] = -mu[neg] * psi_inc[1, neg]
+    return out
+
+
+def beam_incident(mu, w, side="left"):
+    """Unit beam: unit incoming partial current carried by the most normal incoming
+    ordinate only, psi = 1 / (w_n |mu_n|) (the paper's beam source of Sec. 4 gives
+    no formula; this is the reading). Returns psi_inc of shape (2, N)."""
+    N = mu.size
+    out = np.zeros((2, N))
+    n = N - 1 if side == "left" else 0
+    out[0 if side == "left" else 1, n] = 1.0 / (w[n] * abs(mu[n]))
+    return out
 
 
 def mass_weight(h, q):
