@@ -352,6 +352,9 @@ def main():
                    "tol": TOL, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set (262 MB FP64 factors) larger than L2; no flush"},
         "cell_angles_per_s": dev_stats["cell_angles"] * world * args.steps / (ms * 1e-3),
+        # the same numerator over the sweep kernels' own event time
+        "sweep_cell_angles_per_s": (dev_stats["cell_angles"] * world * args.steps
+                                    / (phases["sweep"]["ms"] * 1e-3) if phases.get("sweep") else None),
         "iterations": dev_stats["iterations"], "oracle_iterations_1e-10": its_ref,
         "setup_ms": dev_stats["setup_ms"], "solve_ms": dev_stats["solve_ms"],
         "max_rel_err_vs_oracle": rel_err,

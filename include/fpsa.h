@@ -61,6 +61,10 @@ enum fpsa_laplacian { FPSA_LAPLACIAN_MPD = 0, FPSA_LAPLACIAN_WFD = 1 };
 enum fpsa_precision { FPSA_PRECISION_FP64 = 0, FPSA_PRECISION_MIXED = 1 };
 enum fpsa_method    { FPSA_METHOD_SI = 0, FPSA_METHOD_FPSA = 1, FPSA_METHOD_GMRES = 2 };
 enum fpsa_mem       { FPSA_MEM_HOST = 0, FPSA_MEM_DEVICE = 1 };
+/* Edge conditions. VACUUM: the incoming flux is given (zero unless set by
+ * fpsa_set_incident; Eq. trans-equation-bc). REFLECT: incoming psi(mu) = outgoing
+ * psi(-mu) at that edge (the symmetry plane of a slab twice as wide). */
+enum fpsa_bc        { FPSA_BC_VACUUM = 0, FPSA_BC_REFLECT = 1 };
 
 typedef struct fpsa_ctx fpsa_ctx;
 
@@ -75,19 +79,25 @@ typedef struct {
     int32_t precision;        /* enum fpsa_precision */
     int32_t device;           /* CUDA device ordinal */
     void *stream;             /* cudaStream_t the library launches on; NULL = legacy default */
+    const int32_t *bc;        /* host [B][2]: (left, right) enum fpsa_bc per instance; NULL = all vacuum */
 } fpsa_desc;
 
 typedef struct {
     int32_t method;           /* enum fpsa_method */
     int32_t max_iterations;   /* cap on transport sweeps (FP64) / refinement steps (MIXED) */
-    double tol;               /* SI / FPSA: stop when max|phi_0^{m+1}-phi_0^m| / max|phi_0^{m+1}| < tol,
-                                 the worst instance/right-hand side deciding (Eq. iterate);
-                                 GMRES: stop when every (rhs, instance) system has
+    double tol;               /* SI / FPSA, and every method in MIXED: stop when
+                                 max|phi_0^{m+1}-phi_0^m| / max|phi_0^{m+1}| < tol between
+                                 iterates (MIXED: between FP64 refinement steps), the worst
+                                 instance/right-hand side deciding (Eq. iterate);
+                                 GMRES in FP64: stop when every (rhs, instance) system has
                                  ||b - (I-T) phi||_2 / ||b||_2 < tol on the moments */
-    int32_t inner_iterations; /* MIXED: FP32 FPSA iterations per FP64 refinement step (0 = default 4) */
-    double inner_tol;         /* MIXED: inner relative-change target (0 = default 1e-5) */
+    int32_t inner_iterations; /* MIXED, SI / FPSA: FP32 iterations per FP64 refinement step
+                                 (0 = default 4); MIXED, GMRES: cap on the FP32 Krylov
+                                 iterations per refinement step (0 = the restart length) */
+    double inner_tol;         /* MIXED, GMRES: relative residual target of each FP32 inner
+                                 GMRES solve (0 = default 1e-5); unused otherwise */
     int32_t check_every;      /* test convergence every this many iterations (0 = 1) */
-    int32_t contraction;      /* MIXED inner contractions: 0 = auto (tensor cores when N is a
+    int32_t contraction;      /* MIXED inner SI / FPSA contractions: 0 = auto (tensor cores when N is a
                                  multiple of 16 and <= 128), 1 = SIMT FP32, 2 = tensor cores
                                  (tcgen05, split BF16 x3; FPSA_ENOTSUP if N does not qualify) */
     int32_t restart;          /* GMRES restart length m (0 = 30) */
@@ -95,7 +105,8 @@ typedef struct {
 
 typedef struct {
     int32_t status;           /* same as the return value of fpsa_solve */
-    int32_t iterations;       /* FP64: FPSA/SI iterations; MIXED: total inner iterations */
+    int32_t iterations;       /* FP64: FPSA/SI iterations (GMRES: Krylov iterations); MIXED:
+                                 total inner iterations (GMRES: inner Krylov iterations) */
     int32_t outer_iterations; /* MIXED: FP64 refinement steps; FP64: = iterations */
     int32_t sweeps;           /* transport sweeps launched (each covers all instances and rhs) */
     double rel_change;        /* last tested relative change of phi_0 */
@@ -149,12 +160,25 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *desc);
 int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s,
                 const double *q, int32_t mem);
 
+/* Given incoming angular fluxes at the vacuum edges, psi_inc [R][B][2][N] of kind
+ * mem: [r][b][0][n] is the inflow at the left edge (read for mu_n > 0), [r][b][1][n]
+ * at the right edge (read for mu_n < 0); other entries and reflective edges are
+ * ignored. A unit beam (Sec. 4's beam source) is 1/(w_n |mu_n|) on the most normal
+ * incoming ordinate. NULL clears them (no incoming flux). They enter the transport
+ * source of fpsa_solve only (fpsa_adjoint solves with homogeneous edges). Values are
+ * copied; a later fpsa_solve is needed before fpsa_adjoint. Host values must be
+ * finite (FPSA_ENONFINITE). */
+int fpsa_set_incident(fpsa_ctx *ctx, const double *psi_inc, int32_t mem);
+
 /* Iterate to convergence (opts may be NULL: FPSA, tol 1e-10, 10000 iterations).
  * Methods: source iteration (Eq. trsi); FPSA source iteration (Eqs. predict,
  * correct, iterate); GMRES(m) on the moment equation (I - T) phi = b with right
  * preconditioning by the FP correction, (I - T)(I + C) u = b, phi = (I + C) u,
  * T = D L^{-1} M Sigma, C = D F^{-1} (m (x) M Sigma) (Sec. 4's FPSA-preconditioned
- * GMRES; FP64 precision only, FPSA_ENOTSUP with MIXED).
+ * GMRES). MIXED runs every method inside FP64 iterative refinement of psi: SI and
+ * FPSA as inner_iterations FP32 iterations, GMRES as one FP32 GMRES(m) solve of the
+ * moment correction equation per refinement step (GMRES-IR) plus one sweep for the
+ * angular correction; GMRES with phi0 is FPSA_ENOTSUP in FP64.
  * phi: output [R][sumK][2][L+1]; phi0: optional initial moments, same layout
  * (NULL = zero). Both pointers are of kind mem. stats may be NULL.
  * Returns FPSA_ENOTCONV (with phi holding the last iterate) if max_iterations

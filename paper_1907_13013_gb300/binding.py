@@ -22,6 +22,7 @@ LAPLACIAN = {"mpd": 0, "wfd": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 METHOD = {"si": 0, "fpsa": 1, "gmres": 2}
 CONTRACTION = {"auto": 0, "simt": 1, "tensor": 2}
+BC = {"vacuum": 0, "reflective": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
 MAX_ORDINATES = 256
 
@@ -31,7 +32,8 @@ class FpsaDesc(ctypes.Structure):
                 ("n_moments", ctypes.c_int32), ("n_rhs", ctypes.c_int32),
                 ("n_cells", ctypes.POINTER(ctypes.c_int32)), ("h", ctypes.POINTER(ctypes.c_double)),
                 ("laplacian", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("bc", ctypes.POINTER(ctypes.c_int32))]
 
 
 class FpsaOpts(ctypes.Structure):
@@ -63,7 +65,8 @@ class FpsaProfile(ctypes.Structure):
 
 
 EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error",
-           "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc", "fpsa_adjoint"]
+           "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc", "fpsa_adjoint",
+           "fpsa_set_incident"]
 NOALLOC_MAX_CELL_ANGLES = 131072
 
 _lib = None
@@ -96,6 +99,8 @@ def load():
     lib.fpsa_profile_read.restype = ctypes.c_int
     lib.fpsa_adjoint.argtypes = [vp, ctypes.POINTER(FpsaOpts), dp, dp, dp, dp, i32, ctypes.POINTER(FpsaStats)]
     lib.fpsa_adjoint.restype = ctypes.c_int
+    lib.fpsa_set_incident.argtypes = [vp, dp, i32]
+    lib.fpsa_set_incident.restype = ctypes.c_int
     lib.fpsa_sweep_noalloc.argtypes = [i32, i32, dp, dp, dp, dp, vp]
     lib.fpsa_sweep_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -131,7 +136,10 @@ def _stream_handle(stream):
 class Context:
     """One fpsa_ctx: B slab instances sharing (N, L), ragged cell counts, R right-hand sides."""
 
-    def __init__(self, n_cells, h, N, L, n_rhs=1, laplacian="mpd", precision="fp64", device=0, stream=None):
+    def __init__(self, n_cells, h, N, L, n_rhs=1, laplacian="mpd", precision="fp64", device=0, stream=None,
+                 bc=None):
+        """bc: None / 'vacuum' / 'reflective' / a (left, right) pair for every instance, or a
+        list with one of those per instance."""
         lib = load()
         self.n_cells = np.ascontiguousarray(np.atleast_1d(n_cells), dtype=np.int32)
         self.h = np.ascontiguousarray(h, dtype=np.float64)
@@ -141,10 +149,12 @@ class Context:
         if self.h.size != self.sumK:
             raise ValueError("h must hold sum(n_cells) widths")
         self.stream = _stream_handle(stream)
+        self.bc = _bc_array(bc, self.B)
         d = FpsaDesc(self.B, self.N, self.L + 1, self.R,
                      self.n_cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                      self.h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                     LAPLACIAN[laplacian], PRECISION[precision], int(device), ctypes.c_void_p(self.stream))
+                     LAPLACIAN[laplacian], PRECISION[precision], int(device), ctypes.c_void_p(self.stream),
+                     self.bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if self.bc is not None else None)
         self._h = ctypes.c_void_p()
         rc = lib.fpsa_create(ctypes.byref(self._h), ctypes.byref(d))
         if rc != OK:
@@ -162,6 +172,18 @@ class Context:
         if len(mems) != 1:
             raise TypeError("sigma_t, sigma_s and q must all be host or all device")
         self._check(self._lib.fpsa_set_xs(self._h, ps[0][0], ps[1][0], ps[2][0], mems.pop()), "fpsa_set_xs")
+
+    def set_incident(self, psi_inc):
+        """Incoming angular fluxes at the vacuum edges, psi_inc [R][B][2][N] (numpy or torch
+        cuda float64): [r][b][0] at the left edge (read for mu > 0), [r][b][1] at the right
+        edge (read for mu < 0). None clears them."""
+        if psi_inc is None:
+            self._check(self._lib.fpsa_set_incident(self._h, None, MEM_HOST), "fpsa_set_incident")
+            return
+        if tuple(psi_inc.shape) != (self.R, self.B, 2, self.N):
+            raise ValueError("psi_inc must have shape (R, B, 2, N)")
+        pi, mem, keep = _ptr(psi_inc)
+        self._check(self._lib.fpsa_set_incident(self._h, pi, mem), "fpsa_set_incident")
 
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, out=None, phi0=None,
               inner_iterations=0, inner_tol=0.0, check_every=1, raise_on_notconv=True, contraction="auto",
@@ -261,8 +283,24 @@ def sweep_noalloc(N, h, sigma_t, q, psi, stream=None):
     return psi
 
 
+def _bc_array(bc, B):
+    """[B][2] int32 edge conditions, or None when every edge is vacuum."""
+    if bc is None:
+        return None
+    per = bc if isinstance(bc, list) else [bc] * B
+    if len(per) != B:
+        raise ValueError("one boundary condition entry per instance")
+    out = np.zeros((B, 2), dtype=np.int32)
+    for b, x in enumerate(per):
+        pair = (x, x) if isinstance(x, str) else tuple(x)
+        out[b] = [BC[pair[0]], BC[pair[1]]]
+    return out if out.any() else None
+
+
 def context_for(problems, n_rhs=None, **kw):
-    """Context + set_xs for a list of problem dicts (see inputs.py) sharing N and L."""
+    """Context + set_xs for a list of problem dicts (see inputs.py) sharing N and L; the
+    problems' edge conditions ('bc') and incoming fluxes ('psi_inc', [2][N] shared by all
+    right-hand sides or [R][2][N]) are passed on."""
     probs = problems if isinstance(problems, (list, tuple)) else [problems]
     N, L = probs[0]["N"], probs[0]["L"]
     K = [p["h"].size for p in probs]
@@ -272,8 +310,16 @@ def context_for(problems, n_rhs=None, **kw):
     Qs = [p["Q"] if p["Q"].ndim == 4 else p["Q"][None] for p in probs]
     R = Qs[0].shape[0] if n_rhs is None else n_rhs
     q = np.concatenate(Qs, axis=1)
+    if "bc" not in kw and any(p.get("bc", "vacuum") != "vacuum" for p in probs):
+        kw["bc"] = [p.get("bc", "vacuum") for p in probs]
     ctx = Context(K, h, N, L, n_rhs=R, **kw)
     ctx.set_xs(st, ss, q)
+    if any(p.get("psi_inc") is not None for p in probs):
+        inc = np.zeros((R, len(probs), 2, N))
+        for b, p in enumerate(probs):
+            if p.get("psi_inc") is not None:
+                inc[:, b] = np.broadcast_to(p["psi_inc"], (R, 2, N))
+        ctx.set_incident(inc)
     return ctx
 
 

@@ -42,6 +42,7 @@ struct PathBuffers {
     T *phi = nullptr, *phi_half = nullptr, *q = nullptr, *psi = nullptr, *rhs = nullptr;
     T *qang = nullptr;                       // MIXED inner path: nodal residual source [R][sumK][2][N]
     T *ybuf = nullptr;                       // BCR solve: intermediate y, then the solution [R][sumK][2N]
+    T *tot = nullptr;                        // reflective edges: whole-slab sweep maps [R][B][N][2]
     // recursive block inversion (2N too large for one CTA): per-depth scratch X, Y
     std::vector<T *> inv_scratch;
     double *inv_amax = nullptr;
@@ -60,6 +61,10 @@ struct fpsa_ctx {
     std::vector<void *> allocs;
 
     int32_t *d_off = nullptr, *d_K = nullptr, *d_cell_inst = nullptr, *d_slot_base = nullptr;
+    int32_t *d_bc = nullptr;     // [B][2] edge conditions; NULL when every edge is vacuum
+    double *d_inc = nullptr;     // [R][B][2][N] given incoming edge fluxes (FP64)
+    bool has_inc = false;
+    float *d_Afp32 = nullptr, *d_mu32 = nullptr;  // angular Laplacian and mu rounded to FP32 (FP32 assembly)
     double *d_mu = nullptr, *d_Afp = nullptr, *d_h = nullptr, *d_sigma_t = nullptr, *d_s0 = nullptr,
            *d_s1 = nullptr;
     std::vector<BcrItem *> d_levels;
@@ -78,9 +83,10 @@ struct fpsa_ctx {
     double *d_Pm = nullptr, *d_cJ = nullptr;                              // (-1)^l P_l(mu_n), exit-current weights
     double *d_J = nullptr, *d_grad_t = nullptr, *d_grad_s = nullptr;
 
-    // GMRES (FP64 path): Krylov basis and work vectors, allocated at first use
+    // GMRES: Krylov basis and work vectors (double for FP64 contexts, float for the
+    // inner solves of MIXED), allocated at first use
     int gm_restart = 0;
-    double *gm_V = nullptr, *gm_u = nullptr, *gm_w = nullptr, *gm_b = nullptr;
+    unsigned char *gm_V = nullptr, *gm_u = nullptr, *gm_w = nullptr, *gm_b = nullptr;
     double *gm_partial = nullptr, *gm_dots = nullptr, *gm_coef = nullptr, *gm_alpha = nullptr;
     long long *gm_seg_begin = nullptr, *gm_seg_end = nullptr;
     int32_t *gm_col_sys = nullptr;
@@ -185,7 +191,7 @@ int solve_rc(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
 // shared scratch of the cooperative BCR solve (one unit per block)
 template <typename T>
 size_t solve_smem(int N, int RC) {
-    return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V, RC) * sizeof(T);
+    return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V, RC, (int)sizeof(T)) * sizeof(T);
 }
 
 template <typename T>
@@ -237,6 +243,7 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         CK(dalloc(ctx, &p.q, ang));
         CK(dalloc(ctx, &p.rhs, ang));
         CK(dalloc(ctx, &p.ybuf, ang));
+        if (ctx->d_bc) CK(dalloc(ctx, &p.tot, (size_t)g.R * g.B * N * 2));
         // scratch of the recursive block inversion: X and Y per recursion depth
         for (int n = 2 * g.N; !cta_invertible<T>(n); n /= 2) {
             T *s = nullptr;
@@ -411,9 +418,17 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
     CK(cudaMemsetAsync(p.Cc, 0, (size_t)g.n_slots * h2 * h2 * sizeof(T), st));
     {
         Launch L_(ctx, FPSA_PHASE_ASSEMBLE);
-        k_fp_assemble<T><<<g.sumK, 256, 0, st>>>(ctx->d_mu, ctx->d_Afp, ctx->d_h, ctx->d_sigma_t, ctx->d_s0, ctx->d_s1,
+        const T *afp, *muT;
+        if constexpr (sizeof(T) == sizeof(double)) {
+            afp = ctx->d_Afp;
+            muT = ctx->d_mu;
+        } else {
+            afp = ctx->d_Afp32;
+            muT = ctx->d_mu32;
+        }
+        k_fp_assemble<T><<<g.sumK, dim3(32, 8), 0, st>>>(muT, afp, ctx->d_h, ctx->d_sigma_t, ctx->d_s0, ctx->d_s1,
                                                  ctx->d_cell_inst, ctx->d_off, ctx->d_K, ctx->d_slot_base, N, p.A, p.Bc,
-                                                 p.Cc);
+                                                 p.Cc, ctx->d_bc);
     }
     CK(cudaGetLastError());
     for (int l = 0; l < g.n_levels; ++l) {
@@ -439,6 +454,27 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
 
 // F u = rhs by block cyclic reduction over the stored factors: one cooperative
 // launch (forward levels, roots, backward levels); the solution is left in p.ybuf.
+// psi = L^{-1} q for every (ordinate, instance, rhs) with the given incoming edge
+// fluxes inc (NULL: none); reflective edges take the totals pass first.
+template <typename T>
+int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
+    const Geometry &g = ctx->geo;
+    const dim3 sgrid(g.N, g.B, g.R);
+    if (ctx->d_bc) {
+        Launch L_(ctx, FPSA_PHASE_SWEEP);
+        k_sweep<T, kSweepThreads, true><<<sgrid, kSweepThreads, 0, ctx->stream>>>(
+            q, psi, p.coef, ctx->d_mu, ctx->d_off, ctx->d_K, g.N, g.sumK, inc, ctx->d_bc, p.tot);
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_SWEEP);
+        k_sweep<T, kSweepThreads><<<sgrid, kSweepThreads, 0, ctx->stream>>>(q, psi, p.coef, ctx->d_mu, ctx->d_off,
+                                                                           ctx->d_K, g.N, g.sumK, inc, ctx->d_bc,
+                                                                           p.tot);
+    }
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
 template <typename T>
 int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     const Geometry &g = ctx->geo;
@@ -476,17 +512,16 @@ int check_xs(fpsa_ctx *ctx, const double *st, const double *ss, const double *q)
 }
 
 template <typename T>
-// Qm: source moments (may be NULL), Qa: nodal angular source (may be NULL).
-// phi_out may be NULL (the iterate stays in p.phi).
+// Qm: source moments (may be NULL), Qa: nodal angular source (may be NULL), inc:
+// incoming edge fluxes (may be NULL). phi_out may be NULL (the iterate stays in p.phi).
 int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const double *phi0, int mem, double *phi_out,
-               fpsa_stats &stats, const T *Qm, const T *Qa) {
+               fpsa_stats &stats, const T *Qm, const T *Qa, const T *inc) {
     const Geometry &g = ctx->geo;
     const int N = g.N, L1 = g.L1;
     cudaStream_t st = ctx->stream;
     const size_t ncol = (size_t)g.R * g.sumK * 2;
     const size_t csm = contract_smem<T>(N);
     const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
-    const dim3 sgrid(N, g.B, g.R);
     const bool fpsa = o.method == FPSA_METHOD_FPSA;
 
     if (phi0) {
@@ -507,11 +542,8 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
     double e = INFINITY;
     int it = 0;
     for (it = 1; it <= o.max_iterations; ++it) {
-        {
-            Launch L_(ctx, FPSA_PHASE_SWEEP);
-            k_sweep<T, kSweepThreads><<<sgrid, kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu, ctx->d_off, ctx->d_K,
-                                                                      N, g.sumK);
-        }
+        int rc0 = sweep(ctx, p, p.q, p.psi, inc);
+        if (rc0) return rc0;
         if (fpsa) {
             {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
@@ -573,8 +605,15 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
 //   inner:    `inner` FPSA iterations (Eqs. predict, correct) on L dpsi = S dpsi + dq
 //             from dpsi = 0, all in FP32: sweep, contractions, BCR solve
 //   update:   psi64 += psi_half + upsilon of the last inner iteration (FP64)
+// With the GMRES method the inner solve is FP32 GMRES(m) on the moment form of the
+// correction equation (to a relative residual of inner_tol, at most inner_cap Krylov
+// iterations), followed by one sweep for the angular correction.
+template <typename T>
+int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, const T *Qm, const T *Qa,
+               const T *inc, int &it, int &sweeps, double &worst);
+
 int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats,
-                const double *Qm, const double *Qa) {
+                const double *Qm, const double *Qa, const double *inc) {
     const Geometry &g = ctx->geo;
     const int N = g.N, L1 = g.L1;
     cudaStream_t st = ctx->stream;
@@ -582,12 +621,15 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     PathBuffers<float> &f = ctx->p32;
     const size_t ncol = (size_t)g.R * g.sumK * 2, nang = ncol * N;
     const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
-    const dim3 sgrid(N, g.B, g.R);
     const int inner = o.inner_iterations > 0 ? o.inner_iterations : 4;
-    const bool fpsa = o.method == FPSA_METHOD_FPSA;
+    const bool fpsa = o.method == FPSA_METHOD_FPSA, gmres = o.method == FPSA_METHOD_GMRES;
+    const int m = o.restart > 0 ? o.restart : 30;
+    const int inner_cap = o.inner_iterations > 0 ? o.inner_iterations : m;
+    const double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
+    int krylov = 0;
     if (o.contraction == 2 && !ctx->tc_able)
         return fail(ctx, FPSA_ENOTSUP, "tensor-core contractions need N a multiple of 16 and <= 128");
-    const bool use_tc = ctx->tc_able && o.contraction != 1;
+    const bool use_tc = ctx->tc_able && o.contraction != 1 && !gmres;
     const TcOps tcops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
     const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
     const int tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
@@ -612,7 +654,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             Launch L_(ctx, FPSA_PHASE_RESIDUAL);
             k_mixed_residual<<<cgrid, kContractThreads, contract_smem<double>(N), st>>>(
                 p.psi, p.phi, p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst,
-                ctx->d_off, ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa);
+                ctx->d_off, ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc, ctx->d_bc);
         }
         {
             Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
@@ -636,15 +678,36 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             break;
         }
         if (outer > o.max_iterations) break;
+        if (gmres) {
+            // inner FP32 GMRES on the correction equation (moments), then the angular
+            // correction dpsi = L^{-1} (M Sigma dphi + dq) by one more sweep
+            int git = 0, gsw = 0;
+            double gres = 0.0;
+            int rc = gmres_core<float>(ctx, f, m, inner_tol, inner_cap, (const float *)nullptr, f.qang,
+                                       (const float *)nullptr, git, gsw, gres);
+            if (rc != FPSA_OK && rc != FPSA_ENOTCONV) return rc;
+            krylov += git;
+            sweeps += gsw + 1;
+            {
+                Launch L_(ctx, FPSA_PHASE_CONTRACT);
+                k_scatter<float><<<cgrid, kContractThreads, contract_smem<float>(N) / 2, st>>>(
+                    f.phi, f.sigma_s, (const float *)nullptr, f.MT, f.q, N, g.sumK, f.qang);
+            }
+            rc = sweep(ctx, f, f.q, f.psi, (const float *)nullptr);
+            if (rc) return rc;
+            {
+                Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, (const float *)nullptr, nang);
+            }
+            CK(cudaGetLastError());
+            continue;
+        }
         // inner FP32 solve of the correction from zero
         CK(cudaMemsetAsync(f.phi, 0, nang * sizeof(float), st));
         CK(cudaMemcpyAsync(f.q, f.qang, nang * sizeof(float), cudaMemcpyDeviceToDevice, st));
         for (int j = 1; j <= inner; ++j) {
-            {
-                Launch L_(ctx, FPSA_PHASE_SWEEP);
-                k_sweep<float, kSweepThreads><<<sgrid, kSweepThreads, 0, st>>>(f.q, f.psi, f.coef, ctx->d_mu,
-                                                                               ctx->d_off, ctx->d_K, N, g.sumK);
-            }
+            int rcs = sweep(ctx, f, f.q, f.psi, (const float *)nullptr);
+            if (rcs) return rcs;
             ++sweeps;
             const float *vin = f.psi, *base = nullptr;
             if (fpsa) {
@@ -675,16 +738,11 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         }
         {
             Launch L_(ctx, FPSA_PHASE_RESIDUAL);
-            if (fpsa) {
-                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, f.ybuf, nang);
-            } else {
-                CK(cudaMemsetAsync(f.rhs, 0, nang * sizeof(float), st));
-                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, f.rhs, nang);
-            }
+            k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, fpsa ? f.ybuf : (const float *)nullptr, nang);
         }
         CK(cudaGetLastError());
     }
-    stats.iterations = sweeps;
+    stats.iterations = gmres ? krylov : sweeps;
     stats.outer_iterations = std::min(outer, o.max_iterations + 1);
     stats.sweeps = sweeps;
     stats.rel_change = e;
@@ -698,22 +756,25 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
 }
 
 
-// Lazily allocate the GMRES work space for restart length m.
+// Lazily allocate the GMRES work space for restart length m. The basis and work
+// vectors hold the precision of the Krylov solve (FP64 contexts: double; MIXED:
+// float, the inner solve of the refinement loop); dots are always FP64.
 int gmres_alloc(fpsa_ctx *ctx, int m) {
     if (ctx->gm_restart >= m) return FPSA_OK;
     const Geometry &g = ctx->geo;
     const size_t n = (size_t)g.R * g.sumK * 2 * g.N;
+    const size_t es = ctx->precision == FPSA_PRECISION_FP64 ? sizeof(double) : sizeof(float);
     const int nsys = g.R * g.B;
     if (ctx->gm_V) {  // grow: release the old basis (the allocations list keeps the pointer)
         CK(cudaFree(ctx->gm_V));
         ctx->allocs.erase(std::find(ctx->allocs.begin(), ctx->allocs.end(), (void *)ctx->gm_V));
         ctx->gm_V = nullptr;
     }
-    CK(dalloc(ctx, &ctx->gm_V, (size_t)(m + 1) * n));
+    CK(dalloc(ctx, &ctx->gm_V, (size_t)(m + 1) * n * es));
     if (!ctx->gm_u) {
-        CK(dalloc(ctx, &ctx->gm_u, n));
-        CK(dalloc(ctx, &ctx->gm_w, n));
-        CK(dalloc(ctx, &ctx->gm_b, n));
+        CK(dalloc(ctx, &ctx->gm_u, n * es));
+        CK(dalloc(ctx, &ctx->gm_w, n * es));
+        CK(dalloc(ctx, &ctx->gm_b, n * es));
         CK(dalloc(ctx, &ctx->gm_seg_begin, nsys));
         CK(dalloc(ctx, &ctx->gm_seg_end, nsys));
         CK(dalloc(ctx, &ctx->gm_col_sys, (size_t)g.R * g.sumK * 2));
@@ -748,17 +809,17 @@ int gmres_alloc(fpsa_ctx *ctx, int m) {
     return FPSA_OK;
 }
 
-// out[s][i] = <V_i, w>_s for i < nv, all systems s; result copied to host hdots.
-int gm_dots(fpsa_ctx *ctx, const double *V, int nv, const double *w, std::vector<double> &hdots) {
+// out[s][i] = <V_i, w>_s for i < nv, all systems s (FP64 sums); result copied to host hdots.
+template <typename T>
+int gm_dots(fpsa_ctx *ctx, const T *V, int nv, const T *w, std::vector<double> &hdots) {
     const Geometry &g = ctx->geo;
     const int nsys = g.R * g.B;
     const size_t n = (size_t)g.R * g.sumK * 2 * g.N;
     cudaStream_t st = ctx->stream;
     {
         Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
-        k_seg_dots<double><<<dim3(ctx->gm_nchunks, nsys), 256, 0, st>>>(V, n, nv, w, ctx->gm_seg_begin,
-                                                                      ctx->gm_seg_end, ctx->gm_nchunks,
-                                                                      ctx->gm_partial);
+        k_seg_dots<T><<<dim3(ctx->gm_nchunks, nsys), 256, 0, st>>>(V, n, nv, w, ctx->gm_seg_begin, ctx->gm_seg_end,
+                                                                   ctx->gm_nchunks, ctx->gm_partial);
     }
     {
         Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
@@ -773,7 +834,8 @@ int gm_dots(fpsa_ctx *ctx, const double *V, int nv, const double *w, std::vector
 }
 
 // y = alpha_s y + sum_i coef[s][i] V_i (alpha NULL: y = sum ...), coefficients from the host.
-int gm_combine(fpsa_ctx *ctx, double *y, const std::vector<double> *alpha, const double *V, int nv,
+template <typename T>
+int gm_combine(fpsa_ctx *ctx, T *y, const std::vector<double> *alpha, const T *V, int nv,
                const std::vector<double> &coef) {
     const Geometry &g = ctx->geo;
     const size_t n = (size_t)g.R * g.sumK * 2 * g.N;
@@ -783,95 +845,94 @@ int gm_combine(fpsa_ctx *ctx, double *y, const std::vector<double> *alpha, const
         CK(cudaMemcpyAsync(ctx->gm_alpha, alpha->data(), alpha->size() * sizeof(double), cudaMemcpyHostToDevice, st));
     {
         Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
-        k_seg_combine<double><<<4 * 152, 256, 0, st>>>(y, alpha ? ctx->gm_alpha : nullptr, V, n, nv, ctx->gm_coef,
-                                                       ctx->gm_col_sys, g.N, n);
+        k_seg_combine<T><<<4 * 152, 256, 0, st>>>(y, alpha ? ctx->gm_alpha : nullptr, V, n, nv, ctx->gm_coef,
+                                                  ctx->gm_col_sys, g.N, n);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));  // the host vectors are reused right away
     return FPSA_OK;
 }
 
-// out = (I - T)(I + C) v  (FP64 path buffers; out may not alias v)
-int gm_apply(fpsa_ctx *ctx, PathBuffers<double> &p, const double *v, double *out) {
+// out = (I - T)(I + C) v  (out may not alias v)
+template <typename T>
+int gm_apply(fpsa_ctx *ctx, PathBuffers<T> &p, const T *v, T *out) {
     const Geometry &g = ctx->geo;
     const int N = g.N;
     cudaStream_t st = ctx->stream;
-    const size_t csm = contract_smem<double>(N);
+    const size_t csm = contract_smem<T>(N);
     const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_fp_rhs_moments<double><<<cgrid, kContractThreads, csm, st>>>(v, p.sigma_s, ctx->d_h, p.MT, p.rhs, N, g.sumK);
+        k_fp_rhs_moments<T><<<cgrid, kContractThreads, csm, st>>>(v, p.sigma_s, ctx->d_h, p.MT, p.rhs, N, g.sumK);
     }
     int rc = bcr_solve(ctx, p, p.rhs);
     if (rc) return rc;
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);  // out = z = v + D upsilon;  q = M Sigma z
-        k_update_scatter<double><<<cgrid, kContractThreads, csm, st>>>(
-            p.ybuf, v, out, p.sigma_s, (const double *)nullptr, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
-            (unsigned long long *)nullptr, N, g.sumK, (const double *)nullptr);
+        k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.ybuf, v, out, p.sigma_s, (const T *)nullptr, p.DT,
+                                                                  p.MT, p.q, ctx->d_cell_inst, g.B,
+                                                                  (unsigned long long *)nullptr, N, g.sumK,
+                                                                  (const T *)nullptr);
     }
-    {
-        Launch L_(ctx, FPSA_PHASE_SWEEP);
-        k_sweep<double, kSweepThreads><<<dim3(N, g.B, g.R), kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu,
-                                                                                  ctx->d_off, ctx->d_K, N, g.sumK);
-    }
+    rc = sweep(ctx, p, p.q, p.psi, (const T *)nullptr);
+    if (rc) return rc;
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);  // out = z - D psi
-        k_moments_axpy<double><<<cgrid, kContractThreads, csm, st>>>(p.psi, out, -1.0, p.DT, out, N, g.sumK);
+        k_moments_axpy<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, out, T(-1), p.DT, out, N, g.sumK);
     }
     CK(cudaGetLastError());
     return FPSA_OK;
 }
 
-// GMRES(m) with right FPSA preconditioning, FP64, batched over (rhs, instance) systems.
-int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats,
-                const double *Qm, const double *Qa) {
-    PathBuffers<double> &p = ctx->p64;
+// GMRES(m) with right FPSA preconditioning in precision T, batched over (rhs, instance)
+// systems: (I - T)(I + C) u = b, b = D L^{-1} (M Qm + Qa) with the incoming edge
+// fluxes inc (the applications of T take none), from u = 0; on return p.phi
+// holds phi = (I + C) u. Stops when every system's relative residual 2-norm (the
+// Givens estimate, and the true residual at each restart) is below tol, or after
+// max_it Krylov iterations (FPSA_ENOTCONV, no message: the caller decides).
+template <typename T>
+int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, const T *Qm, const T *Qa,
+               const T *inc, int &it, int &sweeps, double &worst) {
     const Geometry &g = ctx->geo;
-    const int N = g.N, L1 = g.L1, nsys = g.R * g.B;
-    const int m = o.restart > 0 ? o.restart : 30;
-    const size_t n = (size_t)g.R * g.sumK * 2 * N, ncol = (size_t)g.R * g.sumK * 2;
+    const int N = g.N, nsys = g.R * g.B;
+    const size_t n = (size_t)g.R * g.sumK * 2 * N;
     cudaStream_t st = ctx->stream;
-    if (phi0) return fail(ctx, FPSA_ENOTSUP, "GMRES starts from zero (phi0 not supported)");
     int rc = gmres_alloc(ctx, m);
     if (rc) return rc;
-    const size_t csm = contract_smem<double>(N);
+    T *V = reinterpret_cast<T *>(ctx->gm_V), *u = reinterpret_cast<T *>(ctx->gm_u),
+      *w = reinterpret_cast<T *>(ctx->gm_w), *b = reinterpret_cast<T *>(ctx->gm_b);
+    const size_t csm = contract_smem<T>(N);
     const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
-    // b = D L^{-1} (M Q + q_ang)
-    CK(cudaMemsetAsync(ctx->gm_u, 0, n * sizeof(double), st));
+    // b = D L^{-1} (M Qm + Qa)
+    CK(cudaMemsetAsync(u, 0, n * sizeof(T), st));
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_scatter<double><<<cgrid, kContractThreads, csm / 2, st>>>(ctx->gm_u, p.sigma_s, Qm, p.MT, p.q, N, g.sumK, Qa);
+        k_scatter<T><<<cgrid, kContractThreads, csm / 2, st>>>(u, p.sigma_s, Qm, p.MT, p.q, N, g.sumK, Qa);
     }
-    {
-        Launch L_(ctx, FPSA_PHASE_SWEEP);
-        k_sweep<double, kSweepThreads><<<dim3(N, g.B, g.R), kSweepThreads, 0, st>>>(p.q, p.psi, p.coef, ctx->d_mu,
-                                                                                  ctx->d_off, ctx->d_K, N, g.sumK);
-    }
+    rc = sweep(ctx, p, p.q, p.psi, inc);
+    if (rc) return rc;
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_moments_axpy<double><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const double *)nullptr, 1.0, p.DT,
-                                                                     ctx->gm_b, N, g.sumK);
+        k_moments_axpy<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const T *)nullptr, T(1), p.DT, b, N, g.sumK);
     }
     CK(cudaGetLastError());
-    std::vector<double> dots, bnorm(nsys), coef, alpha(nsys);
-    rc = gm_dots(ctx, ctx->gm_b, 1, ctx->gm_b, dots);
+    std::vector<double> dots, bnorm(nsys), coef, alpha(nsys), c1(nsys, 1.0);
+    rc = gm_dots(ctx, b, 1, b, dots);
     if (rc) return rc;
     for (int s = 0; s < nsys; ++s) bnorm[s] = std::sqrt(dots[s]);
-    int it = 0, sweeps = 1, status = FPSA_ENOTCONV;
-    double worst = INFINITY;
-    double *V = ctx->gm_V;
-    while (it < o.max_iterations) {
+    it = 0;
+    sweeps = 1;
+    worst = INFINITY;
+    int status = FPSA_ENOTCONV;
+    while (it < max_it) {
         // r = b - A' u  (u = 0 on the first cycle)
-        if (it == 0) {
-            CK(cudaMemcpyAsync(V, ctx->gm_b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        } else {
-            rc = gm_apply(ctx, p, ctx->gm_u, ctx->gm_w);
+        CK(cudaMemcpyAsync(V, b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        if (it > 0) {
+            rc = gm_apply(ctx, p, u, w);
             if (rc) return rc;
             ++sweeps;
-            std::vector<double> one(nsys, -1.0), c1(nsys, 1.0);
-            CK(cudaMemcpyAsync(V, ctx->gm_b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            rc = gm_combine(ctx, V, &c1, ctx->gm_w, 1, one);  // V_0 = b - A' u
+            std::vector<double> one(nsys, -1.0);
+            rc = gm_combine(ctx, V, &c1, w, 1, one);  // V_0 = b - A' u
             if (rc) return rc;
         }
         rc = gm_dots(ctx, V, 1, V, dots);
@@ -884,7 +945,7 @@ int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             alpha[s] = beta[s] > 0 ? 1.0 / beta[s] : 0.0;
         }
         if (!std::isfinite(worst)) return fail(ctx, FPSA_ENONFINITE, "non-finite GMRES residual");
-        if (worst < o.tol) { status = FPSA_OK; break; }
+        if (worst < tol) { status = FPSA_OK; break; }
         rc = gm_combine(ctx, V, &alpha, V, 0, coef);  // V_0 = r / beta
         if (rc) return rc;
         // Arnoldi with classical Gram-Schmidt applied twice, Givens rotations per system
@@ -893,9 +954,8 @@ int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         for (int s = 0; s < nsys; ++s) gvec[(size_t)s * (m + 1)] = beta[s];
         auto Hs = [&](int s, int i, int j) -> double & { return H[((size_t)s * (m + 1) + i) * m + j]; };
         int j = 0, jdone = 0;
-        for (j = 0; j < m && it < o.max_iterations; ++j) {
-            double *Vj = V + (size_t)j * n, *w = ctx->gm_w;
-            rc = gm_apply(ctx, p, Vj, w);
+        for (j = 0; j < m && it < max_it; ++j) {
+            rc = gm_apply(ctx, p, V + (size_t)j * n, w);
             if (rc) return rc;
             ++sweeps;
             std::vector<double> hsum((size_t)nsys * (j + 1), 0.0);
@@ -907,7 +967,6 @@ int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
                     neg[q] = -dots[q];
                     hsum[q] += dots[q];
                 }
-                std::vector<double> c1(nsys, 1.0);
                 rc = gm_combine(ctx, w, &c1, V, j + 1, neg);
                 if (rc) return rc;
             }
@@ -937,9 +996,9 @@ int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             ++it;
             jdone = j + 1;
             if (!std::isfinite(worst)) return fail(ctx, FPSA_ENONFINITE, "non-finite GMRES residual");
-            if (worst < o.tol) break;
+            if (worst < tol) break;
             if (j + 1 < m) {  // V_{j+1} = w / h_{j+1,j}
-                CK(cudaMemcpyAsync(V + (size_t)(j + 1) * n, w, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(V + (size_t)(j + 1) * n, w, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
                 rc = gm_combine(ctx, V + (size_t)(j + 1) * n, &alpha, V, 0, coef);
                 if (rc) return rc;
             }
@@ -952,34 +1011,48 @@ int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
                 for (int k2 = i + 1; k2 < jdone; ++k2) acc -= Hs(s, i, k2) * y[(size_t)s * jdone + k2];
                 y[(size_t)s * jdone + i] = Hs(s, i, i) != 0.0 ? acc / Hs(s, i, i) : 0.0;
             }
-        std::vector<double> c1(nsys, 1.0);
-        rc = gm_combine(ctx, ctx->gm_u, &c1, V, jdone, y);
+        rc = gm_combine(ctx, u, &c1, V, jdone, y);
         if (rc) return rc;
-        if (worst < o.tol) { status = FPSA_OK; break; }
+        if (worst < tol) { status = FPSA_OK; break; }
     }
     // phi = (I + C) u
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_fp_rhs_moments<double><<<cgrid, kContractThreads, csm, st>>>(ctx->gm_u, p.sigma_s, ctx->d_h, p.MT, p.rhs, N,
-                                                                      g.sumK);
+        k_fp_rhs_moments<T><<<cgrid, kContractThreads, csm, st>>>(u, p.sigma_s, ctx->d_h, p.MT, p.rhs, N, g.sumK);
     }
     rc = bcr_solve(ctx, p, p.rhs);
     if (rc) return rc;
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_update_scatter<double><<<cgrid, kContractThreads, csm, st>>>(
-            p.ybuf, ctx->gm_u, p.phi, p.sigma_s, (const double *)nullptr, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
-            (unsigned long long *)nullptr, N, g.sumK, (const double *)nullptr);
+        k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.ybuf, u, p.phi, p.sigma_s, (const T *)nullptr, p.DT,
+                                                                  p.MT, p.q, ctx->d_cell_inst, g.B,
+                                                                  (unsigned long long *)nullptr, N, g.sumK,
+                                                                  (const T *)nullptr);
     }
     CK(cudaGetLastError());
+    return status;
+}
+
+// GMRES(m) with right FPSA preconditioning, FP64 (Sec. 4).
+int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats,
+                const double *Qm, const double *Qa, const double *inc) {
+    PathBuffers<double> &p = ctx->p64;
+    const Geometry &g = ctx->geo;
+    const size_t ncol = (size_t)g.R * g.sumK * 2;
+    if (phi0) return fail(ctx, FPSA_ENOTSUP, "GMRES starts from zero (phi0 not supported)");
+    int it = 0, sweeps = 0;
+    double worst = INFINITY;
+    const int status = gmres_core<double>(ctx, p, o.restart > 0 ? o.restart : 30, o.tol, o.max_iterations, Qm, Qa,
+                                          inc, it, sweeps, worst);
+    if (status != FPSA_OK && status != FPSA_ENOTCONV) return status;
     stats.iterations = it;
     stats.outer_iterations = it;
     stats.sweeps = sweeps;
     stats.rel_change = worst;
     if (phi_out)
-        CK(cudaMemcpy2DAsync(phi_out, L1 * sizeof(double), p.phi, N * sizeof(double), L1 * sizeof(double), ncol,
-                             mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-    CK(cudaStreamSynchronize(st));
+        CK(cudaMemcpy2DAsync(phi_out, g.L1 * sizeof(double), p.phi, g.N * sizeof(double), g.L1 * sizeof(double), ncol,
+                             mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     if (status == FPSA_ENOTCONV)
         fail(ctx, FPSA_ENOTCONV, "GMRES not converged after " + std::to_string(it) + " iterations");
     return status;
@@ -1036,6 +1109,12 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
     if (sumK > (1ll << 30)) return FPSA_EINVAL;
     for (long long c = 0; c < sumK; ++c)
         if (!(d->h[c] > 0.0) || !std::isfinite(d->h[c])) return FPSA_EINVAL;
+    bool any_reflect = false;
+    if (d->bc)
+        for (int e = 0; e < 2 * d->n_instances; ++e) {
+            if (d->bc[e] != FPSA_BC_VACUUM && d->bc[e] != FPSA_BC_REFLECT) return FPSA_EINVAL;
+            any_reflect |= d->bc[e] == FPSA_BC_REFLECT;
+        }
 
     fpsa_ctx *ctx = new fpsa_ctx();
     ctx->laplacian = d->laplacian;
@@ -1072,7 +1151,19 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         CK(cudaMemcpy(ctx->d_slot_base, g.slot_base.data(), g.sumK * sizeof(int32_t), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_mu, ctx->tab.mu.data(), g.N * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_Afp, ctx->tab.Afp.data(), (size_t)g.N * g.N * sizeof(double), cudaMemcpyHostToDevice));
+        {
+            std::vector<float> a32(ctx->tab.Afp.begin(), ctx->tab.Afp.end());
+            CK(dalloc(ctx, &ctx->d_Afp32, a32.size()));
+            CK(cudaMemcpy(ctx->d_Afp32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
+            std::vector<float> m32(ctx->tab.mu.begin(), ctx->tab.mu.end());
+            CK(dalloc(ctx, &ctx->d_mu32, m32.size()));
+            CK(cudaMemcpy(ctx->d_mu32, m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
         CK(cudaMemcpy(ctx->d_h, d->h, g.sumK * sizeof(double), cudaMemcpyHostToDevice));
+        if (any_reflect) {
+            CK(dalloc(ctx, &ctx->d_bc, 2 * g.B));
+            CK(cudaMemcpy(ctx->d_bc, d->bc, 2 * g.B * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
         ctx->d_levels.assign(g.n_levels, nullptr);
         for (int l = 0; l < g.n_levels; ++l) {
             CK(dalloc(ctx, &ctx->d_levels[l], g.levels[l].size()));
@@ -1208,6 +1299,28 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     return FPSA_OK;
 }
 
+int fpsa_set_incident(fpsa_ctx *ctx, const double *psi_inc, int32_t mem) {
+    if (!ctx) return FPSA_EINVAL;
+    if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(ctx, FPSA_EINVAL, "bad mem kind");
+    CK(cudaSetDevice(ctx->device));
+    const Geometry &g = ctx->geo;
+    const size_t n = (size_t)g.R * g.B * 2 * g.N;
+    ctx->fwd_ready = false;
+    if (!psi_inc) {
+        ctx->has_inc = false;
+        return FPSA_OK;
+    }
+    if (mem == FPSA_MEM_HOST)
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(psi_inc[i])) return fail(ctx, FPSA_ENONFINITE, "non-finite incoming flux");
+    if (!ctx->d_inc) CK(dalloc(ctx, &ctx->d_inc, n));
+    CK(cudaMemcpyAsync(ctx->d_inc, psi_inc, n * sizeof(double),
+                       mem == FPSA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->has_inc = true;
+    return FPSA_OK;
+}
+
 int fpsa_profile_enable(fpsa_ctx *ctx, int32_t on) {
     if (!ctx) return FPSA_EINVAL;
     CK(cudaSetDevice(ctx->device));
@@ -1245,17 +1358,17 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
     if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA && o.method != FPSA_METHOD_GMRES)
         return fail(ctx, FPSA_EINVAL, "bad method");
     if (o.max_iterations < 1 || !(o.tol >= 0.0) || o.restart < 0) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol / restart");
-    if (o.method == FPSA_METHOD_GMRES && ctx->precision != FPSA_PRECISION_FP64)
-        return fail(ctx, FPSA_ENOTSUP, "GMRES is available in FP64 precision");
     CK(cudaSetDevice(ctx->device));
     fpsa_stats s{};
     const auto t0 = std::chrono::steady_clock::now();
     ctx->fwd_ready = false;
-    int rc = o.method == FPSA_METHOD_GMRES
-                 ? solve_gmres(ctx, o, phi0, mem, phi, s, ctx->p64.Q, nullptr)
+    const double *inc = ctx->has_inc ? ctx->d_inc : nullptr;
+    int rc = o.method == FPSA_METHOD_GMRES && ctx->precision == FPSA_PRECISION_FP64
+                 ? solve_gmres(ctx, o, phi0, mem, phi, s, ctx->p64.Q, nullptr, inc)
                  : ctx->precision == FPSA_PRECISION_FP64
-                 ? solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s, (const double *)ctx->p64.Q, (const double *)nullptr)
-                 : solve_mixed(ctx, o, phi0, mem, phi, s, ctx->p64.Q, nullptr);
+                 ? solve_fp64(ctx, ctx->p64, o, phi0, mem, phi, s, (const double *)ctx->p64.Q, (const double *)nullptr,
+                              inc)
+                 : solve_mixed(ctx, o, phi0, mem, phi, s, ctx->p64.Q, nullptr, inc);
     if (rc == FPSA_OK) {
         // keep the converged moments (all N) for fpsa_adjoint
         const size_t nang = (size_t)ctx->geo.R * ctx->geo.sumK * 2 * ctx->geo.N;
@@ -1282,9 +1395,8 @@ int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, do
     if (opts) o = *opts;
     if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA && o.method != FPSA_METHOD_GMRES)
         return fail(ctx, FPSA_EINVAL, "bad method");
-    if (o.method == FPSA_METHOD_GMRES && ctx->precision != FPSA_PRECISION_FP64)
-        return fail(ctx, FPSA_ENOTSUP, "GMRES is available in FP64 precision");
-    if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol");
+    if (o.max_iterations < 1 || !(o.tol >= 0.0) || o.restart < 0)
+        return fail(ctx, FPSA_EINVAL, "bad max_iterations / tol / restart");
     CK(cudaSetDevice(ctx->device));
     const Geometry &g = ctx->geo;
     const int N = g.N, L1 = g.L1;
@@ -1312,12 +1424,13 @@ int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, do
     CK(cudaGetLastError());
     fpsa_stats s{};
     // A x = Pi W^{-1} dJ/dpsi with the forward machinery and factors
-    int rc = o.method == FPSA_METHOD_GMRES
-                 ? solve_gmres(ctx, o, nullptr, mem, nullptr, s, nullptr, ctx->d_adj_src)
+    // (homogeneous edges: the given incoming fluxes belong to the forward source only)
+    int rc = o.method == FPSA_METHOD_GMRES && ctx->precision == FPSA_PRECISION_FP64
+                 ? solve_gmres(ctx, o, nullptr, mem, nullptr, s, nullptr, ctx->d_adj_src, nullptr)
                  : ctx->precision == FPSA_PRECISION_FP64
                  ? solve_fp64(ctx, ctx->p64, o, nullptr, mem, nullptr, s, (const double *)nullptr,
-                              (const double *)ctx->d_adj_src)
-                 : solve_mixed(ctx, o, nullptr, mem, nullptr, s, nullptr, ctx->d_adj_src);
+                              (const double *)ctx->d_adj_src, (const double *)nullptr)
+                 : solve_mixed(ctx, o, nullptr, mem, nullptr, s, nullptr, ctx->d_adj_src, nullptr);
     if (rc != FPSA_OK) return rc;
     {
         Launch L_(ctx, FPSA_PHASE_RESIDUAL);

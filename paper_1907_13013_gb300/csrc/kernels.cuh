@@ -67,7 +67,16 @@ __global__ void k_sweep_coef(const double *__restrict__ mu, const double *__rest
 // associatively, so each thread composes the maps of a contiguous chunk of
 // cells (pass 1), the block scans the chunk maps (warp shuffles, then across
 // warps), and each thread re-sweeps its chunk from the exact inflow (pass 2).
-// Vacuum inflow at the domain edge.
+//
+// Edge inflow x0 of ordinate n (upwind edge s: left for mu > 0):
+//   vacuum edge       x0 = psi_inc[r][b][s][n] (given incoming flux; 0 if none)
+//   reflective edge   x0 = outflow at s of the mirror ordinate n' = N-1-n. With the
+//                     whole-slab maps x -> A x + E of n and n' for zero inflow
+//                     (the totals pass, kTotals = true, writes them to tot), this is
+//                     A' x0' + E' with x0' the inflow of n' at the far edge: its
+//                     given flux, or, if that edge reflects too, A x0 + E, so that
+//                     x0 = (A' E + E') / (1 - A A')  (|A A'| < 1 for sigma_t > 0).
+// The mirror-ordinate coupling is thus exact per sweep (no lagged edge values).
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Affine {
@@ -79,13 +88,16 @@ __device__ __forceinline__ Affine<T> compose(Affine<T> first, Affine<T> then) {
     return {then.a * first.a, then.a * first.b + then.b};
 }
 
-template <typename T, int NT>
+constexpr int32_t kBcReflect = 1;
+
+template <typename T, int NT, bool kTotals = false>
 __global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__restrict__ psi,
                                               const T *__restrict__ coef, const double *__restrict__ mu,
                                               const int32_t *__restrict__ off, const int32_t *__restrict__ Kc,
-                                              int N, int sumK) {
+                                              int N, int sumK, const T *__restrict__ psi_inc = nullptr,
+                                              const int32_t *__restrict__ bc = nullptr, T *__restrict__ tot = nullptr) {
     __shared__ Affine<T> warp_tot[NT / 32];
-    const int n = blockIdx.x, b = blockIdx.y, r = blockIdx.z;
+    const int n = blockIdx.x, b = blockIdx.y, r = blockIdx.z, B = gridDim.y;
     const int K = Kc[b], o = off[b];
     const bool fwd = mu[n] > 0.0;
     const int nu_ = fwd ? 0 : 1, nd_ = 1 - nu_;
@@ -127,8 +139,31 @@ __global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__rest
         if (lane < NT / 32) warp_tot[lane] = t;  // inclusive prefix over warps
     }
     __syncthreads();
-    // exclusive prefix for this thread, applied to the vacuum inflow 0
-    T before_warp = (wid > 0) ? warp_tot[wid - 1].b : T(0);
+    if (kTotals) {
+        if (threadIdx.x == 0) {
+            const Affine<T> t = warp_tot[NT / 32 - 1];
+            T *o = tot + (((size_t)r * B + b) * N + n) * 2;
+            o[0] = t.a;
+            o[1] = t.b;
+        }
+        return;
+    }
+    // inflow at the upwind edge
+    const int s = fwd ? 0 : 1;
+    const size_t ib = (size_t)r * B + b;
+    T x0 = psi_inc ? psi_inc[(ib * 2 + s) * N + n] : T(0);
+    if (bc && bc[2 * b + s] == kBcReflect) {
+        const int nm = N - 1 - n;
+        const T *tn = tot + (ib * N + n) * 2, *tm = tot + (ib * N + nm) * 2;
+        if (bc[2 * b + 1 - s] == kBcReflect) {
+            x0 = (tm[0] * tn[1] + tm[1]) / (T(1) - tn[0] * tm[0]);
+        } else {
+            const T far = psi_inc ? psi_inc[(ib * 2 + 1 - s) * N + nm] : T(0);
+            x0 = tm[0] * far + tm[1];
+        }
+    }
+    // exclusive prefix for this thread, applied to the inflow x0
+    T before_warp = (wid > 0) ? warp_tot[wid - 1].a * x0 + warp_tot[wid - 1].b : x0;
     T inc_b_full = inc.a * before_warp + inc.b;  // inclusive, thread-level
     T x = __shfl_up_sync(0xffffffffu, inc_b_full, 1);
     if (lane == 0) x = before_warp;
@@ -295,7 +330,8 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
                                  const double *__restrict__ mu, const int32_t *__restrict__ cell_inst,
                                  const int32_t *__restrict__ off, const int32_t *__restrict__ Kc, int B,
                                  unsigned long long *__restrict__ conv, float *__restrict__ dq, int N, int sumK,
-                                 const double *__restrict__ Qang) {
+                                 const double *__restrict__ Qang, const double *__restrict__ psi_inc,
+                                 const int32_t *__restrict__ bc) {
     extern __shared__ unsigned char smem_raw[];
     double *Xs = reinterpret_cast<double *>(smem_raw);
     double *Ys = Xs + 2 * kContractCells * N;
@@ -332,12 +368,20 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
         const double m = mu[n], hh = h[g], st = sigma_t[g];
         const double pL = psr[((size_t)2 * g) * N + n], pR = psr[((size_t)2 * g + 1) * N + n];
         double tL, tR;
+        // inflow: the upwind neighbour's outflow, else the edge value (given incoming
+        // flux, or the mirror ordinate's outflow at a reflective edge)
         if (m > 0.0) {
-            const double pin = loc > 0 ? psr[((size_t)2 * (g - 1) + 1) * N + n] : 0.0;
+            double pin;
+            if (loc > 0) pin = psr[((size_t)2 * (g - 1) + 1) * N + n];
+            else if (bc && bc[2 * b] == kBcReflect) pin = psr[((size_t)2 * g) * N + (N - 1 - n)];
+            else pin = psi_inc ? psi_inc[(((size_t)r * B + b) * 2) * N + n] : 0.0;
             tL = 0.5 * m * (pL + pR) - m * pin;
             tR = 0.5 * m * (pR - pL);
         } else {
-            const double pin = loc < Kc[b] - 1 ? psr[((size_t)2 * (g + 1)) * N + n] : 0.0;
+            double pin;
+            if (loc < Kc[b] - 1) pin = psr[((size_t)2 * (g + 1)) * N + n];
+            else if (bc && bc[2 * b + 1] == kBcReflect) pin = psr[((size_t)2 * g + 1) * N + (N - 1 - n)];
+            else pin = psi_inc ? psi_inc[(((size_t)r * B + b) * 2 + 1) * N + n] : 0.0;
             tL = 0.5 * m * (pR - pL);
             tR = -0.5 * m * (pL + pR) + m * pin;  // -|mu| psi_in with mu < 0
         }
@@ -348,11 +392,12 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
     }
 }
 
-// psi64 += dpsi, dpsi = psi_half + upsilon of the last inner FPSA iteration (Eq. correct).
+// psi64 += dpsi, dpsi = psi_half + upsilon of the last inner FPSA iteration (Eq. correct);
+// ups NULL: dpsi = psi_half (inner SI, or the sweep after an inner GMRES solve).
 static __global__ void k_mixed_accumulate(double *__restrict__ psi, const float *__restrict__ psi_half,
                                    const float *__restrict__ ups, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        psi[i] += (double)psi_half[i] + (double)ups[i];
+        psi[i] += (double)psi_half[i] + (ups ? (double)ups[i] : 0.0);
 }
 
 // x (moments, padded to N) -> nodal angular values M x, used to turn a moment
@@ -405,41 +450,62 @@ static __global__ void k_conv_finalize(unsigned long long *conv, int nrb, double
 // Upwind couplings at level 0: B_g[p][p] = -mu_{N/2+p} (row L+ of g, column
 // R+ of g-1), C_g[p][p] = mu_p (row R- of g, column L- of g+1).
 // ---------------------------------------------------------------------------
+// Arithmetic in T (per-cell scalars in FP64, rounded once; mu passed in T): FP64
+// throughput is a small fraction of FP32 on this GPU, and the FP32 factor path
+// stores T anyway. Block (32, 8): x runs over the 2N columns of a row (coalesced
+// stores), y over rows. Reflective edges add -|mu_n| at (incoming n, mirror N-1-n)
+// of the edge node.
+// ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_fp_assemble(const double *__restrict__ mu, const double *__restrict__ Afp,
+__global__ void k_fp_assemble(const T *__restrict__ muT, const T *__restrict__ Afp,
                               const double *__restrict__ h, const double *__restrict__ sigma_t,
                               const double *__restrict__ sigma_s0, const double *__restrict__ sigma_s1,
                               const int32_t *__restrict__ cell_inst, const int32_t *__restrict__ off,
                               const int32_t *__restrict__ Kc, const int32_t *__restrict__ slot_base, int N,
-                              T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc) {
+                              T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc,
+                              const int32_t *__restrict__ bc = nullptr) {
     const int g = blockIdx.x;
-    const int n2 = 2 * N, h2 = N / 2;
-    const double hh = h[g];
-    const double sa = sigma_t[g] - sigma_s0[g];
-    const double str = sigma_s0[g] - sigma_s1[g];
-    T *Ag = A + (size_t)g * n2 * n2;
-    for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
-        const int row = idx / n2, col = idx - row * n2;
-        const int a = row / N, n = row - a * N, bb = col / N, m = col - bb * N;
-        const double mass = hh / 6.0 * (a == bb ? 2.0 : 1.0);
-        double v = mass * ((n == m ? sa : 0.0) - 0.5 * str * Afp[(size_t)n * N + m]);
-        if (n == m) {
-            const double x = mu[n];
-            const double pos = x > 0.0 ? 1.0 : 0.0, neg = 1.0 - pos;
-            const double G = (a == 0) ? (bb == 0 ? 0.5 * x - x * neg : 0.5 * x)
-                                      : (bb == 0 ? -0.5 * x : -0.5 * x + x * pos);
-            v += G;
-        }
-        Ag[idx] = (T)v;
-    }
     const int b = cell_inst[g];
     const int local = g - off[b];
+    const bool refl_l = bc && local == 0 && bc[2 * b] == kBcReflect;
+    const bool refl_r = bc && local == Kc[b] - 1 && bc[2 * b + 1] == kBcReflect;
+    const int n2 = 2 * N, h2 = N / 2;
+    // the cell's scalars, formed once per block in FP64 (kept in shared memory so the
+    // compiler does not re-form the FP64 divisions inside the element loop)
+    __shared__ T sc[4];
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const double hh = h[g];
+        sc[0] = (T)(hh / 3.0);
+        sc[1] = (T)(hh / 6.0);
+        sc[2] = (T)(sigma_t[g] - sigma_s0[g]);
+        sc[3] = (T)(-0.5 * (sigma_s0[g] - sigma_s1[g]));
+    }
+    __syncthreads();
+    const T m_d = sc[0], m_o = sc[1], sa = sc[2], hs = sc[3];
+    T *Ag = A + (size_t)g * n2 * n2;
+    for (int row = threadIdx.y; row < n2; row += blockDim.y) {
+        const int a = row >= N, n = row - a * N;
+        const T x = muT[n], half = T(0.5) * x;
+        const T gdiag = (a == 0) ? (x > T(0) ? half : -half) : (x > T(0) ? half : -half);  // G_aa
+        const T goff = (a == 0) ? half : -half;                                               // G_a,1-a
+        const bool refl = (refl_l && a == 0 && x > T(0)) || (refl_r && a == 1 && x < T(0));
+        const T* arow = Afp + (size_t)n * N;
+        T *out = Ag + (size_t)row * n2;
+        for (int col = threadIdx.x; col < n2; col += blockDim.x) {
+            const int bb = col >= N, m = col - bb * N;
+            T v = (a == bb ? m_d : m_o) * fma(hs, arow[m], n == m ? sa : T(0));
+            if (n == m) v += (a == bb) ? gdiag : goff;
+            if (refl && a == bb && m == N - 1 - n) v -= (x > T(0) ? x : -x);
+            out[col] = v;
+        }
+    }
     T *Bg = Bc + (size_t)slot_base[g] * h2 * h2;
     T *Cg = Cc + (size_t)slot_base[g] * h2 * h2;
-    for (int idx = threadIdx.x; idx < h2 * h2; idx += blockDim.x) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int idx = tid; idx < h2 * h2; idx += nt) {
         const int p = idx / h2, qq = idx - p * h2;
-        Bg[idx] = (p == qq && local > 0) ? (T)(-mu[h2 + p]) : T(0);
-        Cg[idx] = (p == qq && local < Kc[b] - 1) ? (T)(mu[p]) : T(0);
+        Bg[idx] = (p == qq && local > 0) ? -muT[h2 + p] : T(0);
+        Cg[idx] = (p == qq && local < Kc[b] - 1) ? muT[p] : T(0);
     }
 }
 
@@ -560,109 +626,166 @@ __global__ void k_bcr_invert(T *__restrict__ A, const BcrItem *__restrict__ item
 // (i < n2/32), so every thread holds an (n2/32) x (n2/16) tile in registers and
 // column k lives in one warp. Pivoting is implicit: step k picks, among rows not
 // yet used, the row p_k of largest |a[p][k]| (partial pivoting without moving
-// rows). The in-place update is the usual one with row p_k as pivot row; at the
-// end the array X holds A^{-1}[r][c] = X[p_r][q_c] with q the inverse of p
-// (row p_k carries step k's identity column). Written back transposed.
+// rows; the comparison key is |a| rounded to FP32). The in-place update is the
+// usual one with row p_k as pivot row; at the end the array X holds
+// A^{-1}[r][c] = X[p_r][q_c] with q the inverse of p (row p_k carries step k's
+// identity column). Written back transposed.
+//
+// One block barrier per step: the pivot row reaches the other lanes of each warp
+// by shuffles (every warp holds all rows of its columns), only column k goes
+// through shared memory, and the warp owning column k+1 updates that column first
+// and picks pivot k+1 (look-ahead) while the other warps are still updating.
 // Body shared by the in-place kernel and the strided sub-block variant: src / dst
 // are N2 x N2 row-major with leading dimensions lds / ldd; transposed output when
 // tout; growth may be NULL.
+template <typename T, int RI>
+__device__ __forceinline__ void gj_pick_pivot(const T (&colv)[RI], unsigned used, int lane, int &p) {
+    // key 0: no candidate; else the FP32 bits of |v| plus one (|v| >= 0 orders as unsigned)
+    unsigned best = 0u;
+    int bi = 0;
+#pragma unroll
+    for (int i = 0; i < RI; ++i) {
+        const unsigned key = (used >> i) & 1u ? 0u : __float_as_uint(fabsf((float)colv[i])) + 1u;
+        if (key > best) { best = key; bi = lane + 32 * i; }
+    }
+    const unsigned m = __reduce_max_sync(0xffffffffu, best);
+    const unsigned who = __ballot_sync(0xffffffffu, best == m);
+    p = __shfl_sync(0xffffffffu, bi, __ffs(who) - 1);
+}
+
+// rv[j] = (row ip of lane pl's register tile)[j] * inv, broadcast to the warp by
+// shuffles; ip and pl are warp-uniform, so the row is chosen by a branch.
+template <typename T, int RI, int CJ>
+__device__ __forceinline__ void gj_pivot_row(const T (&x)[RI][CJ], int ip, int pl, T inv, T (&rv)[CJ]) {
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+        if (i == ip) {
+#pragma unroll
+            for (int j = 0; j < CJ; ++j) rv[j] = __shfl_sync(0xffffffffu, x[i][j], pl) * inv;
+        }
+}
+
+// x[I][j] = rv[j] for every j except jskip (the look-ahead column, already set).
+template <typename T, int RI, int CJ, int I>
+__device__ __forceinline__ void gj_set_row_i(T (&x)[RI][CJ], const T (&rv)[CJ], int jskip) {
+    if constexpr (I < RI) {
+#pragma unroll
+        for (int j = 0; j < CJ; ++j)
+            if (j != jskip) x[I][j] = rv[j];
+    }
+}
+
+template <typename T, int RI, int CJ>
+__device__ __forceinline__ void gj_set_row_elem(T (&x)[RI][CJ], int ip, int j, T val) {
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+        if (i == ip) x[i][j] = val;
+}
+
 template <typename T, int N2>
 __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int ldd, bool tout,
                                             unsigned long long *__restrict__ growth, int *__restrict__ status) {
     constexpr int RI = N2 / 32, CJ = N2 / 16;
-    __shared__ T colbuf[2][N2], rowbuf[2][N2];
-    __shared__ int s_p[2], used[N2], perm[N2], iperm[N2];
+    __shared__ T colbuf[2][N2];
+    __shared__ int s_p[2], perm[N2], iperm[N2];
     __shared__ double s_red[16];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     T x[RI][CJ];
-    double amax = 0.0;
+    T amax = T(0);  // growth bookkeeping in T (FP64 only for the final product)
 #pragma unroll
     for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int j = 0; j < CJ; ++j) {
             x[i][j] = src[(size_t)(lane + 32 * i) * lds + w + 16 * j];
-            amax = fmax(amax, fabs((double)x[i][j]));
+            amax = fmax(amax, fabs(x[i][j]));
         }
-    for (int r = threadIdx.x; r < N2; r += blockDim.x) used[r] = 0;
+    unsigned used = 0u;  // bit i: row lane + 32 i has been a pivot row
     bool bad = false;
+    if (w == 0) {  // pivot of step 0 (column 0 = x[.][0] of warp 0)
+        T colv[RI];
+#pragma unroll
+        for (int i = 0; i < RI; ++i) {
+            colv[i] = x[i][0];
+            colbuf[0][lane + 32 * i] = colv[i];
+        }
+        int pn;
+        gj_pick_pivot<T, RI>(colv, used, lane, pn);
+        if (lane == 0) {
+            s_p[0] = pn;
+            perm[0] = pn;
+            iperm[pn] = 0;
+        }
+    }
     __syncthreads();
     for (int k = 0; k < N2; ++k) {
         const int b = k & 1;
-        const int jk = k >> 4;  // column k is x[.][jk] of warp k % 16
-        if (w == (k & 15)) {
-            T best = T(-1);
-            int bi = N2;
-            T colv[RI];
-#pragma unroll
-            for (int i = 0; i < RI; ++i) {
-#pragma unroll
-                for (int j = 0; j < CJ; ++j)
-                    if (j == jk) colv[i] = x[i][j];
-                const int row = lane + 32 * i;
-                colbuf[b][row] = colv[i];
-                const T v = fabs(colv[i]);
-                if (!used[row] && v > best) { best = v; bi = row; }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) {
-                s_p[b] = bi;
-                used[bi] = 1;
-                perm[k] = bi;
-                iperm[bi] = k;
-            }
-        }
-        __syncthreads();
         const int p = s_p[b];
         const T pv = colbuf[b][p];
         if (pv == T(0) || !isfinite(pv)) bad = true;
         const T inv = T(1) / pv;
-        const int ip = p >> 5;
-        if (lane == (p & 31)) {
-#pragma unroll
-            for (int i = 0; i < RI; ++i)
-                if (i == ip)
-#pragma unroll
-                    for (int j = 0; j < CJ; ++j) {
-                        const int col = w + 16 * j;
-                        rowbuf[b][col] = (col == k) ? inv : x[i][j] * inv;
-                    }
-        }
-        __syncthreads();
+        const int ip = p >> 5, pl = p & 31;
+        if (lane == pl) used |= 1u << ip;
         T f[RI], rv[CJ];
 #pragma unroll
         for (int i = 0; i < RI; ++i) f[i] = colbuf[b][lane + 32 * i];
-#pragma unroll
-        for (int j = 0; j < CJ; ++j) rv[j] = rowbuf[b][w + 16 * j];
-        if (w == (k & 15)) {
-            // this warp owns column k: its old value is replaced, not updated
+        // pivot row values of this warp's columns, from lane pl
+        gj_pivot_row<T, RI, CJ>(x, ip, pl, inv, rv);
+        const bool own = w == (k & 15);
+        const int jk = k >> 4;
+        if (own) {  // column k: its old value is replaced, not updated
 #pragma unroll
             for (int j = 0; j < CJ; ++j)
-                if (j == jk)
+                if (j == jk) {
+                    rv[j] = inv;
 #pragma unroll
                     for (int i = 0; i < RI; ++i) x[i][j] = T(0);
+                }
+        }
+        const bool ahead = k + 1 < N2 && w == ((k + 1) & 15);
+        const int jn = (k + 1) >> 4;
+        if (ahead) {
+            // look-ahead: update column k+1 now and pick pivot k+1
+            T colv[RI];
+#pragma unroll
+            for (int j = 0; j < CJ; ++j)
+                if (j == jn) {
+#pragma unroll
+                    for (int i = 0; i < RI; ++i) x[i][j] = fma(-f[i], rv[j], x[i][j]);
+                    if (lane == pl) gj_set_row_elem<T, RI, CJ>(x, ip, j, rv[j]);
+#pragma unroll
+                    for (int i = 0; i < RI; ++i) colv[i] = x[i][j];
+                }
+#pragma unroll
+            for (int i = 0; i < RI; ++i) colbuf[b ^ 1][lane + 32 * i] = colv[i];
+            int pn;
+            gj_pick_pivot<T, RI>(colv, used, lane, pn);
+            if (lane == 0) {
+                s_p[b ^ 1] = pn;
+                perm[k + 1] = pn;
+                iperm[pn] = k + 1;
+            }
         }
 #pragma unroll
-        for (int i = 0; i < RI; ++i)
+        for (int j = 0; j < CJ; ++j) {
+            if (ahead && j == jn) continue;
 #pragma unroll
-            for (int j = 0; j < CJ; ++j) x[i][j] = fma(-f[i], rv[j], x[i][j]);
-        if (lane == (p & 31)) {
-            // the pivot row becomes the scaled row (its f is the pivot itself)
-#pragma unroll
-            for (int i = 0; i < RI; ++i)
-                if (i == ip)
-#pragma unroll
-                    for (int j = 0; j < CJ; ++j) x[i][j] = rv[j];
+            for (int i = 0; i < RI; ++i) x[i][j] = fma(-f[i], rv[j], x[i][j]);
         }
+        // the pivot row becomes the scaled row (its own update used f = pv)
+        if (lane == pl) {
+            const int js = ahead ? jn : -1;
+            switch (ip) {
+                case 0: gj_set_row_i<T, RI, CJ, 0>(x, rv, js); break;
+                case 1: gj_set_row_i<T, RI, CJ, 1>(x, rv, js); break;
+                case 2: gj_set_row_i<T, RI, CJ, 2>(x, rv, js); break;
+                default: gj_set_row_i<T, RI, CJ, 3>(x, rv, js); break;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // Thread holds X[row][col] = A^{-1}[r][c] with perm[r] = row (r = iperm[row]) and
-    // iperm[c] = col (c = perm[col]); written transposed, Ag[c][r].
-    double ainv = 0.0;
+    // iperm[c] = col (c = perm[col]); written transposed when tout.
+    T ainv = T(0);
 #pragma unroll
     for (int i = 0; i < RI; ++i)
 #pragma unroll
@@ -671,14 +794,14 @@ __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int l
             const int r = iperm[row], c = perm[col];
             if (tout) dst[(size_t)c * ldd + r] = x[i][j];
             else dst[(size_t)r * ldd + c] = x[i][j];
-            ainv = fmax(ainv, fabs((double)x[i][j]));
-            if (!isfinite((double)x[i][j])) bad = true;
+            ainv = fmax(ainv, fabs(x[i][j]));
+            if (!isfinite(x[i][j])) bad = true;
         }
     for (int o = 16; o > 0; o >>= 1) {
         amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         ainv = fmax(ainv, __shfl_xor_sync(0xffffffffu, ainv, o));
     }
-    if (lane == 0) s_red[w] = amax;
+    if (lane == 0) s_red[w] = (double)amax;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = 0.0;
@@ -686,7 +809,7 @@ __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int l
         s_red[0] = m;
     }
     __syncthreads();
-    if (growth && lane == 0) atomicMax(growth, dkey(ainv * s_red[0]));
+    if (growth && lane == 0) atomicMax(growth, dkey((double)ainv * s_red[0]));
     if (bad) atomicExch(status, 1);
 }
 
@@ -836,9 +959,45 @@ struct VecOf<double> {
     static constexpr int V = 2;
 };
 
-// shared scratch (values of T) of one solve block handling RC right-hand sides
-__host__ __device__ constexpr int bcr_unit_smem_values(int N, int NT, int V, int RC) {
-    return RC * (2 * N) + RC * (2 * N) + RC * N + NT * V * RC;
+// Coupling blocks of one unit (the two N/2 x N/2 blocks it multiplies) are staged
+// in shared memory by asynchronous copies issued when the unit starts, when both
+// fit in 16 KB and a block is a whole number of 16-byte chunks.
+__host__ __device__ constexpr int bcr_coupling_values(int N) { return 2 * (N / 2) * (N / 2); }
+__host__ __device__ constexpr bool bcr_couplings_staged(int N, int esize) {
+    return bcr_coupling_values(N) * esize <= 16384 && ((N / 2) * (N / 2) * esize) % 16 == 0;
+}
+
+// shared scratch (values of T) of one solve block handling RC right-hand sides:
+// rs, ys (RC x 2N), pushed products (RC x N), partial sums (NT x V x RC), couplings
+__host__ __device__ constexpr int bcr_unit_smem_values(int N, int NT, int V, int RC, int esize) {
+    return RC * (2 * N) + RC * (2 * N) + RC * N + NT * V * RC + (bcr_couplings_staged(N, esize) ? bcr_coupling_values(N) : 0);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Start copying the coupling blocks m0, m1 (either may be NULL) into cbuf[0, hh) and
+// cbuf[hh, 2 hh); returns the shared-memory copies (NULL where absent), or m0, m1
+// themselves when cbuf is NULL (blocks read from global memory).
+template <typename T>
+__device__ __forceinline__ void stage_couplings(const T *&m0, const T *&m1, T *cbuf, int hh) {
+    if (!cbuf) return;
+    const int chunks = hh * (int)sizeof(T) / 16;
+    for (int c = threadIdx.x; c < 2 * chunks; c += blockDim.x) {
+        const int side = c >= chunks, cc = c - side * chunks;
+        const T *src = side ? m1 : m0;
+        if (src)
+            cp_async16(reinterpret_cast<unsigned char *>(cbuf + side * hh) + 16 * cc,
+                       reinterpret_cast<const unsigned char *>(src) + 16 * cc);
+    }
+    cp_async_commit();
+    m0 = m0 ? cbuf : nullptr;
+    m1 = m1 ? cbuf + hh : nullptr;
 }
 
 template <typename T>
@@ -850,42 +1009,67 @@ __device__ __forceinline__ T group_sum(T v, int G) {
 // For RC right-hand sides at once (coef[rc][k], row stride cstride):
 // part[ks][rc][row] = sum over the k of slice ks of Mt[col(k)][row0 + row] * coef[rc][k],
 // rows [row0, row0 + nr), col(k) = col_off0 + k for k < col_split else col_off1 + k - col_split.
+// Each thread owns one (row group of V rows, k-slice) task and loads its A^{-1}
+// vectors into registers in chunks of KC columns; the first chunk is requested
+// BEFORE stage() runs (stage stages the coefficients and ends with a block
+// barrier), so the factor reads overlap the wait for the right-hand side.
 // Each A^{-1} vector is loaded once and used for all RC right-hand sides.
 // Returns the number of k-slices.
-template <typename T, int NT, int RC>
+constexpr int kMatvecChunk = 16;
+template <typename T, int NT, int RC, typename Stage>
 __device__ __forceinline__ int sliced_matvec(const T *__restrict__ Mt, int n2, int row0, int nr, int nk,
                                              int col_split, int col_off0, int col_off1, const T *coef, int cstride,
-                                             T *part) {
+                                             T *part, Stage stage) {
     using VT = typename VecOf<T>::type;
-    constexpr int V = VecOf<T>::V;
+    constexpr int V = VecOf<T>::V, KC = kMatvecChunk;
     const int RG = nr / V;
     int KS = NT / RG;
     if (KS > nk) KS = nk;
     if (KS < 1) KS = 1;
     const int kl = (nk + KS - 1) / KS;
-    for (int t = threadIdx.x; t < RG * KS; t += NT) {
-        const int rg = t % RG, ks = t / RG;
-        const int k0 = ks * kl, k1 = min(nk, k0 + kl);
-        T acc[RC][V];
+    const int t = threadIdx.x;
+    const bool act = t < RG * KS;  // RG * KS <= NT for nr <= V * NT
+    const int rg = act ? t % RG : 0, ks = act ? t / RG : 0;
+    const int k0 = ks * kl, k1 = act ? min(nk, k0 + kl) : k0;
+    auto col_of = [&](int k) { return (k < col_split) ? col_off0 + k : col_off1 + (k - col_split); };
+    VT a[KC];
 #pragma unroll
-        for (int rc = 0; rc < RC; ++rc)
+    for (int kk = 0; kk < KC; ++kk) {
+        const int k = k0 + kk;
+        if (k < k1) a[kk] = __ldg(reinterpret_cast<const VT *>(Mt + (size_t)col_of(k) * n2 + row0) + rg);
+    }
+    stage();
+    T acc[RC][V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[rc][v] = T(0);
-#pragma unroll 8
-        for (int k = k0; k < k1; ++k) {
-            const int col = (k < col_split) ? col_off0 + k : col_off1 + (k - col_split);
-            const VT a = __ldg(reinterpret_cast<const VT *>(Mt + (size_t)col * n2 + row0) + rg);
+    for (int rc = 0; rc < RC; ++rc)
 #pragma unroll
-            for (int rc = 0; rc < RC; ++rc) {
-                const T c = coef[rc * cstride + k];
-                if constexpr (V == 4) {
-                    acc[rc][0] = fma(a.x, c, acc[rc][0]); acc[rc][1] = fma(a.y, c, acc[rc][1]);
-                    acc[rc][2] = fma(a.z, c, acc[rc][2]); acc[rc][3] = fma(a.w, c, acc[rc][3]);
-                } else {
-                    acc[rc][0] = fma(a.x, c, acc[rc][0]); acc[rc][1] = fma(a.y, c, acc[rc][1]);
+        for (int v = 0; v < V; ++v) acc[rc][v] = T(0);
+    for (int c0 = k0; c0 < k1; c0 += KC) {
+        if (c0 > k0) {
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                const int k = c0 + kk;
+                if (k < k1) a[kk] = __ldg(reinterpret_cast<const VT *>(Mt + (size_t)col_of(k) * n2 + row0) + rg);
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+            const int k = c0 + kk;
+            if (k < k1) {
+#pragma unroll
+                for (int rc = 0; rc < RC; ++rc) {
+                    const T cv = coef[rc * cstride + k];
+                    if constexpr (V == 4) {
+                        acc[rc][0] = fma(a[kk].x, cv, acc[rc][0]); acc[rc][1] = fma(a[kk].y, cv, acc[rc][1]);
+                        acc[rc][2] = fma(a[kk].z, cv, acc[rc][2]); acc[rc][3] = fma(a[kk].w, cv, acc[rc][3]);
+                    } else {
+                        acc[rc][0] = fma(a[kk].x, cv, acc[rc][0]); acc[rc][1] = fma(a[kk].y, cv, acc[rc][1]);
+                    }
                 }
             }
         }
+    }
+    if (act) {
 #pragma unroll
         for (int rc = 0; rc < RC; ++rc)
 #pragma unroll
@@ -897,11 +1081,14 @@ __device__ __forceinline__ int sliced_matvec(const T *__restrict__ Mt, int n2, i
 // Up to two h2 x h2 coupling products for RC vectors at once, all NT threads:
 // rows (side, p) of M_side (row-major), a group of G threads per row, each
 // reading a contiguous k-range once for all RC vectors; partial sums meet by
-// shuffles. out_side[rc * ostride + p] = sum_k M_side[p][k] v_side[rc * vstride + k].
+// shuffles (M_side in global or shared memory). With nred = 0:
+// out_side[rc * ostride + p] = sum_k M_side[p][k] v_side[rc * vstride + k]
+// (shared memory). With nred > 0: out_side[rc * ostride + p] -= that sum for rc < nred, as a
+// reduction without return in global memory.
 template <typename T, int NT, int RC>
 __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, const T *v0, T *out0,
                                                   const T *__restrict__ M1, const T *v1, T *out1, int h2,
-                                                  int vstride, int ostride) {
+                                                  int vstride, size_t ostride, int nred = 0) {
     const int nrows = (M0 ? h2 : 0) + (M1 ? h2 : 0);
     if (nrows == 0) return;
     int G = 1;
@@ -921,7 +1108,7 @@ __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, cons
             const int k0 = gq * kl, k1 = min(h2, k0 + kl);
 #pragma unroll 4
             for (int k = k0; k < k1; ++k) {
-                const T m = __ldg(M + (size_t)p * h2 + k);
+                const T m = M[(size_t)p * h2 + k];
 #pragma unroll
                 for (int rc = 0; rc < RC; ++rc) acc[rc] = fma(m, v[rc * vstride + k], acc[rc]);
             }
@@ -929,7 +1116,11 @@ __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, cons
 #pragma unroll
         for (int rc = 0; rc < RC; ++rc) {
             const T s = group_sum(acc[rc], G);
-            if (live && gq == 0) (second ? out1 : out0)[rc * ostride + p] = s;
+            if (live && gq == 0) {
+                T *o = (second ? out1 : out0) + rc * ostride + p;
+                if (nred == 0) *o = s;
+                else if (rc < nred) atomicAdd(o, -s);
+            }
         }
     }
 }
@@ -940,16 +1131,23 @@ __device__ __forceinline__ void bcr_fwd_unit(const T *__restrict__ A, const T *_
                                              const T *__restrict__ Cc, const BcrItem &it, int r0, int nrc, int sl,
                                              int S, T *rhs, T *Y, int N, int sumK, T *sm) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
-    T *rs = sm, *ys = sm + RC * n2, *pr = ys + RC * n2, *part = pr + RC * N;  // pr: pushed products
+    T *rs = sm, *ys = sm + RC * n2, *part = ys + RC * n2 + RC * N;
+    T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
     const size_t rstride = (size_t)sumK * n2;  // between right-hand sides
-    for (int i = threadIdx.x; i < RC * n2; i += NT) {
-        const int rc = i / n2, k = i - rc * n2;
-        rs[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
-    }
-    __syncthreads();
     const int nr = n2 / S, row0 = sl * nr;
     const T *Ai = A + (size_t)it.cell * n2 * n2;
-    const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, n2, n2, 0, 0, rs, n2, part);
+    const bool push_right = it.right >= 0 && row0 + nr == n2;  // this slice holds R+
+    const bool push_left = it.left >= 0 && row0 == 0;          // this slice holds L-
+    const T *mB = push_right ? Bc + (size_t)it.s_right * hh : nullptr;
+    const T *mC = push_left ? Cc + (size_t)it.s_left * hh : nullptr;
+    stage_couplings(mB, mC, cbuf, hh);  // in flight during the matrix-vector product
+    const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, n2, n2, 0, 0, rs, n2, part, [&] {
+        for (int i = threadIdx.x; i < RC * n2; i += NT) {
+            const int rc = i / n2, k = i - rc * n2;
+            rs[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
+        }
+        __syncthreads();
+    });
     __syncthreads();
     for (int idx = threadIdx.x; idx < RC * nr; idx += NT) {
         const int rc = idx / nr, row = idx - rc * nr;
@@ -958,24 +1156,14 @@ __device__ __forceinline__ void bcr_fwd_unit(const T *__restrict__ A, const T *_
         ys[rc * n2 + row0 + row] = y;
         if (rc < nrc) Y[(size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row] = y;
     }
+    if (cbuf) cp_async_wait_all();
     __syncthreads();
-    const bool push_right = it.right >= 0 && row0 + nr == n2;  // this slice holds R+
-    const bool push_left = it.left >= 0 && row0 == 0;          // this slice holds L-
-    coupling_products<T, NT, RC>(push_right ? Bc + (size_t)it.s_right * hh : nullptr, ys + N + h2, pr,
-                                 push_left ? Cc + (size_t)it.s_left * hh : nullptr, ys, pr + h2, h2, n2, N);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nrc * N; idx += NT) {
-        const int rc = idx / N, p = idx - rc * N;
-        T *base = rhs + (size_t)(r0 + rc) * rstride;
-        if (p < h2 && push_right) {
-            T *rj = base + (size_t)it.right * n2 + h2 + p;  // L+
-            *rj = __ldcg(rj) - pr[rc * N + p];
-        }
-        if (p >= h2 && push_left) {
-            T *rj = base + (size_t)it.left * n2 + N + (p - h2);  // R-
-            *rj = __ldcg(rj) - pr[rc * N + p];
-        }
-    }
+    // pushes as reductions without return (one writer per sub-vector and level, so
+    // old - product is formed exactly as a read-modify-write would)
+    coupling_products<T, NT, RC>(mB, ys + N + h2,
+                                 push_right ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr,
+                                 mC, ys, push_left ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr,
+                                 h2, n2, rstride, nrc);
     __syncthreads();  // scratch reuse by the block's next unit
 }
 
@@ -984,34 +1172,37 @@ __device__ __forceinline__ void bcr_bwd_unit(const T *__restrict__ A, const T *_
                                              const T *__restrict__ Cc, const BcrItem &it, int r0, int nrc, int sl,
                                              int S, T *Y, int N, int sumK, T *sm) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
-    T *gv = sm, *g = sm + RC * N, *part = g + RC * N;  // gv[rc] = [u_left[R+], u_right[L-]]
+    T *gv = sm, *g = sm + RC * N, *part = sm + RC * (5 * N);  // gv[rc] = [u_left[R+], u_right[L-]]
+    T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
     const size_t rstride = (size_t)sumK * n2;
-    for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
-        const int rc = idx / N, k = idx - rc * N;
-        T v = T(0);
-        if (rc < nrc) {
-            const T *base = Y + (size_t)(r0 + rc) * rstride;
-            if (k < h2) v = __ldcg(base + (size_t)it.left * n2 + N + h2 + k);
-            else if (it.right >= 0) v = __ldcg(base + (size_t)it.right * n2 + (k - h2));
-        }
-        gv[idx] = v;
-    }
-    __syncthreads();
-    coupling_products<T, NT, RC>(Bc + (size_t)it.s_cell * hh, gv, g,
-                                 it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr, gv + h2, g + h2, h2, N, N);
-    if (it.right < 0)
-        for (int idx = threadIdx.x; idx < RC * h2; idx += NT) g[(idx / h2) * N + h2 + idx % h2] = T(0);
-    __syncthreads();
     const int nr = n2 / S, row0 = sl * nr;
     const T *Ai = A + (size_t)it.cell * n2 * n2;
-    const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, N, h2, h2, N, g, N, part);
+    const T *mB = Bc + (size_t)it.s_cell * hh, *mC = it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr;
+    stage_couplings(mB, mC, cbuf, hh);
+    const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, N, h2, h2, N, g, N, part, [&] {
+        for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
+            const int rc = idx / N, k = idx - rc * N;
+            T v = T(0);
+            if (rc < nrc) {
+                const T *base = Y + (size_t)(r0 + rc) * rstride;
+                if (k < h2) v = __ldcg(base + (size_t)it.left * n2 + N + h2 + k);
+                else if (it.right >= 0) v = __ldcg(base + (size_t)it.right * n2 + (k - h2));
+            }
+            gv[idx] = v;
+        }
+        if (cbuf) cp_async_wait_all();
+        __syncthreads();
+        coupling_products<T, NT, RC>(mB, gv, g, mC, gv + h2, g + h2, h2, N, N);
+        if (it.right < 0)
+            for (int idx = threadIdx.x; idx < RC * h2; idx += NT) g[(idx / h2) * N + h2 + idx % h2] = T(0);
+        __syncthreads();
+    });
     __syncthreads();
     for (int idx = threadIdx.x; idx < nrc * nr; idx += NT) {
         const int rc = idx / nr, row = idx - rc * nr;
         T s = T(0);
         for (int q = 0; q < KS; ++q) s += part[(q * RC + rc) * nr + row];
-        T *ui = Y + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row;
-        *ui = __ldcg(ui) - s;
+        atomicAdd(Y + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row, -s);
     }
     __syncthreads();
 }
@@ -1026,11 +1217,6 @@ struct LevelTable {
     int32_t n_levels, n_roots;
 };
 
-// The whole BCR solve in one cooperative launch: forward levels, roots, backward
-// levels, separated by grid-wide barriers (all blocks are co-resident by the
-// cooperative launch, so every barrier completes). Blocks take
-// (item, right-hand-side chunk of RC, row slice) units block-stride within a level.
-// Solution left in Y.
 // L2 prefetch of the data a forward (bwd = false) or backward unit will read:
 // its A^{-1} row slice (all 2N columns forward, the N inflow columns backward;
 // one 128-byte line per column for slices of <= 128 bytes) and its coupling blocks.
@@ -1072,6 +1258,7 @@ __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, 
     T *sm = reinterpret_cast<T *>(smem_raw);
     cg::grid_group grid = cg::this_grid();
     const int nchunk = (R + RC - 1) / RC;
+
     auto level_units = [&](int l) {
         const int nitems = (l < lv.n_levels) ? lv.off[l + 1] - lv.off[l] : lv.n_roots;
         return nitems * nchunk * lv.slices[l];
@@ -1082,29 +1269,37 @@ __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, 
         for (int w = blockIdx.x; w < nw; w += gridDim.x)
             prefetch_unit(A, Bc, Cc, items[lv.off[l] + w / (S * nchunk)], w % S, S, N, bwd);
     };
+    // A level with more units than blocks runs long enough to hide the next level's
+    // prefetch behind its own work; after a short level the prefetch is issued once the
+    // block's unit is done, so it overlaps the barrier instead of delaying the unit.
     for (int l = 0; l <= lv.n_levels; ++l) {  // level n_levels = the roots
-        prefetch_level(l + 1, false);
         const int base = lv.off[l], S = lv.slices[l];
         const int nw = level_units(l);
+        const bool early = nw > (int)gridDim.x;
+        if (early) prefetch_level(l + 1, false);
         for (int w = blockIdx.x; w < nw; w += gridDim.x) {
             const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
             const int r0 = ch * RC;
             bcr_fwd_unit<T, NT, RC>(A, Bc, Cc, items[base + item], r0, min(RC, R - r0), sl, S, rhs, Y, N, sumK, sm);
         }
+        if (!early) prefetch_level(l < lv.n_levels ? l + 1 : lv.n_levels - 1, l == lv.n_levels);
         if (l < lv.n_levels) grid.sync();
     }
     for (int l = lv.n_levels - 1; l >= 0; --l) {
         grid.sync();
-        prefetch_level(l - 1, true);
         const int base = lv.off[l], S = lv.slices[l];
         const int nw = (lv.off[l + 1] - base) * nchunk * S;
+        const bool early = nw > (int)gridDim.x;
+        if (early) prefetch_level(l - 1, true);
         for (int w = blockIdx.x; w < nw; w += gridDim.x) {
             const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
             const int r0 = ch * RC;
             bcr_bwd_unit<T, NT, RC>(A, Bc, Cc, items[base + item], r0, min(RC, R - r0), sl, S, Y, N, sumK, sm);
         }
+        if (!early) prefetch_level(l - 1, true);
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // Adjoint (implicit differentiation of the converged discrete solution; the

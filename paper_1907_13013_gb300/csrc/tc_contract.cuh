@@ -155,9 +155,18 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Shared-memory plan of one contraction CTA for N (multiple of 16, <= 256):
+// Staged global I/O: a tile's 128 columns are 128 contiguous rows of N floats in
+// global memory; they move through padded shared buffers [128][kStageLd] in
+// k-chunks of kStageK with coalesced 16-byte accesses, and each thread then reads
+// or writes its own row (the accumulator lane layout) without bank conflicts.
+constexpr int kStageK = 16;
+constexpr int kStageLd = kStageK + 4;
+constexpr uint32_t kStageBytes = 128u * kStageLd * 4;
+
+// Shared-memory plan of one contraction CTA for N (multiple of 16, <= 128):
 //   opD_hi, opD_lo, opM_hi, opM_lo: N x N BF16 each (constant operands)
 //   x_hi, x_lo:                     128 x N BF16 each (the column tile)
+//   stage[3]:                       [128][kStageLd] FP32 each (staged I/O)
 //   bars: 2 mbarriers (bulk copy, MMA), tmem slot
 struct Plan {
     uint32_t op_bytes, x_bytes, total;
@@ -165,10 +174,47 @@ struct Plan {
         Plan p;
         p.op_bytes = (uint32_t)N * N * 2;
         p.x_bytes = 128u * N * 2;
-        p.total = 4 * p.op_bytes + 2 * p.x_bytes + 64;
+        p.total = 4 * p.op_bytes + 2 * p.x_bytes + 3 * kStageBytes + 64;
         return p;
     }
 };
+
+// st[row][0..kStageK) = src[row * N + k0 ..] for rows < nrows, 0 above (all 128 threads).
+__device__ __forceinline__ void stage_in(float *st, const float *src, int N, int nrows, int k0) {
+    constexpr int Q = kStageK / 4;  // float4 per row chunk
+    for (int f = threadIdx.x; f < 128 * Q; f += 128) {
+        const int row = f / Q, q = f - row * Q;
+        const float4 v = row < nrows ? __ldg(reinterpret_cast<const float4 *>(src + (size_t)row * N + k0) + q)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4 *>(st + row * kStageLd + 4 * q) = v;
+    }
+}
+
+// dst[row * N + k0 ..] = st[row][0..kStageK) for rows < nrows (all 128 threads).
+__device__ __forceinline__ void stage_out(const float *st, float *dst, int N, int nrows, int k0) {
+    constexpr int Q = kStageK / 4;
+    for (int f = threadIdx.x; f < 128 * Q; f += 128) {
+        const int row = f / Q, q = f - row * Q;
+        if (row < nrows)
+            reinterpret_cast<float4 *>(dst + (size_t)row * N + k0)[q] =
+                *reinterpret_cast<const float4 *>(st + row * kStageLd + 4 * q);
+    }
+}
+
+__device__ __forceinline__ void row_get16(const float *st, int row, float *v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 x = *reinterpret_cast<const float4 *>(st + row * kStageLd + 4 * q);
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+}
+
+__device__ __forceinline__ void row_put16(float *st, int row, const float *v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4 *>(st + row * kStageLd + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2],
+                                                                              v[4 * q + 3]);
+}
 
 __host__ __device__ constexpr uint32_t tmem_cols_for(int N) { return N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u)); }
 
@@ -206,21 +252,13 @@ __device__ __forceinline__ void store_split_row16(unsigned char *x_hi, unsigned 
     }
 }
 
-// 16 consecutive floats from 16-byte aligned global memory (or zeros).
-__device__ __forceinline__ void load16(const float *p, bool live, float *v) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 x = live ? __ldg(reinterpret_cast<const float4 *>(p) + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
-    }
-}
-
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
 // Fused FPSA contraction kernels on tensor cores (FP32 data), persistent over
 // 128-column tiles. Columns are (cell, node) pairs of one rhs: column index
-// j = 2 g + a within rhs r. 128 threads: thread t owns tile row t.
+// j = 2 g + a within rhs r. 128 threads: thread t owns tile row t (accumulator
+// lane t); global reads and writes go through the staged, coalesced k-chunks.
 //   k_tc_fp_rhs:        phi_half = D psi;  rhs = m (x) M Sigma (phi_half - phi)
 //   k_tc_update_scatter: phi = phi_base + D v;  q = M (Sigma phi) + q_ang
 // err is set to 1 if an mbarrier wait ran out (the kernel then stops).
@@ -233,6 +271,7 @@ struct TcOps {
 // Common prologue: smem carve-up, TMEM allocation, operand staging. Returns false on timeout.
 struct TcCta {
     unsigned char *opD_hi, *opD_lo, *opM_hi, *opM_lo, *x_hi, *x_lo;
+    float *stA, *stB, *stC;
     uint64_t *bar_copy, *bar_mma;
     uint32_t *tmem_slot;
     uint32_t tmem;
@@ -247,7 +286,10 @@ __device__ __forceinline__ bool tc_cta_setup(TcCta &s, unsigned char *smem, cons
     s.opM_lo = smem + 3 * pl.op_bytes;
     s.x_hi = smem + 4 * pl.op_bytes;
     s.x_lo = s.x_hi + pl.x_bytes;
-    unsigned char *tail = s.x_lo + pl.x_bytes;
+    s.stA = reinterpret_cast<float *>(s.x_lo + pl.x_bytes);
+    s.stB = s.stA + 128 * tc::kStageLd;
+    s.stC = s.stB + 128 * tc::kStageLd;
+    unsigned char *tail = reinterpret_cast<unsigned char *>(s.stC + 128 * tc::kStageLd);
     s.bar_copy = reinterpret_cast<uint64_t *>(tail);
     s.bar_mma = s.bar_copy + 1;
     s.tmem_slot = reinterpret_cast<uint32_t *>(s.bar_mma + 1);
@@ -312,44 +354,53 @@ __global__ void __launch_bounds__(128) k_tc_fp_rhs(const float *__restrict__ psi
     bool ok = ok0;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
-        const int j = j0 + t;  // this thread's column
-        const bool live = j < 2 * sumK;
-        const size_t col = (size_t)r * sumK * 2 + j;
+        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const bool live = t < ncols;
+        const int g = (j0 + t) >> 1;
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;  // the tile's first element
+        const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
         // A = psi columns
-        for (int k0 = 0; k0 < N; k0 += 16) {
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(s.stA, psi_half + cb, N, ncols, k0);
+            __syncthreads();
             float v[16];
-            tc::load16(psi_half + col * N + k0, live, v);
+            tc::row_get16(s.stA, t, v);
             tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
         }
         if (!(ok = tc_gemm(s, s.opD_hi, s.opD_lo, N, err))) break;
         // phi_half = D psi; next A = Sigma (phi_half - phi)
-        const int g = j >> 1;
-        for (int k0 = 0; k0 < N; k0 += 16) {
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(s.stA, phi + cb, N, ncols, k0);
+            tc::stage_in(s.stB, sig, N, ncell, k0);
             float a[16];
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
-            float v[16];
+            __syncthreads();
+            float ph[16], sg[16], v[16];
+            tc::row_get16(s.stA, t, ph);
+            tc::row_get16(s.stB, t >> 1, sg);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if (live) {
-                    phi_half[col * N + k0 + i] = a[i];
-                    v[i] = sigma_s[(size_t)g * N + k0 + i] * (a[i] - phi[col * N + k0 + i]);
-                } else {
-                    v[i] = 0.f;
-                }
-            }
+            for (int i = 0; i < 16; ++i) v[i] = live ? sg[i] * (a[i] - ph[i]) : 0.f;
+            tc::row_put16(s.stC, t, a);
             tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
+            tc::stage_out(s.stC, phi_half + cb, N, ncols, k0);
         }
         if (!(ok = tc_gemm(s, s.opM_hi, s.opM_lo, N, err))) break;
         // rhs = m (x) r: node partner is the adjacent lane (column j ^ 1)
         const float w = live ? (float)(h[g] / 6.0) : 0.f;
-        for (int k0 = 0; k0 < N; k0 += 16) {
-            float a[16];
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            float a[16], o[16];
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);  // r at the other node
-                if (live) rhs[col * N + k0 + i] = w * (2.f * a[i] + other);
+                o[i] = w * (2.f * a[i] + other);
             }
+            __syncthreads();  // stC of the previous chunk has been written out
+            tc::row_put16(s.stC, t, o);
+            __syncthreads();
+            tc::stage_out(s.stC, rhs + cb, N, ncols, k0);
         }
     }
     tc_cta_teardown(s, N);
@@ -371,39 +422,55 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter(const float *__restri
     bool ok = ok0;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
-        const int j = j0 + t;
-        const bool live = j < 2 * sumK;
-        const size_t col = (size_t)r * sumK * 2 + j;
-        for (int k0 = 0; k0 < N; k0 += 16) {
+        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const bool live = t < ncols;
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
+        const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(s.stA, v_in + cb, N, ncols, k0);
+            __syncthreads();
             float v[16];
-            tc::load16(v_in + col * N + k0, live, v);
+            tc::row_get16(s.stA, t, v);
             tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
         }
         if (!(ok = tc_gemm(s, s.opD_hi, s.opD_lo, N, err))) break;
-        const int g = j >> 1;
-        for (int k0 = 0; k0 < N; k0 += 16) {
+        // phi = phi_base + D v; next A = Sigma phi
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            if (phi_base) tc::stage_in(s.stA, phi_base + cb, N, ncols, k0);
+            tc::stage_in(s.stB, sig, N, ncell, k0);
             float a[16];
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
-            float v[16];
+            __syncthreads();
+            float pb[16], sg[16], v[16];
+            if (phi_base) tc::row_get16(s.stA, t, pb);
+            tc::row_get16(s.stB, t >> 1, sg);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                if (live) {
-                    const float pn = a[i] + (phi_base ? phi_base[col * N + k0 + i] : 0.f);
-                    phi[col * N + k0 + i] = pn;
-                    v[i] = sigma_s[(size_t)g * N + k0 + i] * pn;
-                } else {
-                    v[i] = 0.f;
-                }
+                a[i] += phi_base ? pb[i] : 0.f;
+                v[i] = live ? sg[i] * a[i] : 0.f;
             }
+            tc::row_put16(s.stC, t, a);
             tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
+            tc::stage_out(s.stC, phi + cb, N, ncols, k0);
         }
         if (!(ok = tc_gemm(s, s.opM_hi, s.opM_lo, N, err))) break;
-        for (int k0 = 0; k0 < N; k0 += 16) {
+        // q = M (Sigma phi) + q_ang
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            if (qang) tc::stage_in(s.stA, qang + cb, N, ncols, k0);
             float a[16];
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            __syncthreads();
+            if (qang) {
+                float qa[16];
+                tc::row_get16(s.stA, t, qa);
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-                if (live) q[col * N + k0 + i] = a[i] + (qang ? qang[col * N + k0 + i] : 0.f);
+                for (int i = 0; i < 16; ++i) a[i] += qa[i];
+            }
+            tc::row_put16(s.stC, t, a);
+            __syncthreads();
+            tc::stage_out(s.stC, q + cb, N, ncols, k0);
         }
     }
     tc_cta_teardown(s, N);

@@ -11,7 +11,9 @@ A problem is a dict:
   sigma_s[K,L+1]  scattering moments sigma_{s,l} = sigma_{s,0} f_l
   Q[K,2,L+1]      external source moments at the two LD nodes of every cell
                   (isotropic scalar source S -> Q_0 = S; angular source S/2)
-  bc              'vacuum' (both edges)
+  bc              'vacuum' (both edges), 'reflective', or a (left, right) pair of them
+  psi_inc         optional [2][N] incoming fluxes at the vacuum edges (row 0 left edge,
+                  read for mu > 0; row 1 right edge, read for mu < 0)
 Batched / multi-right-hand-side problems carry Q[R,K,2,L+1].
 
 Scattering kernels (Sec. 1 and Sec. 4 of the paper name them; their moment
@@ -106,6 +108,25 @@ def random_slab(K, N, L, seed, kernel="hg", regions=3, thick=(1.0, 300.0), c=(0.
     if L >= 1:
         Q[..., 1] = rng.uniform(-0.2, 0.2, shape) * Q[..., 0]
     return dict(N=N, L=L, h=h, sigma_t=st, sigma_s=ss, Q=Q, bc="vacuum")
+
+
+def mirrored_half_slab(K, N, L, seed, side):
+    """A seeded heterogeneous half slab with a reflective edge on `side`, and the
+    symmetric slab of 2K cells (vacuum both edges) that it is one half of. The mirror
+    image of a cell has its cross sections and width, and its nodal source values in
+    reversed node order; only even source moments are used so that the source is
+    reflection-symmetric in angle. Returns (half, full, slice of the half in full)."""
+    p = random_slab(K, N, L, seed=seed, kernel="hg", thick=(2, 40), c=(0.5, 0.95))
+    p["Q"][..., 1::2] = 0.0
+    mir = {k: p[k][::-1].copy() for k in ("h", "sigma_t", "sigma_s")}
+    mir["Q"] = p["Q"][::-1, ::-1].copy()
+    full = dict(N=N, L=L, bc="vacuum")
+    first, second = (mir, p) if side == "left" else (p, mir)
+    for k in ("h", "sigma_t", "sigma_s", "Q"):
+        full[k] = np.concatenate([first[k], second[k]])
+    half = dict(p, bc=("reflective", "vacuum") if side == "left" else ("vacuum", "reflective"))
+    part = slice(K, 2 * K) if side == "left" else slice(0, K)
+    return half, full, part
 
 
 def pl_equivalent_slab(K, N, seed):

@@ -47,17 +47,20 @@ def test_create_rejects_bad_descriptors_before_any_cuda_call(lib):
     h = np.full(4, 0.25)
 
     def create(**kw):
-        args = dict(n_instances=1, n_ordinates=8, n_moments=8, n_rhs=1, laplacian=0, precision=0)
+        args = dict(n_instances=1, n_ordinates=8, n_moments=8, n_rhs=1, laplacian=0, precision=0, bc=None)
         args.update(kw)
+        bc = None if args["bc"] is None else np.asarray(args["bc"], dtype=np.int32)
         d = binding.FpsaDesc(args["n_instances"], args["n_ordinates"], args["n_moments"], args["n_rhs"],
                              K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                              h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                             args["laplacian"], args["precision"], 0, None)
+                             args["laplacian"], args["precision"], 0, None,
+                             None if bc is None else bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         out = ctypes.c_void_p()
         return lib.fpsa_create(ctypes.byref(out), ctypes.byref(d)), out
 
     for bad in (dict(n_ordinates=7), dict(n_ordinates=0), dict(n_moments=9), dict(n_moments=0),
-                dict(n_rhs=0), dict(n_instances=0), dict(laplacian=5), dict(precision=7)):
+                dict(n_rhs=0), dict(n_instances=0), dict(laplacian=5), dict(precision=7),
+                dict(bc=[0, 2]), dict(bc=[-1, 0])):
         rc, out = create(**bad)
         assert rc == binding.EINVAL and not out.value, bad
     rc, out = create(n_ordinates=2 * binding.MAX_ORDINATES, n_moments=2)
@@ -76,3 +79,15 @@ def test_batch_wave_planning():
         assert all(probs[i]["N"] == N and probs[i]["L"] == L for i in idx)
         total = sum(batch.factor_bytes(probs[i]["h"].size, N, "mixed") for i in idx)
         assert total <= budget or len(idx) == 1
+
+
+def test_boundary_condition_marshalling():
+    from paper_1907_13013_gb300 import binding
+    assert binding._bc_array(None, 3) is None
+    assert binding._bc_array("vacuum", 2) is None
+    a = binding._bc_array(["vacuum", ("reflective", "vacuum"), "reflective"], 3)
+    assert a.tolist() == [[0, 0], [1, 0], [1, 1]]
+    with pytest.raises(ValueError):
+        binding._bc_array(["vacuum"], 2)
+    with pytest.raises(KeyError):
+        binding._bc_array("periodic", 1)

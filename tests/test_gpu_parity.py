@@ -501,9 +501,40 @@ def test_gmres_batch_systems_and_adjoint(binding):
     assert np.abs(gt - gt2).max() < 1e-8 * np.abs(gt2).max()
 
 
-def test_gmres_precision_rules(binding):
+def test_gmres_phi0_rule(binding):
     p = inputs.random_slab(10, 8, 7, seed=90)
-    ctx = binding.context_for(p, precision="mixed")
+    ctx = binding.context_for(p)
     with pytest.raises(binding.FpsaError) as e:
-        ctx.solve("gmres", tol=1e-10)
+        ctx.solve("gmres", tol=1e-10, phi0=np.zeros((1, 10, 2, 8)))
     assert e.value.code == binding.ENOTSUP
+
+
+# GMRES in MIXED precision: FP32 GMRES(m) inner solves of the correction equation
+# inside the FP64 refinement loop reach the FP64 fixed point.
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+@pytest.mark.parametrize("N,K,seed,restart", [(16, 60, 74, 30), (64, 40, 75, 30), (32, 50, 76, 4)])
+def test_gmres_mixed_against_oracle(binding, lap, N, K, seed, restart):
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel="srk", thick=(5, 300), c=(0.9, 0.999))
+    ctx = binding.context_for(p, laplacian=lap, precision="mixed")
+    phi, st = ctx.solve("gmres", tol=1e-12, max_iterations=60, restart=restart)
+    assert relerr(phi[0], oit.direct_solve(p)) < TOL
+    assert st["outer_iterations"] <= 12, st
+
+
+def test_gmres_mixed_batch_and_adjoint(binding):
+    R = 2
+    probs = [inputs.random_slab(K, 16, 15, seed=80 + i, kernel="hg", c=(0.8, 0.99), nrhs=R) for i, K in enumerate([25, 9])]
+    ctx = binding.context_for(probs, precision="mixed")
+    phi, st = ctx.solve("gmres", tol=1e-12, max_iterations=60)
+    off = 0
+    for p in probs:
+        K = p["h"].size
+        for r in range(R):
+            assert relerr(phi[r, off:off + K], oit.direct_solve(dict(p, Q=p["Q"][r]))) < TOL
+        off += K
+    gt, gs, J, _ = ctx.adjoint(method="gmres", tol=1e-12)
+    ref = binding.context_for(probs)
+    ref.solve("fpsa", tol=1e-13)
+    gt2, gs2, _, _ = ref.adjoint(method="fpsa", tol=1e-13)
+    assert np.abs(gt - gt2).max() < 1e-8 * np.abs(gt2).max()
+    assert np.abs(gs - gs2).max() < 1e-8 * np.abs(gs2).max()

@@ -9,35 +9,11 @@ from oracle import transport as tr
 from paper_1907_13013_gb300 import inputs
 
 
-def mirrored_pair(K, N, L, seed, side):
-    """A seeded heterogeneous half slab with a reflective edge on `side`, and the
-    symmetric slab of 2K cells (vacuum both edges) that it is one half of. The
-    mirror image of a cell has its cross sections, its width and its nodal source
-    values in reversed node order; only even source moments are used so that the
-    source is reflection-symmetric in angle."""
-    p = inputs.random_slab(K, N, L, seed=seed, kernel="hg", thick=(2, 40), c=(0.5, 0.95))
-    p["Q"][..., 1::2] = 0.0
-    mir = {k: p[k][::-1].copy() for k in ("h", "sigma_t", "sigma_s")}
-    mir["Q"] = p["Q"][::-1, ::-1].copy()
-    full = dict(N=N, L=L, bc="vacuum")
-    if side == "left":       # the half slab is the right half of the symmetric slab
-        for k in ("h", "sigma_t", "sigma_s", "Q"):
-            full[k] = np.concatenate([mir[k], p[k]])
-        half = dict(p, bc=("reflective", "vacuum"))
-        part = slice(K, 2 * K)
-    else:                    # the half slab is the left half
-        for k in ("h", "sigma_t", "sigma_s", "Q"):
-            full[k] = np.concatenate([p[k], mir[k]])
-        half = dict(p, bc=("vacuum", "reflective"))
-        part = slice(0, K)
-    return half, full, part
-
-
 @pytest.mark.parametrize("side", ["left", "right"])
 @pytest.mark.parametrize("N,K,seed", [(4, 5, 0), (8, 9, 1), (16, 7, 2)])
 def test_reflective_half_slab_equals_symmetric_slab(side, N, K, seed):
     # Mirror symmetry: a reflective edge is the symmetry plane of a slab twice as wide.
-    half, full, part = mirrored_pair(K, N, N - 1, seed, side)
+    half, full, part = inputs.mirrored_half_slab(K, N, N - 1, seed, side)
     ref = it.direct_solve(full)[part]
     got = it.direct_solve(half)
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
