@@ -683,6 +683,88 @@ __device__ __forceinline__ void gj_set_row_elem(T (&x)[RI][CJ], int ip, int j, T
 }
 
 template <typename T, int N2>
+struct GjShared {
+    T (*colbuf)[N2];
+    int *s_p, *perm, *iperm;
+};
+
+// One elimination step k = 16 JK + wk with the look-ahead column register JN
+// (JN = CJ: no look-ahead, the last step).
+template <typename T, int N2, int JK, int JN>
+__device__ __forceinline__ void gj_step(T (&x)[N2 / 32][N2 / 16], const GjShared<T, N2> &sh, unsigned &used,
+                                        bool &bad, int lane, int w, int wk) {
+    constexpr int RI = N2 / 32, CJ = N2 / 16;
+    const int k = 16 * JK + wk, b = k & 1;
+    const int p = sh.s_p[b];
+    const T pv = sh.colbuf[b][p];
+    if (pv == T(0) || !isfinite(pv)) bad = true;
+    const T inv = __frcp_rn(pv);  // correctly rounded, as 1 / pv
+    const int ip = p >> 5, pl = p & 31;
+    if (lane == pl) used |= 1u << ip;
+    T f[RI], rv[CJ];
+#pragma unroll
+    for (int i = 0; i < RI; ++i) f[i] = sh.colbuf[b][lane + 32 * i];
+    gj_pivot_row<T, RI, CJ>(x, ip, pl, inv, rv);  // pivot row of this warp's columns, from lane pl
+    if (w == wk) {  // column k: its old value is replaced, not updated
+        rv[JK] = inv;
+#pragma unroll
+        for (int i = 0; i < RI; ++i) x[i][JK] = T(0);
+    }
+    bool ahead = false;
+    if constexpr (JN < CJ) {
+        ahead = w == ((wk + 1) & 15);
+        if (ahead) {
+            // look-ahead: update column k+1 now and pick pivot k+1
+            T colv[RI];
+#pragma unroll
+            for (int i = 0; i < RI; ++i) x[i][JN] = fma(-f[i], rv[JN], x[i][JN]);
+            if (lane == pl) gj_set_row_elem<T, RI, CJ>(x, ip, JN, rv[JN]);
+#pragma unroll
+            for (int i = 0; i < RI; ++i) {
+                colv[i] = x[i][JN];
+                sh.colbuf[b ^ 1][lane + 32 * i] = colv[i];
+            }
+            int pn;
+            gj_pick_pivot<T, RI>(colv, used, lane, pn);
+            if (lane == 0) {
+                sh.s_p[b ^ 1] = pn;
+                sh.perm[k + 1] = pn;
+                sh.iperm[pn] = k + 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) {
+        if (j == JN && ahead) continue;
+#pragma unroll
+        for (int i = 0; i < RI; ++i) x[i][j] = fma(-f[i], rv[j], x[i][j]);
+    }
+    // the pivot row becomes the scaled row (its own update used f = pv)
+    if (lane == pl) {
+        const int js = ahead ? JN : -1;
+        switch (ip) {
+            case 0: gj_set_row_i<T, RI, CJ, 0>(x, rv, js); break;
+            case 1: gj_set_row_i<T, RI, CJ, 1>(x, rv, js); break;
+            case 2: gj_set_row_i<T, RI, CJ, 2>(x, rv, js); break;
+            default: gj_set_row_i<T, RI, CJ, 3>(x, rv, js); break;
+        }
+    }
+    __syncthreads();
+}
+
+// All steps with column register JK (k = 16 JK .. 16 JK + 15), then JK + 1.
+template <typename T, int N2, int JK>
+__device__ __forceinline__ void gj_steps(T (&x)[N2 / 32][N2 / 16], const GjShared<T, N2> &sh, unsigned &used,
+                                         bool &bad, int lane, int w) {
+    constexpr int CJ = N2 / 16;
+    if constexpr (JK < CJ) {
+        for (int wk = 0; wk < 15; ++wk) gj_step<T, N2, JK, JK>(x, sh, used, bad, lane, w, wk);
+        gj_step<T, N2, JK, JK + 1>(x, sh, used, bad, lane, w, 15);
+        gj_steps<T, N2, JK + 1>(x, sh, used, bad, lane, w);
+    }
+}
+
+template <typename T, int N2>
 __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int ldd, bool tout,
                                             unsigned long long *__restrict__ growth, int *__restrict__ status) {
     constexpr int RI = N2 / 32, CJ = N2 / 16;
@@ -717,71 +799,81 @@ __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int l
         }
     }
     __syncthreads();
-    for (int k = 0; k < N2; ++k) {
-        const int b = k & 1;
-        const int p = s_p[b];
-        const T pv = colbuf[b][p];
-        if (pv == T(0) || !isfinite(pv)) bad = true;
-        const T inv = T(1) / pv;
-        const int ip = p >> 5, pl = p & 31;
-        if (lane == pl) used |= 1u << ip;
-        T f[RI], rv[CJ];
-#pragma unroll
-        for (int i = 0; i < RI; ++i) f[i] = colbuf[b][lane + 32 * i];
-        // pivot row values of this warp's columns, from lane pl
-        gj_pivot_row<T, RI, CJ>(x, ip, pl, inv, rv);
-        const bool own = w == (k & 15);
-        const int jk = k >> 4;
-        if (own) {  // column k: its old value is replaced, not updated
-#pragma unroll
-            for (int j = 0; j < CJ; ++j)
-                if (j == jk) {
-                    rv[j] = inv;
-#pragma unroll
-                    for (int i = 0; i < RI; ++i) x[i][j] = T(0);
-                }
-        }
-        const bool ahead = k + 1 < N2 && w == ((k + 1) & 15);
-        const int jn = (k + 1) >> 4;
-        if (ahead) {
-            // look-ahead: update column k+1 now and pick pivot k+1
-            T colv[RI];
-#pragma unroll
-            for (int j = 0; j < CJ; ++j)
-                if (j == jn) {
-#pragma unroll
-                    for (int i = 0; i < RI; ++i) x[i][j] = fma(-f[i], rv[j], x[i][j]);
-                    if (lane == pl) gj_set_row_elem<T, RI, CJ>(x, ip, j, rv[j]);
-#pragma unroll
-                    for (int i = 0; i < RI; ++i) colv[i] = x[i][j];
-                }
-#pragma unroll
-            for (int i = 0; i < RI; ++i) colbuf[b ^ 1][lane + 32 * i] = colv[i];
-            int pn;
-            gj_pick_pivot<T, RI>(colv, used, lane, pn);
-            if (lane == 0) {
-                s_p[b ^ 1] = pn;
-                perm[k + 1] = pn;
-                iperm[pn] = k + 1;
+    // step k = 16 JK + wk: column k is x[.][JK] of warp wk. JK is a compile-time index
+    // (the loop over it is unrolled) so the owner's and the look-ahead column's
+    // registers are addressed statically; the look-ahead column is JK (wk < 15) or
+    // JK + 1 (wk = 15).
+    // (FP32; the FP64 tile is register-bound, so there the loop stays rolled)
+    if constexpr (sizeof(T) == 4) {
+        GjShared<T, N2> sh{colbuf, s_p, perm, iperm};
+        gj_steps<T, N2, 0>(x, sh, used, bad, lane, w);
+    } else {
+        for (int k = 0; k < N2; ++k) {
+            const int b = k & 1;
+            const int p = s_p[b];
+            const T pv = colbuf[b][p];
+            if (pv == T(0) || !isfinite(pv)) bad = true;
+            const T inv = T(1) / pv;
+            const int ip = p >> 5, pl = p & 31;
+            if (lane == pl) used |= 1u << ip;
+            T f[RI], rv[CJ];
+    #pragma unroll
+            for (int i = 0; i < RI; ++i) f[i] = colbuf[b][lane + 32 * i];
+            // pivot row values of this warp's columns, from lane pl
+            gj_pivot_row<T, RI, CJ>(x, ip, pl, inv, rv);
+            const bool own = w == (k & 15);
+            const int jk = k >> 4;
+            if (own) {  // column k: its old value is replaced, not updated
+    #pragma unroll
+                for (int j = 0; j < CJ; ++j)
+                    if (j == jk) {
+                        rv[j] = inv;
+    #pragma unroll
+                        for (int i = 0; i < RI; ++i) x[i][j] = T(0);
+                    }
             }
-        }
-#pragma unroll
-        for (int j = 0; j < CJ; ++j) {
-            if (ahead && j == jn) continue;
-#pragma unroll
-            for (int i = 0; i < RI; ++i) x[i][j] = fma(-f[i], rv[j], x[i][j]);
-        }
-        // the pivot row becomes the scaled row (its own update used f = pv)
-        if (lane == pl) {
-            const int js = ahead ? jn : -1;
-            switch (ip) {
-                case 0: gj_set_row_i<T, RI, CJ, 0>(x, rv, js); break;
-                case 1: gj_set_row_i<T, RI, CJ, 1>(x, rv, js); break;
-                case 2: gj_set_row_i<T, RI, CJ, 2>(x, rv, js); break;
-                default: gj_set_row_i<T, RI, CJ, 3>(x, rv, js); break;
+            const bool ahead = k + 1 < N2 && w == ((k + 1) & 15);
+            const int jn = (k + 1) >> 4;
+            if (ahead) {
+                // look-ahead: update column k+1 now and pick pivot k+1
+                T colv[RI];
+    #pragma unroll
+                for (int j = 0; j < CJ; ++j)
+                    if (j == jn) {
+    #pragma unroll
+                        for (int i = 0; i < RI; ++i) x[i][j] = fma(-f[i], rv[j], x[i][j]);
+                        if (lane == pl) gj_set_row_elem<T, RI, CJ>(x, ip, j, rv[j]);
+    #pragma unroll
+                        for (int i = 0; i < RI; ++i) colv[i] = x[i][j];
+                    }
+    #pragma unroll
+                for (int i = 0; i < RI; ++i) colbuf[b ^ 1][lane + 32 * i] = colv[i];
+                int pn;
+                gj_pick_pivot<T, RI>(colv, used, lane, pn);
+                if (lane == 0) {
+                    s_p[b ^ 1] = pn;
+                    perm[k + 1] = pn;
+                    iperm[pn] = k + 1;
+                }
             }
+    #pragma unroll
+            for (int j = 0; j < CJ; ++j) {
+                if (ahead && j == jn) continue;
+    #pragma unroll
+                for (int i = 0; i < RI; ++i) x[i][j] = fma(-f[i], rv[j], x[i][j]);
+            }
+            // the pivot row becomes the scaled row (its own update used f = pv)
+            if (lane == pl) {
+                const int js = ahead ? jn : -1;
+                switch (ip) {
+                    case 0: gj_set_row_i<T, RI, CJ, 0>(x, rv, js); break;
+                    case 1: gj_set_row_i<T, RI, CJ, 1>(x, rv, js); break;
+                    case 2: gj_set_row_i<T, RI, CJ, 2>(x, rv, js); break;
+                    default: gj_set_row_i<T, RI, CJ, 3>(x, rv, js); break;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     // Thread holds X[row][col] = A^{-1}[r][c] with perm[r] = row (r = iperm[row]) and
     // iperm[c] = col (c = perm[col]); written transposed when tout.
