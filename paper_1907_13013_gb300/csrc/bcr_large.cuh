@@ -39,7 +39,8 @@ template <typename T, int N2>
 __global__ void __launch_bounds__(512) k_binv_reg_rm(BMat<T> M, const BcrItem *__restrict__ items,
                                                      int *__restrict__ status) {
     T *p = bmat_ptr(M, items, blockIdx.x);
-    gj_reg_body<T, N2>(p, M.ld, p, M.ld, false, nullptr, status);
+    if constexpr (sizeof(T) == 4) gj_panel_body<N2>(p, M.ld, p, M.ld, false, nullptr, status);
+    else gj_reg_body<T, N2>(p, M.ld, p, M.ld, false, nullptr, status);
 }
 
 template <typename T>

@@ -764,6 +764,170 @@ __device__ __forceinline__ void gj_steps(T (&x)[N2 / 32][N2 / 16], const GjShare
     }
 }
 
+// Blocked Gauss-Jordan inversion (FP32) for n2 = N2 in {32, 64, 128}: 16 warps, warp
+// w owns the CJ = N2/16 consecutive columns CJ w .. CJ w + CJ - 1 (a panel), lane t
+// the rows t + 32 i. Panel q is eliminated by its owner warp alone (CJ pivot steps
+// with implicit partial pivoting: warp shuffles and reductions only), which leaves in
+// its columns W = E[:, P], E the product of the panel's elementary transformations
+// and P its pivot rows; every other warp then applies E to its own columns,
+//   X[r][c] <- (r in P ? 0 : X[r][c]) + sum_j W[r][j] X[P_j][c],
+// a rank-CJ update. One block barrier per panel (16 in all); the owner of panel q+1
+// starts eliminating as soon as its own update for panel q is done. The result is
+// the same in-place inverse as the unblocked elimination (same pivots; only the
+// rounding order of the updates differs): A^{-1}[r][c] = X[p_r][q_c].
+template <int RI, int CJ>
+__device__ __forceinline__ void gj_store_row(const float (&x)[RI][CJ], int i, float *dst) {
+    switch (i) {
+        case 0: {
+#pragma unroll
+            for (int j = 0; j < CJ; ++j) dst[j] = x[0][j];
+        } break;
+        case 1: if constexpr (RI > 1) {
+#pragma unroll
+            for (int j = 0; j < CJ; ++j) dst[j] = x[1][j];
+        } break;
+        case 2: if constexpr (RI > 2) {
+#pragma unroll
+            for (int j = 0; j < CJ; ++j) dst[j] = x[2][j];
+        } break;
+        default: if constexpr (RI > 3) {
+#pragma unroll
+            for (int j = 0; j < CJ; ++j) dst[j] = x[3][j];
+        } break;
+    }
+}
+
+template <int N2>
+__device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *dst, int ldd, bool tout,
+                                              unsigned long long *__restrict__ growth, int *__restrict__ status) {
+    constexpr int RI = N2 / 32, CJ = N2 / 16;
+    __shared__ __align__(16) float Wb[2][N2][CJ];
+    __shared__ __align__(16) float PRb[16][CJ][CJ];
+    __shared__ int Pb[2][CJ], piv_panel[N2], perm[N2], iperm[N2];
+    __shared__ double s_red[16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float x[RI][CJ];
+    float amax = 0.f;
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+            x[i][j] = src[(size_t)(lane + 32 * i) * lds + CJ * w + j];
+            amax = fmaxf(amax, fabsf(x[i][j]));
+        }
+    for (int r = threadIdx.x; r < N2; r += blockDim.x) piv_panel[r] = -1;
+    unsigned used = 0u;  // bit i: row lane + 32 i has been a pivot row
+    bool bad = false;
+    __syncthreads();
+    for (int q = 0; q < 16; ++q) {
+        const int qb = q & 1;
+        if (w == q) {
+#pragma unroll
+            for (int c = 0; c < CJ; ++c) {
+                float colv[RI];
+#pragma unroll
+                for (int i = 0; i < RI; ++i) colv[i] = x[i][c];
+                int p;
+                gj_pick_pivot<float, RI>(colv, used, lane, p);
+                const int ip = p >> 5, pl = p & 31;
+                float rv[CJ];
+                gj_pivot_row<float, RI, CJ>(x, ip, pl, 1.f, rv);
+                const float pv = rv[c];
+                if (pv == 0.f || !isfinite(pv)) bad = true;
+                const float inv = __frcp_rn(pv);
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) rv[j] = (j == c) ? inv : rv[j] * inv;
+                float f[RI];
+#pragma unroll
+                for (int i = 0; i < RI; ++i) {
+                    f[i] = x[i][c];
+                    x[i][c] = 0.f;  // column c is replaced, not updated
+                }
+#pragma unroll
+                for (int i = 0; i < RI; ++i)
+#pragma unroll
+                    for (int j = 0; j < CJ; ++j) x[i][j] = fmaf(-f[i], rv[j], x[i][j]);
+                if (lane == pl) {
+                    used |= 1u << ip;
+                    switch (ip) {  // the pivot row becomes the scaled row
+                        case 0: gj_set_row_i<float, RI, CJ, 0>(x, rv, -1); break;
+                        case 1: gj_set_row_i<float, RI, CJ, 1>(x, rv, -1); break;
+                        case 2: gj_set_row_i<float, RI, CJ, 2>(x, rv, -1); break;
+                        default: gj_set_row_i<float, RI, CJ, 3>(x, rv, -1); break;
+                    }
+                }
+                if (lane == 0) {
+                    const int k = q * CJ + c;
+                    perm[k] = p;
+                    iperm[p] = k;
+                    Pb[qb][c] = p;
+                    piv_panel[p] = q;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RI; ++i)
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) Wb[qb][lane + 32 * i][j] = x[i][j];
+        }
+        __syncthreads();
+        if (w != q) {
+            int P[CJ];
+#pragma unroll
+            for (int c = 0; c < CJ; ++c) {
+                P[c] = Pb[qb][c];
+                if (lane == (P[c] & 31)) {
+                    used |= 1u << (P[c] >> 5);
+                    gj_store_row<RI, CJ>(x, P[c] >> 5, &PRb[w][c][0]);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < RI; ++i) {
+                const int row = lane + 32 * i;
+                const bool isP = piv_panel[row] == q;
+                float wr[CJ];
+#pragma unroll
+                for (int c = 0; c < CJ; ++c) wr[c] = Wb[qb][row][c];
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) {
+                    float acc = isP ? 0.f : x[i][j];
+#pragma unroll
+                    for (int c = 0; c < CJ; ++c) acc = fmaf(wr[c], PRb[w][c][j], acc);
+                    x[i][j] = acc;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // X[row][col] = A^{-1}[r][c] with r = iperm[row], c = perm[col]; written transposed when tout
+    float ainv = 0.f;
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+            const int row = lane + 32 * i, col = CJ * w + j;
+            const int r = iperm[row], c = perm[col];
+            if (tout) dst[(size_t)c * ldd + r] = x[i][j];
+            else dst[(size_t)r * ldd + c] = x[i][j];
+            ainv = fmaxf(ainv, fabsf(x[i][j]));
+            if (!isfinite(x[i][j])) bad = true;
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        ainv = fmaxf(ainv, __shfl_xor_sync(0xffffffffu, ainv, o));
+    }
+    if (lane == 0) s_red[w] = (double)amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < 16; ++i) m = fmax(m, s_red[i]);
+        s_red[0] = m;
+    }
+    __syncthreads();
+    if (growth && lane == 0) atomicMax(growth, dkey((double)ainv * s_red[0]));
+    if (bad) atomicExch(status, 1);
+}
+
 template <typename T, int N2>
 __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int ldd, bool tout,
                                             unsigned long long *__restrict__ growth, int *__restrict__ status) {
@@ -910,7 +1074,8 @@ __global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const
                                                         unsigned long long *__restrict__ growth,
                                                         int *__restrict__ status) {
     T *Ag = A + (size_t)items[blockIdx.x].cell * N2 * N2;
-    gj_reg_body<T, N2>(Ag, N2, Ag, N2, true, growth, status);
+    if constexpr (sizeof(T) == 4) gj_panel_body<N2>(Ag, N2, Ag, N2, true, growth, status);
+    else gj_reg_body<T, N2>(Ag, N2, Ag, N2, true, growth, status);
 }
 
 // out (+)= X Y for h2 x h2 operands through shared memory: both operands are
