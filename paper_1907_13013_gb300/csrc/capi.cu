@@ -62,6 +62,8 @@ struct fpsa_ctx {
 
     int32_t *d_off = nullptr, *d_K = nullptr, *d_cell_inst = nullptr, *d_slot_base = nullptr;
     int32_t *d_bc = nullptr;     // [B][2] edge conditions; NULL when every edge is vacuum
+    double *d_in_st = nullptr, *d_in_ss = nullptr, *d_in_q = nullptr;  // fpsa_set_xs staging of host inputs
+    int *d_xs_err = nullptr;     // [2] validation of fpsa_set_xs
     double *d_inc = nullptr;     // [R][B][2][N] given incoming edge fluxes (FP64)
     bool has_inc = false;
     float *d_Afp32 = nullptr, *d_mu32 = nullptr;  // angular Laplacian and mu rounded to FP32 (FP32 assembly)
@@ -388,22 +390,10 @@ int setup_tc(fpsa_ctx *ctx) {
 // Upload per-path cross sections / sources (padded to N moments); with full, also the
 // sweep coefficients, the FP operator assembly and its block factorization.
 template <typename T>
-int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, const std::vector<double> &qm,
-               bool full) {
+int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     const Geometry &g = ctx->geo;
-    const int N = g.N, L1 = g.L1, n2 = 2 * N, h2 = N / 2;
+    const int N = g.N, h2 = N / 2;
     cudaStream_t st = ctx->stream;
-    std::vector<T> sp((size_t)g.sumK * N, T(0));
-    for (int c = 0; c < g.sumK; ++c)
-        for (int l = 0; l < L1; ++l) sp[(size_t)c * N + l] = (T)ss[(size_t)c * L1 + l];
-    const size_t ncol = (size_t)g.R * g.sumK * 2;
-    std::vector<T> Qp(ncol * N, T(0));
-    for (size_t c = 0; c < ncol; ++c)
-        for (int l = 0; l < L1; ++l) Qp[c * N + l] = (T)qm[c * L1 + l];
-    CK(cudaMemcpyAsync(p.sigma_s, sp.data(), sp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-    if (p.Q) CK(cudaMemcpyAsync(p.Q, Qp.data(), Qp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-    // the pageable staging vectors must outlive the asynchronous copies
-    CK(cudaStreamSynchronize(st));
     if (!full) return FPSA_OK;
     {
         const size_t tot = (size_t)g.sumK * N;
@@ -452,8 +442,6 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, const std::vector<double> &ss, 
     return FPSA_OK;
 }
 
-// F u = rhs by block cyclic reduction over the stored factors: one cooperative
-// launch (forward levels, roots, backward levels); the solution is left in p.ybuf.
 // psi = L^{-1} q for every (ordinate, instance, rhs) with the given incoming edge
 // fluxes inc (NULL: none); reflective edges take the totals pass first.
 template <typename T>
@@ -475,6 +463,8 @@ int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
     return FPSA_OK;
 }
 
+// F u = rhs by block cyclic reduction over the stored factors: one cooperative
+// launch (forward levels, roots, backward levels); the solution is left in p.ybuf.
 template <typename T>
 int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     const Geometry &g = ctx->geo;
@@ -490,24 +480,6 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     const int RC = solve_rc(R);
     CK(cudaLaunchCooperativeKernel(coop_kernel<T>(RC), dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC),
                                    ctx->stream));
-    return FPSA_OK;
-}
-
-int check_xs(fpsa_ctx *ctx, const double *st, const double *ss, const double *q) {
-    const Geometry &g = ctx->geo;
-    for (int c = 0; c < g.sumK; ++c) {
-        if (!std::isfinite(st[c]) || !(st[c] > 0.0))
-            return fail(ctx, FPSA_EINVAL, "sigma_t must be finite and > 0 (cell " + std::to_string(c) + ")");
-        for (int l = 0; l < g.L1; ++l)
-            if (!std::isfinite(ss[(size_t)c * g.L1 + l]))
-                return fail(ctx, FPSA_ENONFINITE, "non-finite sigma_s at cell " + std::to_string(c));
-        const double s0 = ss[(size_t)c * g.L1];
-        if (s0 < 0.0 || s0 > st[c])
-            return fail(ctx, FPSA_EINVAL, "need 0 <= sigma_s0 <= sigma_t (cell " + std::to_string(c) + ")");
-    }
-    const size_t nq = (size_t)g.R * g.sumK * 2 * g.L1;
-    for (size_t i = 0; i < nq; ++i)
-        if (!std::isfinite(q[i])) return fail(ctx, FPSA_ENONFINITE, "non-finite source moment");
     return FPSA_OK;
 }
 
@@ -1141,6 +1113,10 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         CK(dalloc(ctx, &ctx->d_s0, g.sumK));
         CK(dalloc(ctx, &ctx->d_s1, g.sumK));
         CK(dalloc(ctx, &ctx->d_conv, (size_t)g.R * g.B * 2));
+        CK(dalloc(ctx, &ctx->d_in_st, g.sumK));
+        CK(dalloc(ctx, &ctx->d_in_ss, (size_t)g.sumK * g.L1));
+        CK(dalloc(ctx, &ctx->d_in_q, (size_t)g.R * g.sumK * 2 * g.L1));
+        CK(dalloc(ctx, &ctx->d_xs_err, 2));
         CK(dalloc(ctx, &ctx->d_growth, 1));
         CK(dalloc(ctx, &ctx->d_status, 1));
         CK(dalloc(ctx, &ctx->d_result, 2));
@@ -1257,32 +1233,42 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     const auto t0 = std::chrono::steady_clock::now();
     const Geometry &g = ctx->geo;
     const size_t nss = (size_t)g.sumK * g.L1, nq = (size_t)g.R * g.sumK * 2 * g.L1;
-    std::vector<double> st(g.sumK), ss(nss), qm(nq);
-    const cudaMemcpyKind k = mem == FPSA_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
-    CK(cudaMemcpy(st.data(), sigma_t, g.sumK * sizeof(double), k));
-    CK(cudaMemcpy(ss.data(), sigma_s, nss * sizeof(double), k));
-    CK(cudaMemcpy(qm.data(), q, nq * sizeof(double), k));
+    cudaStream_t s = ctx->stream;
     ctx->xs_ready = false;
     ctx->fwd_ready = false;
-    int rc = check_xs(ctx, st.data(), ss.data(), qm.data());
-    if (rc) return rc;
-    std::vector<double> s0(g.sumK), s1(g.sumK);
-    for (int c = 0; c < g.sumK; ++c) {
-        s0[c] = ss[(size_t)c * g.L1];
-        s1[c] = g.L1 > 1 ? ss[(size_t)c * g.L1 + 1] : 0.0;
+    const double *st_in = sigma_t, *ss_in = sigma_s, *q_in = q;
+    if (mem == FPSA_MEM_HOST) {  // one upload of the caller's arrays; conversion happens on the device
+        CK(cudaMemcpyAsync(ctx->d_in_st, sigma_t, g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->d_in_ss, sigma_s, nss * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->d_in_q, q, nq * sizeof(double), cudaMemcpyHostToDevice, s));
+        st_in = ctx->d_in_st;
+        ss_in = ctx->d_in_ss;
+        q_in = ctx->d_in_q;
     }
-    cudaStream_t s = ctx->stream;
-    CK(cudaMemcpyAsync(ctx->d_sigma_t, st.data(), g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->d_s0, s0.data(), g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->d_s1, s1.data(), g.sumK * sizeof(double), cudaMemcpyHostToDevice, s));
+    const int big = 0x7fffffff;
+    CK(cudaMemcpyAsync(ctx->d_xs_err, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_xs_err + 1, 0, sizeof(int), s));
     CK(cudaMemsetAsync(ctx->d_growth, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
-    if (ctx->precision == FPSA_PRECISION_FP64) {
-        rc = setup_path(ctx, ctx->p64, ss, qm, true);
-    } else {
-        rc = setup_path(ctx, ctx->p64, ss, qm, false);
-        if (!rc) rc = setup_path(ctx, ctx->p32, ss, qm, true);
+    const bool mixed = ctx->precision == FPSA_PRECISION_MIXED;
+    {
+        Launch L_(ctx, FPSA_PHASE_ASSEMBLE);
+        k_prepare_xs<<<4 * 152, 256, 0, s>>>(st_in, ss_in, q_in, g.N, g.L1, g.sumK, g.R, ctx->p64.sigma_s,
+                                              mixed ? ctx->p32.sigma_s : nullptr, ctx->p64.Q, nullptr, ctx->d_sigma_t,
+                                              ctx->d_s0, ctx->d_s1, ctx->d_xs_err, ctx->d_xs_err + 1);
     }
+    CK(cudaGetLastError());
+    int err[2];
+    CK(cudaMemcpyAsync(err, ctx->d_xs_err, sizeof(err), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err[0] != big) {
+        const int c = err[0] / 4, check = err[0] % 4;
+        if (check == 0) return fail(ctx, FPSA_EINVAL, "sigma_t must be finite and > 0 (cell " + std::to_string(c) + ")");
+        if (check == 1) return fail(ctx, FPSA_ENONFINITE, "non-finite sigma_s at cell " + std::to_string(c));
+        return fail(ctx, FPSA_EINVAL, "need 0 <= sigma_s0 <= sigma_t (cell " + std::to_string(c) + ")");
+    }
+    if (err[1]) return fail(ctx, FPSA_ENONFINITE, "non-finite source moment");
+    int rc = mixed ? setup_path(ctx, ctx->p32, true) : setup_path(ctx, ctx->p64, true);
     if (rc) return rc;
     unsigned long long growth = 0;
     int status = 0;

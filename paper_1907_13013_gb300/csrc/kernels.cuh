@@ -443,6 +443,52 @@ static __global__ void k_conv_finalize(unsigned long long *conv, int nrb, double
 }
 
 // ---------------------------------------------------------------------------
+// Cross sections and sources of fpsa_set_xs, converted on the device from the
+// caller's FP64 layout (moments l < L+1) to the padded working layouts (l < N):
+// sigma_s -> sig64 / sig32 [sumK][N], q -> Q64 / Q32 [R][sumK][2][N] (any output
+// may be NULL), sigma_t, sigma_s0, sigma_s1 per cell. Validation (the first failing
+// cell wins, in the order sigma_t, finite sigma_s, 0 <= sigma_s0 <= sigma_t):
+// *err_cell = min(4 cell + check), *err_q = 1 on a non-finite source moment.
+// ---------------------------------------------------------------------------
+static __global__ void k_prepare_xs(const double *__restrict__ st_in, const double *__restrict__ ss_in,
+                                    const double *__restrict__ q_in, int N, int L1, int sumK, int R,
+                                    double *__restrict__ sig64, float *__restrict__ sig32, double *__restrict__ Q64,
+                                    float *__restrict__ Q32, double *__restrict__ d_st, double *__restrict__ d_s0,
+                                    double *__restrict__ d_s1, int *__restrict__ err_cell, int *__restrict__ err_q) {
+    const size_t nthr = (size_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (size_t c = t0; c < (size_t)sumK; c += nthr) {
+        const double st = st_in[c], s0 = ss_in[c * L1], s1 = L1 > 1 ? ss_in[c * L1 + 1] : 0.0;
+        int check = -1;
+        if (!isfinite(st) || !(st > 0.0)) check = 0;
+        else {
+            for (int l = 0; l < L1 && check < 0; ++l)
+                if (!isfinite(ss_in[c * L1 + l])) check = 1;
+            if (check < 0 && (s0 < 0.0 || s0 > st)) check = 2;
+        }
+        if (check >= 0) atomicMin(err_cell, (int)(4 * c) + check);
+        d_st[c] = st;
+        d_s0[c] = s0;
+        d_s1[c] = s1;
+    }
+    for (size_t e = t0; e < (size_t)sumK * N; e += nthr) {
+        const size_t c = e / N;
+        const int l = (int)(e - c * N);
+        const double v = l < L1 ? ss_in[c * L1 + l] : 0.0;
+        if (sig64) sig64[e] = v;
+        if (sig32) sig32[e] = (float)v;
+    }
+    const size_t ncol = (size_t)R * sumK * 2;
+    for (size_t e = t0; e < ncol * N; e += nthr) {
+        const size_t col = e / N;
+        const int l = (int)(e - col * N);
+        const double v = l < L1 ? q_in[col * L1 + l] : 0.0;
+        if (!isfinite(v)) *err_q = 1;
+        if (Q64) Q64[e] = v;
+        if (Q32) Q32[e] = (float)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP operator, LD in space (Eqs. fpop, fp-mpd-oper, wd-eq-oper):
 //   mu d/dz + K_g,  K_g = sigma_a I - sigma_tr/2 A_FP,
 // cell block A_g[a*N+n][b*N+m] = G(mu_n)_ab delta_nm + m_ab K_g[n][m] with
@@ -775,6 +821,23 @@ __device__ __forceinline__ void gj_steps(T (&x)[N2 / 32][N2 / 16], const GjShare
 // starts eliminating as soon as its own update for panel q is done. The result is
 // the same in-place inverse as the unblocked elimination (same pivots; only the
 // rounding order of the updates differs): A^{-1}[r][c] = X[p_r][q_c].
+// gj_pick_pivot that also returns the pivot value itself (broadcast with its row).
+template <typename T, int RI>
+__device__ __forceinline__ void gj_pick_pivot_v(const T (&colv)[RI], unsigned used, int lane, int &p, T &pv) {
+    unsigned best = 0u;
+    int bi = 0;
+    T bv = T(0);
+#pragma unroll
+    for (int i = 0; i < RI; ++i) {
+        const unsigned key = (used >> i) & 1u ? 0u : __float_as_uint(fabsf((float)colv[i])) + 1u;
+        if (key > best) { best = key; bi = lane + 32 * i; bv = colv[i]; }
+    }
+    const unsigned m = __reduce_max_sync(0xffffffffu, best);
+    const int src = __ffs(__ballot_sync(0xffffffffu, best == m)) - 1;
+    p = __shfl_sync(0xffffffffu, bi, src);
+    pv = __shfl_sync(0xffffffffu, bv, src);
+}
+
 template <int RI, int CJ>
 __device__ __forceinline__ void gj_store_row(const float (&x)[RI][CJ], int i, float *dst) {
     switch (i) {
@@ -828,34 +891,43 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
 #pragma unroll
                 for (int i = 0; i < RI; ++i) colv[i] = x[i][c];
                 int p;
-                gj_pick_pivot<float, RI>(colv, used, lane, p);
-                const int ip = p >> 5, pl = p & 31;
-                float rv[CJ];
-                gj_pivot_row<float, RI, CJ>(x, ip, pl, 1.f, rv);
-                const float pv = rv[c];
+                float pv;
+                gj_pick_pivot_v<float, RI>(colv, used, lane, p, pv);
                 if (pv == 0.f || !isfinite(pv)) bad = true;
-                const float inv = __frcp_rn(pv);
+                const float inv = __frcp_rn(pv);  // overlaps the pivot-row shuffles below
+                const int ip = p >> 5, pl = p & 31;
+                // pivot row of this warp's columns (select chain on the warp-uniform ip)
+                float rv[CJ];
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) {
+                    float v = x[0][j];
+#pragma unroll
+                    for (int i = 1; i < RI; ++i) v = (ip == i) ? x[i][j] : v;
+                    rv[j] = __shfl_sync(0xffffffffu, v, pl);
+                }
 #pragma unroll
                 for (int j = 0; j < CJ; ++j) rv[j] = (j == c) ? inv : rv[j] * inv;
-                float f[RI];
+                // x <- s_i x + g_i rv: s = 1, g = -x[i][c] for the other rows (column c
+                // first cleared: it is replaced), s = 0, g = 1 for the pivot row
+                float sg[RI], gg[RI];
 #pragma unroll
                 for (int i = 0; i < RI; ++i) {
-                    f[i] = x[i][c];
-                    x[i][c] = 0.f;  // column c is replaced, not updated
+                    const bool prow = lane == pl && i == ip;
+                    sg[i] = prow ? 0.f : 1.f;
+                    gg[i] = prow ? 1.f : -x[i][c];
+                    x[i][c] = 0.f;
                 }
 #pragma unroll
                 for (int i = 0; i < RI; ++i)
 #pragma unroll
-                    for (int j = 0; j < CJ; ++j) x[i][j] = fmaf(-f[i], rv[j], x[i][j]);
-                if (lane == pl) {
-                    used |= 1u << ip;
-                    switch (ip) {  // the pivot row becomes the scaled row
-                        case 0: gj_set_row_i<float, RI, CJ, 0>(x, rv, -1); break;
-                        case 1: gj_set_row_i<float, RI, CJ, 1>(x, rv, -1); break;
-                        case 2: gj_set_row_i<float, RI, CJ, 2>(x, rv, -1); break;
-                        default: gj_set_row_i<float, RI, CJ, 3>(x, rv, -1); break;
+                    for (int j = 0; j < CJ; j += 2) {
+                        float2 xv = make_float2(x[i][j], x[i][j + 1]);
+                        xv = __ffma2_rn(make_float2(gg[i], gg[i]), make_float2(rv[j], rv[j + 1]),
+                                        __fmul2_rn(make_float2(sg[i], sg[i]), xv));
+                        x[i][j] = xv.x;
+                        x[i][j + 1] = xv.y;
                     }
-                }
+                used |= (lane == pl) ? (1u << ip) : 0u;
                 if (lane == 0) {
                     const int k = q * CJ + c;
                     perm[k] = p;
@@ -889,11 +961,14 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
 #pragma unroll
                 for (int c = 0; c < CJ; ++c) wr[c] = Wb[qb][row][c];
 #pragma unroll
-                for (int j = 0; j < CJ; ++j) {
-                    float acc = isP ? 0.f : x[i][j];
+                for (int j = 0; j < CJ; j += 2) {
+                    float2 acc = isP ? make_float2(0.f, 0.f) : make_float2(x[i][j], x[i][j + 1]);
 #pragma unroll
-                    for (int c = 0; c < CJ; ++c) acc = fmaf(wr[c], PRb[w][c][j], acc);
-                    x[i][j] = acc;
+                    for (int c = 0; c < CJ; ++c)
+                        acc = __ffma2_rn(make_float2(wr[c], wr[c]), *reinterpret_cast<const float2 *>(&PRb[w][c][j]),
+                                         acc);
+                    x[i][j] = acc.x;
+                    x[i][j + 1] = acc.y;
                 }
             }
         }
