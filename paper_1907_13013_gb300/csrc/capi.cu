@@ -64,6 +64,7 @@ struct fpsa_ctx {
     int32_t *d_bc = nullptr;     // [B][2] edge conditions; NULL when every edge is vacuum
     double *d_in_st = nullptr, *d_in_ss = nullptr, *d_in_q = nullptr;  // fpsa_set_xs staging of host inputs
     int *d_xs_err = nullptr;     // [2] validation of fpsa_set_xs
+    int *d_flow_cnt = nullptr, *d_flow_done = nullptr;  // BCR dataflow counters [rhs chunks][sumK]
     double *d_inc = nullptr;     // [R][B][2][N] given incoming edge fluxes (FP64)
     bool has_inc = false;
     float *d_Afp32 = nullptr, *d_mu32 = nullptr;  // angular Laplacian and mu rounded to FP32 (FP32 assembly)
@@ -99,7 +100,7 @@ struct fpsa_ctx {
     // tensor-core contractions of the FP32 inner solve
     bool tc_able = false;               // N multiple of 16, 16 <= N <= 128
     unsigned char *d_tc_ops = nullptr;  // D_hi, D_lo, M_hi, M_lo (BF16, core-matrix layout)
-    int *d_tc_err = nullptr, *h_flag = nullptr;
+    int *d_dev_err = nullptr, *h_flag = nullptr;  // a bounded device wait ran out (tensor-core or BCR dataflow)
     int tc_grid = 0;
 
     // built-in profiler: launch counters (always) and event pairs (when on)
@@ -199,10 +200,10 @@ size_t solve_smem(int N, int RC) {
 template <typename T>
 const void *coop_kernel(int RC) {
     switch (RC) {
-        case 8: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 8>;
-        case 4: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 4>;
-        case 2: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 2>;
-        default: return (const void *)k_bcr_solve_coop<T, kSolveThreads, 1>;
+        case 8: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 8>;
+        case 4: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 4>;
+        case 2: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 2>;
+        default: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 1>;
     }
 }
 
@@ -357,9 +358,6 @@ int invert_level(fpsa_ctx *ctx, PathBuffers<T> &p, const BcrItem *items, int ni)
 // K-major core-matrix layout (Op_D[l][n] = D[l][n], Op_M[n][l] = M[n][l]).
 int setup_tc(fpsa_ctx *ctx) {
     const int N = ctx->geo.N;
-    CK(dalloc(ctx, &ctx->d_tc_err, 1));
-    CK(cudaMallocHost(&ctx->h_flag, sizeof(int)));
-    CK(cudaMemset(ctx->d_tc_err, 0, sizeof(int)));
     ctx->tc_able = (N % 16 == 0) && N >= 16 && N <= 128;
     if (!ctx->tc_able) return FPSA_OK;
     const size_t nn = (size_t)N * N;
@@ -473,11 +471,15 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     LevelTable lv = ctx->lvt[sizeof(T) == 8 ? 1 : 0];
     const T *A = p.A, *Bc = p.Bc, *Cc = p.Cc;
     T *Y = p.ybuf;
+    int *cnt = ctx->d_flow_cnt, *done = ctx->d_flow_done, *err = ctx->d_dev_err;
     void *args[] = {(void *)&A, (void *)&Bc, (void *)&Cc, (void *)&items, (void *)&lv, (void *)&rhs,
-                    (void *)&Y, (void *)&N, (void *)&sumK, (void *)&R};
+                    (void *)&Y, (void *)&N, (void *)&sumK, (void *)&R, (void *)&cnt, (void *)&done, (void *)&err};
     const int grid = ctx->coop_grid[sizeof(T) == 8 ? 1 : 0];
-    Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
     const int RC = solve_rc(R);
+    const size_t ncnt = (size_t)((R + RC - 1) / RC) * sumK * sizeof(int);
+    CK(cudaMemsetAsync(cnt, 0, ncnt, ctx->stream));
+    CK(cudaMemsetAsync(done, 0, ncnt, ctx->stream));
+    Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
     CK(cudaLaunchCooperativeKernel(coop_kernel<T>(RC), dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC),
                                    ctx->stream));
     return FPSA_OK;
@@ -504,6 +506,7 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
         CK(cudaMemsetAsync(p.phi, 0, ncol * N * sizeof(T), st));
     }
     CK(cudaMemsetAsync(ctx->d_conv, 0, (size_t)g.R * g.B * 2 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), st));
     {
         Launch L_(ctx, FPSA_PHASE_CONTRACT);
         k_scatter<T><<<cgrid, kContractThreads, csm / 2, st>>>(p.phi, p.sigma_s, Qm, p.MT, p.q, N, g.sumK, Qa);
@@ -545,8 +548,13 @@ int solve_fp64(fpsa_ctx *ctx, PathBuffers<T> &p, const fpsa_opts &o, const doubl
                 k_conv_finalize<<<1, 256, 0, st>>>(ctx->d_conv, g.R * g.B, ctx->d_result);
             }
             CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             e = ctx->h_result[0];
+            if (*ctx->h_flag) {
+                status = fail(ctx, FPSA_ETIMEOUT, "a bounded device wait ran out (BCR dataflow)");
+                break;
+            }
             if (std::isnan(e)) {
                 status = fail(ctx, FPSA_ENONFINITE, "non-finite iterate at iteration " + std::to_string(it));
                 break;
@@ -606,7 +614,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
     const int tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
     const size_t tc_smem = tc::Plan::make(N).total;
-    if (use_tc) CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), st));
 
     CK(cudaMemsetAsync(p.phi, 0, nang * sizeof(double), st));
     if (phi0) {
@@ -634,11 +642,11 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
-        if (use_tc) CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         e = ctx->h_result[0];
-        if (use_tc && *ctx->h_flag) {
-            status = fail(ctx, FPSA_ETIMEOUT, "a tensor-core contraction wait ran out");
+        if (*ctx->h_flag) {
+            status = fail(ctx, FPSA_ETIMEOUT, "a bounded device wait ran out (tensor-core contraction or BCR dataflow)");
             break;
         }
         if (std::isnan(e)) {
@@ -687,7 +695,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
                     Launch L_(ctx, FPSA_PHASE_CONTRACT);
                     if (use_tc)
                         k_tc_fp_rhs<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h,
-                                                                     tcops, f.rhs, N, g.sumK, g.R, ctx->d_tc_err);
+                                                                     tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err);
                     else
                         k_fp_rhs<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
                             f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h, f.DT, f.MT, f.rhs, N, g.sumK);
@@ -701,7 +709,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
                 if (use_tc)
                     k_tc_update_scatter<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops, f.q,
-                                                                         f.qang, N, g.sumK, g.R, ctx->d_tc_err);
+                                                                         f.qang, N, g.sumK, g.R, ctx->d_dev_err);
                 else
                     k_update_scatter<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
                         vin, base, f.phi, f.sigma_s, (const float *)nullptr, f.DT, f.MT, f.q, ctx->d_cell_inst, g.B,
@@ -801,7 +809,9 @@ int gm_dots(fpsa_ctx *ctx, const T *V, int nv, const T *w, std::vector<double> &
     CK(cudaGetLastError());
     hdots.resize((size_t)nsys * nv);
     CK(cudaMemcpyAsync(hdots.data(), ctx->gm_dots, hdots.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (*ctx->h_flag) return fail(ctx, FPSA_ETIMEOUT, "a bounded device wait ran out (BCR dataflow)");
     return FPSA_OK;
 }
 
@@ -871,6 +881,7 @@ int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, 
     cudaStream_t st = ctx->stream;
     int rc = gmres_alloc(ctx, m);
     if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), st));
     T *V = reinterpret_cast<T *>(ctx->gm_V), *u = reinterpret_cast<T *>(ctx->gm_u),
       *w = reinterpret_cast<T *>(ctx->gm_w), *b = reinterpret_cast<T *>(ctx->gm_b);
     const size_t csm = contract_smem<T>(N);
@@ -1117,6 +1128,14 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         CK(dalloc(ctx, &ctx->d_in_ss, (size_t)g.sumK * g.L1));
         CK(dalloc(ctx, &ctx->d_in_q, (size_t)g.R * g.sumK * 2 * g.L1));
         CK(dalloc(ctx, &ctx->d_xs_err, 2));
+        CK(dalloc(ctx, &ctx->d_dev_err, 1));
+        CK(cudaMemset(ctx->d_dev_err, 0, sizeof(int)));
+        CK(cudaMallocHost(&ctx->h_flag, sizeof(int)));
+        {
+            const int nchunk = (g.R + solve_rc(g.R) - 1) / solve_rc(g.R);
+            CK(dalloc(ctx, &ctx->d_flow_cnt, (size_t)nchunk * g.sumK));
+            CK(dalloc(ctx, &ctx->d_flow_done, (size_t)nchunk * g.sumK));
+        }
         CK(dalloc(ctx, &ctx->d_growth, 1));
         CK(dalloc(ctx, &ctx->d_status, 1));
         CK(dalloc(ctx, &ctx->d_result, 2));

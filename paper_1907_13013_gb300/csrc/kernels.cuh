@@ -1457,11 +1457,63 @@ __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, cons
     }
 }
 
+// Dataflow synchronisation of the BCR solve units (k_bcr_solve_flow): a unit waits
+// until the counters it depends on reach their targets (thread 0 polls with acquire
+// loads, at most kFlowSpinLimit times, then records *err = 1 and goes on), and after
+// its writes (every thread fences, block barrier) bumps the counters of the units
+// that depend on it. NULL pointers are absent waits / signals.
+constexpr unsigned kFlowSpinLimit = 1u << 25;  // x >= 32 ns: about a second
+struct FlowSync {
+    const int *wait0, *wait1;
+    int want0, want1;
+    int *sig0, *sig1, *sig2;
+    int *err;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void flow_wait(const FlowSync *fs) {
+    if (!fs) return;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int *c = k ? fs->wait1 : fs->wait0;
+            const int want = k ? fs->want1 : fs->want0;
+            if (!c) continue;
+            unsigned spins = 0;
+            while (ld_acquire_gpu(c) < want) {
+                if (++spins > kFlowSpinLimit) {
+                    atomicExch(fs->err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void flow_signal(const FlowSync *fs) {
+    if (!fs) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (fs->sig0) atomicAdd(fs->sig0, 1);
+        if (fs->sig1) atomicAdd(fs->sig1, 1);
+        if (fs->sig2) atomicAdd(fs->sig2, 1);
+    }
+}
+
 // Units cover RC consecutive right-hand sides r0 .. r0 + nrc - 1 (nrc <= RC).
 template <typename T, int NT, int RC>
 __device__ __forceinline__ void bcr_fwd_unit(const T *__restrict__ A, const T *__restrict__ Bc,
                                              const T *__restrict__ Cc, const BcrItem &it, int r0, int nrc, int sl,
-                                             int S, T *rhs, T *Y, int N, int sumK, T *sm) {
+                                             int S, T *rhs, T *Y, int N, int sumK, T *sm,
+                                             const FlowSync *fs = nullptr) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
     T *rs = sm, *ys = sm + RC * n2, *part = ys + RC * n2 + RC * N;
     T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
@@ -1474,6 +1526,7 @@ __device__ __forceinline__ void bcr_fwd_unit(const T *__restrict__ A, const T *_
     const T *mC = push_left ? Cc + (size_t)it.s_left * hh : nullptr;
     stage_couplings(mB, mC, cbuf, hh);  // in flight during the matrix-vector product
     const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, n2, n2, 0, 0, rs, n2, part, [&] {
+        flow_wait(fs);  // r_i complete (every push into it has landed)
         for (int i = threadIdx.x; i < RC * n2; i += NT) {
             const int rc = i / n2, k = i - rc * n2;
             rs[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
@@ -1496,13 +1549,14 @@ __device__ __forceinline__ void bcr_fwd_unit(const T *__restrict__ A, const T *_
                                  push_right ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr,
                                  mC, ys, push_left ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr,
                                  h2, n2, rstride, nrc);
+    flow_signal(fs);
     __syncthreads();  // scratch reuse by the block's next unit
 }
 
 template <typename T, int NT, int RC>
 __device__ __forceinline__ void bcr_bwd_unit(const T *__restrict__ A, const T *__restrict__ Bc,
                                              const T *__restrict__ Cc, const BcrItem &it, int r0, int nrc, int sl,
-                                             int S, T *Y, int N, int sumK, T *sm) {
+                                             int S, T *Y, int N, int sumK, T *sm, const FlowSync *fs = nullptr) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
     T *gv = sm, *g = sm + RC * N, *part = sm + RC * (5 * N);  // gv[rc] = [u_left[R+], u_right[L-]]
     T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
@@ -1512,6 +1566,7 @@ __device__ __forceinline__ void bcr_bwd_unit(const T *__restrict__ A, const T *_
     const T *mB = Bc + (size_t)it.s_cell * hh, *mC = it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr;
     stage_couplings(mB, mC, cbuf, hh);
     const int KS = sliced_matvec<T, NT, RC>(Ai, n2, row0, nr, N, h2, h2, N, g, N, part, [&] {
+        flow_wait(fs);  // u of both kept neighbours final
         for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
             const int rc = idx / N, k = idx - rc * N;
             T v = T(0);
@@ -1536,6 +1591,7 @@ __device__ __forceinline__ void bcr_bwd_unit(const T *__restrict__ A, const T *_
         for (int q = 0; q < KS; ++q) s += part[(q * RC + rc) * nr + row];
         atomicAdd(Y + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row, -s);
     }
+    flow_signal(fs);
     __syncthreads();
 }
 
@@ -1632,6 +1688,76 @@ __global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, 
     }
 }
 
+
+// The BCR solve as a dataflow over all units in one cooperative launch, without
+// grid-wide barriers. Units are numbered phase by phase (forward levels, roots,
+// backward levels) and taken block-stride in that order, so every unit depends only
+// on units numbered before it and, all blocks being co-resident, every wait ends.
+// Counters per (right-hand-side chunk, cell), zero at launch:
+//   cnt[ch][i]   pushes landed in r_i; the forward unit of item i at level l (local
+//                index a, instance size K) waits for sum_{l' < l} ([a >= 2^l'] + [a + 2^l' < K])
+//   done[ch][i]  slices of cell i whose u is final (its root solve or backward update);
+//                the backward unit of item i waits for all slices of both kept neighbours
+// A unit requests its A^{-1} vectors before it waits, so the factor reads overlap the
+// wait. The levels thus overlap: a unit starts as soon as its own inputs are final.
+__device__ __forceinline__ int bcr_cell_level(int local, int n_levels) {
+    return local == 0 ? n_levels : __ffs(local) - 1;
+}
+
+template <typename T, int NT, int RC>
+__global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ A, const T *__restrict__ Bc,
+                                                       const T *__restrict__ Cc, const BcrItem *__restrict__ items,
+                                                       LevelTable lv, T *rhs, T *Y, int N, int sumK, int R, int *cnt,
+                                                       int *done, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, P = 2 * nl;
+    auto phase_level = [&](int ph) { return ph <= nl ? ph : 2 * nl - ph; };
+    auto units = [&](int ph) {
+        const int l = phase_level(ph);
+        const int nitems = (l < nl) ? lv.off[l + 1] - lv.off[l] : lv.n_roots;
+        return nitems * nchunk * lv.slices[l];
+    };
+    int ph = 0, start = 0;  // phase of the current unit and its first global index
+    for (int gidx = blockIdx.x;; gidx += gridDim.x) {
+        while (ph <= P && gidx >= start + units(ph)) {
+            start += units(ph);
+            ++ph;
+        }
+        if (ph > P) break;
+        const int l = phase_level(ph), S = lv.slices[l], w = gidx - start;
+        const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
+        const int r0 = ch * RC, nrc = min(RC, R - r0);
+        const BcrItem it = items[lv.off[l] + item];
+        int *cnt_c = cnt + (size_t)ch * sumK, *done_c = done + (size_t)ch * sumK;
+        const int n2 = 2 * N, nr = n2 / S, row0 = sl * nr;
+        FlowSync fs{};
+        fs.err = err;
+        if (ph <= nl) {
+            int want = 0;
+            for (int lp = 0; lp < it.level; ++lp)
+                want += (it.local >= (1 << lp)) + (it.local + (1 << lp) < it.K_inst);
+            if (want) {
+                fs.wait0 = cnt_c + it.cell;
+                fs.want0 = want;
+            }
+            if (it.right >= 0 && row0 + nr == n2) fs.sig0 = cnt_c + it.right;
+            if (it.left >= 0 && row0 == 0) fs.sig1 = cnt_c + it.left;
+            if (it.left < 0) fs.sig2 = done_c + it.cell;  // a root: its solution is final
+            bcr_fwd_unit<T, NT, RC>(A, Bc, Cc, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, &fs);
+        } else {
+            const int step = 1 << it.level;
+            fs.wait0 = done_c + it.left;
+            fs.want0 = lv.slices[bcr_cell_level(it.local - step, nl)];
+            if (it.right >= 0) {
+                fs.wait1 = done_c + it.right;
+                fs.want1 = lv.slices[bcr_cell_level(it.local + step, nl)];
+            }
+            fs.sig0 = done_c + it.cell;
+            bcr_bwd_unit<T, NT, RC>(A, Bc, Cc, it, r0, nrc, sl, S, Y, N, sumK, sm, &fs);
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Adjoint (implicit differentiation of the converged discrete solution; the
