@@ -378,6 +378,8 @@ int setup_tc(fpsa_ctx *ctx) {
     const int smem = (int)tc::Plan::make(N).total;
     CK(raise_smem_limit((const void *)k_tc_fp_rhs, smem));
     CK(raise_smem_limit((const void *)k_tc_update_scatter, smem));
+    CK(raise_smem_limit((const void *)k_tc_fp_rhs_tile, smem));
+    CK(raise_smem_limit((const void *)k_tc_update_scatter_tile, smem));
     int nsm = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_update_scatter, 128, smem));
@@ -614,6 +616,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
     const int tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
     const size_t tc_smem = tc::Plan::make(N).total;
+    const bool tc_full = tc::Plan::make(N).full;
     CK(cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), st));
 
     CK(cudaMemsetAsync(p.phi, 0, nang * sizeof(double), st));
@@ -693,7 +696,11 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             if (fpsa) {
                 {
                     Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                    if (use_tc)
+                    if (use_tc && tc_full)
+                        k_tc_fp_rhs_tile<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s,
+                                                                          ctx->d_h, tcops, f.rhs, N, g.sumK, g.R,
+                                                                          ctx->d_dev_err);
+                    else if (use_tc)
                         k_tc_fp_rhs<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h,
                                                                      tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err);
                     else
@@ -707,7 +714,11 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             }
             if (j < inner) {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                if (use_tc)
+                if (use_tc && tc_full)
+                    k_tc_update_scatter_tile<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops,
+                                                                              f.q, f.qang, N, g.sumK, g.R,
+                                                                              ctx->d_dev_err);
+                else if (use_tc)
                     k_tc_update_scatter<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops, f.q,
                                                                          f.qang, N, g.sumK, g.R, ctx->d_dev_err);
                 else

@@ -90,6 +90,8 @@ __device__ __forceinline__ Affine<T> compose(Affine<T> first, Affine<T> then) {
 
 constexpr int32_t kBcReflect = 1;
 
+constexpr int kSweepBatch = 8;  // cells whose inputs one thread requests together
+
 template <typename T, int NT, bool kTotals = false>
 __global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__restrict__ psi,
                                               const T *__restrict__ coef, const double *__restrict__ mu,
@@ -105,17 +107,33 @@ __global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__rest
     const int p0 = min((int)threadIdx.x * chunk, K), p1 = min(p0 + chunk, K);
     const size_t base = ((size_t)r * sumK + o) * 2 * N + n;
     const T *qb = q + base;
-    T *pb = psi + base;
+    T *pb_ = psi + base;
     const T *cb = coef + (size_t)o * 6 * N + n;
 
+    // pass 1: the chunk's affine map, inputs requested kSweepBatch cells at a time
+    // (all loads of a batch in flight together, then the dependent recurrence)
     Affine<T> m{T(1), T(0)};
-    for (int p = p0; p < p1; ++p) {
-        const int c = fwd ? p : K - 1 - p;
-        const T qu = qb[(size_t)(2 * c + nu_) * N], qd = qb[(size_t)(2 * c + nd_) * N];
-        const T *cc = cb + (size_t)c * 6 * N;
-        const T al = cc[0], gdu = cc[4 * N], gdd = cc[5 * N];
-        m.b = al * m.b + (gdu * qu + gdd * qd);
-        m.a = al * m.a;
+    for (int pb = p0; pb < p1; pb += kSweepBatch) {
+        T qu[kSweepBatch], qd[kSweepBatch], al[kSweepBatch], gdu[kSweepBatch], gdd[kSweepBatch];
+#pragma unroll
+        for (int t = 0; t < kSweepBatch; ++t) {
+            const int p = pb + t;
+            if (p < p1) {
+                const int c = fwd ? p : K - 1 - p;
+                const T *cc = cb + (size_t)c * 6 * N;
+                qu[t] = qb[(size_t)(2 * c + nu_) * N];
+                qd[t] = qb[(size_t)(2 * c + nd_) * N];
+                al[t] = cc[0];
+                gdu[t] = cc[4 * N];
+                gdd[t] = cc[5 * N];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSweepBatch; ++t)
+            if (pb + t < p1) {
+                m.b = al[t] * m.b + (gdu[t] * qu[t] + gdd[t] * qd[t]);
+                m.a = al[t] * m.a;
+            }
     }
     // inclusive scan over the block (thread order = sweep order)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -168,16 +186,34 @@ __global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__rest
     T x = __shfl_up_sync(0xffffffffu, inc_b_full, 1);
     if (lane == 0) x = before_warp;
 
-    for (int p = p0; p < p1; ++p) {
-        const int c = fwd ? p : K - 1 - p;
-        const T qu = qb[(size_t)(2 * c + nu_) * N], qd = qb[(size_t)(2 * c + nd_) * N];
-        const T *cc = cb + (size_t)c * 6 * N;
-        const T al = cc[0], au = cc[N], guu = cc[2 * N], gud = cc[3 * N], gdu = cc[4 * N], gdd = cc[5 * N];
-        const T pu = guu * qu + gud * qd + au * x;
-        const T pd = gdu * qu + gdd * qd + al * x;
-        pb[(size_t)(2 * c + nu_) * N] = pu;
-        pb[(size_t)(2 * c + nd_) * N] = pd;
-        x = pd;
+    // pass 2: re-sweep the chunk from its exact inflow, in batches as in pass 1
+    for (int pb = p0; pb < p1; pb += kSweepBatch) {
+        T qu[kSweepBatch], qd[kSweepBatch], cf[6][kSweepBatch];
+#pragma unroll
+        for (int t = 0; t < kSweepBatch; ++t) {
+            const int p = pb + t;
+            if (p < p1) {
+                const int c = fwd ? p : K - 1 - p;
+                const T *cc = cb + (size_t)c * 6 * N;
+                qu[t] = qb[(size_t)(2 * c + nu_) * N];
+                qd[t] = qb[(size_t)(2 * c + nd_) * N];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) cf[k][t] = cc[(size_t)k * N];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSweepBatch; ++t) {
+            const int p = pb + t;
+            if (p < p1) {
+                const int c = fwd ? p : K - 1 - p;
+                // cf: 0 alpha, 1 a_u, 2 G_uu, 3 G_ud, 4 G_du, 5 G_dd
+                const T pu = cf[2][t] * qu[t] + cf[3][t] * qd[t] + cf[1][t] * x;
+                const T pd = cf[4][t] * qu[t] + cf[5][t] * qd[t] + cf[0][t] * x;
+                pb_[(size_t)(2 * c + nu_) * N] = pu;
+                pb_[(size_t)(2 * c + nd_) * N] = pd;
+                x = pd;
+            }
+        }
     }
 }
 
@@ -1604,90 +1640,6 @@ struct LevelTable {
     int32_t slices[kMaxLevels + 2];
     int32_t n_levels, n_roots;
 };
-
-// L2 prefetch of the data a forward (bwd = false) or backward unit will read:
-// its A^{-1} row slice (all 2N columns forward, the N inflow columns backward;
-// one 128-byte line per column for slices of <= 128 bytes) and its coupling blocks.
-template <typename T>
-__device__ __forceinline__ void prefetch_unit(const T *A, const T *Bc, const T *Cc, const BcrItem &it, int sl, int S,
-                                              int N, bool bwd) {
-    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
-    const int nr = n2 / S, row0 = sl * nr;
-    const int lines_per_col = (int)((nr * sizeof(T) + 127) / 128);
-    const int ncols = bwd ? N : n2;
-    const T *Ai = A + (size_t)it.cell * n2 * n2;
-    for (int idx = threadIdx.x; idx < ncols * lines_per_col; idx += blockDim.x) {
-        const int kk = idx / lines_per_col, ln = idx - kk * lines_per_col;
-        const int col = bwd ? (kk < h2 ? h2 + kk : N + (kk - h2)) : kk;
-        const char *p = reinterpret_cast<const char *>(Ai + (size_t)col * n2 + row0) + 128 * ln;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-    }
-    const int cl = (int)((hh * sizeof(T) + 127) / 128);
-    const T *blk[2] = {bwd ? Bc + (size_t)it.s_cell * hh : (it.right >= 0 ? Bc + (size_t)it.s_right * hh : nullptr),
-                       bwd ? (it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr)
-                           : (it.left >= 0 ? Cc + (size_t)it.s_left * hh : nullptr)};
-    for (int idx = threadIdx.x; idx < 2 * cl; idx += blockDim.x) {
-        const T *b = blk[idx / cl];
-        if (b) asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(b) + 128 * (idx % cl)));
-    }
-}
-
-// The whole BCR solve in one cooperative launch: forward levels, roots, backward
-// levels, separated by grid-wide barriers (all blocks are co-resident by the
-// cooperative launch, so every barrier completes). Blocks take
-// (item, right-hand-side chunk of RC, row slice) units block-stride within a level;
-// before working on a level each block asks L2 for the data of its units of the
-// next level, so that level's factor reads hit L2. Solution left in Y.
-template <typename T, int NT, int RC>
-__global__ void __launch_bounds__(NT) k_bcr_solve_coop(const T *__restrict__ A, const T *__restrict__ Bc,
-                                                       const T *__restrict__ Cc, const BcrItem *__restrict__ items,
-                                                       LevelTable lv, T *rhs, T *Y, int N, int sumK, int R) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    cg::grid_group grid = cg::this_grid();
-    const int nchunk = (R + RC - 1) / RC;
-
-    auto level_units = [&](int l) {
-        const int nitems = (l < lv.n_levels) ? lv.off[l + 1] - lv.off[l] : lv.n_roots;
-        return nitems * nchunk * lv.slices[l];
-    };
-    auto prefetch_level = [&](int l, bool bwd) {
-        if (l < 0 || l > lv.n_levels) return;
-        const int S = lv.slices[l], nw = level_units(l);
-        for (int w = blockIdx.x; w < nw; w += gridDim.x)
-            prefetch_unit(A, Bc, Cc, items[lv.off[l] + w / (S * nchunk)], w % S, S, N, bwd);
-    };
-    // A level with more units than blocks runs long enough to hide the next level's
-    // prefetch behind its own work; after a short level the prefetch is issued once the
-    // block's unit is done, so it overlaps the barrier instead of delaying the unit.
-    for (int l = 0; l <= lv.n_levels; ++l) {  // level n_levels = the roots
-        const int base = lv.off[l], S = lv.slices[l];
-        const int nw = level_units(l);
-        const bool early = nw > (int)gridDim.x;
-        if (early) prefetch_level(l + 1, false);
-        for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-            const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
-            const int r0 = ch * RC;
-            bcr_fwd_unit<T, NT, RC>(A, Bc, Cc, items[base + item], r0, min(RC, R - r0), sl, S, rhs, Y, N, sumK, sm);
-        }
-        if (!early) prefetch_level(l < lv.n_levels ? l + 1 : lv.n_levels - 1, l == lv.n_levels);
-        if (l < lv.n_levels) grid.sync();
-    }
-    for (int l = lv.n_levels - 1; l >= 0; --l) {
-        grid.sync();
-        const int base = lv.off[l], S = lv.slices[l];
-        const int nw = (lv.off[l + 1] - base) * nchunk * S;
-        const bool early = nw > (int)gridDim.x;
-        if (early) prefetch_level(l - 1, true);
-        for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-            const int sl = w % S, ch = (w / S) % nchunk, item = w / (S * nchunk);
-            const int r0 = ch * RC;
-            bcr_bwd_unit<T, NT, RC>(A, Bc, Cc, items[base + item], r0, min(RC, R - r0), sl, S, Y, N, sumK, sm);
-        }
-        if (!early) prefetch_level(l - 1, true);
-    }
-}
-
 
 // The BCR solve as a dataflow over all units in one cooperative launch, without
 // grid-wide barriers. Units are numbered phase by phase (forward levels, roots,

@@ -169,15 +169,49 @@ constexpr uint32_t kStageBytes = 128u * kStageLd * 4;
 //   stage[3]:                       [128][kStageLd] FP32 each (staged I/O)
 //   bars: 2 mbarriers (bulk copy, MMA), tmem slot
 struct Plan {
-    uint32_t op_bytes, x_bytes, total;
+    uint32_t op_bytes, x_bytes, stage_bytes, total;
+    bool full;  // whole-tile staging ([128][N + 4] FP32 per buffer, N <= 64)
     __host__ __device__ static Plan make(int N) {
         Plan p;
         p.op_bytes = (uint32_t)N * N * 2;
         p.x_bytes = 128u * N * 2;
-        p.total = 4 * p.op_bytes + 2 * p.x_bytes + 3 * kStageBytes + 64;
+        p.full = N <= 64;
+        p.stage_bytes = p.full ? 128u * (N + 4) * 4 : kStageBytes;
+        p.total = 4 * p.op_bytes + 2 * p.x_bytes + 3 * p.stage_bytes + 64;
         return p;
     }
 };
+
+// Whole-tile staging: asynchronous 16-byte copies of rows [0, nrows) of src (row
+// length N floats, N a multiple of 4) into st[row][0..N) with row stride N + 4
+// (conflict-free row reads); rows >= nrows are zero-filled. Not committed here.
+__device__ __forceinline__ void tile_load_async(float *st, const float *src, int N, int nrows) {
+    const int Q = N / 4, ld = N + 4;
+    for (int f = threadIdx.x; f < 128 * Q; f += 128) {
+        const int row = f / Q, q = f - row * Q;
+        float *dst = st + row * ld + 4 * q;
+        if (row < nrows)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
+                         "l"(src + (size_t)row * N + 4 * q)
+                         : "memory");
+        else
+            *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPending>
+__device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPending) : "memory"); }
+
+// dst[row * N + k] = st[row][k] for rows < nrows, coalesced 16-byte stores.
+__device__ __forceinline__ void tile_store(const float *st, float *dst, int N, int nrows) {
+    const int Q = N / 4, ld = N + 4;
+    for (int f = threadIdx.x; f < 128 * Q; f += 128) {
+        const int row = f / Q, q = f - row * Q;
+        if (row < nrows)
+            reinterpret_cast<float4 *>(dst + (size_t)row * N)[q] =
+                *reinterpret_cast<const float4 *>(st + row * ld + 4 * q);
+    }
+}
 
 // st[row][0..kStageK) = src[row * N + k0 ..] for rows < nrows, 0 above (all 128 threads).
 __device__ __forceinline__ void stage_in(float *st, const float *src, int N, int nrows, int k0) {
@@ -199,6 +233,21 @@ __device__ __forceinline__ void stage_out(const float *st, float *dst, int N, in
             reinterpret_cast<float4 *>(dst + (size_t)row * N + k0)[q] =
                 *reinterpret_cast<const float4 *>(st + row * kStageLd + 4 * q);
     }
+}
+
+// 16 floats of row `row` from k0 in a padded buffer of row stride ld (16-byte aligned rows).
+__device__ __forceinline__ void row_get16_ld(const float *st, int ld, int row, int k0, float *v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 x = *reinterpret_cast<const float4 *>(st + row * ld + k0 + 4 * q);
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+}
+__device__ __forceinline__ void row_put16_ld(float *st, int ld, int row, int k0, const float *v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4 *>(st + row * ld + k0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2],
+                                                                            v[4 * q + 3]);
 }
 
 __device__ __forceinline__ void row_get16(const float *st, int row, float *v) {
@@ -278,7 +327,8 @@ struct TcCta {
     uint32_t mma_phase;
 };
 
-__device__ __forceinline__ bool tc_cta_setup(TcCta &s, unsigned char *smem, const TcOps &ops, int N, int *err) {
+__device__ __forceinline__ bool tc_cta_setup(TcCta &s, unsigned char *smem, const TcOps &ops, int N, int *err,
+                                             bool wait_ops = true) {
     const tc::Plan pl = tc::Plan::make(N);
     s.opD_hi = smem;
     s.opD_lo = smem + pl.op_bytes;
@@ -287,9 +337,9 @@ __device__ __forceinline__ bool tc_cta_setup(TcCta &s, unsigned char *smem, cons
     s.x_hi = smem + 4 * pl.op_bytes;
     s.x_lo = s.x_hi + pl.x_bytes;
     s.stA = reinterpret_cast<float *>(s.x_lo + pl.x_bytes);
-    s.stB = s.stA + 128 * tc::kStageLd;
-    s.stC = s.stB + 128 * tc::kStageLd;
-    unsigned char *tail = reinterpret_cast<unsigned char *>(s.stC + 128 * tc::kStageLd);
+    s.stB = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s.stA) + pl.stage_bytes);
+    s.stC = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s.stB) + pl.stage_bytes);
+    unsigned char *tail = reinterpret_cast<unsigned char *>(s.stC) + pl.stage_bytes;
     s.bar_copy = reinterpret_cast<uint64_t *>(tail);
     s.bar_mma = s.bar_copy + 1;
     s.tmem_slot = reinterpret_cast<uint32_t *>(s.bar_mma + 1);
@@ -311,6 +361,14 @@ __device__ __forceinline__ bool tc_cta_setup(TcCta &s, unsigned char *smem, cons
         tc::bulk_copy_g2s(s.opD_hi, ops.D, 2 * pl.op_bytes, s.bar_copy);
         tc::bulk_copy_g2s(s.opM_hi, ops.M, 2 * pl.op_bytes, s.bar_copy);
     }
+    if (!wait_ops) return true;
+    const bool ok = tc::mbar_wait(s.bar_copy, 0);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    return ok;
+}
+
+// Wait for the operator copy started by tc_cta_setup(..., wait_ops = false).
+__device__ __forceinline__ bool tc_wait_ops(TcCta &s, int *err) {
     const bool ok = tc::mbar_wait(s.bar_copy, 0);
     if (!ok && threadIdx.x == 0) atomicExch(err, 1);
     return ok;
@@ -473,6 +531,162 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter(const float *__restri
             tc::stage_out(s.stC, q + cb, N, ncols, k0);
         }
     }
+    tc_cta_teardown(s, N);
+}
+
+// Whole-tile variants for N <= 64: every global input of a tile is requested by
+// asynchronous copies as soon as its buffer is free (the psi / v tile and the phi and
+// sigma tiles at the start, overlapping the operator copy and the first GEMM), and
+// outputs leave through the staging buffers with coalesced 16-byte stores.
+//   stA: psi / v tile, then the outputs;  stB: phi / phi_base, then q_ang;  stC: sigma rows
+__global__ void __launch_bounds__(128) k_tc_fp_rhs_tile(const float *__restrict__ psi_half,
+                                                        const float *__restrict__ phi, float *__restrict__ phi_half,
+                                                        const float *__restrict__ sigma_s, const double *__restrict__ h,
+                                                        TcOps ops, float *__restrict__ rhs, int N, int sumK, int R,
+                                                        int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcCta s;
+    const int t = threadIdx.x, ld = N + 4;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    bool ok = tc_cta_setup(s, smem_tc, ops, N, err, false);
+    bool first = true;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const bool live = t < ncols;
+        const int g = (j0 + t) >> 1;
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
+        tc::tile_load_async(s.stA, psi_half + cb, N, ncols);
+        tc::async_commit();
+        tc::tile_load_async(s.stB, phi + cb, N, ncols);
+        tc::tile_load_async(s.stC, sigma_s + (size_t)(j0 >> 1) * N, N, ncell);
+        tc::async_commit();
+        if (first && !(ok = tc_wait_ops(s, err))) break;
+        first = false;
+        tc::async_wait<1>();
+        __syncthreads();
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float v[16];
+            tc::row_get16_ld(s.stA, ld, t, k0, v);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        if (!(ok = tc_gemm(s, s.opD_hi, s.opD_lo, N, err))) break;
+        tc::async_wait<0>();
+        __syncthreads();
+        // phi_half = D psi -> stA; next A = Sigma (phi_half - phi)
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16], ph[16], sg[16], v[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            tc::row_get16_ld(s.stB, ld, t, k0, ph);
+            tc::row_get16_ld(s.stC, ld, t >> 1, k0, sg);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = live ? sg[i] * (a[i] - ph[i]) : 0.f;
+            tc::row_put16_ld(s.stA, ld, t, k0, a);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        __syncthreads();
+        tc::tile_store(s.stA, phi_half + cb, N, ncols);
+        if (!(ok = tc_gemm(s, s.opM_hi, s.opM_lo, N, err))) break;
+        // rhs = m (x) r: node partner is the adjacent lane (column j ^ 1)
+        const float w = live ? (float)(h[g] / 6.0) : 0.f;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16], o[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);
+                o[i] = w * (2.f * a[i] + other);
+            }
+            tc::row_put16_ld(s.stA, ld, t, k0, o);
+        }
+        __syncthreads();
+        tc::tile_store(s.stA, rhs + cb, N, ncols);
+        __syncthreads();  // stA / stB / stC free for the next tile's copies
+    }
+    if (first) tc_wait_ops(s, err);  // no copy may land after the CTA has gone
+    tc::async_wait<0>();
+    tc_cta_teardown(s, N);
+}
+
+__global__ void __launch_bounds__(128) k_tc_update_scatter_tile(const float *__restrict__ v_in,
+                                                                const float *__restrict__ phi_base,
+                                                                float *__restrict__ phi,
+                                                                const float *__restrict__ sigma_s, TcOps ops,
+                                                                float *__restrict__ q, const float *__restrict__ qang,
+                                                                int N, int sumK, int R, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcCta s;
+    const int t = threadIdx.x, ld = N + 4;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    bool ok = tc_cta_setup(s, smem_tc, ops, N, err, false);
+    bool first = true;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const bool live = t < ncols;
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
+        tc::tile_load_async(s.stA, v_in + cb, N, ncols);
+        tc::async_commit();
+        if (phi_base) tc::tile_load_async(s.stB, phi_base + cb, N, ncols);
+        tc::tile_load_async(s.stC, sigma_s + (size_t)(j0 >> 1) * N, N, ncell);
+        tc::async_commit();
+        if (first && !(ok = tc_wait_ops(s, err))) break;
+        first = false;
+        tc::async_wait<1>();
+        __syncthreads();
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float v[16];
+            tc::row_get16_ld(s.stA, ld, t, k0, v);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        if (!(ok = tc_gemm(s, s.opD_hi, s.opD_lo, N, err))) break;
+        tc::async_wait<0>();
+        __syncthreads();
+        // phi = phi_base + D v -> stA; next A = Sigma phi
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16], pb[16], sg[16], v[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            if (phi_base) tc::row_get16_ld(s.stB, ld, t, k0, pb);
+            tc::row_get16_ld(s.stC, ld, t >> 1, k0, sg);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                a[i] += phi_base ? pb[i] : 0.f;
+                v[i] = live ? sg[i] * a[i] : 0.f;
+            }
+            tc::row_put16_ld(s.stA, ld, t, k0, a);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+        }
+        __syncthreads();
+        if (qang) {  // stB is free now: the q_ang tile arrives during the second GEMM
+            tc::tile_load_async(s.stB, qang + cb, N, ncols);
+        }
+        tc::async_commit();
+        tc::tile_store(s.stA, phi + cb, N, ncols);
+        if (!(ok = tc_gemm(s, s.opM_hi, s.opM_lo, N, err))) break;
+        tc::async_wait<0>();
+        __syncthreads();
+        // q = M (Sigma phi) + q_ang
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            if (qang) {
+                float qa[16];
+                tc::row_get16_ld(s.stB, ld, t, k0, qa);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a[i] += qa[i];
+            }
+            tc::row_put16_ld(s.stA, ld, t, k0, a);
+        }
+        __syncthreads();
+        tc::tile_store(s.stA, q + cb, N, ncols);
+        __syncthreads();
+    }
+    if (first) tc_wait_ops(s, err);  // no copy may land after the CTA has gone
+    tc::async_wait<0>();
     tc_cta_teardown(s, N);
 }
 
