@@ -43,7 +43,7 @@ WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, 
 METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
 TOL = 1e-10
 # per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload
-NCU_TRAFFIC = {("k_bcr_solve_coop", "mixed"): 232.8e6}
+NCU_TRAFFIC = {("k_bcr_solve_flow", "mixed"): 206.6e6}
 
 
 def dist_env():
@@ -298,9 +298,9 @@ def main():
         byt = esize * (K * n2 * n2 + (K - 1) * n2 * N + 2 * (K - 1) * (N // 2) ** 2)
         achieved = byt / (per_launch_ms * 1e-3) / 1e9
         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel for this
-        # workload (FP32), from profiles/k_bcr_solve_coop_precision_srk_slab.md
-        traffic = NCU_TRAFFIC.get(("k_bcr_solve_coop", args.precision))
-        roof = {"kernel": "k_bcr_solve_coop", "bound": "hbm", "achieved": achieved, "peak": hbm,
+        # workload (FP32), from profiles/k_bcr_solve_flow_precision_srk_slab.md
+        traffic = NCU_TRAFFIC.get(("k_bcr_solve_flow", args.precision))
+        roof = {"kernel": "k_bcr_solve_flow", "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "algorithmic_bytes": byt}
     elif dom == "bcr_invert":
         flops = 2.0 * n2 ** 3 * K / 12.0  # per launch: K blocks over 12 launches on average

@@ -4,7 +4,7 @@
 // is, per sweep, the launch sequence
 //   k_sweep            psi^{m+1/2} = L^{-1} q                      (LD upwind sweep)
 //   k_fp_rhs           phi^{m+1/2} = D psi^{m+1/2};  rhs = m (x) M Sigma (phi^{m+1/2} - phi^m)
-//   k_bcr_solve_coop   upsilon = F^{-1} rhs (all reduction levels in one cooperative launch)
+//   k_bcr_solve_flow   upsilon = F^{-1} rhs (all reduction levels in one cooperative launch)
 //   k_update_scatter   phi^{m+1} = phi^{m+1/2} + D upsilon; q = M (Sigma phi^{m+1} + Q)
 // with the convergence maxima of Eq. iterate accumulated in k_update_scatter.
 #include <algorithm>
