@@ -43,7 +43,7 @@ WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, 
 METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
 TOL = 1e-10
 # per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload
-NCU_TRAFFIC = {("k_bcr_solve_flow", "mixed"): 206.6e6}
+NCU_TRAFFIC = {}
 
 
 def dist_env():
@@ -299,8 +299,9 @@ def main():
         achieved = byt / (per_launch_ms * 1e-3) / 1e9
         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel for this
         # workload (FP32), from profiles/k_bcr_solve_flow_precision_srk_slab.md
-        traffic = NCU_TRAFFIC.get(("k_bcr_solve_flow", args.precision))
-        roof = {"kernel": "k_bcr_solve_flow", "bound": "hbm", "achieved": achieved, "peak": hbm,
+        kname = "k_bcr_solve_flow_s" if (2 * N) * (2 * N) * esize <= 64 * 1024 else "k_bcr_solve_flow"
+        traffic = NCU_TRAFFIC.get((kname, args.precision))
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "algorithmic_bytes": byt}
     elif dom == "bcr_invert":
         flops = 2.0 * n2 ** 3 * K / 12.0  # per launch: K blocks over 12 launches on average

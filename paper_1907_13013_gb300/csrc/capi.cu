@@ -191,14 +191,26 @@ size_t schur_smem(int N) { return (size_t)(schur_staged<T>(N) ? 3 : 1) * (N / 2)
 // right-hand sides per BCR solve unit
 int solve_rc(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
 
-// shared scratch of the cooperative BCR solve (one unit per block)
+// shared memory of the cooperative BCR solve: the unit scratch and, when one unit's
+// A^{-1} slice fits, the staged slice buffer
 template <typename T>
 size_t solve_smem(int N, int RC) {
+    if (bcr_slice_staged(N, (int)sizeof(T)))
+        return (size_t)bcr_slice_offset_values<T>(N, kSolveThreads, RC) * sizeof(T) +
+               (size_t)(2 * N) * (2 * N) * sizeof(T);
     return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V, RC, (int)sizeof(T)) * sizeof(T);
 }
 
 template <typename T>
-const void *coop_kernel(int RC) {
+const void *coop_kernel(int RC, int N) {
+    if (bcr_slice_staged(N, (int)sizeof(T))) {
+        switch (RC) {
+            case 8: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 8>;
+            case 4: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 4>;
+            case 2: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 2>;
+            default: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 1>;
+        }
+    }
     switch (RC) {
         case 8: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 8>;
         case 4: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 4>;
@@ -482,7 +494,7 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     CK(cudaMemsetAsync(cnt, 0, ncnt, ctx->stream));
     CK(cudaMemsetAsync(done, 0, ncnt, ctx->stream));
     Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
-    CK(cudaLaunchCooperativeKernel(coop_kernel<T>(RC), dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC),
+    CK(cudaLaunchCooperativeKernel(coop_kernel<T>(RC, N), dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC),
                                    ctx->stream));
     return FPSA_OK;
 }
@@ -1217,12 +1229,12 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             int nsm = 0, per_sm = 0;
             CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
             const int RC = solve_rc(g.R);
-            CK(raise_smem_limit((const void *)coop_kernel<float>(RC), (int)solve_smem<float>(g.N, RC)));
-            CK(raise_smem_limit((const void *)coop_kernel<double>(RC), (int)solve_smem<double>(g.N, RC)));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<float>(RC), kSolveThreads,
+            CK(raise_smem_limit((const void *)coop_kernel<float>(RC, g.N), (int)solve_smem<float>(g.N, RC)));
+            CK(raise_smem_limit((const void *)coop_kernel<double>(RC, g.N), (int)solve_smem<double>(g.N, RC)));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<float>(RC, g.N), kSolveThreads,
                                                              solve_smem<float>(g.N, RC)));
             ctx->coop_grid[0] = std::max(1, std::min(per_sm, 4)) * nsm;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<double>(RC), kSolveThreads,
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<double>(RC, g.N), kSolveThreads,
                                                              solve_smem<double>(g.N, RC)));
             ctx->coop_grid[1] = std::max(1, std::min(per_sm, 4)) * nsm;
             // Row slices per item: split an item's 2N rows (in vectors of V) into S in {1, 2, 4}

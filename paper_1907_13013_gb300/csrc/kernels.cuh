@@ -874,28 +874,6 @@ __device__ __forceinline__ void gj_pick_pivot_v(const T (&colv)[RI], unsigned us
     pv = __shfl_sync(0xffffffffu, bv, src);
 }
 
-template <int RI, int CJ>
-__device__ __forceinline__ void gj_store_row(const float (&x)[RI][CJ], int i, float *dst) {
-    switch (i) {
-        case 0: {
-#pragma unroll
-            for (int j = 0; j < CJ; ++j) dst[j] = x[0][j];
-        } break;
-        case 1: if constexpr (RI > 1) {
-#pragma unroll
-            for (int j = 0; j < CJ; ++j) dst[j] = x[1][j];
-        } break;
-        case 2: if constexpr (RI > 2) {
-#pragma unroll
-            for (int j = 0; j < CJ; ++j) dst[j] = x[2][j];
-        } break;
-        default: if constexpr (RI > 3) {
-#pragma unroll
-            for (int j = 0; j < CJ; ++j) dst[j] = x[3][j];
-        } break;
-    }
-}
-
 template <int N2>
 __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *dst, int ldd, bool tout,
                                               unsigned long long *__restrict__ growth, int *__restrict__ status) {
@@ -908,12 +886,25 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
     float x[RI][CJ];
     float amax = 0.f;
 #pragma unroll
-    for (int i = 0; i < RI; ++i)
+    for (int i = 0; i < RI; ++i) {
+        // this lane's CJ consecutive values of row lane + 32 i (16-byte / 8-byte vectors)
+        const float *rp = src + (size_t)(lane + 32 * i) * lds + CJ * w;
+        if constexpr (CJ % 4 == 0) {
 #pragma unroll
-        for (int j = 0; j < CJ; ++j) {
-            x[i][j] = src[(size_t)(lane + 32 * i) * lds + CJ * w + j];
-            amax = fmaxf(amax, fabsf(x[i][j]));
+            for (int j = 0; j < CJ; j += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(rp + j);
+                x[i][j] = v.x; x[i][j + 1] = v.y; x[i][j + 2] = v.z; x[i][j + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CJ; j += 2) {
+                const float2 v = *reinterpret_cast<const float2 *>(rp + j);
+                x[i][j] = v.x; x[i][j + 1] = v.y;
+            }
         }
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) amax = fmaxf(amax, fabsf(x[i][j]));
+    }
     for (int r = threadIdx.x; r < N2; r += blockDim.x) piv_panel[r] = -1;
     unsigned used = 0u;  // bit i: row lane + 32 i has been a pivot row
     bool bad = false;
@@ -979,33 +970,58 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
         }
         __syncthreads();
         if (w != q) {
-            int P[CJ];
+            // the panel's pivot rows in this warp's columns -> PRb[w] (selects on the
+            // row register index: no indirect branch)
 #pragma unroll
             for (int c = 0; c < CJ; ++c) {
-                P[c] = Pb[qb][c];
-                if (lane == (P[c] & 31)) {
-                    used |= 1u << (P[c] >> 5);
-                    gj_store_row<RI, CJ>(x, P[c] >> 5, &PRb[w][c][0]);
+                const int pr = Pb[qb][c], ip = pr >> 5;
+                if (lane == (pr & 31)) {
+                    used |= 1u << ip;
+#pragma unroll
+                    for (int j = 0; j < CJ; ++j) {
+                        float v = x[0][j];
+#pragma unroll
+                        for (int i = 1; i < RI; ++i) v = (ip == i) ? x[i][j] : v;
+                        PRb[w][c][j] = v;
+                    }
                 }
             }
             __syncwarp();
+            // X[r][:] <- (r in P ? 0 : X[r][:]) + W[r][:] PR: W rows first, then one
+            // pivot row of PR at a time against all of this lane's rows
+            float wr[RI][CJ];
 #pragma unroll
             for (int i = 0; i < RI; ++i) {
                 const int row = lane + 32 * i;
-                const bool isP = piv_panel[row] == q;
-                float wr[CJ];
+                if (piv_panel[row] == q) {
 #pragma unroll
-                for (int c = 0; c < CJ; ++c) wr[c] = Wb[qb][row][c];
+                    for (int j = 0; j < CJ; ++j) x[i][j] = 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < CJ; c += 2) {
+                    const float2 v = *reinterpret_cast<const float2 *>(&Wb[qb][row][c]);
+                    wr[i][c] = v.x;
+                    wr[i][c + 1] = v.y;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CJ; ++c) {
+                float prc[CJ];
 #pragma unroll
                 for (int j = 0; j < CJ; j += 2) {
-                    float2 acc = isP ? make_float2(0.f, 0.f) : make_float2(x[i][j], x[i][j + 1]);
-#pragma unroll
-                    for (int c = 0; c < CJ; ++c)
-                        acc = __ffma2_rn(make_float2(wr[c], wr[c]), *reinterpret_cast<const float2 *>(&PRb[w][c][j]),
-                                         acc);
-                    x[i][j] = acc.x;
-                    x[i][j + 1] = acc.y;
+                    const float2 v = *reinterpret_cast<const float2 *>(&PRb[w][c][j]);
+                    prc[j] = v.x;
+                    prc[j + 1] = v.y;
                 }
+#pragma unroll
+                for (int i = 0; i < RI; ++i)
+#pragma unroll
+                    for (int j = 0; j < CJ; j += 2) {
+                        float2 acc = make_float2(x[i][j], x[i][j + 1]);
+                        acc = __ffma2_rn(make_float2(wr[i][c], wr[i][c]), make_float2(prc[j], prc[j + 1]), acc);
+                        x[i][j] = acc.x;
+                        x[i][j + 1] = acc.y;
+                    }
             }
         }
     }
@@ -1709,6 +1725,263 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ 
             bcr_bwd_unit<T, NT, RC>(A, Bc, Cc, it, r0, nrc, sl, S, Y, N, sumK, sm, &fs);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory staged variant of the dataflow BCR solve (used when one unit's
+// A^{-1} slice fits in kSolveStageBytes): a unit's slice [its columns][its rows] is
+// copied into shared memory by asynchronous 16-byte copies, and the copy for the
+// block's NEXT unit is issued as soon as the current unit's matrix-vector product
+// has read its slice, so the factor stream of a block is double-buffered by the
+// copy engine while the unit finishes (reduction, pushes, fence, counter bump) and
+// the next one waits for its inputs. No A^{-1} registers are held across units.
+// ---------------------------------------------------------------------------
+constexpr int kSolveStageBytes = 64 * 1024;
+
+__host__ __device__ constexpr bool bcr_slice_staged(int N, int esize) {
+    return (size_t)(2 * N) * (2 * N) * esize <= (size_t)kSolveStageBytes && (2 * N * esize) % 16 == 0;
+}
+
+// offset (in values) of the slice buffer: after the unit scratch, 16-byte aligned
+template <typename T>
+__host__ __device__ constexpr int bcr_slice_offset_values(int N, int NT, int RC) {
+    return (bcr_unit_smem_values(N, NT, VecOf<T>::V, RC, (int)sizeof(T)) * (int)sizeof(T) + 15) / 16 * 16 /
+           (int)sizeof(T);
+}
+
+// Copy unit (it, sl, S, bwd)'s A^{-1} slice into As[k][row - row0] (k over the unit's
+// columns in matvec order), then commit one copy group. All threads.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_slice(const T *__restrict__ A, const BcrItem &it, int sl, int S, bool bwd,
+                                            int N, T *As) {
+    const int n2 = 2 * N, h2 = N / 2, nr = n2 / S, row0 = sl * nr;
+    const int nk = bwd ? N : n2, q4 = nr * (int)sizeof(T) / 16;  // 16-byte chunks per column
+    const T *Ai = A + (size_t)it.cell * n2 * n2;
+    for (int idx = threadIdx.x; idx < nk * q4; idx += NT) {
+        const int k = idx / q4, q = idx - k * q4;
+        const int col = bwd ? (k < h2 ? h2 + k : N + (k - h2)) : k;
+        cp_async16(reinterpret_cast<unsigned char *>(As + (size_t)k * nr) + 16 * q,
+                   reinterpret_cast<const unsigned char *>(Ai + (size_t)col * n2 + row0) + 16 * q);
+    }
+    cp_async_commit();
+}
+
+// part[ks][rc][row] for this thread's (row group, k-slice) task, A^{-1} slice in smem.
+template <typename T, int NT, int RC>
+__device__ __forceinline__ int smem_matvec(const T *As, int nr, int nk, const T *coef, int cstride, T *part) {
+    using VT = typename VecOf<T>::type;
+    constexpr int V = VecOf<T>::V;
+    const int RG = nr / V;
+    int KS = NT / RG;
+    if (KS > nk) KS = nk;
+    if (KS < 1) KS = 1;
+    const int kl = (nk + KS - 1) / KS;
+    const int t = threadIdx.x;
+    if (t < RG * KS) {
+        const int rg = t % RG, ks = t / RG;
+        const int k0 = ks * kl, k1 = min(nk, k0 + kl);
+        T acc[RC][V];
+#pragma unroll
+        for (int rc = 0; rc < RC; ++rc)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[rc][v] = T(0);
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            const VT a = *reinterpret_cast<const VT *>(As + (size_t)k * nr + rg * V);
+#pragma unroll
+            for (int rc = 0; rc < RC; ++rc) {
+                const T cv = coef[rc * cstride + k];
+                if constexpr (V == 4) {
+                    acc[rc][0] = fma(a.x, cv, acc[rc][0]); acc[rc][1] = fma(a.y, cv, acc[rc][1]);
+                    acc[rc][2] = fma(a.z, cv, acc[rc][2]); acc[rc][3] = fma(a.w, cv, acc[rc][3]);
+                } else {
+                    acc[rc][0] = fma(a.x, cv, acc[rc][0]); acc[rc][1] = fma(a.y, cv, acc[rc][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int rc = 0; rc < RC; ++rc)
+#pragma unroll
+            for (int v = 0; v < V; ++v) part[(ks * RC + rc) * nr + rg * V + v] = acc[rc][v];
+    }
+    return KS;
+}
+
+// Forward / backward unit with the A^{-1} slice already being copied into As (its
+// copy group committed before the unit's coupling group). next_copy() issues the
+// copy for the block's next unit (always commits a group).
+template <typename T, int NT, int RC, typename NextCopy>
+__device__ __forceinline__ void flow_fwd_unit_s(const T *__restrict__ Bc, const T *__restrict__ Cc,
+                                                const BcrItem &it, int r0, int nrc, int sl, int S, T *rhs, T *Y,
+                                                int N, int sumK, T *sm, const T *As, const FlowSync *fs,
+                                                NextCopy next_copy) {
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+    T *rs = sm, *ys = sm + RC * n2, *part = ys + RC * n2 + RC * N;
+    T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
+    const size_t rstride = (size_t)sumK * n2;
+    const int nr = n2 / S, row0 = sl * nr;
+    const bool push_right = it.right >= 0 && row0 + nr == n2;
+    const bool push_left = it.left >= 0 && row0 == 0;
+    const T *mB = push_right ? Bc + (size_t)it.s_right * hh : nullptr;
+    const T *mC = push_left ? Cc + (size_t)it.s_left * hh : nullptr;
+    stage_couplings(mB, mC, cbuf, hh);
+    if (!cbuf) cp_async_commit();  // keep one coupling group per unit
+    flow_wait(fs);
+    for (int i = threadIdx.x; i < RC * n2; i += NT) {
+        const int rc = i / n2, k = i - rc * n2;
+        rs[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
+    }
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's slice
+    __syncthreads();
+    const int KS = smem_matvec<T, NT, RC>(As, nr, n2, rs, n2, part);
+    __syncthreads();
+    next_copy();  // the slice buffer is free
+    for (int idx = threadIdx.x; idx < RC * nr; idx += NT) {
+        const int rc = idx / nr, row = idx - rc * nr;
+        T y = T(0);
+        for (int q = 0; q < KS; ++q) y += part[(q * RC + rc) * nr + row];
+        ys[rc * n2 + row0 + row] = y;
+        if (rc < nrc) Y[(size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row] = y;
+    }
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's couplings (the next slice may fly)
+    __syncthreads();
+    coupling_products<T, NT, RC>(mB, ys + N + h2,
+                                 push_right ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr,
+                                 mC, ys, push_left ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr,
+                                 h2, n2, rstride, nrc);
+    flow_signal(fs);
+    __syncthreads();
+}
+
+template <typename T, int NT, int RC, typename NextCopy>
+__device__ __forceinline__ void flow_bwd_unit_s(const T *__restrict__ Bc, const T *__restrict__ Cc,
+                                                const BcrItem &it, int r0, int nrc, int sl, int S, T *Y, int N,
+                                                int sumK, T *sm, const T *As, const FlowSync *fs,
+                                                NextCopy next_copy) {
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+    T *gv = sm, *g = sm + RC * N, *part = sm + RC * (5 * N);
+    T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
+    const size_t rstride = (size_t)sumK * n2;
+    const int nr = n2 / S, row0 = sl * nr;
+    const T *mB = Bc + (size_t)it.s_cell * hh, *mC = it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr;
+    stage_couplings(mB, mC, cbuf, hh);
+    if (!cbuf) cp_async_commit();
+    flow_wait(fs);
+    for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
+        const int rc = idx / N, k = idx - rc * N;
+        T v = T(0);
+        if (rc < nrc) {
+            const T *base = Y + (size_t)(r0 + rc) * rstride;
+            if (k < h2) v = __ldcg(base + (size_t)it.left * n2 + N + h2 + k);
+            else if (it.right >= 0) v = __ldcg(base + (size_t)it.right * n2 + (k - h2));
+        }
+        gv[idx] = v;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // slice and couplings
+    __syncthreads();
+    coupling_products<T, NT, RC>(mB, gv, g, mC, gv + h2, g + h2, h2, N, N);
+    if (it.right < 0)
+        for (int idx = threadIdx.x; idx < RC * h2; idx += NT) g[(idx / h2) * N + h2 + idx % h2] = T(0);
+    __syncthreads();
+    const int KS = smem_matvec<T, NT, RC>(As, nr, N, g, N, part);
+    __syncthreads();
+    next_copy();
+    for (int idx = threadIdx.x; idx < nrc * nr; idx += NT) {
+        const int rc = idx / nr, row = idx - rc * nr;
+        T sacc = T(0);
+        for (int q = 0; q < KS; ++q) sacc += part[(q * RC + rc) * nr + row];
+        atomicAdd(Y + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row, -sacc);
+    }
+    flow_signal(fs);
+    __syncthreads();
+}
+
+// The dataflow BCR solve with staged slices (same unit order, counters and waits as
+// k_bcr_solve_flow). Shared memory: the unit scratch, then the slice buffer.
+template <typename T, int NT, int RC>
+__global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict__ A, const T *__restrict__ Bc,
+                                                            const T *__restrict__ Cc,
+                                                            const BcrItem *__restrict__ items, LevelTable lv, T *rhs,
+                                                            T *Y, int N, int sumK, int R, int *cnt, int *done,
+                                                            int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *As = sm + bcr_slice_offset_values<T>(N, NT, RC);
+    const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, P = 2 * nl;
+    auto phase_level = [&](int ph) { return ph <= nl ? ph : 2 * nl - ph; };
+    auto units = [&](int ph) {
+        const int l = phase_level(ph);
+        const int nitems = (l < nl) ? lv.off[l + 1] - lv.off[l] : lv.n_roots;
+        return nitems * nchunk * lv.slices[l];
+    };
+    struct Pos {
+        int ph, start, l, S, sl, ch, item;
+        bool valid;
+    };
+    auto locate = [&](Pos &q, int gidx) {
+        while (q.ph <= P && gidx >= q.start + units(q.ph)) {
+            q.start += units(q.ph);
+            ++q.ph;
+        }
+        q.valid = q.ph <= P;
+        if (!q.valid) return;
+        q.l = phase_level(q.ph);
+        q.S = lv.slices[q.l];
+        const int w = gidx - q.start;
+        q.sl = w % q.S;
+        q.ch = (w / q.S) % nchunk;
+        q.item = w / (q.S * nchunk);
+    };
+    Pos cur{0, 0, 0, 0, 0, 0, 0, false};
+    int gidx = blockIdx.x;
+    locate(cur, gidx);
+    BcrItem it_nx{};
+    if (cur.valid) {
+        it_nx = items[lv.off[cur.l] + cur.item];
+        stage_slice<T, NT>(A, it_nx, cur.sl, cur.S, cur.ph > nl, N, As);
+    }
+    while (cur.valid) {
+        const BcrItem it = it_nx;
+        Pos nxt = cur;
+        locate(nxt, gidx + gridDim.x);
+        if (nxt.valid) it_nx = items[lv.off[nxt.l] + nxt.item];  // arrives while this unit runs
+        auto next_copy = [&]() {
+            if (nxt.valid) stage_slice<T, NT>(A, it_nx, nxt.sl, nxt.S, nxt.ph > nl, N, As);
+            else cp_async_commit();
+        };
+        const int S = cur.S, sl = cur.sl, ch = cur.ch;
+        const int r0 = ch * RC, nrc = min(RC, R - r0);
+        int *cnt_c = cnt + (size_t)ch * sumK, *done_c = done + (size_t)ch * sumK;
+        const int n2 = 2 * N, nr = n2 / S, row0 = sl * nr;
+        FlowSync fs{};
+        fs.err = err;
+        if (cur.ph <= nl) {
+            int want = 0;
+            for (int lp = 0; lp < it.level; ++lp)
+                want += (it.local >= (1 << lp)) + (it.local + (1 << lp) < it.K_inst);
+            if (want) {
+                fs.wait0 = cnt_c + it.cell;
+                fs.want0 = want;
+            }
+            if (it.right >= 0 && row0 + nr == n2) fs.sig0 = cnt_c + it.right;
+            if (it.left >= 0 && row0 == 0) fs.sig1 = cnt_c + it.left;
+            if (it.left < 0) fs.sig2 = done_c + it.cell;
+            flow_fwd_unit_s<T, NT, RC>(Bc, Cc, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, &fs, next_copy);
+        } else {
+            const int step = 1 << it.level;
+            fs.wait0 = done_c + it.left;
+            fs.want0 = lv.slices[bcr_cell_level(it.local - step, nl)];
+            if (it.right >= 0) {
+                fs.wait1 = done_c + it.right;
+                fs.want1 = lv.slices[bcr_cell_level(it.local + step, nl)];
+            }
+            fs.sig0 = done_c + it.cell;
+            flow_bwd_unit_s<T, NT, RC>(Bc, Cc, it, r0, nrc, sl, S, Y, N, sumK, sm, As, &fs, next_copy);
+        }
+        cur = nxt;
+        gidx += gridDim.x;
+    }
+    cp_async_wait_all();  // no copy in flight when the block exits
 }
 
 // ---------------------------------------------------------------------------
