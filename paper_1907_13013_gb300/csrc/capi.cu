@@ -338,16 +338,24 @@ int invert_inplace(fpsa_ctx *ctx, PathBuffers<T> &p, BMat<T> M, int n, const Bcr
 // Invert the eliminated blocks of `items` (ni of them) in place, transposed, with
 // the FP64 growth check: one CTA per block when it fits, else the recursive path.
 template <typename T>
-int invert_level(fpsa_ctx *ctx, PathBuffers<T> &p, const BcrItem *items, int ni) {
-    const int n2 = 2 * ctx->geo.N;
+// with_schur: the level's Schur updates are fused into the register-tile inversion
+// kernel when it is used; *fused reports whether they were (else the caller launches
+// k_bcr_schur).
+int invert_level(fpsa_ctx *ctx, PathBuffers<T> &p, const BcrItem *items, int ni, bool with_schur = false,
+                 bool *fused = nullptr) {
+    const int N = ctx->geo.N, n2 = 2 * N;
     cudaStream_t st = ctx->stream;
     Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+    const int staged = with_schur ? (schur_staged<T>(N) ? 1 : 0) : -1;
+    const size_t ssm = with_schur ? schur_smem<T>(N) : 0;
+    const bool reg = (n2 == 128 && cta_invertible<T>(128)) || n2 == 64 || n2 == 32;
+    if (fused) *fused = reg && with_schur;
     if (n2 == 128 && cta_invertible<T>(128)) {
-        k_bcr_invert_reg<T, 128><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+        k_bcr_invert_reg<T, 128><<<ni, 512, ssm, st>>>(p.A, items, ctx->d_growth, ctx->d_status, p.Bc, p.Cc, staged);
     } else if (n2 == 64) {
-        k_bcr_invert_reg<T, 64><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+        k_bcr_invert_reg<T, 64><<<ni, 512, ssm, st>>>(p.A, items, ctx->d_growth, ctx->d_status, p.Bc, p.Cc, staged);
     } else if (n2 == 32) {
-        k_bcr_invert_reg<T, 32><<<ni, 512, 0, st>>>(p.A, items, ctx->d_growth, ctx->d_status);
+        k_bcr_invert_reg<T, 32><<<ni, 512, ssm, st>>>(p.A, items, ctx->d_growth, ctx->d_status, p.Bc, p.Cc, staged);
     } else if (cta_invertible<T>(n2)) {
         k_bcr_invert<T><<<ni, kInvertThreads, invert_smem<T>(ctx->geo.N), st>>>(p.A, items, n2, ctx->d_growth,
                                                                                ctx->d_status);
@@ -436,10 +444,11 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     for (int l = 0; l < g.n_levels; ++l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
-        int rc = invert_level(ctx, p, ctx->d_levels[l], ni);
+        bool fused = false;
+        int rc = invert_level(ctx, p, ctx->d_levels[l], ni, true, &fused);
         if (rc) return rc;
         CK(cudaGetLastError());
-        {
+        if (!fused) {
             Launch L_(ctx, FPSA_PHASE_BCR_SCHUR);
             k_bcr_schur<T><<<ni, 256, schur_smem<T>(N), st>>>(p.A, p.Bc, p.Cc, ctx->d_levels[l], N,
                                                               schur_staged<T>(N) ? 1 : 0);

@@ -1196,13 +1196,26 @@ __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int l
     if (bad) atomicExch(status, 1);
 }
 
+template <typename T>
+__device__ __forceinline__ void schur_body(T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc,
+                                           const BcrItem &it, int N, int staged, unsigned char *smem_raw);
+
 template <typename T, int N2>
 __global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const BcrItem *__restrict__ items,
                                                         unsigned long long *__restrict__ growth,
-                                                        int *__restrict__ status) {
-    T *Ag = A + (size_t)items[blockIdx.x].cell * N2 * N2;
+                                                        int *__restrict__ status, T *__restrict__ Bc = nullptr,
+                                                        T *__restrict__ Cc = nullptr, int schur_staged = -1) {
+    const BcrItem it = items[blockIdx.x];
+    T *Ag = A + (size_t)it.cell * N2 * N2;
     if constexpr (sizeof(T) == 4) gj_panel_body<N2>(Ag, N2, Ag, N2, true, growth, status);
     else gj_reg_body<T, N2>(Ag, N2, Ag, N2, true, growth, status);
+    if (schur_staged >= 0) {
+        // the level's Schur updates of this cell's neighbours, from the inverse this block
+        // just wrote (block barrier: its global writes are visible to the whole block)
+        extern __shared__ unsigned char smem_dyn[];
+        __syncthreads();
+        schur_body(A, Bc, Cc, it, N2 / 2, schur_staged, smem_dyn);
+    }
 }
 
 // out (+)= X Y for h2 x h2 operands through shared memory: both operands are
@@ -1272,13 +1285,11 @@ __device__ __forceinline__ void smem_mm(T *out, int ldo, int mode, const T *X, i
 // Shared memory: 3 (N/2)^2 values (the product X and the staging buffer) when
 // staged, else (N/2)^2 (X only; operands read from global memory).
 template <typename T>
-__global__ void k_bcr_schur(T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc,
-                            const BcrItem *__restrict__ items, int N, int staged) {
-    extern __shared__ unsigned char smem_raw[];
+__device__ __forceinline__ void schur_body(T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc,
+                                           const BcrItem &it, int N, int staged, unsigned char *smem_raw) {
     const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
     T *X = reinterpret_cast<T *>(smem_raw);
     T *buf = staged ? X + hh : nullptr;
-    const BcrItem it = items[blockIdx.x];
     const T *Ai = A + (size_t)it.cell * n2 * n2;  // transposed inverse: Ainv[r][c] = Ai[c*n2 + r]
     const int Lm = 0, Lp = h2, Rm = N, Rp = N + h2;
     const T *Bi = Bc + (size_t)it.s_cell * hh;
@@ -1305,6 +1316,13 @@ __global__ void k_bcr_schur(T *__restrict__ A, T *__restrict__ Bc, T *__restrict
             for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) Cn[idx] = T(0);
         }
     }
+}
+
+template <typename T>
+__global__ void k_bcr_schur(T *__restrict__ A, T *__restrict__ Bc, T *__restrict__ Cc,
+                            const BcrItem *__restrict__ items, int N, int staged) {
+    extern __shared__ unsigned char smem_raw[];
+    schur_body(A, Bc, Cc, items[blockIdx.x], N, staged, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -1512,7 +1530,7 @@ __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, cons
 // Dataflow synchronisation of the BCR solve units (k_bcr_solve_flow): a unit waits
 // until the counters it depends on reach their targets (thread 0 polls with acquire
 // loads, at most kFlowSpinLimit times, then records *err = 1 and goes on), and after
-// its writes (every thread fences, block barrier) bumps the counters of the units
+// its writes (block barrier, then thread 0 fences) bumps the counters of the units
 // that depend on it. NULL pointers are absent waits / signals.
 constexpr unsigned kFlowSpinLimit = 1u << 25;  // x >= 32 ns: about a second
 struct FlowSync {
@@ -1537,23 +1555,26 @@ __device__ __forceinline__ void flow_wait(const FlowSync *fs) {
             const int want = k ? fs->want1 : fs->want0;
             if (!c) continue;
             unsigned spins = 0;
-            while (ld_acquire_gpu(c) < want) {
+            while (ld_acquire_gpu(c) < want) {  // busy first, then with short sleeps
                 if (++spins > kFlowSpinLimit) {
                     atomicExch(fs->err, 1);
                     break;
                 }
-                __nanosleep(32);
+                if (spins > 256) __nanosleep(32);
             }
         }
     }
     __syncthreads();
 }
 
+// The block barrier orders every thread's earlier writes before thread 0's fence,
+// which then orders them before the counter bumps (the pattern of a cooperative
+// grid barrier's arrival).
 __device__ __forceinline__ void flow_signal(const FlowSync *fs) {
     if (!fs) return;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         if (fs->sig0) atomicAdd(fs->sig0, 1);
         if (fs->sig1) atomicAdd(fs->sig1, 1);
         if (fs->sig2) atomicAdd(fs->sig2, 1);
