@@ -377,15 +377,33 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
     const int ncols = 2 * ncell;
     const size_t colbase = ((size_t)r * sumK + g0) * 2;
     const double *psr = psi + (size_t)r * sumK * 2 * N;  // this rhs
-    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) Xs[idx] = psi[colbase * N + idx];
+    // Both contractions use the mirror symmetry of the S_N set (mu_{N-1-n} = -mu_n,
+    // equal weights, P_l(-mu) = (-1)^l P_l(mu), exact in the tables): half the FP64
+    // multiply-adds of the plain products, same values up to rounding order.
+    //   phi_l = sum_{n < N/2} D[l][n] (psi_n + (-1)^l psi_{N-1-n})
+    //   q_n, q_{N-1-n} = E_n +- O_n,  E_n / O_n = sum over even / odd l of M[n][l] x_l
+    const int h2 = N / 2;
+    for (int idx = threadIdx.x; idx < ncols * h2; idx += blockDim.x) {
+        const int c = idx / h2, n = idx - c * h2;
+        const double a = psi[(colbase + c) * N + n], bm = psi[(colbase + c) * N + (N - 1 - n)];
+        Ys[c * N + n] = a + bm;        // even part
+        Ys[c * N + h2 + n] = a - bm;   // odd part
+    }
     __syncthreads();
-    block_contract(Xs, N, DT, N, ncols, Ys, N);
+    for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
+        const int c = idx / N, l = idx - c * N;
+        const double *f = Ys + c * N + ((l & 1) ? h2 : 0);
+        double acc = 0.0;
+#pragma unroll 8
+        for (int n = 0; n < h2; ++n) acc = fma(DT[(size_t)n * N + l], f[n], acc);
+        Xs[idx] = acc;
+    }
     __syncthreads();
     for (int idx = threadIdx.x; idx < ncols * N; idx += blockDim.x) {
         const int c = idx / N, l = idx - c * N;
         const int g = g0 + c / 2;
         const size_t e = colbase * N + idx;
-        const double pn = Ys[idx];
+        const double pn = Xs[idx];
         if (l == 0) {
             const int slot = (r * B + cell_inst[g]) * 2;
             atomicMax(conv + slot, dkey(pn - phi[e]));
@@ -395,7 +413,19 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
         Xs[idx] = sigma_s[(size_t)g * N + l] * pn + (Qext ? Qext[e] : 0.0);
     }
     __syncthreads();
-    block_contract(Xs, N, MT, N, ncols, Ys, N, Qang ? Qang + colbase * N : nullptr);
+    for (int idx = threadIdx.x; idx < ncols * h2; idx += blockDim.x) {
+        const int c = idx / h2, n = idx - c * h2;
+        const double *x = Xs + c * N;
+        double ev = 0.0, od = 0.0;
+#pragma unroll 4
+        for (int l = 0; l + 1 < N; l += 2) {
+            ev = fma(MT[(size_t)l * N + n], x[l], ev);
+            od = fma(MT[(size_t)(l + 1) * N + n], x[l + 1], od);
+        }
+        const double *qa = Qang ? Qang + (colbase + c) * N : nullptr;
+        Ys[c * N + n] = ev + od + (qa ? qa[n] : 0.0);
+        Ys[c * N + (N - 1 - n)] = ev - od + (qa ? qa[N - 1 - n] : 0.0);
+    }
     __syncthreads();
     for (int idx = threadIdx.x; idx < ncell * N; idx += blockDim.x) {
         const int cl = idx / N, n = idx - cl * N;
