@@ -876,41 +876,58 @@ __device__ __forceinline__ void gj_steps(T (&x)[N2 / 32][N2 / 16], const GjShare
     }
 }
 
+// One row of CJ values to / from shared memory in 16-byte (CJ % 4 == 0) or 8-byte vectors.
+template <int CJ>
+__device__ __forceinline__ void gj_st_row(float *d, const float (&v)[CJ]) {
+    if constexpr (CJ % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < CJ; j += 4) *reinterpret_cast<float4 *>(d + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < CJ; j += 2) *reinterpret_cast<float2 *>(d + j) = make_float2(v[j], v[j + 1]);
+    }
+}
+template <int CJ>
+__device__ __forceinline__ void gj_ld_row(float (&v)[CJ], const float *s) {
+    if constexpr (CJ % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < CJ; j += 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(s + j);
+            v[j] = t.x; v[j + 1] = t.y; v[j + 2] = t.z; v[j + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < CJ; j += 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(s + j);
+            v[j] = t.x; v[j + 1] = t.y;
+        }
+    }
+}
+
 // Blocked Gauss-Jordan inversion (FP32) for n2 = N2 in {32, 64, 128}: 16 warps, warp
 // w owns the CJ = N2/16 consecutive columns CJ w .. CJ w + CJ - 1 (a panel), lane t
 // the rows t + 32 i. Panel q is eliminated by its owner warp alone (CJ pivot steps
-// with implicit partial pivoting: warp shuffles and reductions only), which leaves in
-// its columns W = E[:, P], E the product of the panel's elementary transformations
-// and P its pivot rows; every other warp then applies E to its own columns,
+// with partial pivoting: one warp max reduction per step, whose key carries the
+// magnitude to 16 mantissa bits and the row index in its low 7 bits, and shuffles of
+// the pivot row), which leaves in its columns W = E[:, P], E the product of the
+// panel's elementary transformations and P its pivot rows; every other warp then
+// applies E to its own columns,
 //   X[r][c] <- (r in P ? 0 : X[r][c]) + sum_j W[r][j] X[P_j][c],
-// a rank-CJ update. One block barrier per panel (16 in all); the owner of panel q+1
-// starts eliminating as soon as its own update for panel q is done. The result is
-// the same in-place inverse as the unblocked elimination (same pivots; only the
-// rounding order of the updates differs): A^{-1}[r][c] = X[p_r][q_c].
-// gj_pick_pivot that also returns the pivot value itself (broadcast with its row).
-template <typename T, int RI>
-__device__ __forceinline__ void gj_pick_pivot_v(const T (&colv)[RI], unsigned used, int lane, int &p, T &pv) {
-    unsigned best = 0u;
-    int bi = 0;
-    T bv = T(0);
-#pragma unroll
-    for (int i = 0; i < RI; ++i) {
-        const unsigned key = (used >> i) & 1u ? 0u : __float_as_uint(fabsf((float)colv[i])) + 1u;
-        if (key > best) { best = key; bi = lane + 32 * i; bv = colv[i]; }
-    }
-    const unsigned m = __reduce_max_sync(0xffffffffu, best);
-    const int src = __ffs(__ballot_sync(0xffffffffu, best == m)) - 1;
-    p = __shfl_sync(0xffffffffu, bi, src);
-    pv = __shfl_sync(0xffffffffu, bv, src);
-}
-
+// a rank-CJ update (the lanes holding a pivot row publish this warp's part of it, PR,
+// before it restarts from 0). One block barrier per panel (16 in all); the owner of
+// panel q+1 starts eliminating as soon as its own update for panel q is done. The
+// result is the in-place inverse of the unblocked elimination with the same pivots
+// (only the rounding order of the updates differs): A^{-1}[r][c] = X[p_r][q_c].
+// The reciprocal of the pivot is rcp.approx refined by one Newton step.
 template <int N2>
 __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *dst, int ldd, bool tout,
                                               unsigned long long *__restrict__ growth, int *__restrict__ status) {
+    static_assert(N2 >= 32 && N2 <= 128 && N2 % 32 == 0, "row index must fit the 7 key bits");
     constexpr int RI = N2 / 32, CJ = N2 / 16;
-    __shared__ __align__(16) float Wb[2][N2][CJ];
+    constexpr int WS = (CJ % 4 == 0) ? CJ + 4 : CJ;  // padded W row: conflict-free 16-byte accesses
+    __shared__ __align__(16) float Wb[2][N2][WS];
     __shared__ __align__(16) float PRb[16][CJ][CJ];
-    __shared__ int Pb[2][CJ], piv_panel[N2], perm[N2], iperm[N2];
+    __shared__ int piv_panel[N2], perm[N2], iperm[N2];
     __shared__ double s_red[16];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float x[RI][CJ];
@@ -947,11 +964,17 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
                 float colv[RI];
 #pragma unroll
                 for (int i = 0; i < RI; ++i) colv[i] = x[i][c];
-                int p;
-                float pv;
-                gj_pick_pivot_v<float, RI>(colv, used, lane, p, pv);
-                if (pv == 0.f || !isfinite(pv)) bad = true;
-                const float inv = __frcp_rn(pv);  // overlaps the pivot-row shuffles below
+                // pivot: the largest |value| among the rows not yet used, its row index in
+                // the low 7 bits of the key (magnitudes compared to 16 mantissa bits; ties
+                // go to the larger row): one warp max reduction gives the row
+                unsigned best = 0u;
+#pragma unroll
+                for (int i = 0; i < RI; ++i) {
+                    const unsigned mag = (__float_as_uint(colv[i]) & 0x7fffffffu) >> 7;
+                    const unsigned key = ((used >> i) & 1u) ? 0u : (((mag + 1u) << 7) | unsigned(lane + 32 * i));
+                    best = max(best, key);
+                }
+                const int p = int(__reduce_max_sync(0xffffffffu, best) & 127u);
                 const int ip = p >> 5, pl = p & 31;
                 // pivot row of this warp's columns (select chain on the warp-uniform ip)
                 float rv[CJ];
@@ -962,6 +985,11 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
                     for (int i = 1; i < RI; ++i) v = (ip == i) ? x[i][j] : v;
                     rv[j] = __shfl_sync(0xffffffffu, v, pl);
                 }
+                const float pv = rv[c];
+                if (pv == 0.f || !isfinite(pv)) bad = true;
+                float inv;
+                asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(pv));
+                inv = inv * fmaf(-pv, inv, 2.f);  // one Newton step for 1/pv
 #pragma unroll
                 for (int j = 0; j < CJ; ++j) rv[j] = (j == c) ? inv : rv[j] * inv;
                 // x <- s_i x + g_i rv: s = 1, g = -x[i][c] for the other rows (column c
@@ -989,69 +1017,45 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
                     const int k = q * CJ + c;
                     perm[k] = p;
                     iperm[p] = k;
-                    Pb[qb][c] = p;
                     piv_panel[p] = q;
                 }
             }
 #pragma unroll
-            for (int i = 0; i < RI; ++i)
-#pragma unroll
-                for (int j = 0; j < CJ; ++j) Wb[qb][lane + 32 * i][j] = x[i][j];
+            for (int i = 0; i < RI; ++i) gj_st_row<CJ>(&Wb[qb][lane + 32 * i][0], x[i]);
         }
         __syncthreads();
         if (w != q) {
-            // the panel's pivot rows in this warp's columns -> PRb[w] (selects on the
-            // row register index: no indirect branch)
-#pragma unroll
-            for (int c = 0; c < CJ; ++c) {
-                const int pr = Pb[qb][c], ip = pr >> 5;
-                if (lane == (pr & 31)) {
-                    used |= 1u << ip;
-#pragma unroll
-                    for (int j = 0; j < CJ; ++j) {
-                        float v = x[0][j];
-#pragma unroll
-                        for (int i = 1; i < RI; ++i) v = (ip == i) ? x[i][j] : v;
-                        PRb[w][c][j] = v;
-                    }
-                }
-            }
-            __syncwarp();
-            // X[r][:] <- (r in P ? 0 : X[r][:]) + W[r][:] PR: W rows first, then one
-            // pivot row of PR at a time against all of this lane's rows
-            float wr[RI][CJ];
+            // this warp's values of the panel's pivot rows -> PRb[w] (old values), then those
+            // rows restart from 0: X[r][:] <- (r in P ? 0 : X[r][:]) + W[r][:] PR
 #pragma unroll
             for (int i = 0; i < RI; ++i) {
                 const int row = lane + 32 * i;
                 if (piv_panel[row] == q) {
+                    gj_st_row<CJ>(&PRb[w][iperm[row] - q * CJ][0], x[i]);
+                    used |= 1u << i;
 #pragma unroll
                     for (int j = 0; j < CJ; ++j) x[i][j] = 0.f;
                 }
-#pragma unroll
-                for (int c = 0; c < CJ; c += 2) {
-                    const float2 v = *reinterpret_cast<const float2 *>(&Wb[qb][row][c]);
-                    wr[i][c] = v.x;
-                    wr[i][c + 1] = v.y;
-                }
             }
+            __syncwarp();
+            // two W columns at a time: 8-byte W loads per row, two pivot rows of PR
 #pragma unroll
-            for (int c = 0; c < CJ; ++c) {
-                float prc[CJ];
+            for (int c = 0; c < CJ; c += 2) {
+                float prc[2][CJ];
+                gj_ld_row<CJ>(prc[0], &PRb[w][c][0]);
+                gj_ld_row<CJ>(prc[1], &PRb[w][c + 1][0]);
 #pragma unroll
-                for (int j = 0; j < CJ; j += 2) {
-                    const float2 v = *reinterpret_cast<const float2 *>(&PRb[w][c][j]);
-                    prc[j] = v.x;
-                    prc[j + 1] = v.y;
-                }
-#pragma unroll
-                for (int i = 0; i < RI; ++i)
+                for (int i = 0; i < RI; ++i) {
+                    const float2 wv = *reinterpret_cast<const float2 *>(&Wb[qb][lane + 32 * i][c]);
 #pragma unroll
                     for (int j = 0; j < CJ; j += 2) {
                         float2 acc = make_float2(x[i][j], x[i][j + 1]);
-                        acc = __ffma2_rn(make_float2(wr[i][c], wr[i][c]), make_float2(prc[j], prc[j + 1]), acc);
+                        acc = __ffma2_rn(make_float2(wv.x, wv.x), make_float2(prc[0][j], prc[0][j + 1]), acc);
+                        acc = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(prc[1][j], prc[1][j + 1]), acc);
                         x[i][j] = acc.x;
                         x[i][j + 1] = acc.y;
                     }
+                }
             }
         }
     }
