@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "fpsa_internal.h"
+#include "bulk_copy.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1783,13 +1784,16 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory staged variant of the dataflow BCR solve (used when one unit's
-// A^{-1} slice fits in kSolveStageBytes): a unit's slice [its columns][its rows] is
-// copied into shared memory by asynchronous 16-byte copies, and the copy for the
-// block's NEXT unit is issued as soon as the current unit's matrix-vector product
-// has read its slice, so the factor stream of a block is double-buffered by the
-// copy engine while the unit finishes (reduction, pushes, fence, counter bump) and
-// the next one waits for its inputs. No A^{-1} registers are held across units.
+// Shared-memory staged variant of the dataflow BCR solve (used when a cell's whole
+// A^{-1} fits in kSolveStageBytes): the columns a unit multiplies (one contiguous
+// block of the transposed inverse) and its two coupling blocks are copied into
+// shared memory by bulk asynchronous copies (the TMA engine: three instructions of
+// one thread instead of thousands of 16-byte copies, which backed up the load/store
+// path while the wide levels stream), and the copy for the block's NEXT unit is
+// issued as soon as the current unit's matrix-vector product has read its columns,
+// so a block's factor stream overlaps the unit's reduction, pushes, fence and
+// counter bump and the next unit's wait for its inputs. The coupling blocks are
+// double-buffered (the current unit multiplies by them after the next copy starts).
 // ---------------------------------------------------------------------------
 constexpr int kSolveStageBytes = 64 * 1024;
 
@@ -1798,32 +1802,69 @@ __host__ __device__ constexpr bool bcr_slice_staged(int N, int esize) {
 }
 
 // offset (in values) of the slice buffer: after the unit scratch, 16-byte aligned
+// (the staged-slice kernel double-buffers the coupling blocks: one more coupling area)
 template <typename T>
 __host__ __device__ constexpr int bcr_slice_offset_values(int N, int NT, int RC) {
-    return (bcr_unit_smem_values(N, NT, VecOf<T>::V, RC, (int)sizeof(T)) * (int)sizeof(T) + 15) / 16 * 16 /
-           (int)sizeof(T);
+    return ((bcr_unit_smem_values(N, NT, VecOf<T>::V, RC, (int)sizeof(T)) +
+             (bcr_couplings_staged(N, (int)sizeof(T)) ? bcr_coupling_values(N) : 0)) *
+                (int)sizeof(T) +
+            15) /
+           16 * 16 / (int)sizeof(T);
 }
 
-// Copy unit (it, sl, S, bwd)'s A^{-1} slice into As[k][row - row0] (k over the unit's
-// columns in matvec order), then commit one copy group. All threads.
-template <typename T, int NT>
-__device__ __forceinline__ void stage_slice(const T *__restrict__ A, const BcrItem &it, int sl, int S, bool bwd,
-                                            int N, T *As) {
-    const int n2 = 2 * N, h2 = N / 2, nr = n2 / S, row0 = sl * nr;
-    const int nk = bwd ? N : n2, q4 = nr * (int)sizeof(T) / 16;  // 16-byte chunks per column
-    const T *Ai = A + (size_t)it.cell * n2 * n2;
-    for (int idx = threadIdx.x; idx < nk * q4; idx += NT) {
-        const int k = idx / q4, q = idx - k * q4;
-        const int col = bwd ? (k < h2 ? h2 + k : N + (k - h2)) : k;
-        cp_async16(reinterpret_cast<unsigned char *>(As + (size_t)k * nr) + 16 * q,
-                   reinterpret_cast<const unsigned char *>(Ai + (size_t)col * n2 + row0) + 16 * q);
+// offset (in values) of the first coupling area in a solve block's scratch
+__host__ __device__ constexpr int bcr_cbuf_offset_values(int N, int NT, int V, int RC) {
+    return RC * (2 * N) + RC * (2 * N) + RC * N + NT * V * RC;
+}
+
+// The coupling blocks a unit multiplies (global memory; NULL where absent): forward
+// units push through B (right neighbour, from the slice holding R+) and C (left
+// neighbour, from the slice holding L-); backward units multiply the kept
+// neighbours' solutions by the cell's own B and C.
+template <typename T>
+__device__ __forceinline__ void unit_coupling_sources(const BcrItem &it, int sl, int S, bool bwd, int N,
+                                                      const T *Bc, const T *Cc, const T *&m0, const T *&m1) {
+    const int n2 = 2 * N, hh = (N / 2) * (N / 2), nr = n2 / S, row0 = sl * nr;
+    if (!bwd) {
+        m0 = (it.right >= 0 && row0 + nr == n2) ? Bc + (size_t)it.s_right * hh : nullptr;
+        m1 = (it.left >= 0 && row0 == 0) ? Cc + (size_t)it.s_left * hh : nullptr;
+    } else {
+        m0 = Bc + (size_t)it.s_cell * hh;
+        m1 = it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr;
     }
-    cp_async_commit();
 }
 
-// part[ks][rc][row] for this thread's (row group, k-slice) task, A^{-1} slice in smem.
+// Copy the columns of the transposed inverse that unit (it, bwd) multiplies into
+// As[k][row] (all 2N rows, k over the unit's columns in matvec order; forward: all
+// 2N columns, backward: columns N/2 .. 3N/2 - 1, one contiguous block either way)
+// and, with cb, its coupling blocks into cb[0, hh) and cb[hh, 2 hh), by bulk
+// asynchronous copies (the TMA engine) that complete one phase of *bar. A unit with
+// a row slice reads its rows of the block. Issued by one warp (the block's last:
+// thread 0, which fences the unit's signal, is not held up by the copies). Every
+// address and size is a multiple of 16 bytes (rows of 2N values of whole 16-byte
+// vectors; N/2 x N/2 coupling blocks staged only when whole 16-byte chunks).
+template <typename T>
+__device__ __forceinline__ void stage_unit_bulk(const T *__restrict__ A, const T *__restrict__ Bc,
+                                                const T *__restrict__ Cc, const BcrItem &it, int sl, int S, bool bwd,
+                                                int N, T *As, T *cb, uint64_t *bar) {
+    const int lane = threadIdx.x & 31;
+    const int n2 = 2 * N, h2 = N / 2, nk = bwd ? N : n2;
+    const T *m0 = nullptr, *m1 = nullptr;
+    if (cb) unit_coupling_sources(it, sl, S, bwd, N, Bc, Cc, m0, m1);
+    const uint32_t hb = (uint32_t)(h2 * h2 * sizeof(T)), sb = (uint32_t)((size_t)nk * n2 * sizeof(T));
+    tc::fence_async_smem();  // the buffers' earlier generic reads before the copies' writes
+    if (lane == 0) {
+        tc::mbar_arrive_expect_tx(bar, sb + (m0 ? hb : 0u) + (m1 ? hb : 0u));
+        if (m0) tc::bulk_copy_g2s(cb, m0, hb, bar);
+        if (m1) tc::bulk_copy_g2s(cb + h2 * h2, m1, hb, bar);
+        tc::bulk_copy_g2s(As, A + (size_t)it.cell * n2 * n2 + (bwd ? (size_t)h2 * n2 : 0), sb, bar);
+    }
+}
+
+// part[ks][rc][row] for this thread's (row group, k-slice) task: rows [0, nr) of the staged
+// A^{-1} columns As[k * lda + row] (shared memory).
 template <typename T, int NT, int RC>
-__device__ __forceinline__ int smem_matvec(const T *As, int nr, int nk, const T *coef, int cstride, T *part) {
+__device__ __forceinline__ int smem_matvec(const T *As, int lda, int nr, int nk, const T *coef, int cstride, T *part) {
     using VT = typename VecOf<T>::type;
     constexpr int V = VecOf<T>::V;
     const int RG = nr / V;
@@ -1842,7 +1883,7 @@ __device__ __forceinline__ int smem_matvec(const T *As, int nr, int nk, const T 
             for (int v = 0; v < V; ++v) acc[rc][v] = T(0);
 #pragma unroll 4
         for (int k = k0; k < k1; ++k) {
-            const VT a = *reinterpret_cast<const VT *>(As + (size_t)k * nr + rg * V);
+            const VT a = *reinterpret_cast<const VT *>(As + (size_t)k * lda + rg * V);
 #pragma unroll
             for (int rc = 0; rc < RC; ++rc) {
                 const T cv = coef[rc * cstride + k];
@@ -1862,33 +1903,26 @@ __device__ __forceinline__ int smem_matvec(const T *As, int nr, int nk, const T 
     return KS;
 }
 
-// Forward / backward unit with the A^{-1} slice already being copied into As (its
-// copy group committed before the unit's coupling group). next_copy() issues the
-// copy for the block's next unit (always commits a group).
-template <typename T, int NT, int RC, typename NextCopy>
-__device__ __forceinline__ void flow_fwd_unit_s(const T *__restrict__ Bc, const T *__restrict__ Cc,
-                                                const BcrItem &it, int r0, int nrc, int sl, int S, T *rhs, T *Y,
-                                                int N, int sumK, T *sm, const T *As, const FlowSync *fs,
-                                                NextCopy next_copy) {
-    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+// Forward / backward unit whose A^{-1} slice (into As) and coupling blocks (mB, mC:
+// shared-memory copies, or global memory when not staged; NULL where absent) are in
+// flight; wait_copies() returns once they have landed, next_copy() issues the copies
+// for the block's next unit.
+template <typename T, int NT, int RC, typename WaitCopies, typename NextCopy>
+__device__ __forceinline__ void flow_fwd_unit_s(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc,
+                                                int sl, int S, T *rhs, T *Y, int N, int sumK, T *sm, const T *As,
+                                                const FlowSync *fs, WaitCopies wait_copies, NextCopy next_copy) {
+    const int n2 = 2 * N, h2 = N / 2;
     T *rs = sm, *ys = sm + RC * n2, *part = ys + RC * n2 + RC * N;
-    T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
     const size_t rstride = (size_t)sumK * n2;
     const int nr = n2 / S, row0 = sl * nr;
-    const bool push_right = it.right >= 0 && row0 + nr == n2;
-    const bool push_left = it.left >= 0 && row0 == 0;
-    const T *mB = push_right ? Bc + (size_t)it.s_right * hh : nullptr;
-    const T *mC = push_left ? Cc + (size_t)it.s_left * hh : nullptr;
-    stage_couplings(mB, mC, cbuf, hh);
-    if (!cbuf) cp_async_commit();  // keep one coupling group per unit
     flow_wait(fs);
     for (int i = threadIdx.x; i < RC * n2; i += NT) {
         const int rc = i / n2, k = i - rc * n2;
         rs[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
     }
-    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's slice
+    wait_copies();
     __syncthreads();
-    const int KS = smem_matvec<T, NT, RC>(As, nr, n2, rs, n2, part);
+    const int KS = smem_matvec<T, NT, RC>(As + row0, n2, nr, n2, rs, n2, part);
     __syncthreads();
     next_copy();  // the slice buffer is free
     for (int idx = threadIdx.x; idx < RC * nr; idx += NT) {
@@ -1898,29 +1932,22 @@ __device__ __forceinline__ void flow_fwd_unit_s(const T *__restrict__ Bc, const 
         ys[rc * n2 + row0 + row] = y;
         if (rc < nrc) Y[(size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row] = y;
     }
-    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's couplings (the next slice may fly)
     __syncthreads();
-    coupling_products<T, NT, RC>(mB, ys + N + h2,
-                                 push_right ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr,
-                                 mC, ys, push_left ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr,
-                                 h2, n2, rstride, nrc);
+    coupling_products<T, NT, RC>(mB, ys + N + h2, mB ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr,
+                                 mC, ys, mC ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr, h2,
+                                 n2, rstride, nrc);
     flow_signal(fs);
     __syncthreads();
 }
 
-template <typename T, int NT, int RC, typename NextCopy>
-__device__ __forceinline__ void flow_bwd_unit_s(const T *__restrict__ Bc, const T *__restrict__ Cc,
-                                                const BcrItem &it, int r0, int nrc, int sl, int S, T *Y, int N,
-                                                int sumK, T *sm, const T *As, const FlowSync *fs,
-                                                NextCopy next_copy) {
-    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2;
+template <typename T, int NT, int RC, typename WaitCopies, typename NextCopy>
+__device__ __forceinline__ void flow_bwd_unit_s(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc,
+                                                int sl, int S, T *Y, int N, int sumK, T *sm, const T *As,
+                                                const FlowSync *fs, WaitCopies wait_copies, NextCopy next_copy) {
+    const int n2 = 2 * N, h2 = N / 2;
     T *gv = sm, *g = sm + RC * N, *part = sm + RC * (5 * N);
-    T *cbuf = bcr_couplings_staged(N, (int)sizeof(T)) ? part + NT * VecOf<T>::V * RC : nullptr;
     const size_t rstride = (size_t)sumK * n2;
     const int nr = n2 / S, row0 = sl * nr;
-    const T *mB = Bc + (size_t)it.s_cell * hh, *mC = it.right >= 0 ? Cc + (size_t)it.s_cell * hh : nullptr;
-    stage_couplings(mB, mC, cbuf, hh);
-    if (!cbuf) cp_async_commit();
     flow_wait(fs);
     for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
         const int rc = idx / N, k = idx - rc * N;
@@ -1932,13 +1959,13 @@ __device__ __forceinline__ void flow_bwd_unit_s(const T *__restrict__ Bc, const 
         }
         gv[idx] = v;
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");  // slice and couplings
+    wait_copies();
     __syncthreads();
     coupling_products<T, NT, RC>(mB, gv, g, mC, gv + h2, g + h2, h2, N, N);
     if (it.right < 0)
         for (int idx = threadIdx.x; idx < RC * h2; idx += NT) g[(idx / h2) * N + h2 + idx % h2] = T(0);
     __syncthreads();
-    const int KS = smem_matvec<T, NT, RC>(As, nr, N, g, N, part);
+    const int KS = smem_matvec<T, NT, RC>(As + row0, n2, nr, N, g, N, part);
     __syncthreads();
     next_copy();
     for (int idx = threadIdx.x; idx < nrc * nr; idx += NT) {
@@ -1960,8 +1987,18 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                                                             T *Y, int N, int sumK, int R, int *cnt, int *done,
                                                             int *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;  // one phase per unit: its slice and couplings landed
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *As = sm + bcr_slice_offset_values<T>(N, NT, RC);
+    // two coupling areas, alternating between the block's consecutive units (the next
+    // unit's couplings are requested with its slice while this unit still uses its own)
+    const int hh = (N / 2) * (N / 2);
+    T *cb0 = bcr_couplings_staged(N, (int)sizeof(T)) ? sm + bcr_cbuf_offset_values(N, NT, VecOf<T>::V, RC) : nullptr;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, P = 2 * nl;
     auto phase_level = [&](int ph) { return ph <= nl ? ph : 2 * nl - ph; };
     auto units = [&](int ph) {
@@ -1989,21 +2026,36 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
     };
     Pos cur{0, 0, 0, 0, 0, 0, 0, false};
     int gidx = blockIdx.x;
+    uint32_t parity = 0;  // phase of s_bar (and coupling area) of the current unit
+    bool stalled = false;
     locate(cur, gidx);
     BcrItem it_nx{};
     if (cur.valid) {
         it_nx = items[lv.off[cur.l] + cur.item];
-        stage_slice<T, NT>(A, it_nx, cur.sl, cur.S, cur.ph > nl, N, As);
+        if (threadIdx.x >= NT - 32) stage_unit_bulk<T>(A, Bc, Cc, it_nx, cur.sl, cur.S, cur.ph > nl, N, As, cb0, &s_bar);
     }
     while (cur.valid) {
         const BcrItem it = it_nx;
         Pos nxt = cur;
         locate(nxt, gidx + gridDim.x);
         if (nxt.valid) it_nx = items[lv.off[nxt.l] + nxt.item];  // arrives while this unit runs
-        auto next_copy = [&]() {
-            if (nxt.valid) stage_slice<T, NT>(A, it_nx, nxt.sl, nxt.S, nxt.ph > nl, N, As);
-            else cp_async_commit();
+        T *cb = cb0 ? cb0 + parity * 2 * hh : nullptr, *cb_next = cb0 ? cb0 + (parity ^ 1) * 2 * hh : nullptr;
+        auto wait_copies = [&]() {
+            // bounded; a block whose copies never land records the error and stops
+            // issuing (its remaining units are left to time out in their consumers)
+            stalled = __syncthreads_or(!tc::mbar_wait(&s_bar, parity)) != 0;
+            if (stalled && threadIdx.x == 0) atomicExch(err, 1);
         };
+        auto next_copy = [&]() {
+            if (nxt.valid && !stalled && threadIdx.x >= NT - 32)
+                stage_unit_bulk<T>(A, Bc, Cc, it_nx, nxt.sl, nxt.S, nxt.ph > nl, N, As, cb_next, &s_bar);
+        };
+        const T *mB, *mC;
+        unit_coupling_sources(it, cur.sl, cur.S, cur.ph > nl, N, Bc, Cc, mB, mC);
+        if (cb) {
+            mB = mB ? cb : nullptr;
+            mC = mC ? cb + hh : nullptr;
+        }
         const int S = cur.S, sl = cur.sl, ch = cur.ch;
         const int r0 = ch * RC, nrc = min(RC, R - r0);
         int *cnt_c = cnt + (size_t)ch * sumK, *done_c = done + (size_t)ch * sumK;
@@ -2021,7 +2073,8 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
             if (it.right >= 0 && row0 + nr == n2) fs.sig0 = cnt_c + it.right;
             if (it.left >= 0 && row0 == 0) fs.sig1 = cnt_c + it.left;
             if (it.left < 0) fs.sig2 = done_c + it.cell;
-            flow_fwd_unit_s<T, NT, RC>(Bc, Cc, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, &fs, next_copy);
+            flow_fwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, &fs, wait_copies,
+                                       next_copy);
         } else {
             const int step = 1 << it.level;
             fs.wait0 = done_c + it.left;
@@ -2031,12 +2084,18 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                 fs.want1 = lv.slices[bcr_cell_level(it.local + step, nl)];
             }
             fs.sig0 = done_c + it.cell;
-            flow_bwd_unit_s<T, NT, RC>(Bc, Cc, it, r0, nrc, sl, S, Y, N, sumK, sm, As, &fs, next_copy);
+            flow_bwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, Y, N, sumK, sm, As, &fs, wait_copies,
+                                       next_copy);
+        }
+        if (stalled) {
+            // no copy may still be landing when the block exits: wait once more (bounded)
+            tc::mbar_wait(&s_bar, parity);
+            break;
         }
         cur = nxt;
         gidx += gridDim.x;
+        parity ^= 1u;
     }
-    cp_async_wait_all();  // no copy in flight when the block exits
 }
 
 // ---------------------------------------------------------------------------
