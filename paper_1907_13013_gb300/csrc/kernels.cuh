@@ -1602,14 +1602,28 @@ __device__ __forceinline__ void flow_wait(const FlowSync *fs) {
     __syncthreads();
 }
 
-// The block barrier orders every thread's earlier writes before thread 0's fence,
-// which then orders them before the counter bumps (the pattern of a cooperative
-// grid barrier's arrival).
+// The block barrier orders every thread's earlier writes before the signalling
+// thread's fence, which then orders them before the counter bumps (the pattern of a
+// cooperative grid barrier's arrival). The staged-slice solve signals from a thread
+// outside warp 0 (thread 0 polls for the block's next unit meanwhile) with a
+// release fence paired with the consumers' acquire loads; its units end without a
+// second barrier (every read of the unit's scratch precedes the first one).
 __device__ __forceinline__ void flow_signal(const FlowSync *fs) {
     if (!fs) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
+        if (fs->sig0) atomicAdd(fs->sig0, 1);
+        if (fs->sig1) atomicAdd(fs->sig1, 1);
+        if (fs->sig2) atomicAdd(fs->sig2, 1);
+    }
+}
+
+__device__ __forceinline__ void flow_signal_release(const FlowSync *fs, int signaller) {
+    if (!fs) return;
+    __syncthreads();
+    if ((int)threadIdx.x == signaller) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (fs->sig0) atomicAdd(fs->sig0, 1);
         if (fs->sig1) atomicAdd(fs->sig1, 1);
         if (fs->sig2) atomicAdd(fs->sig2, 1);
@@ -1936,8 +1950,7 @@ __device__ __forceinline__ void flow_fwd_unit_s(const T *mB, const T *mC, const 
     coupling_products<T, NT, RC>(mB, ys + N + h2, mB ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr,
                                  mC, ys, mC ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr, h2,
                                  n2, rstride, nrc);
-    flow_signal(fs);
-    __syncthreads();
+    flow_signal_release(fs, NT - 64);  // warp NT/32 - 1 issues the copies
 }
 
 template <typename T, int NT, int RC, typename WaitCopies, typename NextCopy>
@@ -1974,8 +1987,7 @@ __device__ __forceinline__ void flow_bwd_unit_s(const T *mB, const T *mC, const 
         for (int q = 0; q < KS; ++q) sacc += part[(q * RC + rc) * nr + row];
         atomicAdd(Y + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row, -sacc);
     }
-    flow_signal(fs);
-    __syncthreads();
+    flow_signal_release(fs, NT - 64);  // warp NT/32 - 1 issues the copies
 }
 
 // The dataflow BCR solve with staged slices (same unit order, counters and waits as
@@ -1986,6 +1998,7 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                                                             const BcrItem *__restrict__ items, LevelTable lv, T *rhs,
                                                             T *Y, int N, int sumK, int R, int *cnt, int *done,
                                                             int *err) {
+    static_assert(NT >= 64 && NT % 32 == 0, "copies and signals leave warp 0 free");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;  // one phase per unit: its slice and couplings landed
     T *sm = reinterpret_cast<T *>(smem_raw);
