@@ -171,6 +171,34 @@ def fpsa_source_iteration(prob, laplacian="mpd", tol=1e-10, max_it=10000, phi0=N
     return out
 
 
+def fpsa_iteration_matrix(prob, laplacian="mpd"):
+    """Dense matrix G of one homogeneous FPSA iteration on the flux moments, phi -> phi'
+    (Eqs. predict, correct with zero source and zero incoming flux), columns in the
+    order of phi.ravel() ([cell][node][l]); small problems only (one iteration per
+    column). Its spectral radius is the asymptotic error reduction per iteration.
+    Pinned by: on a uniform slab with reflective edges it equals the angularly-discrete
+    Fourier analysis (oracle.fourier) at lambda = 0 exactly and, for a supremum at
+    lambda > 0, to third order in the cell width (tests/test_oracle_fourier.py).
+    """
+    N, L = prob["N"], prob["L"]
+    mu, w, D, M = tables(N, L)
+    K = prob["h"].size
+    Linv = _streaming_inverse(prob, mu)
+    F = spla.splu(fp_matrix(prob, mu, w, laplacian))
+    n = K * 2 * (L + 1)
+    G = np.zeros((n, n))
+    for j in range(n):
+        phi = np.zeros(n)
+        phi[j] = 1.0
+        phi = phi.reshape(K, 2, L + 1)
+        psi_half = Linv(scattering_source(M, prob["sigma_s"], phi), incident=False)
+        phi_half = moments(D, psi_half)
+        r = scattering_source(M, prob["sigma_s"], phi_half - phi)
+        ups = F.solve(tr.mass_weight(prob["h"], r).ravel()).reshape(K, 2, N)
+        G[:, j] = (phi_half + moments(D, ups)).ravel()
+    return G
+
+
 def direct_solve(prob, return_psi=False):
     """The discrete solution itself: (L_h - S_h) psi = m q + (incoming boundary fluxes) by
     sparse LU (the fixed point that SI and FPSA converge to; unique for sigma_a > 0)."""
