@@ -31,9 +31,11 @@ ordinates mu_n (Gauss-Legendre, ascending) is mapped by N x N complex matrices:
 Pinned by (tests/test_oracle_fourier.py): the SI closed form (eigenvalues of A(0)
 are the c_l, rho = c_0, Sec. 3.3 Step 1); the lambda = 0 FPSA-MPD closed form
 c_l - c_l (1 - c_l) / (sigma_a + sigma_tr l(l+1)/2); I_M = 0 at every lambda for
-P_L-equivalent moments with N = L + 1 (Eq. fsa_pl_eq); and the asymptotic error
-ratio of the oracle's own FPSA iteration on a thin-celled uniform slab with
-reflective edges, whose error modes are cos(lambda z) with lambda = k pi / Z.
+P_L-equivalent moments with N = L + 1 (Eq. fsa_pl_eq); and the spectral radius
+of the oracle's own discrete FPSA iteration matrix on uniform slabs with
+reflective edges, whose error modes are cos(lambda z) with lambda = k pi / Z
+(equal when the supremum is at lambda = 0, third-order in the cell width when it
+is not).
 The paper's Table 1 does not state its scattering ratio: with c = 0.9999 the HGK
 row (g = 0.9, N = 16, L = 15) is reproduced in both FA columns to the printed
 digits, which the tests pin; the SRK row comes within 2e-4 but no single c gives
