@@ -43,6 +43,7 @@ struct PathBuffers {
     T *qang = nullptr;                       // MIXED inner path: nodal residual source [R][sumK][2][N]
     T *ybuf = nullptr;                       // BCR solve: intermediate y, then the solution [R][sumK][2N]
     T *tot = nullptr;                        // reflective edges: whole-slab sweep maps [R][B][N][2]
+    T *G = nullptr;                          // coarse step of the BCR solve: inverse of the coarse system [n][n]
     // recursive block inversion (2N too large for one CTA): per-depth scratch X, Y
     std::vector<T *> inv_scratch;
     double *inv_amax = nullptr;
@@ -188,6 +189,51 @@ bool schur_staged(int N) { return (size_t)3 * (N / 2) * (N / 2) * sizeof(T) <= 2
 template <typename T>
 size_t schur_smem(int N) { return (size_t)(schur_staged<T>(N) ? 3 : 1) * (N / 2) * (N / 2) * sizeof(T); }
 
+// usable dynamic shared memory per CTA (227 KB opt-in, less room for static shared memory)
+constexpr size_t kSmemLimit = 227 * 1024 - 1024;
+
+// columns of the coarse inverse per block of k_bcr_coarse_inverse, and its shared memory
+constexpr int kCoarseCols = 16;
+size_t coarse_inverse_smem_bytes(int N, int m, int esize) {
+    return esize == 8 ? coarse_inverse_values<double>(N, m, kCoarseCols) * 8 : coarse_inverse_values<float>(N, m, kCoarseCols) * 4;
+}
+template <typename T>
+size_t coarse_inverse_smem(int N, const LevelTable &lv) {
+    return coarse_inverse_values<T>(N, lv.coarse_m, kCoarseCols) * sizeof(T);
+}
+
+// Coarse step of the staged BCR solve (one instance, one right-hand side): the
+// lowest level c whose coarse cells (local index a multiple of 2^c) number at most
+// N/4 (so that their right-hand sides fit a coupling area), when at least two
+// reduction levels lie above it; G rows per unit: the largest power of two dividing
+// 2N whose rows fit the staged solve's column buffer ((2N)^2 values). Sets
+// coarse_level = -1 otherwise.
+void plan_coarse(LevelTable &lv, const Geometry &g, int esize) {
+    lv.coarse_level = -1;
+    lv.coarse_m = lv.coarse_K = lv.coarse_rpu = lv.coarse_units = 0;
+    const int N = g.N, n2 = 2 * N, K = g.B == 1 ? g.sumK : 0;
+    if (g.B != 1 || g.R != 1 || !bcr_slice_staged(N, esize) || !bcr_couplings_staged(N, esize)) return;
+    if (n2 > 256 / (kCoarseCols / 8)) return;
+    for (int c = 1; c + 2 <= g.n_levels; ++c) {
+        const int m = (K + (1 << c) - 1) >> c;
+        if (m > N / 4) continue;
+        const int n = m * n2;
+        if (n % kCoarseCols) return;
+        // G rows of a unit land in the column buffer of the staged solve: (2N)^2 values
+        const size_t buf = (size_t)n2 * n2 * esize;
+        int rpu = 1;
+        while (rpu * 2 <= n2 && n2 % (rpu * 2) == 0 && (size_t)rpu * 2 * n * esize <= buf) rpu *= 2;
+        if ((size_t)rpu * n * esize > buf) return;
+        if (coarse_inverse_smem_bytes(N, m, esize) > kSmemLimit) return;
+        lv.coarse_level = c;
+        lv.coarse_m = m;
+        lv.coarse_K = K;
+        lv.coarse_rpu = rpu;
+        lv.coarse_units = n / rpu;
+        return;
+    }
+}
+
 // right-hand sides per BCR solve unit
 int solve_rc(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
 
@@ -227,8 +273,6 @@ size_t invert_smem(int N) {
 
 // full: every buffer of an FPSA iteration in precision T. Otherwise only the tables,
 // cross sections, sources and the psi / phi state (the FP64 side of MIXED).
-// usable dynamic shared memory per CTA (227 KB opt-in, less room for static shared memory)
-constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 
 // Does one CTA invert an n x n block directly (registers for n in {32, 64, 128},
 // else shared memory)? (Routing 128 x 128 FP32 blocks through one block-Schur
@@ -259,6 +303,12 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         CK(dalloc(ctx, &p.rhs, ang));
         CK(dalloc(ctx, &p.ybuf, ang));
         if (ctx->d_bc) CK(dalloc(ctx, &p.tot, (size_t)g.R * g.B * N * 2));
+        const LevelTable &lvp = ctx->lvt[sizeof(T) == 8 ? 1 : 0];
+        if (lvp.coarse_level >= 0) {
+            const size_t n = (size_t)lvp.coarse_m * 2 * N;
+            CK(dalloc(ctx, &p.G, n * n));
+            CK(raise_smem_limit((const void *)k_bcr_coarse_inverse<T, kCoarseCols>, (int)coarse_inverse_smem<T>(g.N, lvp)));
+        }
         // scratch of the recursive block inversion: X and Y per recursion depth
         for (int n = 2 * g.N; !cta_invertible<T>(n); n /= 2) {
             T *s = nullptr;
@@ -460,6 +510,14 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         if (rc) return rc;
     }
     CK(cudaGetLastError());
+    if (p.G) {
+        const LevelTable &lv = ctx->lvt[sizeof(T) == 8 ? 1 : 0];
+        const int n = lv.coarse_m * 2 * N;
+        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+        k_bcr_coarse_inverse<T, kCoarseCols><<<n / kCoarseCols, 256, coarse_inverse_smem<T>(N, lv), st>>>(
+            p.A, p.Bc, p.Cc, ctx->d_items_all, lv, N, p.G, ctx->d_dev_err);
+        CK(cudaGetLastError());
+    }
     return FPSA_OK;
 }
 
@@ -495,8 +553,9 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     const T *A = p.A, *Bc = p.Bc, *Cc = p.Cc;
     T *Y = p.ybuf;
     int *cnt = ctx->d_flow_cnt, *done = ctx->d_flow_done, *err = ctx->d_dev_err;
-    void *args[] = {(void *)&A, (void *)&Bc, (void *)&Cc, (void *)&items, (void *)&lv, (void *)&rhs,
-                    (void *)&Y, (void *)&N, (void *)&sumK, (void *)&R, (void *)&cnt, (void *)&done, (void *)&err};
+    const T *G = p.G;
+    void *args[] = {(void *)&A, (void *)&Bc, (void *)&Cc, (void *)&items, (void *)&lv,   (void *)&rhs, (void *)&Y,
+                    (void *)&N, (void *)&sumK, (void *)&R,     (void *)&cnt, (void *)&done, (void *)&err, (void *)&G};
     const int grid = ctx->coop_grid[sizeof(T) == 8 ? 1 : 0];
     const int RC = solve_rc(R);
     const size_t ncnt = (size_t)((R + RC - 1) / RC) * sumK * sizeof(int);
@@ -1255,6 +1314,7 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
                 LevelTable &lv = ctx->lvt[e];
                 lv.n_levels = g.n_levels;
                 lv.n_roots = g.B;
+                plan_coarse(lv, g, e ? (int)sizeof(double) : (int)sizeof(float));
                 int off = 0;
                 for (int l = 0; l <= g.n_levels; ++l) {
                     const int items = l < g.n_levels ? (int)g.levels[l].size() : g.B;
@@ -1310,6 +1370,7 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     CK(cudaMemsetAsync(ctx->d_xs_err + 1, 0, sizeof(int), s));
     CK(cudaMemsetAsync(ctx->d_growth, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), s));
     const bool mixed = ctx->precision == FPSA_PRECISION_MIXED;
     {
         Launch L_(ctx, FPSA_PHASE_ASSEMBLE);
@@ -1331,10 +1392,12 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     int rc = mixed ? setup_path(ctx, ctx->p32, true) : setup_path(ctx, ctx->p64, true);
     if (rc) return rc;
     unsigned long long growth = 0;
-    int status = 0;
+    int status = 0, dev_err = 0;
     CK(cudaMemcpyAsync(&growth, ctx->d_growth, sizeof(growth), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(status), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&dev_err, ctx->d_dev_err, sizeof(dev_err), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (dev_err) return fail(ctx, FPSA_ETIMEOUT, "a bounded device wait of the factorization ran out");
     double gr;
     std::memcpy(&gr, &growth, sizeof(gr));
     ctx->pivot_growth = gr;

@@ -1721,10 +1721,17 @@ __device__ __forceinline__ void bcr_bwd_unit(const T *__restrict__ A, const T *_
 // level l owns items [off[l], off[l+1]); roots follow at [off[n_levels], off[n_levels] + n_roots).
 // slices[l] = row slices per item at level l (index n_levels: the roots).
 constexpr int kMaxLevels = 32;
+// Coarse step (staged-slice solve of a single instance and right-hand side only):
+// with coarse_level = c >= 0 the levels c .. n_levels - 1 and the root are replaced
+// by u_c = G r_c, G the inverse of the block-tridiagonal system that the reduction
+// leaves on the coarse cells (local index a multiple of 2^c, coarse_m of them,
+// coarse_K cells in the instance), computed once per factorization. G rows are
+// taken coarse_rpu at a time by coarse_units units. coarse_level = -1: no coarse step.
 struct LevelTable {
     int32_t off[kMaxLevels + 2];
     int32_t slices[kMaxLevels + 2];
     int32_t n_levels, n_roots;
+    int32_t coarse_level, coarse_m, coarse_K, coarse_rpu, coarse_units;
 };
 
 // The BCR solve as a dataflow over all units in one cooperative launch, without
@@ -1746,7 +1753,8 @@ template <typename T, int NT, int RC>
 __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ A, const T *__restrict__ Bc,
                                                        const T *__restrict__ Cc, const BcrItem *__restrict__ items,
                                                        LevelTable lv, T *rhs, T *Y, int N, int sumK, int R, int *cnt,
-                                                       int *done, int *err) {
+                                                       int *done, int *err,
+                                                       const T *__restrict__ G = nullptr /* coarse step: staged only */) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, P = 2 * nl;
@@ -1990,14 +1998,64 @@ __device__ __forceinline__ void flow_bwd_unit_s(const T *mB, const T *mC, const 
     flow_signal_release(fs, NT - 64);  // warp NT/32 - 1 issues the copies
 }
 
+// The coarse unit u: rows [u rpu, (u + 1) rpu) of u_c = G r_c (G rows staged in As by
+// the unit's bulk copy; r_c, the right-hand sides of the m coarse cells in coarse
+// order, gathered into rc) once every coarse cell has received the pushes of the
+// levels below c; the rows are written to Y and the cell's completion counter bumped.
+template <typename T, int NT, typename WaitCopies, typename NextCopy>
+__device__ __forceinline__ void flow_coarse_unit(int u, const LevelTable &lv, const T *rhs, T *Y, int N, T *rc,
+                                                 const T *As, int *cnt, int *done, int *err,
+                                                 WaitCopies wait_copies, NextCopy next_copy) {
+    const int n2 = 2 * N, cl = lv.coarse_level, m = lv.coarse_m, n = m * n2, rpu = lv.coarse_rpu;
+    if ((int)threadIdx.x < m) {  // one poller per coarse cell
+        const int a = (int)threadIdx.x << cl;
+        int want = 0;
+        for (int lp = 0; lp < cl; ++lp) want += (a >= (1 << lp)) + (a + (1 << lp) < lv.coarse_K);
+        unsigned spins = 0;
+        while (want && ld_acquire_gpu(cnt + a) < want) {
+            if (++spins > kFlowSpinLimit) {
+                atomicExch(err, 1);
+                break;
+            }
+            if (spins > 256) __nanosleep(32);
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n; idx += NT) {
+        const int j = idx / n2;
+        rc[idx] = __ldcg(rhs + (size_t)(j << cl) * n2 + (idx - j * n2));
+    }
+    wait_copies();
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int rr = threadIdx.x >> 5; rr < rpu; rr += NT / 32) {
+        const T *g = As + (size_t)rr * n;
+        T acc = T(0);
+        for (int col = lane; col < n; col += 32) acc = fma(g[col], rc[col], acc);
+        acc = group_sum(acc, 32);
+        if (lane == 0) {
+            const int row = u * rpu + rr, j = row / n2;
+            Y[(size_t)(j << cl) * n2 + (row - j * n2)] = acc;
+        }
+    }
+    __syncthreads();
+    next_copy();
+    FlowSync fs{};
+    fs.err = err;
+    fs.sig0 = done + (((u * rpu) / n2) << cl);
+    flow_signal_release(&fs, NT - 64);
+}
+
 // The dataflow BCR solve with staged slices (same unit order, counters and waits as
-// k_bcr_solve_flow). Shared memory: the unit scratch, then the slice buffer.
+// k_bcr_solve_flow; with a coarse step, the levels from coarse_level up and the
+// root are one phase of coarse units between the forward and backward levels below
+// it). Shared memory: the unit scratch, then the slice buffer.
 template <typename T, int NT, int RC>
 __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict__ A, const T *__restrict__ Bc,
                                                             const T *__restrict__ Cc,
                                                             const BcrItem *__restrict__ items, LevelTable lv, T *rhs,
                                                             T *Y, int N, int sumK, int R, int *cnt, int *done,
-                                                            int *err) {
+                                                            int *err, const T *__restrict__ G) {
     static_assert(NT >= 64 && NT % 32 == 0, "copies and signals leave warp 0 free");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;  // one phase per unit: its slice and couplings landed
@@ -2012,13 +2070,22 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, P = 2 * nl;
-    auto phase_level = [&](int ph) { return ph <= nl ? ph : 2 * nl - ph; };
+    const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, cl = lv.coarse_level;
+    const int P = cl >= 0 ? 2 * cl : 2 * nl;
+    // level of a phase (-1: the coarse phase) and whether it is a backward phase
+    auto phase_level = [&](int ph) {
+        if (cl >= 0) return ph < cl ? ph : (ph == cl ? -1 : 2 * cl - ph);
+        return ph <= nl ? ph : 2 * nl - ph;
+    };
+    auto phase_bwd = [&](int ph) { return cl >= 0 ? ph > cl : ph > nl; };
     auto units = [&](int ph) {
         const int l = phase_level(ph);
+        if (l < 0) return lv.coarse_units;
         const int nitems = (l < nl) ? lv.off[l + 1] - lv.off[l] : lv.n_roots;
         return nitems * nchunk * lv.slices[l];
     };
+    // units that complete a cell of the given level (its row slices, or the coarse units over its rows)
+    auto done_want = [&](int level) { return (cl >= 0 && level >= cl) ? 2 * N / lv.coarse_rpu : lv.slices[level]; };
     struct Pos {
         int ph, start, l, S, sl, ch, item;
         bool valid;
@@ -2031,11 +2098,32 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
         q.valid = q.ph <= P;
         if (!q.valid) return;
         q.l = phase_level(q.ph);
-        q.S = lv.slices[q.l];
         const int w = gidx - q.start;
+        if (q.l < 0) {  // coarse unit w
+            q.S = 1;
+            q.sl = 0;
+            q.ch = 0;
+            q.item = w;
+            return;
+        }
+        q.S = lv.slices[q.l];
         q.sl = w % q.S;
         q.ch = (w / q.S) % nchunk;
         q.item = w / (q.S * nchunk);
+    };
+    // a unit's copies: its A^{-1} columns and couplings, or a coarse unit's rows of G
+    auto stage = [&](const Pos &q, const BcrItem &itq, T *cbq) {
+        if (q.l < 0) {
+            const int n = lv.coarse_m * 2 * N, rpu = lv.coarse_rpu;
+            tc::fence_async_smem();
+            if ((threadIdx.x & 31) == 0) {
+                const uint32_t bytes = (uint32_t)((size_t)rpu * n * sizeof(T));
+                tc::mbar_arrive_expect_tx(&s_bar, bytes);
+                tc::bulk_copy_g2s(As, G + (size_t)q.item * rpu * n, bytes, &s_bar);
+            }
+        } else {
+            stage_unit_bulk<T>(A, Bc, Cc, itq, q.sl, q.S, phase_bwd(q.ph), N, As, cbq, &s_bar);
+        }
     };
     Pos cur{0, 0, 0, 0, 0, 0, 0, false};
     int gidx = blockIdx.x;
@@ -2044,14 +2132,14 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
     locate(cur, gidx);
     BcrItem it_nx{};
     if (cur.valid) {
-        it_nx = items[lv.off[cur.l] + cur.item];
-        if (threadIdx.x >= NT - 32) stage_unit_bulk<T>(A, Bc, Cc, it_nx, cur.sl, cur.S, cur.ph > nl, N, As, cb0, &s_bar);
+        if (cur.l >= 0) it_nx = items[lv.off[cur.l] + cur.item];
+        if (threadIdx.x >= NT - 32) stage(cur, it_nx, cb0);
     }
     while (cur.valid) {
         const BcrItem it = it_nx;
         Pos nxt = cur;
         locate(nxt, gidx + gridDim.x);
-        if (nxt.valid) it_nx = items[lv.off[nxt.l] + nxt.item];  // arrives while this unit runs
+        if (nxt.valid && nxt.l >= 0) it_nx = items[lv.off[nxt.l] + nxt.item];  // arrives while this unit runs
         T *cb = cb0 ? cb0 + parity * 2 * hh : nullptr, *cb_next = cb0 ? cb0 + (parity ^ 1) * 2 * hh : nullptr;
         auto wait_copies = [&]() {
             // bounded; a block whose copies never land records the error and stops
@@ -2060,45 +2148,50 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
             if (stalled && threadIdx.x == 0) atomicExch(err, 1);
         };
         auto next_copy = [&]() {
-            if (nxt.valid && !stalled && threadIdx.x >= NT - 32)
-                stage_unit_bulk<T>(A, Bc, Cc, it_nx, nxt.sl, nxt.S, nxt.ph > nl, N, As, cb_next, &s_bar);
+            if (nxt.valid && !stalled && threadIdx.x >= NT - 32) stage(nxt, it_nx, cb_next);
         };
-        const T *mB, *mC;
-        unit_coupling_sources(it, cur.sl, cur.S, cur.ph > nl, N, Bc, Cc, mB, mC);
-        if (cb) {
-            mB = mB ? cb : nullptr;
-            mC = mC ? cb + hh : nullptr;
-        }
-        const int S = cur.S, sl = cur.sl, ch = cur.ch;
-        const int r0 = ch * RC, nrc = min(RC, R - r0);
-        int *cnt_c = cnt + (size_t)ch * sumK, *done_c = done + (size_t)ch * sumK;
-        const int n2 = 2 * N, nr = n2 / S, row0 = sl * nr;
-        FlowSync fs{};
-        fs.err = err;
-        if (cur.ph <= nl) {
-            int want = 0;
-            for (int lp = 0; lp < it.level; ++lp)
-                want += (it.local >= (1 << lp)) + (it.local + (1 << lp) < it.K_inst);
-            if (want) {
-                fs.wait0 = cnt_c + it.cell;
-                fs.want0 = want;
-            }
-            if (it.right >= 0 && row0 + nr == n2) fs.sig0 = cnt_c + it.right;
-            if (it.left >= 0 && row0 == 0) fs.sig1 = cnt_c + it.left;
-            if (it.left < 0) fs.sig2 = done_c + it.cell;
-            flow_fwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, &fs, wait_copies,
-                                       next_copy);
+        if (cur.l < 0) {
+            // the coarse area of this unit's parity holds r_c (coarse units take no couplings)
+            flow_coarse_unit<T, NT>(cur.item, lv, rhs, Y, N, cb, As, cnt, done, err, wait_copies, next_copy);
         } else {
-            const int step = 1 << it.level;
-            fs.wait0 = done_c + it.left;
-            fs.want0 = lv.slices[bcr_cell_level(it.local - step, nl)];
-            if (it.right >= 0) {
-                fs.wait1 = done_c + it.right;
-                fs.want1 = lv.slices[bcr_cell_level(it.local + step, nl)];
+            const bool bwd = phase_bwd(cur.ph);
+            const T *mB, *mC;
+            unit_coupling_sources(it, cur.sl, cur.S, bwd, N, Bc, Cc, mB, mC);
+            if (cb) {
+                mB = mB ? cb : nullptr;
+                mC = mC ? cb + hh : nullptr;
             }
-            fs.sig0 = done_c + it.cell;
-            flow_bwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, Y, N, sumK, sm, As, &fs, wait_copies,
-                                       next_copy);
+            const int S = cur.S, sl = cur.sl, ch = cur.ch;
+            const int r0 = ch * RC, nrc = min(RC, R - r0);
+            int *cnt_c = cnt + (size_t)ch * sumK, *done_c = done + (size_t)ch * sumK;
+            const int n2 = 2 * N, nr = n2 / S, row0 = sl * nr;
+            FlowSync fs{};
+            fs.err = err;
+            if (!bwd) {
+                int want = 0;
+                for (int lp = 0; lp < it.level; ++lp)
+                    want += (it.local >= (1 << lp)) + (it.local + (1 << lp) < it.K_inst);
+                if (want) {
+                    fs.wait0 = cnt_c + it.cell;
+                    fs.want0 = want;
+                }
+                if (it.right >= 0 && row0 + nr == n2) fs.sig0 = cnt_c + it.right;
+                if (it.left >= 0 && row0 == 0) fs.sig1 = cnt_c + it.left;
+                if (it.left < 0) fs.sig2 = done_c + it.cell;
+                flow_fwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, &fs, wait_copies,
+                                           next_copy);
+            } else {
+                const int step = 1 << it.level;
+                fs.wait0 = done_c + it.left;
+                fs.want0 = done_want(bcr_cell_level(it.local - step, nl));
+                if (it.right >= 0) {
+                    fs.wait1 = done_c + it.right;
+                    fs.want1 = done_want(bcr_cell_level(it.local + step, nl));
+                }
+                fs.sig0 = done_c + it.cell;
+                flow_bwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, Y, N, sumK, sm, As, &fs, wait_copies,
+                                           next_copy);
+            }
         }
         if (stalled) {
             // no copy may still be landing when the block exits: wait once more (bounded)
@@ -2108,6 +2201,157 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
         cur = nxt;
         gidx += gridDim.x;
         parity ^= 1u;
+    }
+}
+
+// The inverse G of the coarse system (coarse_level c >= 0, one instance): the
+// reduction's levels c .. n_levels - 1 and its root applied to the identity on the
+// coarse cells' unknowns. Block b solves for the columns [b CB, (b + 1) CB): X (all
+// coarse cells' 2N rows x CB columns, shared memory) starts as those identity
+// columns; forward, each item of levels c .. up to the root replaces its X block by
+// A^{-1} X and (below the root) pushes -B X[R+] into its right neighbour's L+ rows and
+// -C X[L-] into its left neighbour's R- rows; backward, from the top level down, each
+// item subtracts A^{-1}[:, L+ u R-] [B u_left[R+]; C u_right[L-]]. X then holds the
+// columns of G (row-major, rows and columns in coarse order: cell-major, 2N per cell).
+// Blocks that are still zero are skipped (forward, only the identity's cell and the
+// cells it pushes into carry data). Each operation's A^{-1} columns and coupling
+// blocks arrive in shared memory by bulk asynchronous copies (bounded waits; a block
+// whose copies do not land records *err = 1 and stops).
+template <typename T>
+__host__ __device__ constexpr size_t coarse_inverse_values(int N, int m, int CB) {
+    // X, g, A^{-1} columns, two coupling blocks (each area a whole number of 16-byte chunks)
+    return ((size_t)m * 2 * N * CB + (size_t)N * CB + (size_t)4 * N * N + (size_t)2 * (N / 2) * (N / 2) +
+            3 * 16 / sizeof(T));
+}
+
+template <typename T, int CB>
+__global__ void __launch_bounds__(256) k_bcr_coarse_inverse(const T *__restrict__ A, const T *__restrict__ Bc,
+                                                            const T *__restrict__ Cc,
+                                                            const BcrItem *__restrict__ items, LevelTable lv, int N,
+                                                            T *__restrict__ G, int *err) {
+    static_assert(CB % 8 == 0, "8 columns per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    const int n2 = 2 * N, h2 = N / 2, hh = h2 * h2, cl = lv.coarse_level, nl = lv.n_levels;
+    const int m = lv.coarse_m, n = m * n2, j0 = blockIdx.x * CB;
+    auto align16 = [](size_t v) { return (v * sizeof(T) + 15) / 16 * 16 / sizeof(T); };
+    T *X = reinterpret_cast<T *>(smem_raw);  // [m][n2][CB]
+    T *gs = X + align16((size_t)m * n2 * CB);  // [N][CB]
+    T *F = gs + align16((size_t)N * CB);      // A^{-1} columns [k][n2]
+    T *Cp = F + align16((size_t)n2 * n2);     // two coupling blocks [2][h2][h2]
+    for (int idx = threadIdx.x; idx < n * CB; idx += blockDim.x) {
+        const int row = idx / CB, col = idx - row * CB;
+        X[idx] = (row == j0 + col) ? T(1) : T(0);
+    }
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // coarse cells holding nonzero data: bit j of nz (at most 64 coarse cells per word)
+    unsigned long long nz[4] = {0ull, 0ull, 0ull, 0ull};
+    auto get_nz = [&](int j) { return (nz[j >> 6] >> (j & 63)) & 1ull; };
+    auto set_nz = [&](int j) { nz[j >> 6] |= 1ull << (j & 63); };
+    for (int j = j0 / n2; j <= (j0 + CB - 1) / n2; ++j) set_nz(j);
+    uint32_t parity = 0;
+    bool ok = true;
+    // copy A^{-1} columns [k0, k0 + nk) of cell and the coupling blocks m0, m1 (NULL: absent), then wait
+    auto fetch = [&](int cell, int k0, int nk, const T *m0, const T *m1) {
+        if (threadIdx.x == 0) {
+            const uint32_t fb = (uint32_t)((size_t)nk * n2 * sizeof(T)), hb = (uint32_t)(hh * sizeof(T));
+            tc::fence_async_smem();
+            tc::mbar_arrive_expect_tx(&s_bar, fb + (m0 ? hb : 0u) + (m1 ? hb : 0u));
+            tc::bulk_copy_g2s(F, A + (size_t)cell * n2 * n2 + (size_t)k0 * n2, fb, &s_bar);
+            if (m0) tc::bulk_copy_g2s(Cp, m0, hb, &s_bar);
+            if (m1) tc::bulk_copy_g2s(Cp + hh, m1, hb, &s_bar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&s_bar, parity)) != 0;
+        parity ^= 1u;
+    };
+    constexpr int CG = CB / 8;
+    const int RT = blockDim.x / CG, r = threadIdx.x % RT, cgp = threadIdx.x / RT;
+    // out (n2 x CB) (-)= F^T in: out[row] = sum_{kk < nk} F[kk][row] in[kk]
+    auto apply = [&](int nk, const T *in, T *out, bool subtract) {
+        T acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = T(0);
+        if (r < n2) {
+#pragma unroll 4
+            for (int kk = 0; kk < nk; ++kk) {
+                const T a = F[(size_t)kk * n2 + r];
+                const T *x = in + (size_t)kk * CB + cgp * 8;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[c] = fma(a, x[c], acc[c]);
+            }
+        }
+        __syncthreads();  // every read of in (possibly out) done
+        if (r < n2) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                T *o = out + (size_t)r * CB + cgp * 8 + c;
+                *o = subtract ? *o - acc[c] : acc[c];
+            }
+        }
+        __syncthreads();
+    };
+    // out[p][c] (-)= sum_k M[p][k] v[k][c], p < h2 (M: h2 x h2 in shared memory)
+    auto couple = [&](const T *M, const T *v, T *out, bool subtract) {
+        for (int idx = threadIdx.x; idx < h2 * CB; idx += blockDim.x) {
+            const int p = idx / CB, c = idx - p * CB;
+            T s = T(0);
+            for (int kk = 0; kk < h2; ++kk) s = fma(M[(size_t)p * h2 + kk], v[(size_t)kk * CB + c], s);
+            out[(size_t)p * CB + c] = subtract ? out[(size_t)p * CB + c] - s : s;
+        }
+    };
+    auto Xc = [&](int cell_local) { return X + (size_t)(cell_local >> cl) * n2 * CB; };
+    for (int l = cl; l <= nl && ok; ++l) {
+        const int i0 = lv.off[l], i1 = l < nl ? lv.off[l + 1] : lv.off[nl] + lv.n_roots;
+        for (int ii = i0; ii < i1 && ok; ++ii) {
+            const BcrItem it = items[ii];
+            if (!get_nz(it.local >> cl)) continue;
+            const int step = 1 << l;
+            const bool pr = l < nl && it.right >= 0, pl = l < nl && it.left >= 0;
+            fetch(it.cell, 0, n2, pr ? Bc + (size_t)it.s_right * hh : nullptr,
+                  pl ? Cc + (size_t)it.s_left * hh : nullptr);
+            if (!ok) break;
+            T *Xi = Xc(it.local);
+            apply(n2, Xi, Xi, false);
+            if (pr) {
+                couple(Cp, Xi + (size_t)(N + h2) * CB, Xc(it.local + step) + (size_t)h2 * CB, true);
+                set_nz((it.local + step) >> cl);
+            }
+            if (pl) {
+                couple(Cp + hh, Xi, Xc(it.local - step) + (size_t)N * CB, true);
+                set_nz((it.local - step) >> cl);
+            }
+            __syncthreads();
+        }
+    }
+    for (int l = nl - 1; l >= cl && ok; --l) {
+        for (int ii = lv.off[l]; ii < lv.off[l + 1] && ok; ++ii) {
+            const BcrItem it = items[ii];
+            const int step = 1 << l, jl = (it.local - step) >> cl, jr = (it.local + step) >> cl;
+            const bool rt = it.right >= 0;
+            if (!get_nz(it.local >> cl) && !get_nz(jl) && !(rt && get_nz(jr))) continue;
+            fetch(it.cell, h2, N, Bc + (size_t)it.s_cell * hh, rt ? Cc + (size_t)it.s_cell * hh : nullptr);
+            if (!ok) break;
+            couple(Cp, Xc(it.local - step) + (size_t)(N + h2) * CB, gs, false);
+            if (rt) couple(Cp + hh, Xc(it.local + step), gs + (size_t)h2 * CB, false);
+            else
+                for (int idx = threadIdx.x; idx < h2 * CB; idx += blockDim.x) gs[(size_t)h2 * CB + idx] = T(0);
+            __syncthreads();
+            apply(N, gs, Xc(it.local), true);
+            set_nz(it.local >> cl);
+        }
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        tc::mbar_wait(&s_bar, parity ^ 1u);  // the copy that did not land in time (bounded)
+        return;
+    }
+    for (int idx = threadIdx.x; idx < n * CB; idx += blockDim.x) {
+        const int row = idx / CB, col = idx - row * CB;
+        G[(size_t)row * n + j0 + col] = X[idx];
     }
 }
 
