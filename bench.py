@@ -43,7 +43,7 @@ WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, 
 METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
 TOL = 1e-10
 # per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload
-NCU_TRAFFIC = {("k_bcr_solve_flow_s", "mixed"): 204.1e6}
+NCU_TRAFFIC = {("k_bcr_solve_flow_s", "mixed"): 224.3e6}
 
 
 def dist_env():
@@ -293,9 +293,20 @@ def main():
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     if dom == "bcr_solve":
-        # forward: every eliminated cell and the root read their full (2N)^2 inverse;
-        # backward: the 2N x N inflow columns; plus the N/2 x N/2 couplings (2 per cell)
-        byt = esize * (K * n2 * n2 + (K - 1) * n2 * N + 2 * (K - 1) * (N // 2) ** 2)
+        # forward: every eliminated cell below the coarse level reads its full (2N)^2
+        # inverse; backward: its 2N x N inflow columns; plus its N/2 x N/2 couplings (2 per
+        # cell); the coarse cells (those the library's coarse step covers, the rule of
+        # plan_coarse: the lowest level c with ceil(K / 2^c) <= N/4 and two levels above
+        # it, staged FP32 solves of one slab) are one read of the dense inverse G
+        nl = max(1, (K - 1).bit_length())
+        m_c = 0
+        if (2 * N) * (2 * N) * esize <= 64 * 1024:
+            for c in range(1, nl - 1):
+                if -(-K // (1 << c)) <= N // 4:
+                    m_c = -(-K // (1 << c))
+                    break
+        kf = K - m_c
+        byt = esize * (kf * n2 * n2 + kf * n2 * N + 2 * kf * (N // 2) ** 2 + (m_c * n2) ** 2)
         achieved = byt / (per_launch_ms * 1e-3) / 1e9
         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel for this
         # workload (FP32), from profiles/k_bcr_solve_flow_precision_srk_slab.md
