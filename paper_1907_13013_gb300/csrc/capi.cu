@@ -76,6 +76,7 @@ struct fpsa_ctx {
     BcrItem *d_items_all = nullptr;  // levels concatenated, then roots (cooperative solve)
     LevelTable lvt[2] = {};          // per element type (row slicing depends on the vector width)
     int coop_grid[2] = {0, 0};       // cooperative BCR solve grid for float [0] / double [1]
+    int factor_grid[2] = {0, 0};     // cooperative dataflow factorization grid (0: per-level launches)
     unsigned long long *d_conv = nullptr, *d_growth = nullptr;
     int *d_status = nullptr;
     double *d_result = nullptr;
@@ -459,6 +460,15 @@ int setup_tc(fpsa_ctx *ctx) {
 
 // Upload per-path cross sections / sources (padded to N moments); with full, also the
 // sweep coefficients, the FP operator assembly and its block factorization.
+// The dataflow factorization kernel for blocks of n2 x n2 (register-tiled inversion), or NULL.
+template <typename T>
+const void *factor_kernel(int n2) {
+    if (n2 == 128 && cta_invertible<T>(128)) return (const void *)k_bcr_factor_flow<T, 128>;
+    if (n2 == 64) return (const void *)k_bcr_factor_flow<T, 64>;
+    if (n2 == 32) return (const void *)k_bcr_factor_flow<T, 32>;
+    return nullptr;
+}
+
 template <typename T>
 int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     const Geometry &g = ctx->geo;
@@ -491,7 +501,24 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
                                                  p.Cc, ctx->d_bc);
     }
     CK(cudaGetLastError());
-    for (int l = 0; l < g.n_levels; ++l) {
+    const int e = sizeof(T) == 8 ? 1 : 0;
+    if (ctx->factor_grid[e] > 0) {
+        // every level and the roots in one cooperative launch (dataflow between items)
+        const LevelTable &lv = ctx->lvt[e];
+        T *A = p.A, *Bc = p.Bc, *Cc = p.Cc;
+        const BcrItem *items = ctx->d_items_all;
+        int n_items = lv.off[g.n_levels] + lv.n_roots;
+        unsigned long long *growth = ctx->d_growth;
+        int *status = ctx->d_status, *cnt = ctx->d_flow_cnt, *err = ctx->d_dev_err;
+        int staged = schur_staged<T>(N) ? 1 : 0;
+        void *args[] = {(void *)&A,      (void *)&items,  (void *)&n_items, (void *)&Bc,  (void *)&Cc,
+                        (void *)&growth, (void *)&status, (void *)&cnt,     (void *)&err, (void *)&staged};
+        CK(cudaMemsetAsync(cnt, 0, (size_t)g.sumK * sizeof(int), st));
+        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+        CK(cudaLaunchCooperativeKernel(factor_kernel<T>(2 * N), dim3(ctx->factor_grid[e]), dim3(512), args,
+                                       schur_smem<T>(N), st));
+    }
+    for (int l = 0; l < g.n_levels && ctx->factor_grid[e] == 0; ++l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
         bool fused = false;
@@ -505,7 +532,7 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         }
         CK(cudaGetLastError());
     }
-    {
+    if (ctx->factor_grid[e] == 0) {
         int rc = invert_level(ctx, p, ctx->d_roots, g.B);
         if (rc) return rc;
     }
@@ -1305,6 +1332,13 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<double>(RC, g.N), kSolveThreads,
                                                              solve_smem<double>(g.N, RC)));
             ctx->coop_grid[1] = std::max(1, std::min(per_sm, 4)) * nsm;
+            for (int e = 0; e < 2; ++e) {
+                const void *fk = e ? factor_kernel<double>(2 * g.N) : factor_kernel<float>(2 * g.N);
+                const size_t fsm = e ? schur_smem<double>(g.N) : schur_smem<float>(g.N);
+                int fper = 0;
+                if (fk) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, fk, 512, fsm));
+                ctx->factor_grid[e] = (fk && fper > 0) ? nsm : 0;  // one block per SM
+            }
             // Row slices per item: split an item's 2N rows (in vectors of V) into S in {1, 2, 4}
             // slices (quadrant-aligned) of >= 2 vectors while the level's units still fit in
             // one pass of the grid.

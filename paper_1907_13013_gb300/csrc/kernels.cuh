@@ -647,7 +647,7 @@ __device__ __forceinline__ void gj_smem_body(const T *src, int lds, T *dst, int 
     double amax = 0.0;
     for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
         const int i = idx / n2, j = idx - i * n2;
-        const T v = src[(size_t)i * lds + j];
+        const T v = __ldcg(src + (size_t)i * lds + j);
         a[i * ld + j] = v;
         amax = fmax(amax, fabs((double)v));
     }
@@ -940,13 +940,13 @@ __device__ __forceinline__ void gj_panel_body(const float *src, int lds, float *
         if constexpr (CJ % 4 == 0) {
 #pragma unroll
             for (int j = 0; j < CJ; j += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(rp + j);
+                const float4 v = __ldcg(reinterpret_cast<const float4 *>(rp + j));
                 x[i][j] = v.x; x[i][j + 1] = v.y; x[i][j + 2] = v.z; x[i][j + 3] = v.w;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < CJ; j += 2) {
-                const float2 v = *reinterpret_cast<const float2 *>(rp + j);
+                const float2 v = __ldcg(reinterpret_cast<const float2 *>(rp + j));
                 x[i][j] = v.x; x[i][j + 1] = v.y;
             }
         }
@@ -1104,7 +1104,7 @@ __device__ __forceinline__ void gj_reg_body(const T *src, int lds, T *dst, int l
     for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int j = 0; j < CJ; ++j) {
-            x[i][j] = src[(size_t)(lane + 32 * i) * lds + w + 16 * j];
+            x[i][j] = __ldcg(src + (size_t)(lane + 32 * i) * lds + w + 16 * j);
             amax = fmax(amax, fabs(x[i][j]));
         }
     unsigned used = 0u;  // bit i: row lane + 32 i has been a pivot row
@@ -1253,6 +1253,13 @@ __global__ void __launch_bounds__(512) k_bcr_invert_reg(T *__restrict__ A, const
     }
 }
 
+// A load that bypasses L1 when p is in global memory (data another block may have
+// written during the same launch), a plain load for shared memory.
+template <typename T>
+__device__ __forceinline__ T ld_fresh(const T *p) {
+    return __isGlobal(p) ? __ldcg(p) : *p;
+}
+
 // out (+)= X Y for h2 x h2 operands through shared memory: both operands are
 // staged with coalesced loads (the index that is contiguous in memory runs
 // fastest across threads), then every thread forms a 2 x 2 register tile.
@@ -1268,9 +1275,9 @@ __device__ __forceinline__ void smem_mm(T *out, int ldo, int mode, const T *X, i
             const int p = idx / h2, q = idx - p * h2;
             T acc = T(0);
             for (int kk = 0; kk < h2; ++kk)
-                acc = fma(X[(size_t)p * xr + (size_t)kk * xc], Y[(size_t)kk * yr + (size_t)q * yc], acc);
+                acc = fma(ld_fresh(X + (size_t)p * xr + (size_t)kk * xc), ld_fresh(Y + (size_t)kk * yr + (size_t)q * yc), acc);
             T *o = out + (size_t)p * ldo + q;
-            if (mode == 1) *o -= acc;
+            if (mode == 1) *o = ld_fresh(o) - acc;
             else if (mode == 2) *o = -acc;
             else *o = acc;
         }
@@ -1281,10 +1288,10 @@ __device__ __forceinline__ void smem_mm(T *out, int ldo, int mode, const T *X, i
     for (int idx = threadIdx.x; idx < hh; idx += blockDim.x) {
         int p, kk;
         if (xr == 1) { p = idx % h2; kk = idx / h2; } else { kk = idx % h2; p = idx / h2; }
-        Xs[p * h2 + kk] = X[(size_t)p * xr + (size_t)kk * xc];
+        Xs[p * h2 + kk] = ld_fresh(X + (size_t)p * xr + (size_t)kk * xc);
         int k2, q;
         if (yr == 1) { k2 = idx % h2; q = idx / h2; } else { q = idx % h2; k2 = idx / h2; }
-        Ys[k2 * h2 + q] = Y[(size_t)k2 * yr + (size_t)q * yc];
+        Ys[k2 * h2 + q] = ld_fresh(Y + (size_t)k2 * yr + (size_t)q * yc);
     }
     __syncthreads();
     const int half = (h2 + 1) / 2;
@@ -1303,7 +1310,7 @@ __device__ __forceinline__ void smem_mm(T *out, int ldo, int mode, const T *X, i
             const int p = p0 + (e >> 1), q = q0 + (e & 1);
             if (p >= h2 || q >= h2) continue;
             T *o = out + (size_t)p * ldo + q;
-            if (mode == 1) *o -= v[e];
+            if (mode == 1) *o = ld_fresh(o) - v[e];
             else if (mode == 2) *o = -v[e];
             else *o = v[e];
         }
@@ -1627,6 +1634,50 @@ __device__ __forceinline__ void flow_signal_release(const FlowSync *fs, int sign
         if (fs->sig0) atomicAdd(fs->sig0, 1);
         if (fs->sig1) atomicAdd(fs->sig1, 1);
         if (fs->sig2) atomicAdd(fs->sig2, 1);
+    }
+}
+
+// The factorization as a dataflow over the items of every level and the roots, in
+// one cooperative launch of one 512-thread block per SM (register-tiled inversion,
+// 2N in {32, 64, 128}). Items are taken block-stride in the order of the item array
+// (levels ascending, roots last), and an item waits until its block has received
+// every Schur update of the levels below its own: one from each neighbour at
+// distance 2^l' for l' < its level, the count of the solve's pushes. It then inverts
+// the block, applies its own Schur updates to its two kept neighbours (and their
+// next-level couplings) and bumps their counters. A quadrant of a kept cell is
+// updated by its neighbours at successive levels, each of which waited for the
+// previous one, so plain read-modify-writes suffice; every read of data another
+// block wrote bypasses L1. Waits are bounded (kFlowSpinLimit; *err = 1 on timeout).
+template <typename T, int N2>
+__global__ void __launch_bounds__(512, 1) k_bcr_factor_flow(T *__restrict__ A, const BcrItem *__restrict__ items,
+                                                           int n_items, T *__restrict__ Bc, T *__restrict__ Cc,
+                                                           unsigned long long *__restrict__ growth,
+                                                           int *__restrict__ status, int *cnt, int *err,
+                                                           int schur_staged) {
+    extern __shared__ unsigned char smem_dyn[];
+    for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+        const BcrItem it = items[ii];
+        FlowSync fs{};
+        fs.err = err;
+        int want = 0;
+        for (int lp = 0; lp < it.level; ++lp)
+            want += (it.local >= (1 << lp)) + (it.local + (1 << lp) < it.K_inst);
+        if (want) {
+            fs.wait0 = cnt + it.cell;
+            fs.want0 = want;
+        }
+        flow_wait(&fs);
+        T *Ag = A + (size_t)it.cell * N2 * N2;
+        if constexpr (sizeof(T) == 4) gj_panel_body<N2>(Ag, N2, Ag, N2, true, growth, status);
+        else gj_reg_body<T, N2>(Ag, N2, Ag, N2, true, growth, status);
+        if (it.left >= 0 || it.right >= 0) {
+            __syncthreads();  // the inverse this block just wrote, before the updates read it
+            schur_body(A, Bc, Cc, it, N2 / 2, schur_staged, smem_dyn);
+            if (it.right >= 0) fs.sig0 = cnt + it.right;
+            if (it.left >= 0) fs.sig1 = cnt + it.left;
+            flow_signal(&fs);
+        }
+        __syncthreads();  // shared memory of the inversion reused by the block's next item
     }
 }
 
