@@ -27,7 +27,16 @@ using namespace fpsa;
 
 namespace {
 
-constexpr int kSweepThreads = 256;
+// segmented sweep: cells per thread (at least 4) so that no slab needs more than
+// kSegMax segments of kSegWarps * cpt cells
+inline int sweep_cells_per_thread(const Geometry &g) {
+    const int per = kSegMax * kSegWarps;
+    return std::max(4, (g.Kmax + per - 1) / per);
+}
+inline int sweep_segments(const Geometry &g) {
+    const int len = kSegWarps * sweep_cells_per_thread(g);
+    return (g.Kmax + len - 1) / len;
+}
 constexpr int kContractThreads = 256;
 constexpr int kInvertThreads = 512;
 constexpr int kSolveThreads = 256;  // one (item, rhs) unit per block
@@ -42,7 +51,7 @@ struct PathBuffers {
     T *phi = nullptr, *phi_half = nullptr, *q = nullptr, *psi = nullptr, *rhs = nullptr;
     T *qang = nullptr;                       // MIXED inner path: nodal residual source [R][sumK][2][N]
     T *ybuf = nullptr;                       // BCR solve: intermediate y, then the solution [R][sumK][2N]
-    T *tot = nullptr;                        // reflective edges: whole-slab sweep maps [R][B][N][2]
+    T *cmap = nullptr, *smap = nullptr;      // segmented sweep: chunk and segment maps (k_sweep_maps)
     T *G = nullptr;                          // coarse step of the BCR solve: inverse of the coarse system [n][n]
     // recursive block inversion (2N too large for one CTA): per-depth scratch X, Y
     std::vector<T *> inv_scratch;
@@ -294,6 +303,11 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     CK(dalloc(ctx, &p.sigma_s, (size_t)g.sumK * N));
     CK(dalloc(ctx, &p.phi, ang));
     CK(dalloc(ctx, &p.psi, ang));
+    {
+        const int nseg = sweep_segments(g);
+        CK(dalloc(ctx, &p.smap, (size_t)g.R * g.B * nseg * N * 2));
+        CK(dalloc(ctx, &p.cmap, (size_t)g.R * g.B * nseg * kSegWarps * N * 2));
+    }
     if (full) {
         CK(dalloc(ctx, &p.coef, (size_t)g.sumK * 6 * N));
         CK(dalloc(ctx, &p.A, (size_t)g.sumK * 4 * N * N));
@@ -303,7 +317,7 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         CK(dalloc(ctx, &p.q, ang));
         CK(dalloc(ctx, &p.rhs, ang));
         CK(dalloc(ctx, &p.ybuf, ang));
-        if (ctx->d_bc) CK(dalloc(ctx, &p.tot, (size_t)g.R * g.B * N * 2));
+
         const LevelTable &lvp = ctx->lvt[sizeof(T) == 8 ? 1 : 0];
         if (lvp.coarse_level >= 0) {
             const size_t n = (size_t)lvp.coarse_m * 2 * N;
@@ -549,21 +563,23 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
 }
 
 // psi = L^{-1} q for every (ordinate, instance, rhs) with the given incoming edge
-// fluxes inc (NULL: none); reflective edges take the totals pass first.
+// fluxes inc (NULL: none): the segmented sweep (chunk / segment maps, then the
+// re-sweep from each segment's inflow; reflective edges take their whole-slab maps
+// from the segment maps).
 template <typename T>
 int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
     const Geometry &g = ctx->geo;
-    const dim3 sgrid(g.N, g.B, g.R);
-    if (ctx->d_bc) {
+    const int nseg = sweep_segments(g), cpt = sweep_cells_per_thread(g);
+    const dim3 grid(2 * ((g.N / 2 + 31) / 32), nseg, g.R * g.B);
+    {
         Launch L_(ctx, FPSA_PHASE_SWEEP);
-        k_sweep<T, kSweepThreads, true><<<sgrid, kSweepThreads, 0, ctx->stream>>>(
-            q, psi, p.coef, ctx->d_mu, ctx->d_off, ctx->d_K, g.N, g.sumK, inc, ctx->d_bc, p.tot);
+        k_sweep_maps<T><<<grid, kSegWarps * 32, 0, ctx->stream>>>(q, p.coef, ctx->d_off, ctx->d_K, g.N, g.sumK, g.B,
+                                                                  cpt, nseg, p.cmap, p.smap);
     }
     {
         Launch L_(ctx, FPSA_PHASE_SWEEP);
-        k_sweep<T, kSweepThreads><<<sgrid, kSweepThreads, 0, ctx->stream>>>(q, psi, p.coef, ctx->d_mu, ctx->d_off,
-                                                                           ctx->d_K, g.N, g.sumK, inc, ctx->d_bc,
-                                                                           p.tot);
+        k_sweep_apply<T><<<grid, kSegWarps * 32, 0, ctx->stream>>>(q, psi, p.coef, ctx->d_off, ctx->d_K, g.N, g.sumK,
+                                                                   g.B, cpt, nseg, p.cmap, p.smap, inc, ctx->d_bc);
     }
     CK(cudaGetLastError());
     return FPSA_OK;

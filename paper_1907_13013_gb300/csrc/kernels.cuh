@@ -219,6 +219,219 @@ __global__ void __launch_bounds__(NT) k_sweep(const T *__restrict__ q, T *__rest
 }
 
 // ---------------------------------------------------------------------------
+// Segmented transport sweep (the same recurrence, maps and edge inflows as
+// k_sweep), laid out for coalesced access: a block holds 32 ordinates of one
+// direction in its lanes (consecutive n: one 128-byte line per cell value) and
+// kSegWarps chunks of cpt consecutive cells (in sweep order) in its warps, so a
+// segment covers kSegWarps * cpt cells and a (direction, 32-ordinate group,
+// instance, rhs) is swept by nseg blocks along the slab (nseg <= kSegMax):
+//   k_sweep_maps   each chunk's affine map (x -> a x + b for the chunk's outflow)
+//                  and their composition over the segment, written per ordinate;
+//   k_sweep_apply  the segment's inflow: the edge inflow (as in k_sweep, the
+//                  whole-slab maps of n and of its mirror composed from all
+//                  segment maps at a reflective edge) carried through the maps of
+//                  the segments before it, then through the chunk maps before
+//                  the warp's chunk; then the chunk is re-swept from that inflow.
+// Maps are stored as (a, b) pairs: cmap[zb][seg][warp][n], smap[zb][seg][n].
+// ---------------------------------------------------------------------------
+constexpr int kSegWarps = 8, kSegMax = 64;
+static_assert(kSegMax % kSegWarps == 0, "segment maps split evenly over the warps");
+
+struct SweepLane {
+    int n, K, o, r, b;
+    bool valid, fwd;
+};
+
+__device__ __forceinline__ SweepLane sweep_lane(int N, const int32_t *off, const int32_t *Kc, int B) {
+    SweepLane s;
+    const int gpd = (N / 2 + 31) / 32;
+    const int d = blockIdx.x / gpd, idx = (blockIdx.x % gpd) * 32 + (threadIdx.x & 31);
+    s.valid = idx < N / 2;
+    s.fwd = d == 1;  // ordinates n >= N/2 have mu > 0: swept left to right
+    s.n = d ? N / 2 + idx : idx;
+    s.b = blockIdx.z % B;
+    s.r = blockIdx.z / B;
+    s.K = Kc[s.b];
+    s.o = off[s.b];
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ Affine<T> load_map(const T *m, size_t i) {
+    return {__ldcg(m + 2 * i), __ldcg(m + 2 * i + 1)};
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSegWarps * 32) k_sweep_maps(const T *__restrict__ q, const T *__restrict__ coef,
+                                                               const int32_t *__restrict__ off,
+                                                               const int32_t *__restrict__ Kc, int N, int sumK, int B,
+                                                               int cpt, int nseg, T *__restrict__ cmap,
+                                                               T *__restrict__ smap) {
+    __shared__ Affine<T> part[kSegWarps][32];
+    const SweepLane L = sweep_lane(N, off, Kc, B);
+    const int seg = blockIdx.y, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg_len = kSegWarps * cpt;
+    if (seg * seg_len >= L.K) return;  // whole block: segments beyond this instance's cells
+    const int nu_ = L.fwd ? 0 : 1, nd_ = 1 - nu_;
+    const int p0 = seg * seg_len + w * cpt, p1 = min(p0 + cpt, L.K);
+    Affine<T> m{T(1), T(0)};
+    if (L.valid) {
+        const T *qb = q + ((size_t)L.r * sumK + L.o) * 2 * N + L.n;
+        const T *cb = coef + (size_t)L.o * 6 * N + L.n;
+        for (int pb = p0; pb < p1; pb += kSweepBatch) {
+            T qu[kSweepBatch], qd[kSweepBatch], al[kSweepBatch], gdu[kSweepBatch], gdd[kSweepBatch];
+#pragma unroll
+            for (int t = 0; t < kSweepBatch; ++t) {
+                const int p = pb + t;
+                if (p < p1) {
+                    const int c = L.fwd ? p : L.K - 1 - p;
+                    const T *cc = cb + (size_t)c * 6 * N;
+                    qu[t] = qb[(size_t)(2 * c + nu_) * N];
+                    qd[t] = qb[(size_t)(2 * c + nd_) * N];
+                    al[t] = cc[0];
+                    gdu[t] = cc[4 * N];
+                    gdd[t] = cc[5 * N];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kSweepBatch; ++t)
+                if (pb + t < p1) {
+                    m.b = al[t] * m.b + (gdu[t] * qu[t] + gdd[t] * qd[t]);
+                    m.a = al[t] * m.a;
+                }
+        }
+        const size_t ci = (((size_t)blockIdx.z * nseg + seg) * kSegWarps + w) * N + L.n;
+        cmap[2 * ci] = m.a;
+        cmap[2 * ci + 1] = m.b;
+    }
+    part[w][lane] = m;
+    __syncthreads();
+    if (w == 0 && L.valid) {
+        Affine<T> t = part[0][lane];
+        for (int v = 1; v < kSegWarps; ++v) t = compose(t, part[v][lane]);
+        const size_t si = ((size_t)blockIdx.z * nseg + seg) * N + L.n;
+        smap[2 * si] = t.a;
+        smap[2 * si + 1] = t.b;
+    }
+}
+
+// Composition of the segment maps [s0, s1) of ordinate n (in sweep order), split over
+// the block's warps (contiguous ranges, then combined in order by warp 0; the result
+// is in part[0][lane] after the block barrier). All threads call it.
+template <typename T>
+__device__ __forceinline__ void compose_segments(const T *smap, int zb, int nseg, int N, int n, bool valid, int s0,
+                                                 int s1, Affine<T> (*part)[32]) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kPer = kSegMax / kSegWarps;  // segment maps per warp (all requested at once)
+    const int cnt = max(s1 - s0, 0), per = (cnt + kSegWarps - 1) / kSegWarps;
+    const int a0 = s0 + w * per, a1 = min(s1, a0 + per);
+    Affine<T> m{T(1), T(0)};
+    if (valid) {
+        Affine<T> v[kPer];
+#pragma unroll
+        for (int t = 0; t < kPer; ++t)
+            v[t] = (a0 + t < a1) ? load_map(smap, ((size_t)zb * nseg + a0 + t) * N + n) : Affine<T>{T(1), T(0)};
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) m = compose(m, v[t]);
+    }
+    __syncthreads();  // part may still be read from a previous use
+    part[w][lane] = m;
+    __syncthreads();
+    if (w == 0) {
+        Affine<T> t = part[0][lane];
+        for (int v = 1; v < kSegWarps; ++v) t = compose(t, part[v][lane]);
+        part[0][lane] = t;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSegWarps * 32) k_sweep_apply(const T *__restrict__ q, T *__restrict__ psi,
+                                                                const T *__restrict__ coef,
+                                                                const int32_t *__restrict__ off,
+                                                                const int32_t *__restrict__ Kc, int N, int sumK, int B,
+                                                                int cpt, int nseg, const T *__restrict__ cmap,
+                                                                const T *__restrict__ smap,
+                                                                const T *__restrict__ psi_inc,
+                                                                const int32_t *__restrict__ bc) {
+    __shared__ Affine<T> part[kSegWarps][32];
+    __shared__ T xin[32];
+    const SweepLane L = sweep_lane(N, off, Kc, B);
+    const int seg = blockIdx.y, w = threadIdx.x >> 5, lane = threadIdx.x & 31, zb = blockIdx.z;
+    const int seg_len = kSegWarps * cpt;
+    if (seg * seg_len >= L.K) return;  // whole block
+    const int ns = (L.K + seg_len - 1) / seg_len;  // this instance's segments
+    // edge inflow of ordinate n at its upwind edge s
+    const int s = L.fwd ? 0 : 1;
+    const size_t ib = (size_t)L.r * B + L.b;
+    T x0 = (psi_inc && L.valid) ? psi_inc[(ib * 2 + s) * N + L.n] : T(0);
+    if (bc && bc[2 * L.b + s] == kBcReflect) {
+        // whole-slab maps of n and of its mirror nm (the mirror's lanes sit in the
+        // other direction's blocks; its segment maps are read from smap)
+        const int nm = N - 1 - L.n;
+        compose_segments(smap, zb, nseg, N, L.n, L.valid, 0, ns, part);
+        const Affine<T> tn = part[0][lane];
+        compose_segments(smap, zb, nseg, N, nm, L.valid, 0, ns, part);
+        const Affine<T> tm = part[0][lane];
+        if (bc[2 * L.b + 1 - s] == kBcReflect) {
+            x0 = (tm.a * tn.b + tm.b) / (T(1) - tn.a * tm.a);
+        } else {
+            const T far = (psi_inc && L.valid) ? psi_inc[(ib * 2 + 1 - s) * N + nm] : T(0);
+            x0 = tm.a * far + tm.b;
+        }
+    }
+    // inflow of this segment, then of this warp's chunk
+    compose_segments(smap, zb, nseg, N, L.n, L.valid, 0, seg, part);
+    if (w == 0) xin[lane] = part[0][lane].a * x0 + part[0][lane].b;
+    __syncthreads();
+    T x = xin[lane];
+    if (!L.valid) return;
+    {
+        Affine<T> cm[kSegWarps - 1];
+#pragma unroll
+        for (int v = 0; v < kSegWarps - 1; ++v)
+            cm[v] = v < w ? load_map(cmap, (((size_t)zb * nseg + seg) * kSegWarps + v) * N + L.n) : Affine<T>{T(1), T(0)};
+#pragma unroll
+        for (int v = 0; v < kSegWarps - 1; ++v) x = cm[v].a * x + cm[v].b;
+    }
+    // re-sweep the chunk from its exact inflow
+    const int nu_ = L.fwd ? 0 : 1, nd_ = 1 - nu_;
+    const int p0 = seg * seg_len + w * cpt, p1 = min(p0 + cpt, L.K);
+    const size_t base = ((size_t)L.r * sumK + L.o) * 2 * N + L.n;
+    const T *qb = q + base;
+    T *pb_ = psi + base;
+    const T *cb = coef + (size_t)L.o * 6 * N + L.n;
+    for (int pb = p0; pb < p1; pb += kSweepBatch) {
+        T qu[kSweepBatch], qd[kSweepBatch], cf[6][kSweepBatch];
+#pragma unroll
+        for (int t = 0; t < kSweepBatch; ++t) {
+            const int p = pb + t;
+            if (p < p1) {
+                const int c = L.fwd ? p : L.K - 1 - p;
+                const T *cc = cb + (size_t)c * 6 * N;
+                qu[t] = qb[(size_t)(2 * c + nu_) * N];
+                qd[t] = qb[(size_t)(2 * c + nd_) * N];
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk) cf[kk][t] = cc[(size_t)kk * N];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSweepBatch; ++t) {
+            const int p = pb + t;
+            if (p < p1) {
+                const int c = L.fwd ? p : L.K - 1 - p;
+                // cf: 0 alpha, 1 a_u, 2 G_uu, 3 G_ud, 4 G_du, 5 G_dd
+                const T pu = cf[2][t] * qu[t] + cf[3][t] * qd[t] + cf[1][t] * x;
+                const T pd = cf[4][t] * qu[t] + cf[5][t] * qd[t] + cf[0][t] * x;
+                pb_[(size_t)(2 * c + nu_) * N] = pu;
+                pb_[(size_t)(2 * c + nd_) * N] = pd;
+                x = pd;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Angular contractions. Ys[c][o] = sum_k MatT[k][o] Xs[c][k] over the columns
 // c < ncols of a shared-memory tile; MatT is the transposed operator in global
 // memory (k-major, so consecutive threads read consecutive o).
