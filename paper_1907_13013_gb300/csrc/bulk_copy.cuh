@@ -61,5 +61,10 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Programmatic dependent launch: wait until the grids this one depends on (the
+// previous kernel in the stream) have completed and their writes are visible. A
+// kernel launched without the attribute returns at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace tc
 }  // namespace fpsa

@@ -562,6 +562,25 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     return FPSA_OK;
 }
 
+// Launch with programmatic dependent launch allowed: the kernel's blocks may be
+// scheduled while the previous kernel in the stream drains, and the kernel waits
+// for it (griddepcontrol.wait, before touching its outputs or overwriting its
+// inputs), so launch latency and the kernel's own prologue overlap the tail.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // psi = L^{-1} q for every (ordinate, instance, rhs) with the given incoming edge
 // fluxes inc (NULL: none): the segmented sweep (chunk / segment maps, then the
 // re-sweep from each segment's inflow; reflective edges take their whole-slab maps
@@ -573,13 +592,14 @@ int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
     const dim3 grid(2 * ((g.N / 2 + 31) / 32), nseg, g.R * g.B);
     {
         Launch L_(ctx, FPSA_PHASE_SWEEP);
-        k_sweep_maps<T><<<grid, kSegWarps * 32, 0, ctx->stream>>>(q, p.coef, ctx->d_off, ctx->d_K, g.N, g.sumK, g.B,
-                                                                  cpt, nseg, p.cmap, p.smap);
+        CK(launch_pdl(k_sweep_maps<T>, grid, dim3(kSegWarps * 32), 0, ctx->stream, q, (const T *)p.coef, ctx->d_off,
+                      ctx->d_K, g.N, g.sumK, g.B, cpt, nseg, p.cmap, p.smap));
     }
     {
         Launch L_(ctx, FPSA_PHASE_SWEEP);
-        k_sweep_apply<T><<<grid, kSegWarps * 32, 0, ctx->stream>>>(q, psi, p.coef, ctx->d_off, ctx->d_K, g.N, g.sumK,
-                                                                   g.B, cpt, nseg, p.cmap, p.smap, inc, ctx->d_bc);
+        CK(launch_pdl(k_sweep_apply<T>, grid, dim3(kSegWarps * 32), 0, ctx->stream, q, psi, (const T *)p.coef,
+                      ctx->d_off, ctx->d_K, g.N, g.sumK, g.B, cpt, nseg, (const T *)p.cmap, (const T *)p.smap, inc,
+                      (const int32_t *)ctx->d_bc));
     }
     CK(cudaGetLastError());
     return FPSA_OK;
@@ -758,13 +778,13 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     for (outer = 1; outer <= o.max_iterations + 1; ++outer) {
         {
             Launch L_(ctx, FPSA_PHASE_RESIDUAL);
-            k_mixed_residual<<<cgrid, kContractThreads, contract_smem<double>(N), st>>>(
-                p.psi, p.phi, p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst,
-                ctx->d_off, ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc, ctx->d_bc);
+            CK(launch_pdl(k_mixed_residual, cgrid, dim3(kContractThreads), contract_smem<double>(N), st, p.psi, p.phi,
+                          p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst, ctx->d_off,
+                          ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc, ctx->d_bc));
         }
         {
             Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
-            k_conv_finalize<<<1, 256, 0, st>>>(ctx->d_conv, g.R * g.B, ctx->d_result);
+            CK(launch_pdl(k_conv_finalize, dim3(1), dim3(256), 0, st, ctx->d_conv, g.R * g.B, ctx->d_result));
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -803,7 +823,8 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             if (rc) return rc;
             {
                 Launch L_(ctx, FPSA_PHASE_RESIDUAL);
-                k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, (const float *)nullptr, nang);
+                CK(launch_pdl(k_mixed_accumulate, dim3(4 * 152), dim3(256), 0, st, p.psi, (const float *)f.psi,
+                              (const float *)nullptr, nang));
             }
             CK(cudaGetLastError());
             continue;
@@ -829,9 +850,9 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
                 {
                     Launch L_(ctx, FPSA_PHASE_CONTRACT);
                     if (use_tc && tc_full)
-                        k_tc_fp_rhs_tile<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s,
-                                                                          ctx->d_h, tcops, f.rhs, N, g.sumK, g.R,
-                                                                          ctx->d_dev_err);
+                        CK(launch_pdl(k_tc_fp_rhs_tile, dim3(tc_blocks), dim3(128), tc_smem, st, (const float *)f.psi,
+                                      (const float *)f.phi, f.phi_half, (const float *)f.sigma_s,
+                                      (const double *)ctx->d_h, tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err));
                     else if (use_tc)
                         k_tc_fp_rhs<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h,
                                                                      tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err);
@@ -847,9 +868,9 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             if (j < inner_k) {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
                 if (use_tc && tc_full)
-                    k_tc_update_scatter_tile<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops,
-                                                                              f.q, f.qang, N, g.sumK, g.R,
-                                                                              ctx->d_dev_err);
+                    CK(launch_pdl(k_tc_update_scatter_tile, dim3(tc_blocks), dim3(128), tc_smem, st, vin, base, f.phi,
+                                  (const float *)f.sigma_s, tcops, f.q, (const float *)f.qang, N, g.sumK, g.R,
+                                  ctx->d_dev_err));
                 else if (use_tc)
                     k_tc_update_scatter<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops, f.q,
                                                                          f.qang, N, g.sumK, g.R, ctx->d_dev_err);
@@ -861,7 +882,8 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         }
         {
             Launch L_(ctx, FPSA_PHASE_RESIDUAL);
-            k_mixed_accumulate<<<4 * 152, 256, 0, st>>>(p.psi, f.psi, fpsa ? f.ybuf : (const float *)nullptr, nang);
+            CK(launch_pdl(k_mixed_accumulate, dim3(4 * 152), dim3(256), 0, st, p.psi, (const float *)f.psi,
+                          fpsa ? (const float *)f.ybuf : (const float *)nullptr, nang));
         }
         CK(cudaGetLastError());
     }

@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_sweep_maps(const T *__restri
                                                                const int32_t *__restrict__ Kc, int N, int sumK, int B,
                                                                int cpt, int nseg, T *__restrict__ cmap,
                                                                T *__restrict__ smap) {
+    tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     __shared__ Affine<T> part[kSegWarps][32];
     const SweepLane L = sweep_lane(N, off, Kc, B);
     const int seg = blockIdx.y, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -354,6 +355,7 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_sweep_apply(const T *__restr
                                                                 const T *__restrict__ smap,
                                                                 const T *__restrict__ psi_inc,
                                                                 const int32_t *__restrict__ bc) {
+    tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     __shared__ Affine<T> part[kSegWarps][32];
     __shared__ T xin[32];
     const SweepLane L = sweep_lane(N, off, Kc, B);
@@ -484,6 +486,7 @@ template <typename T>
 __global__ void k_fp_rhs(const T *__restrict__ psi_half, const T *__restrict__ phi, T *__restrict__ phi_half,
                          const T *__restrict__ sigma_s, const double *__restrict__ h, const T *__restrict__ DT,
                          const T *__restrict__ MT, T *__restrict__ rhs, int N, int sumK) {
+    tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     extern __shared__ unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);
     T *Ys = Xs + 2 * kContractCells * N;
@@ -532,6 +535,7 @@ __global__ void k_update_scatter(const T *__restrict__ v, const T *__restrict__ 
                                  const int32_t *__restrict__ cell_inst, int B,
                                  unsigned long long *__restrict__ conv, int N, int sumK,
                                  const T *__restrict__ Qang = nullptr) {
+    tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     extern __shared__ unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);
     T *Ys = Xs + 2 * kContractCells * N;
@@ -582,6 +586,7 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
                                  unsigned long long *__restrict__ conv, float *__restrict__ dq, int N, int sumK,
                                  const double *__restrict__ Qang, const double *__restrict__ psi_inc,
                                  const int32_t *__restrict__ bc) {
+    tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     extern __shared__ unsigned char smem_raw[];
     double *Xs = reinterpret_cast<double *>(smem_raw);
     double *Ys = Xs + 2 * kContractCells * N;
@@ -676,6 +681,7 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
 // ups NULL: dpsi = psi_half (inner SI, or the sweep after an inner GMRES solve).
 static __global__ void k_mixed_accumulate(double *__restrict__ psi, const float *__restrict__ psi_half,
                                    const float *__restrict__ ups, size_t n) {
+    tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         psi[i] += (double)psi_half[i] + (ups ? (double)ups[i] : 0.0);
 }
@@ -698,6 +704,7 @@ __global__ void k_expand(const T *__restrict__ x, const T *__restrict__ MT, T *_
 // Worst relative change over (rhs, instance); resets the accumulators.
 // out[0] = max_rb conv_d / conv_a (NaN if any value was non-finite).
 static __global__ void k_conv_finalize(unsigned long long *conv, int nrb, double *out) {
+    tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     __shared__ double red[256];
     double worst = 0.0;
     bool bad = false;

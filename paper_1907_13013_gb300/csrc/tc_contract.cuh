@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(128) k_tc_fp_rhs(const float *__restrict__ psi
     extern __shared__ __align__(128) unsigned char smem_tc[];
     TcCta s;
     const bool ok0 = tc_cta_setup(s, smem_tc, ops, N, err);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
     const int t = threadIdx.x;
     const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
     const int tiles_per_r = (2 * sumK + 127) / 128;
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter(const float *__restri
     extern __shared__ __align__(128) unsigned char smem_tc[];
     TcCta s;
     const bool ok0 = tc_cta_setup(s, smem_tc, ops, N, err);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
     const int t = threadIdx.x;
     const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
     const int tiles_per_r = (2 * sumK + 127) / 128;
@@ -500,6 +502,7 @@ __global__ void __launch_bounds__(128) k_tc_fp_rhs_tile(const float *__restrict_
     const int tiles_per_r = (2 * sumK + 127) / 128;
     const int ntiles = tiles_per_r * R;
     bool ok = tc_cta_setup(s, smem_tc, ops, N, err, false);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
     bool first = true;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
@@ -572,6 +575,7 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter_tile(const float *__r
     const int tiles_per_r = (2 * sumK + 127) / 128;
     const int ntiles = tiles_per_r * R;
     bool ok = tc_cta_setup(s, smem_tc, ops, N, err, false);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
     bool first = true;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
