@@ -74,7 +74,13 @@ struct fpsa_ctx {
     int32_t *d_bc = nullptr;     // [B][2] edge conditions; NULL when every edge is vacuum
     double *d_in_st = nullptr, *d_in_ss = nullptr, *d_in_q = nullptr;  // fpsa_set_xs staging of host inputs
     int *d_xs_err = nullptr;     // [2] validation of fpsa_set_xs
-    int *d_flow_cnt = nullptr, *d_flow_done = nullptr;  // BCR dataflow counters [rhs chunks][sumK]
+    // BCR solve dataflow counters, double-buffered: [parity][cnt | done][rhs chunks][sumK];
+    // each solve uses one parity and zeroes the other for the next solve
+    int *d_flow = nullptr;
+    size_t flow_n = 0;                      // counters per array (rhs chunks x sumK)
+    int flow_parity = 0;
+    bool solve_pdl = true;                  // cooperative launch with programmatic serialization accepted
+    int *d_factor_cnt = nullptr;            // dataflow factorization counters [sumK]
     double *d_inc = nullptr;     // [R][B][2][N] given incoming edge fluxes (FP64)
     bool has_inc = false;
     float *d_Afp32 = nullptr, *d_mu32 = nullptr;  // angular Laplacian and mu rounded to FP32 (FP32 assembly)
@@ -523,7 +529,7 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         const BcrItem *items = ctx->d_items_all;
         int n_items = lv.off[g.n_levels] + lv.n_roots;
         unsigned long long *growth = ctx->d_growth;
-        int *status = ctx->d_status, *cnt = ctx->d_flow_cnt, *err = ctx->d_dev_err;
+        int *status = ctx->d_status, *cnt = ctx->d_factor_cnt, *err = ctx->d_dev_err;
         int staged = schur_staged<T>(N) ? 1 : 0;
         void *args[] = {(void *)&A,      (void *)&items,  (void *)&n_items, (void *)&Bc,  (void *)&Cc,
                         (void *)&growth, (void *)&status, (void *)&cnt,     (void *)&err, (void *)&staged};
@@ -607,6 +613,8 @@ int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
 
 // F u = rhs by block cyclic reduction over the stored factors: one cooperative
 // launch (forward levels, roots, backward levels); the solution is left in p.ybuf.
+// No memset precedes it (its counters were zeroed by the previous solve), so it can
+// be launched as a programmatic dependent of the kernel before it.
 template <typename T>
 int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     const Geometry &g = ctx->geo;
@@ -615,18 +623,37 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     LevelTable lv = ctx->lvt[sizeof(T) == 8 ? 1 : 0];
     const T *A = p.A, *Bc = p.Bc, *Cc = p.Cc;
     T *Y = p.ybuf;
-    int *cnt = ctx->d_flow_cnt, *done = ctx->d_flow_done, *err = ctx->d_dev_err;
+    const size_t n = ctx->flow_n;
+    int *cnt = ctx->d_flow + 2 * n * ctx->flow_parity, *done = cnt + n, *err = ctx->d_dev_err;
+    int *zero_next = ctx->d_flow + 2 * n * (1 - ctx->flow_parity);
+    long long nzero = (long long)(2 * n);
+    ctx->flow_parity ^= 1;
     const T *G = p.G;
-    void *args[] = {(void *)&A, (void *)&Bc, (void *)&Cc, (void *)&items, (void *)&lv,   (void *)&rhs, (void *)&Y,
-                    (void *)&N, (void *)&sumK, (void *)&R,     (void *)&cnt, (void *)&done, (void *)&err, (void *)&G};
+    void *args[] = {(void *)&A,   (void *)&Bc,  (void *)&Cc,   (void *)&items, (void *)&lv,
+                    (void *)&rhs, (void *)&Y,   (void *)&N,    (void *)&sumK,  (void *)&R,
+                    (void *)&cnt, (void *)&done, (void *)&err, (void *)&G,     (void *)&zero_next, (void *)&nzero};
     const int grid = ctx->coop_grid[sizeof(T) == 8 ? 1 : 0];
     const int RC = solve_rc(R);
-    const size_t ncnt = (size_t)((R + RC - 1) / RC) * sumK * sizeof(int);
-    CK(cudaMemsetAsync(cnt, 0, ncnt, ctx->stream));
-    CK(cudaMemsetAsync(done, 0, ncnt, ctx->stream));
+    const void *kern = coop_kernel<T>(RC, N);
     Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
-    CK(cudaLaunchCooperativeKernel(coop_kernel<T>(RC, N), dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC),
-                                   ctx->stream));
+    if (ctx->solve_pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kSolveThreads);
+        cfg.dynamicSmemBytes = solve_smem<T>(N, RC);
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 2;
+        if (cudaLaunchKernelExC(&cfg, kern, args) == cudaSuccess) return FPSA_OK;
+        (void)cudaGetLastError();  // the combination is refused: plain cooperative launches from now on
+        ctx->solve_pdl = false;
+    }
+    CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC), ctx->stream));
     return FPSA_OK;
 }
 
@@ -1298,8 +1325,10 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         CK(cudaMallocHost(&ctx->h_flag, sizeof(int)));
         {
             const int nchunk = (g.R + solve_rc(g.R) - 1) / solve_rc(g.R);
-            CK(dalloc(ctx, &ctx->d_flow_cnt, (size_t)nchunk * g.sumK));
-            CK(dalloc(ctx, &ctx->d_flow_done, (size_t)nchunk * g.sumK));
+            ctx->flow_n = (size_t)nchunk * g.sumK;
+            CK(dalloc(ctx, &ctx->d_flow, 4 * ctx->flow_n));
+            CK(cudaMemset(ctx->d_flow, 0, 4 * ctx->flow_n * sizeof(int)));
+            CK(dalloc(ctx, &ctx->d_factor_cnt, (size_t)g.sumK));
         }
         CK(dalloc(ctx, &ctx->d_growth, 1));
         CK(dalloc(ctx, &ctx->d_status, 1));

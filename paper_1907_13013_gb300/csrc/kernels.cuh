@@ -2025,7 +2025,11 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ 
                                                        const T *__restrict__ Cc, const BcrItem *__restrict__ items,
                                                        LevelTable lv, T *rhs, T *Y, int N, int sumK, int R, int *cnt,
                                                        int *done, int *err,
-                                                       const T *__restrict__ G = nullptr /* coarse step: staged only */) {
+                                                       const T *__restrict__ G /* coarse step: staged only */,
+                                                       int *zero_next, long long nzero) {
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nzero; i += (long long)gridDim.x * NT)
+        zero_next[i] = 0;
+    tc::grid_dependency_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, P = 2 * nl;
@@ -2326,8 +2330,12 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                                                             const T *__restrict__ Cc,
                                                             const BcrItem *__restrict__ items, LevelTable lv, T *rhs,
                                                             T *Y, int N, int sumK, int R, int *cnt, int *done,
-                                                            int *err, const T *__restrict__ G) {
+                                                            int *err, const T *__restrict__ G, int *zero_next,
+                                                            long long nzero) {
     static_assert(NT >= 64 && NT % 32 == 0, "copies and signals leave warp 0 free");
+    // the next solve's counters (the other half of the double-buffered pair) start at zero
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nzero; i += (long long)gridDim.x * NT)
+        zero_next[i] = 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;  // one phase per unit: its slice and couplings landed
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -2404,8 +2412,9 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
     BcrItem it_nx{};
     if (cur.valid) {
         if (cur.l >= 0) it_nx = items[lv.off[cur.l] + cur.item];
-        if (threadIdx.x >= NT - 32) stage(cur, it_nx, cb0);
+        if (threadIdx.x >= NT - 32) stage(cur, it_nx, cb0);  // factors, couplings, G: not written by the previous kernel
     }
+    tc::grid_dependency_wait();  // the right-hand sides come from the previous kernel
     while (cur.valid) {
         const BcrItem it = it_nx;
         Pos nxt = cur;
