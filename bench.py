@@ -43,7 +43,7 @@ WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, 
 METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
 TOL = 1e-10
 # per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload
-NCU_TRAFFIC = {("k_bcr_solve_flow_s", "mixed"): 224.3e6}
+NCU_TRAFFIC = {("k_bcr_solve_flow_s", "mixed"): 224.7e6}
 
 
 def dist_env():
