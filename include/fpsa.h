@@ -156,7 +156,10 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *desc);
  * FP operator per cell (2N x 2N diagonal blocks, N/2 x N/2 upwind couplings;
  * Eqs. fpop, fp-mpd-oper, wd-eq-oper) and factor it by block cyclic reduction.
  * Requires sigma_t > 0, 0 <= sigma_{s,0} <= sigma_t, finite values.
- * Returns FPSA_EPIVOT if a block is singular or its growth check fails. */
+ * Returns FPSA_EPIVOT if a block is singular or its growth check fails, and
+ * FPSA_ETIMEOUT if a bounded device wait of the factorization ran out (the
+ * dataflow factorization and the coarse inverse of a single-slab solve wait on
+ * counters and copies with limits). */
 int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s,
                 const double *q, int32_t mem);
 
