@@ -807,7 +807,8 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             Launch L_(ctx, FPSA_PHASE_RESIDUAL);
             CK(launch_pdl(k_mixed_residual, cgrid, dim3(kContractThreads), contract_smem<double>(N), st, p.psi, p.phi,
                           p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst, ctx->d_off,
-                          ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc, ctx->d_bc));
+                          ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc, ctx->d_bc,
+                          gmres ? (float *)nullptr : f.q, gmres ? (float *)nullptr : f.phi));
         }
         {
             Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
@@ -866,8 +867,7 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             if (e * r / (1.0 - r) < o.tol) inner_k = 1;
         }
         e_prev = e;
-        CK(cudaMemsetAsync(f.phi, 0, nang * sizeof(float), st));
-        CK(cudaMemcpyAsync(f.q, f.qang, nang * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        // f.phi = 0 and f.q = f.qang were written by the residual kernel
         for (int j = 1; j <= inner_k; ++j) {
             int rcs = sweep(ctx, f, f.q, f.psi, (const float *)nullptr);
             if (rcs) return rcs;

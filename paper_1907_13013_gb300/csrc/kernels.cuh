@@ -585,7 +585,8 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
                                  const int32_t *__restrict__ off, const int32_t *__restrict__ Kc, int B,
                                  unsigned long long *__restrict__ conv, float *__restrict__ dq, int N, int sumK,
                                  const double *__restrict__ Qang, const double *__restrict__ psi_inc,
-                                 const int32_t *__restrict__ bc) {
+                                 const int32_t *__restrict__ bc, float *__restrict__ q32,
+                                 float *__restrict__ phi32) {
     tc::grid_dependency_wait();  // inputs of the previous kernel (programmatic dependent launch)
     extern __shared__ unsigned char smem_raw[];
     double *Xs = reinterpret_cast<double *>(smem_raw);
@@ -672,8 +673,19 @@ static __global__ void k_mixed_residual(const double *__restrict__ psi, double *
         }
         const double w = 2.0 / hh;
         const double sL = Ys[(2 * cl) * N + n], sR = Ys[(2 * cl + 1) * N + n];
-        dq[(colbase + 2 * cl) * N + n] = (float)(sL - st * pL - w * (2.0 * tL - tR));
-        dq[(colbase + 2 * cl + 1) * N + n] = (float)(sR - st * pR - w * (2.0 * tR - tL));
+        const size_t eL = (colbase + 2 * cl) * N + n, eR = eL + N;
+        const float vL = (float)(sL - st * pL - w * (2.0 * tL - tR)), vR = (float)(sR - st * pR - w * (2.0 * tR - tL));
+        dq[eL] = vL;
+        dq[eR] = vR;
+        // the inner FP32 solve starts from zero moments with this source (q32, phi32 NULL: not wanted)
+        if (q32) {
+            q32[eL] = vL;
+            q32[eR] = vR;
+        }
+        if (phi32) {
+            phi32[eL] = 0.f;
+            phi32[eR] = 0.f;
+        }
     }
 }
 
