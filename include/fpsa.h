@@ -54,7 +54,7 @@ extern "C" {
 #define FPSA_EPIVOT     -5   /* FP block factorization: zero/non-finite pivot or growth above limit */
 #define FPSA_ETIMEOUT   -6   /* a bounded device wait ran out */
 #define FPSA_ECUDA      -7   /* a CUDA runtime call failed */
-#define FPSA_ENOTSUP    -8   /* configuration outside what this build supports */
+#define FPSA_ENOTSUP    -8   /* configuration outside what the library supports */
 #define FPSA_ESTATE     -9   /* call order violated (e.g. solve before set_xs) */
 
 enum fpsa_laplacian { FPSA_LAPLACIAN_MPD = 0, FPSA_LAPLACIAN_WFD = 1 };
@@ -142,7 +142,7 @@ int fpsa_profile_enable(fpsa_ctx *ctx, int32_t on);
 /* Synchronise the context stream and return the counters since the last reset. */
 int fpsa_profile_read(fpsa_ctx *ctx, fpsa_profile *out);
 
-/* Largest N this build supports. */
+/* Largest N the library supports. */
 #define FPSA_MAX_ORDINATES 256
 
 /* Create a context: validates the descriptor, builds the S_N tables (mu_n, w_n,

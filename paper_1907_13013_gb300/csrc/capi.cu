@@ -1247,7 +1247,7 @@ const char *fpsa_strerror(int code) {
         case FPSA_EPIVOT: return "FP block factorization failed (pivot or growth)";
         case FPSA_ETIMEOUT: return "bounded device wait timed out";
         case FPSA_ECUDA: return "CUDA runtime error";
-        case FPSA_ENOTSUP: return "configuration not supported by this build";
+        case FPSA_ENOTSUP: return "configuration not supported by the library";
         case FPSA_ESTATE: return "call order violated";
         default: return "unknown status";
     }
