@@ -42,7 +42,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, sigma_s0=1000, sigma_a=0.01, Q=1 on z<0.5, vacuum"
 METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
 TOL = 1e-10
-# per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload
+# per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload,
+# with the library's own launch shapes
 NCU_TRAFFIC = {("k_bcr_solve_flow_s", "mixed"): 224.7e6}
 
 
@@ -198,6 +199,9 @@ def main():
     ap.add_argument("--laplacian", default="wfd", choices=["mpd", "wfd"])
     ap.add_argument("--no-secondary", action="store_true", help="skip the MPD and FP64 comparison runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", default="auto", choices=["library", "auto"],
+                    help="launch shapes: the library's own, or those fpsa_autotune picks on this workload "
+                         "(before the warm-up, outside the timed region)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -255,6 +259,11 @@ def main():
         torch.cuda.synchronize()
         return max_over_ranks(e0.elapsed_time(e1), dev)
 
+    lib_shape = ctx.get_tuning()
+    if args.tune == "auto":
+        ctx.set_xs(d_st, d_ss, d_q)
+        ctx.autotune(tol=TOL, repeats=3)
+    shape = ctx.get_tuning()
     for _ in range(args.warmup):
         step_device()
     sampler = ClockSampler(local)
@@ -311,7 +320,7 @@ def main():
         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel for this
         # workload (FP32), from profiles/k_bcr_solve_flow_precision_srk_slab.md
         kname = "k_bcr_solve_flow_s" if (2 * N) * (2 * N) * esize <= 64 * 1024 else "k_bcr_solve_flow"
-        traffic = NCU_TRAFFIC.get((kname, args.precision))
+        traffic = NCU_TRAFFIC.get((kname, args.precision)) if shape == lib_shape else None
         roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "algorithmic_bytes": byt}
     elif dom == "bcr_invert":
@@ -341,6 +350,10 @@ def main():
                 _, s = c2.solve("fpsa", tol=TOL, out=d_phi)
                 st2.update(s)
 
+            if args.tune == "auto":
+                c2.set_xs(d_st, d_ss, d_q)
+                c2.autotune(tol=TOL, repeats=2)
+
             for _ in range(2):
                 step2()
             ms2 = timed(step2, 3)
@@ -349,7 +362,7 @@ def main():
             secondary[name] = {"laplacian": lap, "precision": prec, "value": whole_job_rate(world, 3, ms2),
                                "unit": "solves/s", "ms_per_step": ms2 / 3, "iterations": st2["iterations"],
                                "setup_ms": st2["setup_ms"], "solve_ms": st2["solve_ms"],
-                               "max_rel_err_vs_oracle": err2}
+                               "max_rel_err_vs_oracle": err2, "tuning": c2.get_tuning()}
             c2.close()
 
     value = whole_job_rate(world, args.steps, ms)
@@ -362,7 +375,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "laplacian": args.laplacian,
                    "tol": TOL, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set (262 MB FP64 factors) larger than L2; no flush"},
+                   "l2": "working set (262 MB FP64 factors) larger than L2; no flush",
+                   "tuning": dict(shape, source=args.tune)},
         "cell_angles_per_s": dev_stats["cell_angles"] * world * args.steps / (ms * 1e-3),
         # the same numerator over the sweep kernels' own event time
         "sweep_cell_angles_per_s": (dev_stats["cell_angles"] * world * args.steps

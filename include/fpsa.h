@@ -214,6 +214,45 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
 int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, double *dJ_dsigma_t,
                  double *dJ_dsigma_s, double *J, int32_t mem, fpsa_stats *stats);
 
+/* ---------------------------------------------------------------------------
+ * Launch shapes and their autotuner. The paper has no counterpart: these choose
+ * how the kernels of one iteration are laid out on the GPU, never what they
+ * compute (every shape gives the same iterates up to rounding order). A zero
+ * field means the library's own choice.
+ */
+typedef struct {
+    int32_t sweep_cells_per_thread; /* transport sweep: consecutive cells a lane carries
+                                       (a segment is 8 such chunks); at least the library's
+                                       choice for the context (its smallest: that bounds the
+                                       segment maps it allocated), at most 1 << 20 */
+    int32_t solve_blocks_per_sm;    /* BCR solve: resident blocks per SM of its cooperative
+                                       grid, 1..4 (capped by the kernel's occupancy) */
+    int32_t solve_max_slices;       /* BCR solve: most row slices one block-row of a level is
+                                       split into, 1, 2 or 4 */
+} fpsa_tuning;
+
+/* The shapes in effect (zero fields resolved to the values used). */
+int fpsa_get_tuning(const fpsa_ctx *ctx, fpsa_tuning *out);
+
+/* Request shapes for the following solves (t == NULL: all library choices).
+ * sweep_cells_per_thread below the context's smallest is raised to it and
+ * solve_blocks_per_sm above the occupancy is lowered to it; other values out of
+ * the ranges above return FPSA_EINVAL and leave the shapes unchanged. */
+int fpsa_set_tuning(fpsa_ctx *ctx, const fpsa_tuning *t);
+
+/* Time fpsa_solve(ctx, opts, ...) on the loaded cross sections for candidate
+ * shapes and keep the fastest: first every (solve_blocks_per_sm, solve_max_slices)
+ * pair with the library's sweep shape, then sweep_cells_per_thread = c, 2c, 4c, 8c
+ * (c the smallest; while the segments per slab still drop) with that solve
+ * shape. Each candidate is solved once untimed and then `repeats` times (>= 1)
+ * between CUDA events on the context stream; its time is the fastest of those.
+ * best (may be NULL) receives the chosen shapes, best_ms (may be NULL) their time
+ * in milliseconds. Requires fpsa_set_xs (FPSA_ESTATE). Any status other than
+ * FPSA_OK from a trial solve ends the search, restores the shapes held before the
+ * call and is returned. Afterwards the context is as after an fpsa_solve (its
+ * moments are kept for fpsa_adjoint). */
+int fpsa_autotune(fpsa_ctx *ctx, const fpsa_opts *opts, int32_t repeats, fpsa_tuning *best, double *best_ms);
+
 /* Release every device buffer of the context (NULL is allowed). */
 void fpsa_destroy(fpsa_ctx *ctx);
 

@@ -6,14 +6,67 @@ per-instance offsets). Groups with different (N, L) run concurrently, each on it
 own CUDA stream from its own host thread (the ctypes calls release the GIL). A
 group whose factor storage would exceed the memory budget is split into waves,
 packed greedily so that each wave's block-inverse storage stays within budget.
-All arithmetic happens in the library; this module only partitions the work.
+Launch shapes per wave can come from the library's autotuner, remembered in a
+JSON cache. All arithmetic happens in the library; this module only partitions
+the work.
 """
 
 import concurrent.futures as cf
+import json
+import os
+import threading
 
 import numpy as np
 
 from . import binding
+
+# fpsa_autotune takes the iteration settings of the solves it times
+_TUNE_KEYS = ("method", "tol", "max_iterations", "inner_iterations", "inner_tol", "check_every", "contraction",
+              "restart")
+
+
+def _bucket(x):
+    """Smallest power of two >= x (x >= 1)."""
+    return 1 << max(0, int(x) - 1).bit_length()
+
+
+class TuningCache:
+    """Launch shapes chosen by fpsa_autotune, keyed by what decides them: (N, L), the
+    right-hand sides, the precision, Laplacian and method, and power-of-two buckets of
+    the instance count and of the largest cell count. Kept in a JSON file when a path
+    is given (read at construction, rewritten by save()); safe to share between the
+    batch driver's threads."""
+
+    def __init__(self, path=None):
+        self.path = path
+        self.entries = {}
+        self._lock = threading.Lock()
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.entries = json.load(f)
+
+    @staticmethod
+    def key(N, L, R, n_instances, max_cells, precision, laplacian, method):
+        return "%s/%s/%s/N%d/L%d/R%d/B%d/K%d" % (precision, laplacian, method, N, L, R, _bucket(n_instances),
+                                                 _bucket(max_cells))
+
+    def get(self, key):
+        with self._lock:
+            e = self.entries.get(key)
+            return dict(e["shapes"]) if e else None
+
+    def put(self, key, shapes, ms):
+        with self._lock:
+            self.entries[key] = {"shapes": dict(shapes), "ms": float(ms)}
+
+    def save(self):
+        if not self.path:
+            return
+        with self._lock:
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.entries, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
 
 
 def factor_bytes(K, N, precision):
@@ -49,12 +102,26 @@ class BatchSolver:
     """Solve a list of problem dicts (see inputs.py; single right-hand side each)."""
 
     def __init__(self, problems, precision="mixed", laplacian="wfd", budget_bytes=32 << 30, device=0,
-                 max_streams=4):
+                 max_streams=4, tuning=None):
+        """tuning: None (the library's launch shapes), or a TuningCache: each wave takes
+        the cached shapes of its key, or runs fpsa_autotune once and stores its choice."""
         self.problems = list(problems)
         self.precision, self.laplacian = precision, laplacian
         self.device = device
         self.waves = plan_waves(self.problems, budget_bytes, precision)
         self.max_streams = max_streams
+        self.tuning = tuning
+
+    def _tune(self, ctx, N, L, probs, solve_kw):
+        key = TuningCache.key(N, L, ctx.R, len(probs), max(p["h"].size for p in probs), self.precision,
+                              self.laplacian, solve_kw.get("method", "fpsa"))
+        shapes = self.tuning.get(key)
+        if shapes is not None:
+            ctx.set_tuning(shapes)
+            return ctx.get_tuning(), "cache"
+        shapes, ms = ctx.autotune(**{k: v for k, v in solve_kw.items() if k in _TUNE_KEYS})
+        self.tuning.put(key, shapes, ms)
+        return shapes, "search"
 
     def _run_wave(self, wave, solve_kw):
         import torch
@@ -65,6 +132,8 @@ class BatchSolver:
         with torch.cuda.stream(stream):
             ctx = binding.context_for(probs, laplacian=self.laplacian, precision=self.precision,
                                       device=self.device, stream=stream.cuda_stream)
+            tuned = (ctx.get_tuning(), "library") if self.tuning is None else self._tune(ctx, N, L, probs,
+                                                                                         solve_kw)
             phi, st = ctx.solve(**solve_kw)
             ctx.close()
         out, off = {}, 0
@@ -72,7 +141,8 @@ class BatchSolver:
             K = p["h"].size
             out[i] = phi[0, off:off + K]
             off += K
-        return out, dict(st, N=N, instances=len(idx), cells=int(sum(p["h"].size for p in probs)))
+        return out, dict(st, N=N, instances=len(idx), cells=int(sum(p["h"].size for p in probs)),
+                         tuning=tuned[0], tuning_source=tuned[1])
 
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, **kw):
         """Returns (list of phi [K][2][L+1] per problem, list of per-wave stats)."""
@@ -84,4 +154,6 @@ class BatchSolver:
                 for i, phi in out.items():
                     results[i] = phi
                 stats.append(st)
+        if self.tuning is not None:
+            self.tuning.save()
         return results, stats

@@ -6,7 +6,8 @@ and the current torch stream, and unpacks results. It raises if the library
 is missing: there is no CPU fallback.
 
 Names follow the C ABI in include/fpsa.h: fpsa_create, fpsa_set_xs,
-fpsa_solve, fpsa_destroy, fpsa_strerror, fpsa_last_error.
+fpsa_solve, fpsa_adjoint, fpsa_get_tuning / fpsa_set_tuning / fpsa_autotune,
+fpsa_destroy, fpsa_strerror, fpsa_last_error.
 """
 
 import ctypes
@@ -53,6 +54,14 @@ class FpsaStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class FpsaTuning(ctypes.Structure):
+    _fields_ = [("sweep_cells_per_thread", ctypes.c_int32), ("solve_blocks_per_sm", ctypes.c_int32),
+                ("solve_max_slices", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 PHASES = ["sweep", "contract", "bcr_solve", "bcr_invert", "bcr_schur", "assemble", "convergence", "residual"]
 
 
@@ -66,7 +75,7 @@ class FpsaProfile(ctypes.Structure):
 
 EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error",
            "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc", "fpsa_adjoint",
-           "fpsa_set_incident"]
+           "fpsa_set_incident", "fpsa_get_tuning", "fpsa_set_tuning", "fpsa_autotune"]
 NOALLOC_MAX_CELL_ANGLES = 131072
 
 _lib = None
@@ -101,6 +110,13 @@ def load():
     lib.fpsa_adjoint.restype = ctypes.c_int
     lib.fpsa_set_incident.argtypes = [vp, dp, i32]
     lib.fpsa_set_incident.restype = ctypes.c_int
+    lib.fpsa_get_tuning.argtypes = [vp, ctypes.POINTER(FpsaTuning)]
+    lib.fpsa_get_tuning.restype = ctypes.c_int
+    lib.fpsa_set_tuning.argtypes = [vp, ctypes.POINTER(FpsaTuning)]
+    lib.fpsa_set_tuning.restype = ctypes.c_int
+    lib.fpsa_autotune.argtypes = [vp, ctypes.POINTER(FpsaOpts), i32, ctypes.POINTER(FpsaTuning),
+                                  ctypes.POINTER(ctypes.c_double)]
+    lib.fpsa_autotune.restype = ctypes.c_int
     lib.fpsa_sweep_noalloc.argtypes = [i32, i32, dp, dp, dp, dp, vp]
     lib.fpsa_sweep_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -243,6 +259,33 @@ class Context:
         if isinstance(out_sigma_s, np.ndarray) and ks is not out_sigma_s:
             out_sigma_s[...] = ks
         return out_sigma_t, out_sigma_s, (J if dJ_dphi is None else None), st.as_dict()
+
+    def get_tuning(self):
+        """Launch shapes in effect (fpsa_get_tuning), as a dict of the fpsa_tuning fields."""
+        t = FpsaTuning()
+        self._check(self._lib.fpsa_get_tuning(self._h, ctypes.byref(t)), "fpsa_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, tuning=None):
+        """Request launch shapes (fpsa_set_tuning): a dict of fpsa_tuning fields (missing or
+        0: the library's choice); None restores every library choice."""
+        if tuning is None:
+            self._check(self._lib.fpsa_set_tuning(self._h, None), "fpsa_set_tuning")
+            return
+        t = FpsaTuning(*(int(tuning.get(k, 0)) for k, _ in FpsaTuning._fields_))
+        self._check(self._lib.fpsa_set_tuning(self._h, ctypes.byref(t)), "fpsa_set_tuning")
+
+    def autotune(self, method="fpsa", tol=1e-10, max_iterations=10000, inner_iterations=0, inner_tol=0.0,
+                 check_every=1, contraction="auto", restart=0, repeats=3):
+        """Time candidate launch shapes on solves with these options and keep the fastest
+        (fpsa_autotune). Returns (shapes dict, milliseconds per solve)."""
+        o = FpsaOpts(METHOD[method], int(max_iterations), float(tol), int(inner_iterations), float(inner_tol),
+                     int(check_every), CONTRACTION[contraction], int(restart))
+        t = FpsaTuning()
+        ms = ctypes.c_double(0.0)
+        self._check(self._lib.fpsa_autotune(self._h, ctypes.byref(o), int(repeats), ctypes.byref(t),
+                                            ctypes.byref(ms)), "fpsa_autotune")
+        return t.as_dict(), ms.value
 
     def profile_enable(self, on=True):
         """Reset the launch counters; with on, bracket every launch with CUDA events."""

@@ -91,6 +91,10 @@ struct fpsa_ctx {
     BcrItem *d_items_all = nullptr;  // levels concatenated, then roots (cooperative solve)
     LevelTable lvt[2] = {};          // per element type (row slicing depends on the vector width)
     int coop_grid[2] = {0, 0};       // cooperative BCR solve grid for float [0] / double [1]
+    int solve_per_sm[2] = {0, 0};    // resident blocks per SM of the cooperative BCR solve (occupancy)
+    int n_sm = 0;
+    int sweep_cpt = 0;               // cells per thread of the segmented sweep in effect
+    fpsa_tuning tuning = {};         // requested launch shapes (0: the library's choice)
     int factor_grid[2] = {0, 0};     // cooperative dataflow factorization grid (0: per-level launches)
     unsigned long long *d_conv = nullptr, *d_growth = nullptr;
     int *d_status = nullptr;
@@ -594,7 +598,7 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 template <typename T>
 int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
     const Geometry &g = ctx->geo;
-    const int nseg = sweep_segments(g), cpt = sweep_cells_per_thread(g);
+    const int cpt = ctx->sweep_cpt, nseg = (g.Kmax + kSegWarps * cpt - 1) / (kSegWarps * cpt);
     const dim3 grid(2 * ((g.N / 2 + 31) / 32), nseg, g.R * g.B);
     {
         Launch L_(ctx, FPSA_PHASE_SWEEP);
@@ -609,6 +613,33 @@ int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
     }
     CK(cudaGetLastError());
     return FPSA_OK;
+}
+
+// Launch shape of the cooperative BCR solve from the requested tuning: the grid
+// (resident blocks per SM, at most the occupancy and 4 by default, times the SMs)
+// and the row slices per item at each level: an item's 2N rows (in vectors of V)
+// are split into S in {1, 2, 4} slices (quadrant-aligned) of >= 2 vectors while the
+// level's units still fit in one pass of the grid, S at most the requested cap.
+// The coarse-step plan does not depend on either.
+void plan_solve_shape(fpsa_ctx *ctx) {
+    const Geometry &g = ctx->geo;
+    const int RC = solve_rc(g.R), nchunk = (g.R + RC - 1) / RC;
+    const int bpsm = ctx->tuning.solve_blocks_per_sm > 0 ? ctx->tuning.solve_blocks_per_sm : 4;
+    const int smax = ctx->tuning.solve_max_slices > 0 ? ctx->tuning.solve_max_slices : 4;
+    for (int e = 0; e < 2; ++e) {
+        ctx->coop_grid[e] = std::min(bpsm, ctx->solve_per_sm[e]) * ctx->n_sm;
+        const int V = e ? VecOf<double>::V : VecOf<float>::V;
+        const int vecs = 2 * g.N / V;
+        LevelTable &lv = ctx->lvt[e];
+        for (int l = 0; l <= g.n_levels; ++l) {
+            const int items = l < g.n_levels ? (int)g.levels[l].size() : g.B;
+            int S = 1;
+            while (2 * S <= smax && vecs % (2 * S) == 0 && vecs / (2 * S) >= 2 &&
+                   (long long)items * nchunk * 2 * S <= ctx->coop_grid[e])
+                S *= 2;
+            lv.slices[l] = S;
+        }
+    }
 }
 
 // F u = rhs by block cyclic reduction over the stored factors: one cooperative
@@ -1395,10 +1426,11 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             CK(raise_smem_limit((const void *)coop_kernel<double>(RC, g.N), (int)solve_smem<double>(g.N, RC)));
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<float>(RC, g.N), kSolveThreads,
                                                              solve_smem<float>(g.N, RC)));
-            ctx->coop_grid[0] = std::max(1, std::min(per_sm, 4)) * nsm;
+            ctx->solve_per_sm[0] = std::max(1, per_sm);
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<double>(RC, g.N), kSolveThreads,
                                                              solve_smem<double>(g.N, RC)));
-            ctx->coop_grid[1] = std::max(1, std::min(per_sm, 4)) * nsm;
+            ctx->solve_per_sm[1] = std::max(1, per_sm);
+            ctx->n_sm = nsm;
             for (int e = 0; e < 2; ++e) {
                 const void *fk = e ? factor_kernel<double>(2 * g.N) : factor_kernel<float>(2 * g.N);
                 const size_t fsm = e ? schur_smem<double>(g.N) : schur_smem<float>(g.N);
@@ -1406,29 +1438,19 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
                 if (fk) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, fk, 512, fsm));
                 ctx->factor_grid[e] = (fk && fper > 0) ? nsm : 0;  // one block per SM
             }
-            // Row slices per item: split an item's 2N rows (in vectors of V) into S in {1, 2, 4}
-            // slices (quadrant-aligned) of >= 2 vectors while the level's units still fit in
-            // one pass of the grid.
             for (int e = 0; e < 2; ++e) {
-                const int V = e ? VecOf<double>::V : VecOf<float>::V;
-                const int vecs = 2 * g.N / V;
                 LevelTable &lv = ctx->lvt[e];
                 lv.n_levels = g.n_levels;
                 lv.n_roots = g.B;
                 plan_coarse(lv, g, e ? (int)sizeof(double) : (int)sizeof(float));
                 int off = 0;
                 for (int l = 0; l <= g.n_levels; ++l) {
-                    const int items = l < g.n_levels ? (int)g.levels[l].size() : g.B;
                     lv.off[l] = off;
-                    off += items;
-                    int S = 1;
-                    const int nchunk = (g.R + RC - 1) / RC;
-                    while (2 * S <= 4 && vecs % (2 * S) == 0 && vecs / (2 * S) >= 2 &&
-                           (long long)items * nchunk * 2 * S <= ctx->coop_grid[e])
-                        S *= 2;
-                    lv.slices[l] = S;
+                    off += l < g.n_levels ? (int)g.levels[l].size() : g.B;
                 }
             }
+            ctx->sweep_cpt = sweep_cells_per_thread(g);
+            plan_solve_shape(ctx);
         }
         if (ctx->precision == FPSA_PRECISION_FP64) return alloc_path(ctx, ctx->p64, true);
         int r2 = alloc_path(ctx, ctx->p64, false);
@@ -1658,6 +1680,104 @@ int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, do
     s.pivot_growth = ctx->pivot_growth;
     s.cell_angles = (double)g.sumK * g.N * g.R * s.sweeps;
     if (stats) *stats = s;
+    return FPSA_OK;
+}
+
+
+int fpsa_get_tuning(const fpsa_ctx *ctx, fpsa_tuning *out) {
+    if (!ctx || !out) return FPSA_EINVAL;
+    const int e = ctx->precision == FPSA_PRECISION_FP64 ? 1 : 0;
+    out->sweep_cells_per_thread = ctx->sweep_cpt;
+    out->solve_blocks_per_sm = ctx->coop_grid[e] / std::max(1, ctx->n_sm);
+    out->solve_max_slices = ctx->tuning.solve_max_slices > 0 ? ctx->tuning.solve_max_slices : 4;
+    return FPSA_OK;
+}
+
+int fpsa_set_tuning(fpsa_ctx *ctx, const fpsa_tuning *t) {
+    if (!ctx) return FPSA_EINVAL;
+    fpsa_tuning r{};
+    if (t) r = *t;
+    if (r.sweep_cells_per_thread < 0 || r.sweep_cells_per_thread > (1 << 20))
+        return fail(ctx, FPSA_EINVAL, "sweep_cells_per_thread outside [0, 1 << 20]");
+    if (r.solve_blocks_per_sm < 0 || r.solve_blocks_per_sm > 4)
+        return fail(ctx, FPSA_EINVAL, "solve_blocks_per_sm outside [0, 4]");
+    if (r.solve_max_slices != 0 && r.solve_max_slices != 1 && r.solve_max_slices != 2 && r.solve_max_slices != 4)
+        return fail(ctx, FPSA_EINVAL, "solve_max_slices not 0, 1, 2 or 4");
+    // the segment maps were allocated for the smallest cells-per-thread (most segments)
+    const int cmin = sweep_cells_per_thread(ctx->geo);
+    ctx->sweep_cpt = std::max(cmin, r.sweep_cells_per_thread);
+    ctx->tuning = r;
+    plan_solve_shape(ctx);
+    return FPSA_OK;
+}
+
+int fpsa_autotune(fpsa_ctx *ctx, const fpsa_opts *opts, int32_t repeats, fpsa_tuning *best, double *best_ms) {
+    if (!ctx) return FPSA_EINVAL;
+    if (repeats < 1) return fail(ctx, FPSA_EINVAL, "repeats < 1");
+    if (!ctx->xs_ready) return fail(ctx, FPSA_ESTATE, "fpsa_set_xs must succeed before fpsa_autotune");
+    CK(cudaSetDevice(ctx->device));
+    const Geometry &g = ctx->geo;
+    struct Scratch {  // released on every return
+        double *phi = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Scratch() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (phi) cudaFree(phi);
+        }
+    } sc;
+    CK(cudaMalloc(&sc.phi, (size_t)g.R * g.sumK * 2 * g.L1 * sizeof(double)));
+    CK(cudaEventCreate(&sc.e0));
+    CK(cudaEventCreate(&sc.e1));
+    const fpsa_tuning saved = ctx->tuning;
+    // fastest of `repeats` timed solves after one untimed solve with shapes t
+    auto trial = [&](const fpsa_tuning &t, double &ms) -> int {
+        int rc = fpsa_set_tuning(ctx, &t);
+        ms = INFINITY;
+        for (int i = 0; rc == FPSA_OK && i <= repeats; ++i) {
+            CK(cudaEventRecord(sc.e0, ctx->stream));
+            rc = fpsa_solve(ctx, opts, sc.phi, nullptr, FPSA_MEM_DEVICE, nullptr);
+            if (rc != FPSA_OK) break;
+            CK(cudaEventRecord(sc.e1, ctx->stream));
+            CK(cudaEventSynchronize(sc.e1));
+            float f = 0.f;
+            CK(cudaEventElapsedTime(&f, sc.e0, sc.e1));
+            if (i > 0) ms = std::min(ms, (double)f);
+        }
+        return rc;
+    };
+    auto give_up = [&](int rc) {
+        const std::string msg = ctx->err;
+        fpsa_set_tuning(ctx, &saved);
+        ctx->err = msg;
+        return rc;
+    };
+    fpsa_tuning bt{};
+    double bms = INFINITY;
+    const int bmax = std::min(4, ctx->solve_per_sm[ctx->precision == FPSA_PRECISION_FP64 ? 1 : 0]);
+    for (int b = 1; b <= bmax; ++b)
+        for (int s = 1; s <= 4; s *= 2) {
+            const fpsa_tuning t{0, b, s};
+            double ms = 0.0;
+            const int rc = trial(t, ms);
+            if (rc != FPSA_OK) return give_up(rc);
+            if (ms < bms) bms = ms, bt = t;
+        }
+    const int cmin = sweep_cells_per_thread(g);
+    auto segments = [&](int c) { return (g.Kmax + kSegWarps * c - 1) / (kSegWarps * c); };
+    for (int k = 1; k <= 3 && segments(cmin << k) < segments(cmin << (k - 1)); ++k) {
+        fpsa_tuning t = bt;
+        t.sweep_cells_per_thread = cmin << k;
+        double ms = 0.0;
+        const int rc = trial(t, ms);
+        if (rc != FPSA_OK) return give_up(rc);
+        if (ms < bms) bms = ms, bt = t;
+    }
+    // keep the winner (the context's moments are those of the last trial solve)
+    const int rc = fpsa_set_tuning(ctx, &bt);
+    if (rc != FPSA_OK) return give_up(rc);
+    if (best) fpsa_get_tuning(ctx, best);
+    if (best_ms) *best_ms = bms;
     return FPSA_OK;
 }
 

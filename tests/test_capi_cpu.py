@@ -91,3 +91,33 @@ def test_boundary_condition_marshalling():
         binding._bc_array(["vacuum"], 2)
     with pytest.raises(KeyError):
         binding._bc_array("periodic", 1)
+
+
+def test_tuning_entry_points_reject_a_null_context(lib):
+    # argument checks come before any CUDA call
+    from paper_1907_13013_gb300 import binding
+    t = binding.FpsaTuning()
+    assert ctypes.sizeof(t) == 12  # three int32 fields, as in include/fpsa.h
+    ms = ctypes.c_double()
+    assert lib.fpsa_get_tuning(None, ctypes.byref(t)) == binding.EINVAL
+    assert lib.fpsa_set_tuning(None, None) == binding.EINVAL
+    assert lib.fpsa_autotune(None, None, 1, ctypes.byref(t), ctypes.byref(ms)) == binding.EINVAL
+
+
+def test_tuning_cache_keys_and_file(tmp_path):
+    from paper_1907_13013_gb300 import batch
+    k = batch.TuningCache.key(64, 63, 1, 3, 1000, "mixed", "wfd", "fpsa")
+    assert k == "mixed/wfd/fpsa/N64/L63/R1/B4/K1024"
+    # the instance count and the largest cell count share a key within a power of two
+    assert batch.TuningCache.key(64, 63, 1, 4, 513, "mixed", "wfd", "fpsa") == k
+    assert batch.TuningCache.key(64, 63, 1, 5, 1000, "mixed", "wfd", "fpsa") != k
+    assert batch.TuningCache.key(16, 15, 1, 1, 1, "fp64", "mpd", "si").endswith("/B1/K1")
+    path = str(tmp_path / "shapes.json")
+    c = batch.TuningCache(path)
+    assert c.get(k) is None
+    shapes = {"sweep_cells_per_thread": 8, "solve_blocks_per_sm": 2, "solve_max_slices": 4}
+    c.put(k, shapes, 3.5)
+    c.save()
+    c2 = batch.TuningCache(path)
+    assert c2.get(k) == shapes and c2.entries[k]["ms"] == 3.5
+    assert batch.TuningCache(None).get(k) is None
