@@ -104,7 +104,9 @@ class BatchSolver:
     def __init__(self, problems, precision="mixed", laplacian="wfd", budget_bytes=32 << 30, device=0,
                  max_streams=4, tuning=None):
         """tuning: None (the library's launch shapes), or a TuningCache: each wave takes
-        the cached shapes of its key, or runs fpsa_autotune once and stores its choice."""
+        the cached shapes of its key; keys missing from the cache are searched first, one
+        wave at a time with nothing else on the GPU (fpsa_autotune times whole solves, so
+        concurrent waves would distort each other's timings), then every wave runs."""
         self.problems = list(problems)
         self.precision, self.laplacian = precision, laplacian
         self.device = device
@@ -112,28 +114,47 @@ class BatchSolver:
         self.max_streams = max_streams
         self.tuning = tuning
 
-    def _tune(self, ctx, N, L, probs, solve_kw):
-        key = TuningCache.key(N, L, ctx.R, len(probs), max(p["h"].size for p in probs), self.precision,
-                              self.laplacian, solve_kw.get("method", "fpsa"))
-        shapes = self.tuning.get(key)
-        if shapes is not None:
-            ctx.set_tuning(shapes)
-            return ctx.get_tuning(), "cache"
-        shapes, ms = ctx.autotune(**{k: v for k, v in solve_kw.items() if k in _TUNE_KEYS})
-        self.tuning.put(key, shapes, ms)
-        return shapes, "search"
+    def _key(self, wave, method):
+        N, L, idx = wave
+        return TuningCache.key(N, L, 1, len(idx), max(self.problems[i]["h"].size for i in idx), self.precision,
+                               self.laplacian, method)
 
-    def _run_wave(self, wave, solve_kw):
+    def _context(self, wave, stream):
+        return binding.context_for([self.problems[i] for i in wave[2]], laplacian=self.laplacian,
+                                   precision=self.precision, device=self.device, stream=stream.cuda_stream)
+
+    def _search(self, solve_kw):
+        """Autotune (serially) one wave of every key the cache lacks; returns the keys searched."""
+        import torch
+        torch.cuda.set_device(self.device)
+        searched = set()
+        for wave in self.waves:
+            key = self._key(wave, solve_kw.get("method", "fpsa"))
+            if key in searched or self.tuning.get(key) is not None:
+                continue
+            stream = torch.cuda.Stream(device=self.device)
+            with torch.cuda.stream(stream):
+                ctx = self._context(wave, stream)
+                shapes, ms = ctx.autotune(**{k: v for k, v in solve_kw.items() if k in _TUNE_KEYS})
+                ctx.close()
+            self.tuning.put(key, shapes, ms)
+            searched.add(key)
+        return searched
+
+    def _run_wave(self, wave, solve_kw, searched):
         import torch
         N, L, idx = wave
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(device=self.device)
         probs = [self.problems[i] for i in idx]
         with torch.cuda.stream(stream):
-            ctx = binding.context_for(probs, laplacian=self.laplacian, precision=self.precision,
-                                      device=self.device, stream=stream.cuda_stream)
-            tuned = (ctx.get_tuning(), "library") if self.tuning is None else self._tune(ctx, N, L, probs,
-                                                                                         solve_kw)
+            ctx = self._context(wave, stream)
+            source = "library"
+            if self.tuning is not None:
+                key = self._key(wave, solve_kw.get("method", "fpsa"))
+                ctx.set_tuning(self.tuning.get(key))
+                source = "search" if key in searched else "cache"
+            tuned = ctx.get_tuning()
             phi, st = ctx.solve(**solve_kw)
             ctx.close()
         out, off = {}, 0
@@ -142,15 +163,16 @@ class BatchSolver:
             out[i] = phi[0, off:off + K]
             off += K
         return out, dict(st, N=N, instances=len(idx), cells=int(sum(p["h"].size for p in probs)),
-                         tuning=tuned[0], tuning_source=tuned[1])
+                         tuning=tuned, tuning_source=source)
 
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, **kw):
         """Returns (list of phi [K][2][L+1] per problem, list of per-wave stats)."""
         solve_kw = dict(method=method, tol=tol, max_iterations=max_iterations, **kw)
         results = [None] * len(self.problems)
         stats = []
+        searched = self._search(solve_kw) if self.tuning is not None else set()
         with cf.ThreadPoolExecutor(max_workers=self.max_streams) as ex:
-            for out, st in ex.map(lambda w: self._run_wave(w, solve_kw), self.waves):
+            for out, st in ex.map(lambda w: self._run_wave(w, solve_kw, searched), self.waves):
                 for i, phi in out.items():
                     results[i] = phi
                 stats.append(st)
