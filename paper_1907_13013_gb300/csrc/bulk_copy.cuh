@@ -1,6 +1,5 @@
-// mbarrier waits and bulk asynchronous copies (cp.async.bulk 1D and 2D tensor
-// tiles, the TMA engine) shared by the tensor-core contractions and the staged-slice
-// BCR solve. Every
+// mbarrier waits and 1D bulk asynchronous copies (cp.async.bulk, the TMA engine)
+// shared by the tensor-core contractions and the staged-slice BCR solve. Every
 // wait is bounded in time; callers record an error when it gives up.
 #pragma once
 
@@ -58,18 +57,6 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
-}
-
-// 2D tiled asynchronous copy global -> shared through a tensor map (the TMA tensor
-// engine): the box at coordinates (x inner, y outer), completing on an mbarrier.
-// x times the element size must be a multiple of 16 bytes; the shared-memory
-// destination is 128-byte aligned; tmap is a __grid_constant__ kernel parameter.
-__device__ __forceinline__ void tensor_copy_2d_g2s(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

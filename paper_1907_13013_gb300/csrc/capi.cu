@@ -17,8 +17,6 @@
 #include <string>
 #include <vector>
 
-#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
-
 #include "fpsa_internal.h"
 #include "kernels.cuh"
 #include "tc_contract.cuh"
@@ -50,7 +48,6 @@ struct PathBuffers {
     T *Q = nullptr;                          // [R][sumK][2][N]
     T *coef = nullptr;                       // [sumK][6][N]
     T *A = nullptr, *Bc = nullptr, *Cc = nullptr;
-    CUtensorMap tmap{};                      // A^{-1} tiles of the BCR solve (bcr_tile_slices > 0)
     T *phi = nullptr, *phi_half = nullptr, *q = nullptr, *psi = nullptr, *rhs = nullptr;
     T *qang = nullptr;                       // MIXED inner path: nodal residual source [R][sumK][2][N]
     T *ybuf = nullptr;                       // BCR solve: intermediate y, then the solution [R][sumK][2N]
@@ -264,15 +261,15 @@ int solve_rc(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
 // A^{-1} slice fits, the staged slice buffer
 template <typename T>
 size_t solve_smem(int N, int RC) {
-    const size_t off = (size_t)bcr_slice_offset_values<T>(N, kSolveThreads, RC) * sizeof(T) + kSliceAlignPad;
-    if (bcr_slice_staged(N, (int)sizeof(T))) return off + (size_t)(2 * N) * (2 * N) * sizeof(T);
-    if (bcr_tile_slices(N, (int)sizeof(T)) > 0) return off + kSolveStageBytes;
+    if (bcr_slice_staged(N, (int)sizeof(T)))
+        return (size_t)bcr_slice_offset_values<T>(N, kSolveThreads, RC) * sizeof(T) +
+               (size_t)(2 * N) * (2 * N) * sizeof(T);
     return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V, RC, (int)sizeof(T)) * sizeof(T);
 }
 
 template <typename T>
 const void *coop_kernel(int RC, int N) {
-    if (bcr_slice_staged(N, (int)sizeof(T)) || bcr_tile_slices(N, (int)sizeof(T)) > 0) {
+    if (bcr_slice_staged(N, (int)sizeof(T))) {
         switch (RC) {
             case 8: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 8>;
             case 4: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 4>;
@@ -306,38 +303,6 @@ bool cta_invertible(int n) {
     return n == 32 || n == 64 || n == 128 || invert_smem<T>(n / 2) <= kSmemLimit;
 }
 
-// Tensor map of the transposed inverses, A viewed as the 2D array [sumK * 2N][2N]
-// (rows contiguous), with boxes of nr = 2N / S rows x N columns (S = bcr_tile_slices),
-// for the tiled staging of the BCR solve; nothing to do when the solve does not tile.
-// The encoder is the driver's, looked up once per process.
-template <typename T>
-int encode_tile_map(fpsa_ctx *ctx, PathBuffers<T> &p) {
-    const Geometry &g = ctx->geo;
-    const int S = bcr_tile_slices(g.N, (int)sizeof(T));
-    if (S == 0) return FPSA_OK;
-    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            fn = nullptr;
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }();
-    if (!encode) return fail(ctx, FPSA_ECUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
-    const int n2 = 2 * g.N, nr = n2 / S;
-    const cuuint64_t dims[2] = {(cuuint64_t)n2, (cuuint64_t)g.sumK * n2};
-    const cuuint64_t strides[1] = {(cuuint64_t)n2 * sizeof(T)};
-    const cuuint32_t box[2] = {(cuuint32_t)nr, (cuuint32_t)g.N};
-    const cuuint32_t elem_strides[2] = {1, 1};
-    const CUresult r =
-        encode(&p.tmap, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-               (void *)p.A, dims, strides, box, elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(ctx, FPSA_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    return FPSA_OK;
-}
-
 template <typename T>
 int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     const Geometry &g = ctx->geo;
@@ -356,7 +321,6 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     if (full) {
         CK(dalloc(ctx, &p.coef, (size_t)g.sumK * 6 * N));
         CK(dalloc(ctx, &p.A, (size_t)g.sumK * 4 * N * N));
-        if (const int rc = encode_tile_map(ctx, p)) return rc;
         CK(dalloc(ctx, &p.Bc, (size_t)g.n_slots * h2 * h2));
         CK(dalloc(ctx, &p.Cc, (size_t)g.n_slots * h2 * h2));
         CK(dalloc(ctx, &p.phi_half, ang));
@@ -655,9 +619,8 @@ int sweep(fpsa_ctx *ctx, PathBuffers<T> &p, const T *q, T *psi, const T *inc) {
 // (resident blocks per SM, at most the occupancy and 4 by default, times the SMs)
 // and the row slices per item at each level: an item's 2N rows (in vectors of V)
 // are split into S in {1, 2, 4} slices (quadrant-aligned) of >= 2 vectors while the
-// level's units still fit in one pass of the grid, S at most the requested cap
-// (tiled staging: the tile's S at every level, whatever the cap). The coarse-step
-// plan does not depend on either.
+// level's units still fit in one pass of the grid, S at most the requested cap.
+// The coarse-step plan does not depend on either.
 void plan_solve_shape(fpsa_ctx *ctx) {
     const Geometry &g = ctx->geo;
     const int RC = solve_rc(g.R), nchunk = (g.R + RC - 1) / RC;
@@ -668,13 +631,8 @@ void plan_solve_shape(fpsa_ctx *ctx) {
         const int V = e ? VecOf<double>::V : VecOf<float>::V;
         const int vecs = 2 * g.N / V;
         LevelTable &lv = ctx->lvt[e];
-        const int tiled = bcr_tile_slices(g.N, e ? (int)sizeof(double) : (int)sizeof(float));
         for (int l = 0; l <= g.n_levels; ++l) {
             const int items = l < g.n_levels ? (int)g.levels[l].size() : g.B;
-            if (tiled) {  // the tensor map's box fixes the slices
-                lv.slices[l] = tiled;
-                continue;
-            }
             int S = 1;
             while (2 * S <= smax && vecs % (2 * S) == 0 && vecs / (2 * S) >= 2 &&
                    (long long)items * nchunk * 2 * S <= ctx->coop_grid[e])
@@ -702,10 +660,9 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     long long nzero = (long long)(2 * n);
     ctx->flow_parity ^= 1;
     const T *G = p.G;
-    void *args[] = {(void *)&A,   (void *)&Bc,   (void *)&Cc,  (void *)&items, (void *)&lv,
-                    (void *)&rhs, (void *)&Y,    (void *)&N,   (void *)&sumK,  (void *)&R,
-                    (void *)&cnt, (void *)&done, (void *)&err, (void *)&G,     (void *)&zero_next,
-                    (void *)&nzero, (void *)&p.tmap};
+    void *args[] = {(void *)&A,   (void *)&Bc,  (void *)&Cc,   (void *)&items, (void *)&lv,
+                    (void *)&rhs, (void *)&Y,   (void *)&N,    (void *)&sumK,  (void *)&R,
+                    (void *)&cnt, (void *)&done, (void *)&err, (void *)&G,     (void *)&zero_next, (void *)&nzero};
     const int grid = ctx->coop_grid[sizeof(T) == 8 ? 1 : 0];
     const int RC = solve_rc(R);
     const void *kern = coop_kernel<T>(RC, N);

@@ -16,7 +16,6 @@
 #pragma once
 
 #include <cooperative_groups.h>
-#include <cuda.h>  // CUtensorMap (the tensor map itself is encoded by the host driver)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -2039,8 +2038,7 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ 
                                                        LevelTable lv, T *rhs, T *Y, int N, int sumK, int R, int *cnt,
                                                        int *done, int *err,
                                                        const T *__restrict__ G /* coarse step: staged only */,
-                                                       int *zero_next, long long nzero,
-                                                       const __grid_constant__ CUtensorMap /* staged only */) {
+                                                       int *zero_next, long long nzero) {
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nzero; i += (long long)gridDim.x * NT)
         zero_next[i] = 0;
     tc::grid_dependency_wait();
@@ -2112,22 +2110,6 @@ __host__ __device__ constexpr bool bcr_slice_staged(int N, int esize) {
     return (size_t)(2 * N) * (2 * N) * esize <= (size_t)kSolveStageBytes && (2 * N * esize) % 16 == 0;
 }
 
-// A cell's A^{-1} too large for the slice buffer whose row slices fit it: S (2 or 4,
-// the smallest that fits) slices of nr = 2N / S rows, each a whole number of 16-byte
-// vectors (nr * esize % 16 == 0, at least two vectors, vectors split evenly), are
-// staged as 2D tiles of the transposed inverse (boxes of nr rows x N columns, at most
-// 256 x 256) by the TMA tensor engine; every level then uses S slices. 0: no tiling.
-__host__ __device__ constexpr int bcr_tile_slices(int N, int esize) {
-    if (bcr_slice_staged(N, esize) || N > 256) return 0;
-    for (int S = 2; S <= 4; S *= 2) {
-        const int nr = 2 * N / S, vecs = 2 * N * esize / 16;
-        if ((size_t)(2 * N) * nr * esize <= (size_t)kSolveStageBytes && (nr * esize) % 16 == 0 && vecs % S == 0 &&
-            vecs / S >= 2)
-            return S;
-    }
-    return 0;
-}
-
 // offset (in values) of the slice buffer: after the unit scratch, 16-byte aligned
 // (the staged-slice kernel double-buffers the coupling blocks: one more coupling area)
 template <typename T>
@@ -2138,9 +2120,6 @@ __host__ __device__ constexpr int bcr_slice_offset_values(int N, int NT, int RC)
             15) /
            16 * 16 / (int)sizeof(T);
 }
-// the slice buffer starts at the first 128-byte boundary (shared-memory address) at
-// or after that offset (tensor tiles land on 128-byte boundaries): room for the pad
-constexpr int kSliceAlignPad = 128;
 
 // offset (in values) of the first coupling area in a solve block's scratch
 __host__ __device__ constexpr int bcr_cbuf_offset_values(int N, int NT, int V, int RC) {
@@ -2169,33 +2148,25 @@ __device__ __forceinline__ void unit_coupling_sources(const BcrItem &it, int sl,
 // 2N columns, backward: columns N/2 .. 3N/2 - 1, one contiguous block either way)
 // and, with cb, its coupling blocks into cb[0, hh) and cb[hh, 2 hh), by bulk
 // asynchronous copies (the TMA engine) that complete one phase of *bar. A unit with
-// a row slice reads its rows of the block. Tiled (tmap != NULL): only the unit's
-// slice, As[k][r] for its nr = 2N / S rows, as one (backward) or two (forward) 2D
-// tiles of nr rows x N columns of the tensor [cell * 2N + k][row]. Issued by one warp (the block's last:
+// a row slice reads its rows of the block. Issued by one warp (the block's last:
 // thread 0, which fences the unit's signal, is not held up by the copies). Every
 // address and size is a multiple of 16 bytes (rows of 2N values of whole 16-byte
 // vectors; N/2 x N/2 coupling blocks staged only when whole 16-byte chunks).
 template <typename T>
 __device__ __forceinline__ void stage_unit_bulk(const T *__restrict__ A, const T *__restrict__ Bc,
                                                 const T *__restrict__ Cc, const BcrItem &it, int sl, int S, bool bwd,
-                                                int N, T *As, T *cb, uint64_t *bar, const void *tmap) {
+                                                int N, T *As, T *cb, uint64_t *bar) {
     const int lane = threadIdx.x & 31;
-    const int n2 = 2 * N, h2 = N / 2, nk = bwd ? N : n2, nr = tmap ? n2 / S : n2;
+    const int n2 = 2 * N, h2 = N / 2, nk = bwd ? N : n2;
     const T *m0 = nullptr, *m1 = nullptr;
     if (cb) unit_coupling_sources(it, sl, S, bwd, N, Bc, Cc, m0, m1);
-    const uint32_t hb = (uint32_t)(h2 * h2 * sizeof(T)), sb = (uint32_t)((size_t)nk * nr * sizeof(T));
+    const uint32_t hb = (uint32_t)(h2 * h2 * sizeof(T)), sb = (uint32_t)((size_t)nk * n2 * sizeof(T));
     tc::fence_async_smem();  // the buffers' earlier generic reads before the copies' writes
     if (lane == 0) {
         tc::mbar_arrive_expect_tx(bar, sb + (m0 ? hb : 0u) + (m1 ? hb : 0u));
         if (m0) tc::bulk_copy_g2s(cb, m0, hb, bar);
         if (m1) tc::bulk_copy_g2s(cb + h2 * h2, m1, hb, bar);
-        if (tmap) {
-            const int y0 = it.cell * n2 + (bwd ? h2 : 0);
-            tc::tensor_copy_2d_g2s(As, tmap, sl * nr, y0, bar);
-            if (!bwd) tc::tensor_copy_2d_g2s(As + (size_t)N * nr, tmap, sl * nr, y0 + N, bar);
-        } else {
-            tc::bulk_copy_g2s(As, A + (size_t)it.cell * n2 * n2 + (bwd ? (size_t)h2 * n2 : 0), sb, bar);
-        }
+        tc::bulk_copy_g2s(As, A + (size_t)it.cell * n2 * n2 + (bwd ? (size_t)h2 * n2 : 0), sb, bar);
     }
 }
 
@@ -2244,19 +2215,15 @@ __device__ __forceinline__ int smem_matvec(const T *As, int lda, int nr, int nk,
 // Forward / backward unit whose A^{-1} slice (into As) and coupling blocks (mB, mC:
 // shared-memory copies, or global memory when not staged; NULL where absent) are in
 // flight; wait_copies() returns once they have landed, next_copy() issues the copies
-// for the block's next unit. As holds the whole column block (rows at row0, leading
-// dimension 2N) or, tiled, only the unit's rows (leading dimension nr).
+// for the block's next unit.
 template <typename T, int NT, int RC, typename WaitCopies, typename NextCopy>
 __device__ __forceinline__ void flow_fwd_unit_s(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc,
                                                 int sl, int S, T *rhs, T *Y, int N, int sumK, T *sm, const T *As,
-                                                bool tiled, const FlowSync *fs, WaitCopies wait_copies,
-                                                NextCopy next_copy) {
+                                                const FlowSync *fs, WaitCopies wait_copies, NextCopy next_copy) {
     const int n2 = 2 * N, h2 = N / 2;
     T *rs = sm, *ys = sm + RC * n2, *part = ys + RC * n2 + RC * N;
     const size_t rstride = (size_t)sumK * n2;
     const int nr = n2 / S, row0 = sl * nr;
-    const T *Au = tiled ? As : As + row0;
-    const int lda = tiled ? nr : n2;
     flow_wait(fs);
     for (int i = threadIdx.x; i < RC * n2; i += NT) {
         const int rc = i / n2, k = i - rc * n2;
@@ -2264,7 +2231,7 @@ __device__ __forceinline__ void flow_fwd_unit_s(const T *mB, const T *mC, const 
     }
     wait_copies();
     __syncthreads();
-    const int KS = smem_matvec<T, NT, RC>(Au, lda, nr, n2, rs, n2, part);
+    const int KS = smem_matvec<T, NT, RC>(As + row0, n2, nr, n2, rs, n2, part);
     __syncthreads();
     next_copy();  // the slice buffer is free
     for (int idx = threadIdx.x; idx < RC * nr; idx += NT) {
@@ -2284,14 +2251,11 @@ __device__ __forceinline__ void flow_fwd_unit_s(const T *mB, const T *mC, const 
 template <typename T, int NT, int RC, typename WaitCopies, typename NextCopy>
 __device__ __forceinline__ void flow_bwd_unit_s(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc,
                                                 int sl, int S, T *Y, int N, int sumK, T *sm, const T *As,
-                                                bool tiled, const FlowSync *fs, WaitCopies wait_copies,
-                                                NextCopy next_copy) {
+                                                const FlowSync *fs, WaitCopies wait_copies, NextCopy next_copy) {
     const int n2 = 2 * N, h2 = N / 2;
     T *gv = sm, *g = sm + RC * N, *part = sm + RC * (5 * N);
     const size_t rstride = (size_t)sumK * n2;
     const int nr = n2 / S, row0 = sl * nr;
-    const T *Au = tiled ? As : As + row0;
-    const int lda = tiled ? nr : n2;
     flow_wait(fs);
     for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
         const int rc = idx / N, k = idx - rc * N;
@@ -2309,7 +2273,7 @@ __device__ __forceinline__ void flow_bwd_unit_s(const T *mB, const T *mC, const 
     if (it.right < 0)
         for (int idx = threadIdx.x; idx < RC * h2; idx += NT) g[(idx / h2) * N + h2 + idx % h2] = T(0);
     __syncthreads();
-    const int KS = smem_matvec<T, NT, RC>(Au, lda, nr, N, g, N, part);
+    const int KS = smem_matvec<T, NT, RC>(As + row0, n2, nr, N, g, N, part);
     __syncthreads();
     next_copy();
     for (int idx = threadIdx.x; idx < nrc * nr; idx += NT) {
@@ -2372,16 +2336,14 @@ __device__ __forceinline__ void flow_coarse_unit(int u, const LevelTable &lv, co
 // The dataflow BCR solve with staged slices (same unit order, counters and waits as
 // k_bcr_solve_flow; with a coarse step, the levels from coarse_level up and the
 // root are one phase of coarse units between the forward and backward levels below
-// it). Shared memory: the unit scratch, then the slice buffer at the next 128-byte
-// boundary: a unit's whole column block, or (bcr_tile_slices > 0) its row slice
-// arriving as 2D tiles through tmap, the tensor map of the transposed inverses.
+// it). Shared memory: the unit scratch, then the slice buffer.
 template <typename T, int NT, int RC>
 __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict__ A, const T *__restrict__ Bc,
                                                             const T *__restrict__ Cc,
                                                             const BcrItem *__restrict__ items, LevelTable lv, T *rhs,
                                                             T *Y, int N, int sumK, int R, int *cnt, int *done,
                                                             int *err, const T *__restrict__ G, int *zero_next,
-                                                            long long nzero, const __grid_constant__ CUtensorMap tmap) {
+                                                            long long nzero) {
     static_assert(NT >= 64 && NT % 32 == 0, "copies and signals leave warp 0 free");
     // the next solve's counters (the other half of the double-buffered pair) start at zero
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nzero; i += (long long)gridDim.x * NT)
@@ -2390,11 +2352,6 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
     __shared__ __align__(8) uint64_t s_bar;  // one phase per unit: its slice and couplings landed
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *As = sm + bcr_slice_offset_values<T>(N, NT, RC);
-    As = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(As) +
-                               ((kSliceAlignPad - (tc::smem_u32(As) & (kSliceAlignPad - 1))) & (kSliceAlignPad - 1)));
-    // tiled slices (A^{-1} larger than the slice buffer): the tensor map is in use
-    const bool tiled = bcr_tile_slices(N, (int)sizeof(T)) > 0;
-    const void *tm = tiled ? reinterpret_cast<const void *>(&tmap) : nullptr;
     // two coupling areas, alternating between the block's consecutive units (the next
     // unit's couplings are requested with its slice while this unit still uses its own)
     const int hh = (N / 2) * (N / 2);
@@ -2456,7 +2413,7 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                 tc::bulk_copy_g2s(As, G + (size_t)q.item * rpu * n, bytes, &s_bar);
             }
         } else {
-            stage_unit_bulk<T>(A, Bc, Cc, itq, q.sl, q.S, phase_bwd(q.ph), N, As, cbq, &s_bar, tm);
+            stage_unit_bulk<T>(A, Bc, Cc, itq, q.sl, q.S, phase_bwd(q.ph), N, As, cbq, &s_bar);
         }
     };
     Pos cur{0, 0, 0, 0, 0, 0, 0, false};
@@ -2513,8 +2470,8 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                 if (it.right >= 0 && row0 + nr == n2) fs.sig0 = cnt_c + it.right;
                 if (it.left >= 0 && row0 == 0) fs.sig1 = cnt_c + it.left;
                 if (it.left < 0) fs.sig2 = done_c + it.cell;
-                flow_fwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, tiled, &fs,
-                                           wait_copies, next_copy);
+                flow_fwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, &fs, wait_copies,
+                                           next_copy);
             } else {
                 const int step = 1 << it.level;
                 fs.wait0 = done_c + it.left;
@@ -2524,8 +2481,8 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                     fs.want1 = done_want(bcr_cell_level(it.local + step, nl));
                 }
                 fs.sig0 = done_c + it.cell;
-                flow_bwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, Y, N, sumK, sm, As, tiled, &fs,
-                                           wait_copies, next_copy);
+                flow_bwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, Y, N, sumK, sm, As, &fs, wait_copies,
+                                           next_copy);
             }
         }
         if (stalled) {
