@@ -21,14 +21,24 @@ import numpy as np
 def gauss_legendre(N):
     """S_N Gauss-Legendre nodes and weights, mu ascending, sum(w) = 2 (Sec. 2.2).
 
-    Uses numpy's Gauss-Legendre routine as a library primitive.
-    Pinned by: exactness for polynomials of degree <= 2N-1 (tests P1).
+    Nodes: the roots of P_N from numpy's Gauss-Legendre routine (a library
+    primitive). Weights: the closed form of the Gauss-Legendre rule at those nodes,
+    w_n = 2 / ((1 - mu_n^2) P_N'(mu_n)^2), with P_N'(x) = N (P_{N-1} - x P_N) / (1 - x^2)
+    from the recurrence below and 1 - x^2 formed as (1 - x)(1 + x), which keeps its
+    relative accuracy next to x = +-1 (numpy's own weights are rescaled
+    approximations, off by up to 2e-11 relative at N = 256).
+    Pinned by: exactness for polynomials of degree <= 2N-1, and nodes and weights
+    against a 50-digit Newton solution of P_N = 0 (tests P1).
     """
     if N < 2 or N % 2:
         raise ValueError("N must be even and >= 2")
-    mu, w = np.polynomial.legendre.leggauss(N)
-    order = np.argsort(mu)
-    return mu[order].astype(np.float64), w[order].astype(np.float64)
+    mu, _ = np.polynomial.legendre.leggauss(N)
+    mu = np.sort(mu).astype(np.float64)
+    P = legendre_table(mu, N)
+    one_minus_x2 = (1.0 - mu) * (1.0 + mu)
+    dP = N * (P[N - 1] - mu * P[N]) / one_minus_x2
+    w = 2.0 / (one_minus_x2 * dP * dP)
+    return mu, w
 
 
 def legendre_table(x, lmax):

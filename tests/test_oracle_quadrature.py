@@ -94,3 +94,38 @@ def test_wfd_consistent_with_continuous_operator():
         inner = np.abs(mu) < 0.8
         errs.append(np.abs((W @ P2 + 6 * P2)[inner]).max())
     assert errs[0] > errs[1] > errs[2] and errs[2] < 0.05
+
+
+@pytest.mark.parametrize("N", [2, 16, 64, 256])
+def test_gauss_legendre_against_50_digit_roots(N):
+    # P1: the S_N rule of Sec. 2.2 is the N-point Gauss-Legendre rule: nodes are the
+    # roots of P_N, weights 2 / ((1 - x^2) P_N'(x)^2). Solved here independently by
+    # Newton's method in 50-digit arithmetic (mpmath), from the cosine initial guess.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+
+    def p_and_dp(x):
+        p0, p1 = mp.mpf(1), x
+        for k in range(2, N + 1):
+            p0, p1 = p1, ((2 * k - 1) * x * p1 - (k - 1) * p0) / k
+        return p1, N * (x * p1 - p0) / (x * x - 1)
+
+    mu, w = qd.gauss_legendre(N)
+    for i in range(N // 2):
+        x = mp.cos(mp.pi * (i + mp.mpf(3) / 4) / (N + mp.mpf(1) / 2))  # (i+1)-th largest root
+        for _ in range(60):
+            p, dp = p_and_dp(x)
+            dx = p / dp
+            x -= dx
+            if abs(dx) < mp.mpf(10) ** -45:
+                break
+        p, dp = p_and_dp(x)
+        wx = 2 / ((1 - x * x) * dp * dp)
+        j = N - 1 - i
+        # nodes: the nearest doubles, to within an ulp
+        dx = mp.mpf(mu[j]) - x
+        assert abs(dx) <= 1.2e-16 and mu[i] == -mu[j], (i, float(x), mu[j])
+        # weights: the exact weight, up to its first-order change at the rounded node
+        # (|w'/w| = 2|x| / (1 - x^2) at a root of P_N) and the recurrence's rounding
+        bound = abs(2 * x * dx / (1 - x * x)) + 4 * N * 2.2e-16
+        assert abs(mp.mpf(w[j]) / wx - 1) <= bound and w[i] == w[j], (i, float(wx), w[j], float(bound))
