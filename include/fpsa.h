@@ -26,8 +26,9 @@
  *       q       [R][sumK][2][L+1]      phi     [R][sumK][2][L+1]
  *     q holds source MOMENTS: the angular source is
  *     q_n = sum_l (2l+1)/2 P_l(mu_n) q_l, so an isotropic scalar source S is q_0 = S.
- *   - Boundary conditions: vacuum at both edges (Eq. trans-equation-bc with
- *     psi_L = psi_R = 0).
+ *   - Boundary conditions, per instance and edge (fpsa_desc.bc): vacuum with a
+ *     given incoming flux (zero unless set by fpsa_set_incident; Eq.
+ *     trans-equation-bc) or reflective.
  *   - Ownership: the caller owns every pointer it passes; the library copies
  *     inputs into device buffers it owns and writes results into the caller's
  *     buffers before returning (the context stream is synchronised).
@@ -252,6 +253,20 @@ int fpsa_set_tuning(fpsa_ctx *ctx, const fpsa_tuning *t);
  * call and is returned. Afterwards the context is as after an fpsa_solve (its
  * moments are kept for fpsa_adjoint). */
 int fpsa_autotune(fpsa_ctx *ctx, const fpsa_opts *opts, int32_t repeats, fpsa_tuning *best, double *best_ms);
+
+/* The S_N tables a context builds, for N = n_ordinates and L = n_moments - 1
+ * (same limits as fpsa_create), host-side only (no CUDA call; Sec. 2.2):
+ *   mu [N], w [N]   Gauss-Legendre ordinates (ascending) and weights: the roots of
+ *                   P_N and 2 / ((1 - mu^2) P_N'(mu)^2)
+ *   D  [L+1][N]     D[l][n] = w_n P_l(mu_n)            (Eq. phi-mom)
+ *   M  [N][L+1]     M[n][l] = (2l+1)/2 P_l(mu_n)       (Eq. treq)
+ *   A  [N][N]       the angular Laplacian: MPD F = M diag(-l(l+1)) D over l < N
+ *                   (Eq. fp-mpd) or WFD W (Eq. w_wfd), per `laplacian`
+ * Every output is a caller-owned host array; any may be NULL (not written).
+ * Returns FPSA_EINVAL for N odd, < 2 or > FPSA_MAX_ORDINATES, n_moments outside
+ * [1, N] or an unknown laplacian. */
+int fpsa_tables(int32_t n_ordinates, int32_t n_moments, int32_t laplacian, double *mu, double *w, double *D,
+                double *M, double *A);
 
 /* Release every device buffer of the context (NULL is allowed). */
 void fpsa_destroy(fpsa_ctx *ctx);

@@ -75,7 +75,7 @@ class FpsaProfile(ctypes.Structure):
 
 EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error",
            "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc", "fpsa_adjoint",
-           "fpsa_set_incident", "fpsa_get_tuning", "fpsa_set_tuning", "fpsa_autotune"]
+           "fpsa_set_incident", "fpsa_get_tuning", "fpsa_set_tuning", "fpsa_autotune", "fpsa_tables"]
 NOALLOC_MAX_CELL_ANGLES = 131072
 
 _lib = None
@@ -117,6 +117,8 @@ def load():
     lib.fpsa_autotune.argtypes = [vp, ctypes.POINTER(FpsaOpts), i32, ctypes.POINTER(FpsaTuning),
                                   ctypes.POINTER(ctypes.c_double)]
     lib.fpsa_autotune.restype = ctypes.c_int
+    lib.fpsa_tables.argtypes = [i32, i32, i32, dp, dp, dp, dp, dp]
+    lib.fpsa_tables.restype = ctypes.c_int
     lib.fpsa_sweep_noalloc.argtypes = [i32, i32, dp, dp, dp, dp, vp]
     lib.fpsa_sweep_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -307,6 +309,18 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def tables(N, L, laplacian="mpd"):
+    """The library's S_N tables (fpsa_tables; host only, no GPU): dict of mu [N], w [N],
+    D [L+1][N], M [N][L+1] and the angular Laplacian A [N][N]."""
+    out = {"mu": np.zeros(N), "w": np.zeros(N), "D": np.zeros((L + 1, N)), "M": np.zeros((N, L + 1)),
+           "A": np.zeros((N, N))}
+    rc = load().fpsa_tables(int(N), int(L + 1), LAPLACIAN[laplacian], *(out[k].ctypes.data for k in
+                                                                     ("mu", "w", "D", "M", "A")))
+    if rc != OK:
+        raise FpsaError(rc, "fpsa_tables (N=%d, L=%d)" % (N, L))
+    return out
 
 
 def sweep_noalloc(N, h, sigma_t, q, psi, stream=None):

@@ -1684,6 +1684,23 @@ int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, do
 }
 
 
+int fpsa_tables(int32_t n_ordinates, int32_t n_moments, int32_t laplacian, double *mu, double *w, double *D,
+                double *M, double *A) {
+    const int N = n_ordinates, L1 = n_moments;
+    if (N < 2 || N % 2 || N > FPSA_MAX_ORDINATES || L1 < 1 || L1 > N) return FPSA_EINVAL;
+    if (laplacian != FPSA_LAPLACIAN_MPD && laplacian != FPSA_LAPLACIAN_WFD) return FPSA_EINVAL;
+    Tables t;
+    build_tables(N, L1, laplacian, t);
+    if (mu) std::copy(t.mu.begin(), t.mu.end(), mu);
+    if (w) std::copy(t.w.begin(), t.w.end(), w);
+    if (D) std::copy(t.D.begin(), t.D.begin() + (size_t)L1 * N, D);  // rows l < L+1
+    if (M)
+        for (int n = 0; n < N; ++n)
+            for (int l = 0; l < L1; ++l) M[(size_t)n * L1 + l] = t.M[(size_t)n * N + l];
+    if (A) std::copy(t.Afp.begin(), t.Afp.end(), A);
+    return FPSA_OK;
+}
+
 int fpsa_get_tuning(const fpsa_ctx *ctx, fpsa_tuning *out) {
     if (!ctx || !out) return FPSA_EINVAL;
     const int e = ctx->precision == FPSA_PRECISION_FP64 ? 1 : 0;

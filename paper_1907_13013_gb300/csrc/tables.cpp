@@ -21,8 +21,8 @@ static void legendre_and_derivative(int N, double x, double *pn, double *dpn) {
         p0 = p1;
         p1 = p2;
     }
-    *pn = p1;                                    // P_N
-    *dpn = N * (x * p1 - p0) / (x * x - 1.0);    // P_N' from P_N, P_{N-1}
+    *pn = p1;                                          // P_N
+    *dpn = N * (p0 - x * p1) / ((1.0 - x) * (1.0 + x));  // P_N' from P_N, P_{N-1}
 }
 
 void build_tables(int N, int L1, int laplacian, Tables &t) {
@@ -42,7 +42,8 @@ void build_tables(int N, int L1, int laplacian, Tables &t) {
         }
         double p, dp;
         legendre_and_derivative(N, x, &p, &dp);
-        double wi = 2.0 / ((1.0 - x * x) * dp * dp);
+        // 1 - x^2 as (1 - x)(1 + x): no cancellation next to x = 1
+        double wi = 2.0 / ((1.0 - x) * (1.0 + x) * dp * dp);
         // x > 0 is the (i+1)-th largest root; store ascending and mirrored
         t.mu[N - 1 - i] = x;
         t.mu[i] = -x;

@@ -121,3 +121,31 @@ def test_tuning_cache_keys_and_file(tmp_path):
     c2 = batch.TuningCache(path)
     assert c2.get(k) == shapes and c2.entries[k]["ms"] == 3.5
     assert batch.TuningCache(None).get(k) is None
+
+
+@pytest.mark.parametrize("N,L", [(2, 1), (16, 15), (16, 7), (64, 63), (256, 255)])
+@pytest.mark.parametrize("lap", ["mpd", "wfd"])
+def test_library_tables_match_the_oracle(lib, N, L, lap):
+    # host logic of the library (fpsa_tables: no GPU): its Gauss-Legendre rule, D, M
+    # and angular Laplacian against the oracle's, which is pinned to 50-digit roots
+    from oracle import quadrature as qd
+    from paper_1907_13013_gb300 import binding
+    t = binding.tables(N, L, lap)
+    mu, w = qd.gauss_legendre(N)
+    assert np.all(np.abs(t["mu"] - mu) <= 2.3e-16)
+    # weights: first-order change at a node one ulp apart, plus the recurrences' rounding
+    bound = 2 * np.abs(mu) * 2.3e-16 / ((1 - mu) * (1 + mu)) + 8 * N * 2.2e-16
+    assert np.all(np.abs(t["w"] / w - 1) <= bound), np.max(np.abs(t["w"] / w - 1) / bound)
+    D = qd.moment_operator(mu, w, L)
+    M = qd.expansion_operator(mu, L)
+    assert np.abs(t["D"] - D).max() <= 1e-13 * np.abs(D).max()
+    assert np.abs(t["M"] - M).max() <= 1e-13 * np.abs(M).max()
+    A = qd.angular_laplacian(mu, w, lap)
+    assert np.abs(t["A"] - A).max() <= 1e-11 * np.abs(A).max()
+
+
+def test_library_tables_reject_bad_sizes(lib):
+    from paper_1907_13013_gb300 import binding
+    for N, L1, lap in ((3, 1, 0), (0, 1, 0), (258, 1, 0), (16, 0, 0), (16, 17, 0), (16, 4, 2)):
+        assert lib.fpsa_tables(N, L1, lap, None, None, None, None, None) == binding.EINVAL
+    assert lib.fpsa_tables(16, 16, 1, None, None, None, None, None) == binding.OK
