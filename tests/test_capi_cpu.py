@@ -149,3 +149,70 @@ def test_library_tables_reject_bad_sizes(lib):
     for N, L1, lap in ((3, 1, 0), (0, 1, 0), (258, 1, 0), (16, 0, 0), (16, 17, 0), (16, 4, 2)):
         assert lib.fpsa_tables(N, L1, lap, None, None, None, None, None) == binding.EINVAL
     assert lib.fpsa_tables(16, 16, 1, None, None, None, None, None) == binding.OK
+
+
+def test_batch_driver_searches_each_missing_key_once_then_uses_the_cache(tmp_path, monkeypatch):
+    # host logic of BatchSolver with a stand-in for the library context and for
+    # torch's CUDA stream objects (no GPU): one serial fpsa_autotune per key the cache
+    # lacks, before any wave solves; every wave then runs with its key's shapes
+    import contextlib
+    import threading
+    import torch
+    from paper_1907_13013_gb300 import batch, binding, inputs
+
+    log, lock = [], threading.Lock()
+    solving = {"n": 0}
+
+    class FakeCtx:
+        def __init__(self, probs):
+            self.probs, self.R = probs, 1
+            self.shape = {"sweep_cells_per_thread": 4, "solve_blocks_per_sm": 2, "solve_max_slices": 4}
+
+        def autotune(self, **kw):
+            with lock:
+                assert solving["n"] == 0  # no wave is solving while a search times solves
+                log.append(("autotune", self.probs[0]["N"], len(self.probs)))
+            return {"sweep_cells_per_thread": 8, "solve_blocks_per_sm": 1, "solve_max_slices": 2}, 1.5
+
+        def set_tuning(self, t):
+            self.shape = dict(t)
+
+        def get_tuning(self):
+            return dict(self.shape)
+
+        def solve(self, **kw):
+            with lock:
+                solving["n"] += 1
+                log.append(("solve", self.probs[0]["N"], tuple(sorted(self.shape.items()))))
+            K = sum(p["h"].size for p in self.probs)
+            with lock:
+                solving["n"] -= 1
+            return np.zeros((1, K, 2, self.probs[0]["L"] + 1)), {"status": 0, "cell_angles": 0.0}
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(binding, "context_for", lambda probs, **kw: FakeCtx(probs))
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda device=None: type("S", (), {"cuda_stream": 0})())
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+
+    probs = inputs.batch_slabs(30, seed=5, K_range=(20, 200))
+    budget = batch.factor_bytes(200, 128, "mixed")  # one large S128 slab: several waves per group
+    cache = batch.TuningCache(str(tmp_path / "shapes.json"))
+    solver = batch.BatchSolver(probs, budget_bytes=budget, tuning=cache)
+    keys = {solver._key(w, "fpsa") for w in solver.waves}
+    assert len(keys) < len(solver.waves)  # some waves share a key
+    phis, stats = solver.solve(tol=1e-10)
+    searches = [e for e in log if e[0] == "autotune"]
+    assert len(searches) == len(keys)
+    first_solve = next(i for i, e in enumerate(log) if e[0] == "solve")
+    assert all(i < first_solve for i, e in enumerate(log) if e[0] == "autotune")
+    assert all(dict(e[2])["solve_max_slices"] == 2 for e in log if e[0] == "solve")
+    assert {s["tuning_source"] for s in stats} == {"search"}
+    assert len(phis) == len(probs) and all(phi.shape == (p["h"].size, 2, p["L"] + 1) for phi, p in zip(phis, probs))
+    # a second driver over the same cache file searches nothing
+    log.clear()
+    _, stats2 = batch.BatchSolver(probs, budget_bytes=budget, tuning=batch.TuningCache(cache.path)).solve(tol=1e-10)
+    assert not [e for e in log if e[0] == "autotune"]
+    assert {s["tuning_source"] for s in stats2} == {"cache"}
