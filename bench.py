@@ -34,7 +34,12 @@ import sys
 import threading
 import time
 
-import numpy as np
+# The oracle's CPU timings are reported as single-core: numpy's BLAS (and any OpenMP
+# pool) in this process runs one thread, set before numpy loads its BLAS.
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ[_var] = "1"
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
