@@ -69,3 +69,30 @@ def test_reference_arm_prints_on_rank_zero_only(tmp_path):
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    # the reference arm's JSON line (the oracle's own solver is replaced by a stand-in
+    # that takes a known time per call, so only the plumbing and arithmetic run)
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    from oracle import iterations as oit
+    calls = []
+
+    def fake(p, lap, tol=0.0, max_it=0):
+        calls.append(max_it)
+        return None, max_it
+
+    monkeypatch.setattr(oit, "fpsa_source_iteration", fake)
+    for v in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(v, raising=False)
+    args = argparse.Namespace(steps=2, warmup=3, gpus=1, laplacian="wfd")
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "solves/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"].startswith("precision_srk_slab")
+    assert calls == [3, 5] * (args.warmup + args.steps)  # setup + 3 and 5 iterations per step
