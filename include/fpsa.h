@@ -282,14 +282,13 @@ const char *fpsa_last_error(const fpsa_ctx *ctx);
 /* ---------------------------------------------------------------------------
  * Allocation-free transport sweep. The paper has no counterpart: this is a
  * service entry point for callers that cannot call cudaMalloc -- code running
- * inside another framework's memory pool or allocator lock, code that must not
- * create device allocations while it records work into a CUDA graph, or a
+ * inside another framework's memory pool or under its allocator lock, or a
  * process whose device memory is reserved up front.
  *
- * Computes one LD upwind sweep psi = L^{-1} q (the sweep of Eq. trsi, vacuum
- * inflow at both edges) for ONE slab of n_cells cells and n_ordinates
- * Gauss-Legendre ordinates, with the same kernels as the context path. All five
- * array pointers are DEVICE memory owned by the caller:
+ * Computes one LD upwind sweep psi = L^{-1} q (the transport operator
+ * mu d/dz + sigma_t in the LD discretization above, zero incoming flux at both
+ * edges) for ONE slab of n_cells cells and n_ordinates Gauss-Legendre ordinates.
+ * All five array pointers are DEVICE memory owned by the caller:
  *   h [K], sigma_t [K]          cell widths and total cross sections
  *   q [K][2][N]                 nodal ANGULAR source (values at the ordinates)
  *   psi [K][2][N]               output angular flux
@@ -297,13 +296,17 @@ const char *fpsa_last_error(const fpsa_ctx *ctx);
  * array of FPSA_SWEEP_NOALLOC_MAX_CELL_ANGLES x 6 doubles (6.3 MB) that every GPU
  * loading the library holds until the process exits; no call allocates device
  * memory. K * N above that limit, or N > 256, returns FPSA_ENOTSUP; malformed
- * arguments return FPSA_EINVAL.
+ * arguments return FPSA_EINVAL; a refused launch returns FPSA_ECUDA (the launch's
+ * own status: an error left pending by earlier, unrelated work is not cleared).
  * Work is enqueued on `stream` (cudaStream_t, NULL = legacy default) and the
- * call returns without synchronising. The first call on a device looks up the
- * array's device address (with that device current); make that first call
- * before any stream capture. All calls share the one array and leave their
- * coefficients in it: calls whose work overlaps on the GPU (e.g. on two
- * streams) race and must be serialised by the caller.
+ * call returns without synchronising. The first call on a device does a one-time
+ * set-up with that device current: it looks up the arrays' device addresses and
+ * copies the ordinate tables of every even N <= 256 into a second fixed array
+ * (a synchronous copy); make that first call before any stream capture. Later
+ * calls copy nothing from host memory. All calls share the one scratch array and
+ * leave their coefficients in it (each call rewrites every coefficient it reads
+ * before the sweep): calls whose work overlaps on the GPU (e.g. on two streams)
+ * race and must be serialised by the caller.
  */
 #define FPSA_SWEEP_NOALLOC_MAX_CELL_ANGLES 131072
 int fpsa_sweep_noalloc(int32_t n_ordinates, int32_t n_cells, const double *h, const double *sigma_t,

@@ -22,7 +22,7 @@ def test_srk_first_moment_closed_form(eta):
     assert abs(f[1] - f1) < 1e-12
 
 
-@pytest.mark.parametrize("eta,L", [(1e-3, 15), (1e-5, 63)])
+@pytest.mark.parametrize("eta,L", [(1e-3, 15), (1e-5, 63), (1e-6, 127)])
 def test_srk_moments_against_quadrature(eta, L):
     # Direct numerical integration of the normalised kernel against P_l.
     f = inputs.srk_moments(eta, L)
