@@ -268,6 +268,21 @@ int fpsa_autotune(fpsa_ctx *ctx, const fpsa_opts *opts, int32_t repeats, fpsa_tu
 int fpsa_tables(int32_t n_ordinates, int32_t n_moments, int32_t laplacian, double *mu, double *w, double *D,
                 double *M, double *A);
 
+/* Limits of the failure checks, for callers that need the error paths to fire on
+ * ordinary inputs (tests of FPSA_ETIMEOUT and FPSA_EPIVOT handling; the paper has no
+ * counterpart). wait_polls: how many times a polling thread of the BCR dataflow
+ * kernels (the factorization of fpsa_set_xs and the solve of every iteration) tests
+ * a counter it waits on before it gives up, records the failure and goes on with
+ * the data it has; the call then returns FPSA_ETIMEOUT (its results are not valid).
+ * growth_limit: fpsa_set_xs returns FPSA_EPIVOT when the pivot growth
+ * max|A| max|A^{-1}| of an eliminated block (fpsa_stats.pivot_growth) exceeds it.
+ * 0 restores each default (2^25 polls, about a second; growth 1e14). A context
+ * whose call returned FPSA_ETIMEOUT or FPSA_EPIVOT stays usable: after
+ * fpsa_set_xs failed, call it again (fpsa_solve needs a successful one); after
+ * fpsa_solve failed, solve again. Waits on copies and tensor-core completions are
+ * bounded by time (2 s) and not affected. Negative values return FPSA_EINVAL. */
+int fpsa_set_limits(fpsa_ctx *ctx, int64_t wait_polls, double growth_limit);
+
 /* Release every device buffer of the context (NULL is allowed). */
 void fpsa_destroy(fpsa_ctx *ctx);
 

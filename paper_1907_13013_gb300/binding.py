@@ -75,7 +75,8 @@ class FpsaProfile(ctypes.Structure):
 
 EXPORTS = ["fpsa_create", "fpsa_set_xs", "fpsa_solve", "fpsa_destroy", "fpsa_strerror", "fpsa_last_error",
            "fpsa_profile_enable", "fpsa_profile_read", "fpsa_sweep_noalloc", "fpsa_adjoint",
-           "fpsa_set_incident", "fpsa_get_tuning", "fpsa_set_tuning", "fpsa_autotune", "fpsa_tables"]
+           "fpsa_set_incident", "fpsa_get_tuning", "fpsa_set_tuning", "fpsa_autotune", "fpsa_tables",
+           "fpsa_set_limits"]
 NOALLOC_MAX_CELL_ANGLES = 131072
 
 _lib = None
@@ -119,6 +120,8 @@ def load():
     lib.fpsa_autotune.restype = ctypes.c_int
     lib.fpsa_tables.argtypes = [i32, i32, i32, dp, dp, dp, dp, dp]
     lib.fpsa_tables.restype = ctypes.c_int
+    lib.fpsa_set_limits.argtypes = [vp, ctypes.c_int64, ctypes.c_double]
+    lib.fpsa_set_limits.restype = ctypes.c_int
     lib.fpsa_sweep_noalloc.argtypes = [i32, i32, dp, dp, dp, dp, vp]
     lib.fpsa_sweep_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -288,6 +291,12 @@ class Context:
         self._check(self._lib.fpsa_autotune(self._h, ctypes.byref(o), int(repeats), ctypes.byref(t),
                                             ctypes.byref(ms)), "fpsa_autotune")
         return t.as_dict(), ms.value
+
+    def set_limits(self, wait_polls=0, growth_limit=0.0):
+        """Limits of the failure checks (fpsa_set_limits): polls of a BCR dataflow wait before
+        it gives up (FPSA_ETIMEOUT) and the pivot-growth limit of fpsa_set_xs (FPSA_EPIVOT);
+        0 restores each default."""
+        self._check(self._lib.fpsa_set_limits(self._h, int(wait_polls), float(growth_limit)), "fpsa_set_limits")
 
     def profile_enable(self, on=True):
         """Reset the launch counters; with on, bracket every launch with CUDA events."""

@@ -60,6 +60,8 @@ struct PathBuffers {
 
 }  // namespace
 
+constexpr double kGrowthLimit = 1e14;  // default pivot-growth limit of the FP block factorization
+
 struct fpsa_ctx {
     Geometry geo;
     Tables tab;
@@ -121,7 +123,10 @@ struct fpsa_ctx {
     // tensor-core contractions of the FP32 inner solve
     bool tc_able = false;               // N multiple of 16, 16 <= N <= 128
     unsigned char *d_tc_ops = nullptr;  // D_hi, D_lo, M_hi, M_lo (BF16, core-matrix layout)
-    int *d_dev_err = nullptr, *h_flag = nullptr;  // a bounded device wait ran out (tensor-core or BCR dataflow)
+    // [0]: a bounded device wait ran out (tensor-core or BCR dataflow); [1]: the polls a
+    // BCR dataflow wait makes before it gives up (fpsa_set_limits)
+    int *d_dev_err = nullptr, *h_flag = nullptr;
+    double growth_limit = kGrowthLimit;  // fpsa_set_xs: FPSA_EPIVOT above this pivot growth
     int tc_grid = 0;
 
     // built-in profiler: launch counters (always) and event pairs (when on)
@@ -1351,8 +1356,11 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         CK(dalloc(ctx, &ctx->d_in_ss, (size_t)g.sumK * g.L1));
         CK(dalloc(ctx, &ctx->d_in_q, (size_t)g.R * g.sumK * 2 * g.L1));
         CK(dalloc(ctx, &ctx->d_xs_err, 2));
-        CK(dalloc(ctx, &ctx->d_dev_err, 1));
-        CK(cudaMemset(ctx->d_dev_err, 0, sizeof(int)));
+        CK(dalloc(ctx, &ctx->d_dev_err, 2));
+        {
+            const int e0[2] = {0, (int)kFlowSpinLimit};
+            CK(cudaMemcpy(ctx->d_dev_err, e0, sizeof(e0), cudaMemcpyHostToDevice));
+        }
         CK(cudaMallocHost(&ctx->h_flag, sizeof(int)));
         {
             const int nchunk = (g.R + solve_rc(g.R) - 1) / solve_rc(g.R);
@@ -1525,7 +1533,7 @@ int fpsa_set_xs(fpsa_ctx *ctx, const double *sigma_t, const double *sigma_s, con
     std::memcpy(&gr, &growth, sizeof(gr));
     ctx->pivot_growth = gr;
     ctx->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (status || !std::isfinite(gr) || gr > 1e14)
+    if (status || !std::isfinite(gr) || gr > ctx->growth_limit)
         return fail(ctx, FPSA_EPIVOT, "FP block factorization failed: growth " + std::to_string(gr));
     ctx->xs_ready = true;
     return FPSA_OK;
@@ -1550,6 +1558,18 @@ int fpsa_set_incident(fpsa_ctx *ctx, const double *psi_inc, int32_t mem) {
                        mem == FPSA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->has_inc = true;
+    return FPSA_OK;
+}
+
+int fpsa_set_limits(fpsa_ctx *ctx, int64_t wait_polls, double growth_limit) {
+    if (!ctx) return FPSA_EINVAL;
+    if (wait_polls < 0 || wait_polls > 0x7fffffffll) return fail(ctx, FPSA_EINVAL, "wait_polls outside [0, 2^31 - 1]");
+    if (!(growth_limit >= 0.0)) return fail(ctx, FPSA_EINVAL, "growth_limit must be >= 0");
+    CK(cudaSetDevice(ctx->device));
+    const int limit = wait_polls > 0 ? (int)wait_polls : (int)kFlowSpinLimit;
+    CK(cudaMemcpyAsync(ctx->d_dev_err + 1, &limit, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->growth_limit = growth_limit > 0.0 ? growth_limit : kGrowthLimit;
     return FPSA_OK;
 }
 

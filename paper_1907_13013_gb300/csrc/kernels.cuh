@@ -1803,15 +1803,19 @@ __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, cons
 
 // Dataflow synchronisation of the BCR solve units (k_bcr_solve_flow): a unit waits
 // until the counters it depends on reach their targets (thread 0 polls with acquire
-// loads, at most kFlowSpinLimit times, then records *err = 1 and goes on), and after
+// loads, at most `limit` times, then records *err = 1 and goes on), and after
 // its writes (block barrier, then thread 0 fences) bumps the counters of the units
 // that depend on it. NULL pointers are absent waits / signals.
-constexpr unsigned kFlowSpinLimit = 1u << 25;  // x >= 32 ns: about a second
+// The limit is the context's: err[1] holds it (err[0] is the error flag), so a host
+// can shorten it to make a wait run out on purpose (tests of the error path).
+constexpr unsigned kFlowSpinLimit = 1u << 25;  // default: x >= 32 ns, about a second
+__device__ __forceinline__ unsigned flow_spin_limit(const int *err) { return (unsigned)__ldg(err + 1); }
 struct FlowSync {
     const int *wait0, *wait1;
     int want0, want1;
     int *sig0, *sig1, *sig2;
     int *err;
+    unsigned limit;
 };
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p) {
@@ -1830,7 +1834,7 @@ __device__ __forceinline__ void flow_wait(const FlowSync *fs) {
             if (!c) continue;
             unsigned spins = 0;
             while (ld_acquire_gpu(c) < want) {  // busy first, then with short sleeps
-                if (++spins > kFlowSpinLimit) {
+                if (++spins > fs->limit) {
                     atomicExch(fs->err, 1);
                     break;
                 }
@@ -1879,7 +1883,7 @@ __device__ __forceinline__ void flow_signal_release(const FlowSync *fs, int sign
 // next-level couplings) and bumps their counters. A quadrant of a kept cell is
 // updated by its neighbours at successive levels, each of which waited for the
 // previous one, so plain read-modify-writes suffice; every read of data another
-// block wrote bypasses L1. Waits are bounded (kFlowSpinLimit; *err = 1 on timeout).
+// block wrote bypasses L1. Waits are bounded (err[1] polls; *err = 1 on timeout).
 template <typename T, int N2>
 __global__ void __launch_bounds__(512, 1) k_bcr_factor_flow(T *__restrict__ A, const BcrItem *__restrict__ items,
                                                            int n_items, T *__restrict__ Bc, T *__restrict__ Cc,
@@ -1887,10 +1891,12 @@ __global__ void __launch_bounds__(512, 1) k_bcr_factor_flow(T *__restrict__ A, c
                                                            int *__restrict__ status, int *cnt, int *err,
                                                            int schur_staged) {
     extern __shared__ unsigned char smem_dyn[];
+    const unsigned limit = flow_spin_limit(err);
     for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
         const BcrItem it = items[ii];
         FlowSync fs{};
         fs.err = err;
+        fs.limit = limit;
         int want = 0;
         for (int lp = 0; lp < it.level; ++lp)
             want += (it.local >= (1 << lp)) + (it.local + (1 << lp) < it.K_inst);
@@ -2044,6 +2050,7 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ 
     tc::grid_dependency_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
+    const unsigned limit = flow_spin_limit(err);
     const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, P = 2 * nl;
     auto phase_level = [&](int ph) { return ph <= nl ? ph : 2 * nl - ph; };
     auto units = [&](int ph) {
@@ -2066,6 +2073,7 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow(const T *__restrict__ 
         const int n2 = 2 * N, nr = n2 / S, row0 = sl * nr;
         FlowSync fs{};
         fs.err = err;
+        fs.limit = limit;
         if (ph <= nl) {
             int want = 0;
             for (int lp = 0; lp < it.level; ++lp)
@@ -2299,8 +2307,9 @@ __device__ __forceinline__ void flow_coarse_unit(int u, const LevelTable &lv, co
         int want = 0;
         for (int lp = 0; lp < cl; ++lp) want += (a >= (1 << lp)) + (a + (1 << lp) < lv.coarse_K);
         unsigned spins = 0;
+        const unsigned limit = flow_spin_limit(err);
         while (want && ld_acquire_gpu(cnt + a) < want) {
-            if (++spins > kFlowSpinLimit) {
+            if (++spins > limit) {
                 atomicExch(err, 1);
                 break;
             }
@@ -2363,6 +2372,7 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
     __syncthreads();
     const int nchunk = (R + RC - 1) / RC, nl = lv.n_levels, cl = lv.coarse_level;
     const int P = cl >= 0 ? 2 * cl : 2 * nl;
+    const unsigned limit = flow_spin_limit(err);
     // level of a phase (-1: the coarse phase) and whether it is a backward phase
     auto phase_level = [&](int ph) {
         if (cl >= 0) return ph < cl ? ph : (ph == cl ? -1 : 2 * cl - ph);
@@ -2459,6 +2469,7 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
             const int n2 = 2 * N, nr = n2 / S, row0 = sl * nr;
             FlowSync fs{};
             fs.err = err;
+            fs.limit = limit;
             if (!bwd) {
                 int want = 0;
                 for (int lp = 0; lp < it.level; ++lp)

@@ -93,6 +93,12 @@ def test_boundary_condition_marshalling():
         binding._bc_array("periodic", 1)
 
 
+def test_limits_entry_point_rejects_a_null_context(lib):
+    from paper_1907_13013_gb300 import binding
+    assert lib.fpsa_set_limits(None, 0, 0.0) == binding.EINVAL
+    assert lib.fpsa_set_limits(None, 4, 1.0) == binding.EINVAL
+
+
 def test_tuning_entry_points_reject_a_null_context(lib):
     # argument checks come before any CUDA call
     from paper_1907_13013_gb300 import binding
