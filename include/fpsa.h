@@ -230,6 +230,13 @@ typedef struct {
                                        grid, 1..4 (capped by the kernel's occupancy) */
     int32_t solve_max_slices;       /* BCR solve: most row slices one block-row of a level is
                                        split into, 1, 2 or 4 */
+    int32_t factor_engine;          /* BCR factorization of the next fpsa_set_xs: 1 = SIMT
+                                       Gauss-Jordan, 2 = tensor cores (blocked Gauss-Jordan with
+                                       tcgen05 trailing updates in split BF16; only for FP32
+                                       factors (MIXED) with 2N = 128, else FPSA_ENOTSUP);
+                                       0 = tensor cores where they apply, else SIMT. Factors
+                                       differ by rounding only (the pivots are chosen in FP32
+                                       either way) */
 } fpsa_tuning;
 
 /* The shapes in effect (zero fields resolved to the values used). */

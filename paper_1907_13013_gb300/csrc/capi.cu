@@ -21,6 +21,7 @@
 #include "kernels.cuh"
 #include "tc_contract.cuh"
 #include "bcr_large.cuh"
+#include "bcr_factor_tc.cuh"
 #include "gmres.cuh"
 
 using namespace fpsa;
@@ -98,6 +99,7 @@ struct fpsa_ctx {
     int sweep_cpt = 0;               // cells per thread of the segmented sweep in effect
     fpsa_tuning tuning = {};         // requested launch shapes (0: the library's choice)
     int factor_grid[2] = {0, 0};     // cooperative dataflow factorization grid (0: per-level launches)
+    int factor_tc_grid = 0;          // grid of the tensor-core factorization (FP32, 2N = 128), 0: unavailable
     unsigned long long *d_conv = nullptr, *d_growth = nullptr;
     int *d_status = nullptr;
     double *d_result = nullptr;
@@ -531,7 +533,23 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     }
     CK(cudaGetLastError());
     const int e = sizeof(T) == 8 ? 1 : 0;
-    if (ctx->factor_grid[e] > 0) {
+    const bool tc_factor = e == 0 && ctx->factor_tc_grid > 0 && ctx->tuning.factor_engine != 1;
+    if (tc_factor) {
+        // every level and the roots in one cooperative launch, inversions on tensor cores
+        const LevelTable &lv = ctx->lvt[e];
+        float *A = reinterpret_cast<float *>(p.A), *Bc = reinterpret_cast<float *>(p.Bc),
+              *Cc = reinterpret_cast<float *>(p.Cc);
+        const BcrItem *items = ctx->d_items_all;
+        int n_items = lv.off[g.n_levels] + lv.n_roots;
+        unsigned long long *growth = ctx->d_growth;
+        int *status = ctx->d_status, *cnt = ctx->d_factor_cnt, *err = ctx->d_dev_err;
+        void *args[] = {(void *)&A,      (void *)&items,  (void *)&n_items, (void *)&Bc, (void *)&Cc,
+                        (void *)&growth, (void *)&status, (void *)&cnt,     (void *)&err};
+        CK(cudaMemsetAsync(cnt, 0, (size_t)g.sumK * sizeof(int), st));
+        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+        CK(cudaLaunchCooperativeKernel((const void *)k_bcr_factor_tc, dim3(ctx->factor_tc_grid),
+                                       dim3(tcf::kThreads), args, tcf::Smem::total, st));
+    } else if (ctx->factor_grid[e] > 0) {
         // every level and the roots in one cooperative launch (dataflow between items)
         const LevelTable &lv = ctx->lvt[e];
         T *A = p.A, *Bc = p.Bc, *Cc = p.Cc;
@@ -547,7 +565,7 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         CK(cudaLaunchCooperativeKernel(factor_kernel<T>(2 * N), dim3(ctx->factor_grid[e]), dim3(512), args,
                                        schur_smem<T>(N), st));
     }
-    for (int l = 0; l < g.n_levels && ctx->factor_grid[e] == 0; ++l) {
+    for (int l = 0; l < g.n_levels && ctx->factor_grid[e] == 0 && !tc_factor; ++l) {
         const int ni = (int)g.levels[l].size();
         if (!ni) continue;
         bool fused = false;
@@ -561,7 +579,7 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         }
         CK(cudaGetLastError());
     }
-    if (ctx->factor_grid[e] == 0) {
+    if (ctx->factor_grid[e] == 0 && !tc_factor) {
         int rc = invert_level(ctx, p, ctx->d_roots, g.B);
         if (rc) return rc;
     }
@@ -1446,6 +1464,14 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
                 if (fk) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, fk, 512, fsm));
                 ctx->factor_grid[e] = (fk && fper > 0) ? nsm : 0;  // one block per SM
             }
+            if (2 * g.N == tcf::kN2 && ctx->precision == FPSA_PRECISION_MIXED) {
+                // up to 4 CTAs per SM (4 x 128 TMEM columns), as occupancy allows
+                int fper = 0;
+                CK(raise_smem_limit((const void *)k_bcr_factor_tc, (int)tcf::Smem::total));
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, k_bcr_factor_tc, tcf::kThreads,
+                                                                 tcf::Smem::total));
+                ctx->factor_tc_grid = std::min(fper, 4) * nsm;
+            }
             for (int e = 0; e < 2; ++e) {
                 LevelTable &lv = ctx->lvt[e];
                 lv.n_levels = g.n_levels;
@@ -1727,6 +1753,7 @@ int fpsa_get_tuning(const fpsa_ctx *ctx, fpsa_tuning *out) {
     out->sweep_cells_per_thread = ctx->sweep_cpt;
     out->solve_blocks_per_sm = ctx->coop_grid[e] / std::max(1, ctx->n_sm);
     out->solve_max_slices = ctx->tuning.solve_max_slices > 0 ? ctx->tuning.solve_max_slices : 4;
+    out->factor_engine = (ctx->factor_tc_grid > 0 && ctx->tuning.factor_engine != 1) ? 2 : 1;
     return FPSA_OK;
 }
 
@@ -1740,6 +1767,9 @@ int fpsa_set_tuning(fpsa_ctx *ctx, const fpsa_tuning *t) {
         return fail(ctx, FPSA_EINVAL, "solve_blocks_per_sm outside [0, 4]");
     if (r.solve_max_slices != 0 && r.solve_max_slices != 1 && r.solve_max_slices != 2 && r.solve_max_slices != 4)
         return fail(ctx, FPSA_EINVAL, "solve_max_slices not 0, 1, 2 or 4");
+    if (r.factor_engine < 0 || r.factor_engine > 2) return fail(ctx, FPSA_EINVAL, "factor_engine not 0, 1 or 2");
+    if (r.factor_engine == 2 && ctx->factor_tc_grid == 0)
+        return fail(ctx, FPSA_ENOTSUP, "tensor-core factorization needs FP32 factors (MIXED) with 2N = 128");
     // the segment maps were allocated for the smallest cells-per-thread (most segments)
     const int cmin = sweep_cells_per_thread(ctx->geo);
     ctx->sweep_cpt = std::max(cmin, r.sweep_cells_per_thread);
@@ -1794,7 +1824,7 @@ int fpsa_autotune(fpsa_ctx *ctx, const fpsa_opts *opts, int32_t repeats, fpsa_tu
     const int bmax = std::min(4, ctx->solve_per_sm[ctx->precision == FPSA_PRECISION_FP64 ? 1 : 0]);
     for (int b = 1; b <= bmax; ++b)
         for (int s = 1; s <= 4; s *= 2) {
-            const fpsa_tuning t{0, b, s};
+            const fpsa_tuning t{0, b, s, saved.factor_engine};
             double ms = 0.0;
             const int rc = trial(t, ms);
             if (rc != FPSA_OK) return give_up(rc);
