@@ -47,9 +47,11 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "precision_srk_slab: 1 cm, K=2000 LD cells, S64, SRK eta=1e-5, L=63, sigma_s0=1000, sigma_a=0.01, Q=1 on z<0.5, vacuum"
 METRIC = "converged slab S_N solves/s (FPSA-SI, tol 1e-10 rel. change of phi_0)"
 TOL = 1e-10
-# per-launch DRAM bytes (read + write) measured by ncu for the dominant kernel on this workload,
-# with the library's own launch shapes
-NCU_TRAFFIC = {("k_bcr_solve_flow_s", "mixed"): 224.7e6}
+# Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernel on this workload, measured by ncu for each row-slice cap of the BCR solve (the
+# launch shape that changes its units; one block per SM), keyed by (kernel, precision,
+# solve_max_slices). A shape missing here reports traffic null.
+NCU_TRAFFIC = {}
 
 
 def dist_env():
@@ -194,6 +196,38 @@ def cpu_baseline_sample(laplacian):
                       % (laplacian.upper(), n, dt)}
 
 
+def _oracle_solve_seconds(laplacian):
+    """One complete oracle solve of the workload in this (worker) process; its seconds."""
+    from oracle import iterations as oit
+    from paper_1907_13013_gb300 import inputs
+    p = inputs.precision_srk_slab()
+    t0 = time.perf_counter()
+    oit.fpsa_source_iteration(p, laplacian, tol=TOL)
+    return time.perf_counter() - t0
+
+
+def _import_oracle(_):
+    from oracle import iterations  # noqa: F401
+    from paper_1907_13013_gb300 import inputs  # noqa: F401
+    return os.getpid()
+
+
+def cpu_baseline_all_cores(laplacian):
+    """Throughput of the oracle on every host core: one complete solve per core at once, in
+    processes started by spawn (the parent has a CUDA context), each single-threaded."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_import_oracle, range(cores))
+        t0 = time.perf_counter()
+        secs = pool.map(_oracle_solve_seconds, [laplacian] * cores)
+        wall = time.perf_counter() - t0
+    return {"value": cores / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": "%d complete FP64 oracle FPSA-SI (%s) solves of the workload, one per core at once; "
+                      "wall %.1f s (single solves %.1f - %.1f s)" % (cores, laplacian.upper(), wall, min(secs),
+                                                                     max(secs))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +241,8 @@ def main():
     ap.add_argument("--tune", default="auto", choices=["library", "auto"],
                     help="launch shapes: the library's own, or those fpsa_autotune picks on this workload "
                          "(before the warm-up, outside the timed region)")
+    ap.add_argument("--solve-slices", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="row-slice cap of the BCR solve after tuning (0: keep the tuned / library value)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -264,10 +300,11 @@ def main():
         torch.cuda.synchronize()
         return max_over_ranks(e0.elapsed_time(e1), dev)
 
-    lib_shape = ctx.get_tuning()
     if args.tune == "auto":
         ctx.set_xs(d_st, d_ss, d_q)
         ctx.autotune(tol=TOL, repeats=3)
+    if args.solve_slices:
+        ctx.set_tuning(dict(ctx.get_tuning(), solve_max_slices=args.solve_slices))
     shape = ctx.get_tuning()
     for _ in range(args.warmup):
         step_device()
@@ -322,10 +359,8 @@ def main():
         kf = K - m_c
         byt = esize * (kf * n2 * n2 + kf * n2 * N + 2 * kf * (N // 2) ** 2 + (m_c * n2) ** 2)
         achieved = byt / (per_launch_ms * 1e-3) / 1e9
-        # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel for this
-        # workload (FP32), from profiles/k_bcr_solve_flow_precision_srk_slab.md
         kname = "k_bcr_solve_flow_s" if (2 * N) * (2 * N) * esize <= 64 * 1024 else "k_bcr_solve_flow"
-        traffic = NCU_TRAFFIC.get((kname, args.precision)) if shape == lib_shape else None
+        traffic = NCU_TRAFFIC.get((kname, args.precision, shape["solve_max_slices"]))
         roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "algorithmic_bytes": byt}
     elif dom == "bcr_invert":
@@ -359,13 +394,15 @@ def main():
                 c2.set_xs(d_st, d_ss, d_q)
                 c2.autotune(tol=TOL, repeats=2)
 
-            for _ in range(2):
+            for _ in range(3):
                 step2()
-            ms2 = timed(step2, 3)
+            n2steps = 10
+            ms2 = timed(step2, n2steps)
             ref2, _ = read_golden("precision_srk_slab_fpsa_%s_phi0.txt" % lap)
             err2 = float(np.abs(d_phi[0, :, :, 0].cpu().numpy().ravel() - ref2).max() / np.abs(ref2).max())
-            secondary[name] = {"laplacian": lap, "precision": prec, "value": whole_job_rate(world, 3, ms2),
-                               "unit": "solves/s", "ms_per_step": ms2 / 3, "iterations": st2["iterations"],
+            secondary[name] = {"laplacian": lap, "precision": prec, "value": whole_job_rate(world, n2steps, ms2),
+                               "unit": "solves/s", "steps": n2steps, "ms_per_step": ms2 / n2steps,
+                               "iterations": st2["iterations"],
                                "setup_ms": st2["setup_ms"], "solve_ms": st2["solve_ms"],
                                "max_rel_err_vs_oracle": err2, "tuning": c2.get_tuning()}
             c2.close()
@@ -401,6 +438,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample(args.laplacian)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.laplacian)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()

@@ -40,7 +40,7 @@ inline int sweep_segments(const Geometry &g) {
 }
 constexpr int kContractThreads = 256;
 constexpr int kInvertThreads = 512;
-constexpr int kSolveThreads = 256;  // one (item, rhs) unit per block
+constexpr int kSolveThreads = 256;  // one (item, rhs) unit per block (the staged solve: its compute groups' threads)
 
 template <typename T>
 struct PathBuffers {
@@ -264,24 +264,43 @@ void plan_coarse(LevelTable &lv, const Geometry &g, int esize) {
 // right-hand sides per BCR solve unit
 int solve_rc(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
 
+// copy stages of the staged-slice BCR solve: as many as fit one block's shared memory
+// (at most kMaxSolveStages); 0 when the slices are not staged
+template <typename T>
+int solve_stages(int N, int RC) {
+    if (!bcr_slice_staged(N, (int)sizeof(T))) return 0;
+    const size_t base = (size_t)kSolveGroups * bcr_stage_base_values<T>(N, kSolveThreads / kSolveGroups, RC) * sizeof(T);
+    const size_t stage = (size_t)bcr_stage_values<T>(N, RC) * sizeof(T);
+    const int ns = (int)((kSmemLimit - base) / stage);
+    return std::max(1, std::min(kMaxSolveStages, ns));
+}
+
 // shared memory of the cooperative BCR solve: the unit scratch and, when one unit's
-// A^{-1} slice fits, the staged slice buffer
+// A^{-1} slice fits, the copy stages
 template <typename T>
 size_t solve_smem(int N, int RC) {
     if (bcr_slice_staged(N, (int)sizeof(T)))
-        return (size_t)bcr_slice_offset_values<T>(N, kSolveThreads, RC) * sizeof(T) +
-               (size_t)(2 * N) * (2 * N) * sizeof(T);
+        return ((size_t)kSolveGroups * bcr_stage_base_values<T>(N, kSolveThreads / kSolveGroups, RC) +
+                (size_t)solve_stages<T>(N, RC) * bcr_stage_values<T>(N, RC)) *
+               sizeof(T);
     return (size_t)bcr_unit_smem_values(N, kSolveThreads, VecOf<T>::V, RC, (int)sizeof(T)) * sizeof(T);
+}
+
+// threads of a cooperative BCR solve block: the staged solve adds a service warp per compute group
+template <typename T>
+int solve_threads(int N) {
+    return bcr_slice_staged(N, (int)sizeof(T)) ? kSolveThreads + 32 * kSolveGroups : kSolveThreads;
 }
 
 template <typename T>
 const void *coop_kernel(int RC, int N) {
     if (bcr_slice_staged(N, (int)sizeof(T))) {
+        constexpr int NT = kSolveThreads + 32 * kSolveGroups;
         switch (RC) {
-            case 8: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 8>;
-            case 4: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 4>;
-            case 2: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 2>;
-            default: return (const void *)k_bcr_solve_flow_s<T, kSolveThreads, 1>;
+            case 8: return (const void *)k_bcr_solve_flow_s<T, NT, 8>;
+            case 4: return (const void *)k_bcr_solve_flow_s<T, NT, 4>;
+            case 2: return (const void *)k_bcr_solve_flow_s<T, NT, 2>;
+            default: return (const void *)k_bcr_solve_flow_s<T, NT, 1>;
         }
     }
     switch (RC) {
@@ -693,7 +712,7 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     if (ctx->solve_pdl) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(kSolveThreads);
+        cfg.blockDim = dim3(solve_threads<T>(N));
         cfg.dynamicSmemBytes = solve_smem<T>(N, RC);
         cfg.stream = ctx->stream;
         cudaLaunchAttribute attr[2];
@@ -707,7 +726,8 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
         (void)cudaGetLastError();  // the combination is refused: plain cooperative launches from now on
         ctx->solve_pdl = false;
     }
-    CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kSolveThreads), args, solve_smem<T>(N, RC), ctx->stream));
+    CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(solve_threads<T>(N)), args, solve_smem<T>(N, RC),
+                                   ctx->stream));
     return FPSA_OK;
 }
 
@@ -1450,11 +1470,11 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             const int RC = solve_rc(g.R);
             CK(raise_smem_limit((const void *)coop_kernel<float>(RC, g.N), (int)solve_smem<float>(g.N, RC)));
             CK(raise_smem_limit((const void *)coop_kernel<double>(RC, g.N), (int)solve_smem<double>(g.N, RC)));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<float>(RC, g.N), kSolveThreads,
-                                                             solve_smem<float>(g.N, RC)));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<float>(RC, g.N),
+                                                             solve_threads<float>(g.N), solve_smem<float>(g.N, RC)));
             ctx->solve_per_sm[0] = std::max(1, per_sm);
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<double>(RC, g.N), kSolveThreads,
-                                                             solve_smem<double>(g.N, RC)));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel<double>(RC, g.N),
+                                                             solve_threads<double>(g.N), solve_smem<double>(g.N, RC)));
             ctx->solve_per_sm[1] = std::max(1, per_sm);
             ctx->n_sm = nsm;
             for (int e = 0; e < 2; ++e) {
@@ -1476,6 +1496,7 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
                 LevelTable &lv = ctx->lvt[e];
                 lv.n_levels = g.n_levels;
                 lv.n_roots = g.B;
+                lv.n_stages = e ? solve_stages<double>(g.N, RC) : solve_stages<float>(g.N, RC);
                 plan_coarse(lv, g, e ? (int)sizeof(double) : (int)sizeof(float));
                 int off = 0;
                 for (int l = 0; l <= g.n_levels; ++l) {

@@ -1764,13 +1764,14 @@ __device__ __forceinline__ int sliced_matvec(const T *__restrict__ Mt, int n2, i
 template <typename T, int NT, int RC>
 __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, const T *v0, T *out0,
                                                   const T *__restrict__ M1, const T *v1, T *out1, int h2,
-                                                  int vstride, size_t ostride, int nred = 0) {
+                                                  int vstride, size_t ostride, int nred = 0,
+                                                  int tid = (int)threadIdx.x) {
     const int nrows = (M0 ? h2 : 0) + (M1 ? h2 : 0);
     if (nrows == 0) return;
     int G = 1;
     while (G < 32 && G * 2 * nrows <= NT && G * 2 <= h2) G *= 2;
     const int kl = (h2 + G - 1) / G;
-    for (int t = threadIdx.x; t < ((nrows * G + 31) & ~31); t += NT) {  // whole warps for the shuffles
+    for (int t = tid; t < ((nrows * G + 31) & ~31); t += NT) {  // whole warps for the shuffles
         const int row = t / G, gq = t % G;
         const bool live = row < nrows;
         const bool second = live && (!M0 || row >= h2);
@@ -1781,9 +1782,14 @@ __device__ __forceinline__ void coupling_products(const T *__restrict__ M0, cons
 #pragma unroll
         for (int rc = 0; rc < RC; ++rc) acc[rc] = T(0);
         if (live) {
-            const int k0 = gq * kl, k1 = min(h2, k0 + kl);
+            const int k0 = gq * kl, k1 = min(h2, k0 + kl), len = k1 - k0;
+            // each row starts its k-range at an offset of its own (p mod len): rows a
+            // warp reads together then fall in different shared-memory banks
+            int j = len > 0 ? p % len : 0;
 #pragma unroll 4
-            for (int k = k0; k < k1; ++k) {
+            for (int c = 0; c < len; ++c) {
+                const int k = k0 + j;
+                j = (j + 1 == len) ? 0 : j + 1;
                 const T m = M[(size_t)p * h2 + k];
 #pragma unroll
                 for (int rc = 0; rc < RC; ++rc) acc[rc] = fma(m, v[rc * vstride + k], acc[rc]);
@@ -2021,6 +2027,7 @@ struct LevelTable {
     int32_t slices[kMaxLevels + 2];
     int32_t n_levels, n_roots;
     int32_t coarse_level, coarse_m, coarse_K, coarse_rpu, coarse_units;
+    int32_t n_stages;  // staged-slice solve: copy stages per block (1 .. kMaxSolveStages)
 };
 
 // The BCR solve as a dataflow over all units in one cooperative launch, without
@@ -2118,20 +2125,30 @@ __host__ __device__ constexpr bool bcr_slice_staged(int N, int esize) {
     return (size_t)(2 * N) * (2 * N) * esize <= (size_t)kSolveStageBytes && (2 * N * esize) % 16 == 0;
 }
 
-// offset (in values) of the slice buffer: after the unit scratch, 16-byte aligned
-// (the staged-slice kernel double-buffers the coupling blocks: one more coupling area)
+// Shared memory of a staged-slice solve block: the unit scratch, then n_stages copy
+// stages, each one unit's A^{-1} columns ((2N)^2 values) followed by its coupling
+// area (2 (N/2)^2 values, when the couplings are staged; a coarse unit's r_c there),
+// every area starting on a 16-byte boundary.
+constexpr int kMaxSolveStages = 4;
+// values of T filling whole 16-byte chunks, at least v
 template <typename T>
-__host__ __device__ constexpr int bcr_slice_offset_values(int N, int NT, int RC) {
-    return ((bcr_unit_smem_values(N, NT, VecOf<T>::V, RC, (int)sizeof(T)) +
-             (bcr_couplings_staged(N, (int)sizeof(T)) ? bcr_coupling_values(N) : 0)) *
-                (int)sizeof(T) +
-            15) /
-           16 * 16 / (int)sizeof(T);
+__host__ __device__ constexpr int bcr_round16(int v) {
+    return (v * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
 }
-
-// offset (in values) of the first coupling area in a solve block's scratch
-__host__ __device__ constexpr int bcr_cbuf_offset_values(int N, int NT, int V, int RC) {
-    return RC * (2 * N) + RC * (2 * N) + RC * N + NT * V * RC;
+template <typename T>
+__host__ __device__ constexpr int bcr_stage_base_values(int N, int NT, int RC) {
+    return bcr_round16<T>(bcr_unit_smem_values(N, NT, VecOf<T>::V, RC, (int)sizeof(T)) -
+                          (bcr_couplings_staged(N, (int)sizeof(T)) ? bcr_coupling_values(N) : 0));
+}
+// one stage: the A^{-1} columns, the coupling area, and the right-hand sides of a
+// unit whose inputs are known at issue time (RC x 2N values)
+template <typename T>
+__host__ __device__ constexpr int bcr_stage_rhs_offset(int N) {
+    return bcr_round16<T>((2 * N) * (2 * N) + (bcr_couplings_staged(N, (int)sizeof(T)) ? bcr_coupling_values(N) : 0));
+}
+template <typename T>
+__host__ __device__ constexpr int bcr_stage_values(int N, int RC) {
+    return bcr_stage_rhs_offset<T>(N) + bcr_round16<T>(RC * 2 * N);
 }
 
 // The coupling blocks a unit multiplies (global memory; NULL where absent): forward
@@ -2181,7 +2198,8 @@ __device__ __forceinline__ void stage_unit_bulk(const T *__restrict__ A, const T
 // part[ks][rc][row] for this thread's (row group, k-slice) task: rows [0, nr) of the staged
 // A^{-1} columns As[k * lda + row] (shared memory).
 template <typename T, int NT, int RC>
-__device__ __forceinline__ int smem_matvec(const T *As, int lda, int nr, int nk, const T *coef, int cstride, T *part) {
+__device__ __forceinline__ int smem_matvec(const T *As, int lda, int nr, int nk, const T *coef, int cstride, T *part,
+                                           int tid = (int)threadIdx.x) {
     using VT = typename VecOf<T>::type;
     constexpr int V = VecOf<T>::V;
     const int RG = nr / V;
@@ -2189,7 +2207,7 @@ __device__ __forceinline__ int smem_matvec(const T *As, int lda, int nr, int nk,
     if (KS > nk) KS = nk;
     if (KS < 1) KS = 1;
     const int kl = (nk + KS - 1) / KS;
-    const int t = threadIdx.x;
+    const int t = tid;
     if (t < RG * KS) {
         const int rg = t % RG, ks = t / RG;
         const int k0 = ks * kl, k1 = min(nk, k0 + kl);
@@ -2198,7 +2216,7 @@ __device__ __forceinline__ int smem_matvec(const T *As, int lda, int nr, int nk,
         for (int rc = 0; rc < RC; ++rc)
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[rc][v] = T(0);
-#pragma unroll 4
+#pragma unroll 8
         for (int k = k0; k < k1; ++k) {
             const VT a = *reinterpret_cast<const VT *>(As + (size_t)k * lda + rg * V);
 #pragma unroll
@@ -2220,52 +2238,117 @@ __device__ __forceinline__ int smem_matvec(const T *As, int lda, int nr, int nk,
     return KS;
 }
 
-// Forward / backward unit whose A^{-1} slice (into As) and coupling blocks (mB, mC:
-// shared-memory copies, or global memory when not staged; NULL where absent) are in
-// flight; wait_copies() returns once they have landed, next_copy() issues the copies
-// for the block's next unit.
-template <typename T, int NT, int RC, typename WaitCopies, typename NextCopy>
-__device__ __forceinline__ void flow_fwd_unit_s(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc,
-                                                int sl, int S, T *rhs, T *Y, int N, int sumK, T *sm, const T *As,
-                                                const FlowSync *fs, WaitCopies wait_copies, NextCopy next_copy) {
-    const int n2 = 2 * N, h2 = N / 2;
-    T *rs = sm, *ys = sm + RC * n2, *part = ys + RC * n2 + RC * N;
+// ---------------------------------------------------------------------------
+// Warp roles of the staged solve: two compute groups of NTG threads (4 warps each)
+// and two service warps. Group g computes the block's units k = g, g + 2, ... and
+// synchronises on its own named barrier (1 + g); when it has finished a unit it only
+// ARRIVES on the unit's handoff barrier (id 3 + (k mod n_stages) + n_stages g, NTG + 32
+// threads) and goes on, while service warp g waits there, fences and bumps the
+// counters of the units that depend on this one (the release fence's latency is off
+// the compute path), then refills the unit's stage with the unit n_stages ahead. A stage's
+// next fill is issued only after its unit has been handed off, and a group waits for a
+// fill only once a service warp has published that it was issued (s_fills): so every
+// earlier phase of the stage's mbarrier has completed (its parity then names the right
+// phase), and a handoff barrier is arrived at again only after its previous round has
+// completed. Two groups keep two units' latencies (input counters, right-hand-side
+// loads) in flight on the SM, two service warps two fences.
+constexpr int kSolveGroups = 2;
+__device__ __forceinline__ void gbar_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ bool gbar_or(int id, int nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void handoff_arrive(int id, int nthreads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The thread indices and barrier of one compute group.
+struct Group {
+    int gt;   // thread index within the group
+    int bar;  // named barrier id of the group
+};
+
+// A unit's input wait on a compute group: its thread 0 polls (bounded), then the group barrier.
+template <int NTG>
+__device__ __forceinline__ void flow_wait_g(const FlowSync *fs, const Group &gr) {
+    if (gr.gt == 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int *c = k ? fs->wait1 : fs->wait0;
+            const int want = k ? fs->want1 : fs->want0;
+            if (!c) continue;
+            unsigned spins = 0;
+            while (ld_acquire_gpu(c) < want) {
+                if (++spins > fs->limit) {
+                    atomicExch(fs->err, 1);
+                    break;
+                }
+                if (spins > 256) __nanosleep(32);
+            }
+        }
+    }
+    gbar_sync(gr.bar, NTG);
+}
+
+// Forward / backward unit on a compute group, its A^{-1} slice in As and its coupling
+// blocks (mB, mC: shared-memory copies, or global memory when not staged; NULL where
+// absent) in flight; wait_copies() returns (true) once they have landed. The unit's
+// results are written when it returns; its signal is the service warp's.
+template <typename T, int NTG, int RC, typename WaitCopies>
+__device__ __forceinline__ bool ring_fwd_unit(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc, int sl,
+                                              int S, T *rhs, T *Y, int N, int sumK, T *sm, const T *As,
+                                              const T *rs_staged, const FlowSync *fs, const Group &gr,
+                                              WaitCopies wait_copies) {
+    const int n2 = 2 * N, h2 = N / 2, gt = gr.gt;
+    T *ys = sm + RC * n2, *part = ys + RC * n2 + RC * N;
+    const T *rs = rs_staged ? rs_staged : sm;  // right-hand sides staged with the unit's copies, or loaded here
     const size_t rstride = (size_t)sumK * n2;
     const int nr = n2 / S, row0 = sl * nr;
-    flow_wait(fs);
-    for (int i = threadIdx.x; i < RC * n2; i += NT) {
-        const int rc = i / n2, k = i - rc * n2;
-        rs[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
+    if (!rs_staged) {
+        flow_wait_g<NTG>(fs, gr);
+        for (int i = gt; i < RC * n2; i += NTG) {
+            const int rc = i / n2, k = i - rc * n2;
+            sm[i] = rc < nrc ? __ldcg(rhs + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + k) : T(0);
+        }
     }
-    wait_copies();
-    __syncthreads();
-    const int KS = smem_matvec<T, NT, RC>(As + row0, n2, nr, n2, rs, n2, part);
-    __syncthreads();
-    next_copy();  // the slice buffer is free
-    for (int idx = threadIdx.x; idx < RC * nr; idx += NT) {
+    if (!wait_copies()) return false;  // a group barrier: rs complete too
+    const int KS = smem_matvec<T, NTG, RC>(As + row0, n2, nr, n2, rs, n2, part, gt);
+    gbar_sync(gr.bar, NTG);
+    for (int idx = gt; idx < RC * nr; idx += NTG) {
         const int rc = idx / nr, row = idx - rc * nr;
         T y = T(0);
         for (int q = 0; q < KS; ++q) y += part[(q * RC + rc) * nr + row];
         ys[rc * n2 + row0 + row] = y;
         if (rc < nrc) Y[(size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row] = y;
     }
-    __syncthreads();
-    coupling_products<T, NT, RC>(mB, ys + N + h2, mB ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr,
-                                 mC, ys, mC ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr, h2,
-                                 n2, rstride, nrc);
-    flow_signal_release(fs, NT - 64);  // warp NT/32 - 1 issues the copies
+    gbar_sync(gr.bar, NTG);
+    coupling_products<T, NTG, RC>(mB, ys + N + h2,
+                                  mB ? rhs + (size_t)r0 * rstride + (size_t)it.right * n2 + h2 : nullptr, mC, ys,
+                                  mC ? rhs + (size_t)r0 * rstride + (size_t)it.left * n2 + N : nullptr, h2, n2,
+                                  rstride, nrc, gt);
+    return true;
 }
 
-template <typename T, int NT, int RC, typename WaitCopies, typename NextCopy>
-__device__ __forceinline__ void flow_bwd_unit_s(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc,
-                                                int sl, int S, T *Y, int N, int sumK, T *sm, const T *As,
-                                                const FlowSync *fs, WaitCopies wait_copies, NextCopy next_copy) {
-    const int n2 = 2 * N, h2 = N / 2;
+template <typename T, int NTG, int RC, typename WaitCopies>
+__device__ __forceinline__ bool ring_bwd_unit(const T *mB, const T *mC, const BcrItem &it, int r0, int nrc, int sl,
+                                              int S, T *Y, int N, int sumK, T *sm, const T *As, const FlowSync *fs,
+                                              const Group &gr, WaitCopies wait_copies) {
+    const int n2 = 2 * N, h2 = N / 2, gt = gr.gt;
     T *gv = sm, *g = sm + RC * N, *part = sm + RC * (5 * N);
     const size_t rstride = (size_t)sumK * n2;
     const int nr = n2 / S, row0 = sl * nr;
-    flow_wait(fs);
-    for (int idx = threadIdx.x; idx < RC * N; idx += NT) {
+    flow_wait_g<NTG>(fs, gr);
+    for (int idx = gt; idx < RC * N; idx += NTG) {
         const int rc = idx / N, k = idx - rc * N;
         T v = T(0);
         if (rc < nrc) {
@@ -2275,39 +2358,36 @@ __device__ __forceinline__ void flow_bwd_unit_s(const T *mB, const T *mC, const 
         }
         gv[idx] = v;
     }
-    wait_copies();
-    __syncthreads();
-    coupling_products<T, NT, RC>(mB, gv, g, mC, gv + h2, g + h2, h2, N, N);
+    if (!wait_copies()) return false;
+    coupling_products<T, NTG, RC>(mB, gv, g, mC, gv + h2, g + h2, h2, N, N, 0, gt);
     if (it.right < 0)
-        for (int idx = threadIdx.x; idx < RC * h2; idx += NT) g[(idx / h2) * N + h2 + idx % h2] = T(0);
-    __syncthreads();
-    const int KS = smem_matvec<T, NT, RC>(As + row0, n2, nr, N, g, N, part);
-    __syncthreads();
-    next_copy();
-    for (int idx = threadIdx.x; idx < nrc * nr; idx += NT) {
+        for (int idx = gt; idx < RC * h2; idx += NTG) g[(idx / h2) * N + h2 + idx % h2] = T(0);
+    gbar_sync(gr.bar, NTG);
+    const int KS = smem_matvec<T, NTG, RC>(As + row0, n2, nr, N, g, N, part, gt);
+    gbar_sync(gr.bar, NTG);
+    for (int idx = gt; idx < nrc * nr; idx += NTG) {
         const int rc = idx / nr, row = idx - rc * nr;
         T sacc = T(0);
         for (int q = 0; q < KS; ++q) sacc += part[(q * RC + rc) * nr + row];
         atomicAdd(Y + (size_t)(r0 + rc) * rstride + (size_t)it.cell * n2 + row0 + row, -sacc);
     }
-    flow_signal_release(fs, NT - 64);  // warp NT/32 - 1 issues the copies
+    return true;
 }
 
-// The coarse unit u: rows [u rpu, (u + 1) rpu) of u_c = G r_c (G rows staged in As by
-// the unit's bulk copy; r_c, the right-hand sides of the m coarse cells in coarse
-// order, gathered into rc) once every coarse cell has received the pushes of the
-// levels below c; the rows are written to Y and the cell's completion counter bumped.
-template <typename T, int NT, typename WaitCopies, typename NextCopy>
-__device__ __forceinline__ void flow_coarse_unit(int u, const LevelTable &lv, const T *rhs, T *Y, int N, T *rc,
-                                                 const T *As, int *cnt, int *done, int *err,
-                                                 WaitCopies wait_copies, NextCopy next_copy) {
-    const int n2 = 2 * N, cl = lv.coarse_level, m = lv.coarse_m, n = m * n2, rpu = lv.coarse_rpu;
-    if ((int)threadIdx.x < m) {  // one poller per coarse cell
-        const int a = (int)threadIdx.x << cl;
+// The coarse unit u on a compute group: rows [u rpu, (u + 1) rpu) of u_c = G r_c (G
+// rows staged in As by the unit's bulk copy; r_c, the right-hand sides of the m coarse
+// cells in coarse order, gathered into rc) once every coarse cell has received the
+// pushes of the levels below c; the rows are written to Y.
+template <typename T, int NTG, typename WaitCopies>
+__device__ __forceinline__ bool ring_coarse_unit(int u, const LevelTable &lv, const T *rhs, T *Y, int N, T *rc,
+                                                 const T *As, const int *cnt, int *err, unsigned limit,
+                                                 const Group &gr, WaitCopies wait_copies) {
+    const int n2 = 2 * N, cl = lv.coarse_level, m = lv.coarse_m, n = m * n2, rpu = lv.coarse_rpu, gt = gr.gt;
+    for (int j = gt; j < m; j += NTG) {  // one poller per coarse cell
+        const int a = j << cl;
         int want = 0;
         for (int lp = 0; lp < cl; ++lp) want += (a >= (1 << lp)) + (a + (1 << lp) < lv.coarse_K);
         unsigned spins = 0;
-        const unsigned limit = flow_spin_limit(err);
         while (want && ld_acquire_gpu(cnt + a) < want) {
             if (++spins > limit) {
                 atomicExch(err, 1);
@@ -2316,15 +2396,14 @@ __device__ __forceinline__ void flow_coarse_unit(int u, const LevelTable &lv, co
             if (spins > 256) __nanosleep(32);
         }
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n; idx += NT) {
+    gbar_sync(gr.bar, NTG);
+    for (int idx = gt; idx < n; idx += NTG) {
         const int j = idx / n2;
         rc[idx] = __ldcg(rhs + (size_t)(j << cl) * n2 + (idx - j * n2));
     }
-    wait_copies();
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (int rr = threadIdx.x >> 5; rr < rpu; rr += NT / 32) {
+    if (!wait_copies()) return false;
+    const int lane = gt & 31;
+    for (int rr = gt >> 5; rr < rpu; rr += NTG / 32) {
         const T *g = As + (size_t)rr * n;
         T acc = T(0);
         for (int col = lane; col < n; col += 32) acc = fma(g[col], rc[col], acc);
@@ -2334,39 +2413,53 @@ __device__ __forceinline__ void flow_coarse_unit(int u, const LevelTable &lv, co
             Y[(size_t)(j << cl) * n2 + (row - j * n2)] = acc;
         }
     }
-    __syncthreads();
-    next_copy();
-    FlowSync fs{};
-    fs.err = err;
-    fs.sig0 = done + (((u * rpu) / n2) << cl);
-    flow_signal_release(&fs, NT - 64);
+    return true;
 }
 
 // The dataflow BCR solve with staged slices (same unit order, counters and waits as
 // k_bcr_solve_flow; with a coarse step, the levels from coarse_level up and the
 // root are one phase of coarse units between the forward and backward levels below
-// it). Shared memory: the unit scratch, then the slice buffer.
+// it). Shared memory: one unit scratch per compute group, then lv.n_stages copy
+// stages. The factor columns, couplings and rows of G a unit reads do not change
+// during the solve, so a block requests them lv.n_stages units ahead of the unit it
+// computes (a ring: unit k of the block uses stage k mod n_stages, refilled with unit
+// k + n_stages once unit k has been handed off); the copies thus stream while the
+// compute groups wait for their units' inputs, and the dataflow waits only order the
+// right-hand sides. The right-hand sides of level-0 forward units (the kernel's
+// input, no dependencies) travel with their stage's copies, except for the first
+// n_stages units, requested before the previous kernel has finished.
+// NT = kSolveGroups compute groups of NTG threads + kSolveGroups service warps; service
+// warp g hands off, signals and refills the units of group g.
 template <typename T, int NT, int RC>
-__global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict__ A, const T *__restrict__ Bc,
+__global__ void __launch_bounds__(NT, 1) k_bcr_solve_flow_s(const T *__restrict__ A, const T *__restrict__ Bc,
                                                             const T *__restrict__ Cc,
                                                             const BcrItem *__restrict__ items, LevelTable lv, T *rhs,
                                                             T *Y, int N, int sumK, int R, int *cnt, int *done,
                                                             int *err, const T *__restrict__ G, int *zero_next,
                                                             long long nzero) {
-    static_assert(NT >= 64 && NT % 32 == 0, "copies and signals leave warp 0 free");
+    constexpr int NTG = (NT - 32 * kSolveGroups) / kSolveGroups;
+    static_assert(NTG >= 64 && NTG % 32 == 0 && NT == kSolveGroups * (NTG + 32), "compute groups and service warps");
     // the next solve's counters (the other half of the double-buffered pair) start at zero
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nzero; i += (long long)gridDim.x * NT)
         zero_next[i] = 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t s_bar;  // one phase per unit: its slice and couplings landed
+    __shared__ __align__(8) uint64_t s_bar[kMaxSolveStages];  // per stage: one phase per fill
+    __shared__ int s_fills[kMaxSolveStages];                   // per stage: fills issued so far
+    __shared__ int s_stop;                                     // a compute group stopped (copy timeout)
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T *As = sm + bcr_slice_offset_values<T>(N, NT, RC);
-    // two coupling areas, alternating between the block's consecutive units (the next
-    // unit's couplings are requested with its slice while this unit still uses its own)
-    const int hh = (N / 2) * (N / 2);
-    T *cb0 = bcr_couplings_staged(N, (int)sizeof(T)) ? sm + bcr_cbuf_offset_values(N, NT, VecOf<T>::V, RC) : nullptr;
+    const int hh = (N / 2) * (N / 2), n2 = 2 * N;
+    const bool cpl_staged = bcr_couplings_staged(N, (int)sizeof(T));
+    const int ns = lv.n_stages, base = bcr_stage_base_values<T>(N, NTG, RC);
+    const size_t rstride = (size_t)sumK * n2;
+    auto stage_slice = [&](int st) { return sm + kSolveGroups * base + st * bcr_stage_values<T>(N, RC); };
+    auto stage_cpl = [&](int st) { return cpl_staged ? stage_slice(st) + n2 * n2 : (T *)nullptr; };
+    auto stage_rhs = [&](int st) { return stage_slice(st) + bcr_stage_rhs_offset<T>(N); };
     if (threadIdx.x == 0) {
-        tc::mbar_init(&s_bar, 1);
+        for (int st = 0; st < ns; ++st) {
+            tc::mbar_init(&s_bar[st], 1);
+            s_fills[st] = 0;
+        }
+        s_stop = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -2412,50 +2505,131 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
         q.ch = (w / q.S) % nchunk;
         q.item = w / (q.S * nchunk);
     };
-    // a unit's copies: its A^{-1} columns and couplings, or a coarse unit's rows of G
-    auto stage = [&](const Pos &q, const BcrItem &itq, T *cbq) {
-        if (q.l < 0) {
-            const int n = lv.coarse_m * 2 * N, rpu = lv.coarse_rpu;
-            tc::fence_async_smem();
-            if ((threadIdx.x & 31) == 0) {
-                const uint32_t bytes = (uint32_t)((size_t)rpu * n * sizeof(T));
-                tc::mbar_arrive_expect_tx(&s_bar, bytes);
-                tc::bulk_copy_g2s(As, G + (size_t)q.item * rpu * n, bytes, &s_bar);
-            }
-        } else {
-            stage_unit_bulk<T>(A, Bc, Cc, itq, q.sl, q.S, phase_bwd(q.ph), N, As, cbq, &s_bar);
-        }
+    // unit k of the block (at q) gets its right-hand sides with its copies: a level-0
+    // forward unit requested after the previous kernel has finished, all RC rhs present
+    auto rhs_staged = [&](const Pos &q, int k) {
+        return k >= ns && q.l == 0 && !phase_bwd(q.ph) && (q.ch + 1) * RC <= R;
     };
-    Pos cur{0, 0, 0, 0, 0, 0, 0, false};
-    int gidx = blockIdx.x;
-    uint32_t parity = 0;  // phase of s_bar (and coupling area) of the current unit
-    bool stalled = false;
-    locate(cur, gidx);
-    BcrItem it_nx{};
-    if (cur.valid) {
-        if (cur.l >= 0) it_nx = items[lv.off[cur.l] + cur.item];
-        if (threadIdx.x >= NT - 32) stage(cur, it_nx, cb0);  // factors, couplings, G: not written by the previous kernel
+    constexpr int kHandoff = NTG + 32;  // threads of a handoff barrier: one group and its service warp
+    if (threadIdx.x >= kSolveGroups * NTG) {
+        // ---- service warps: copies into the ring, then per unit: handoff, refill, signal
+        const int sw = (threadIdx.x - kSolveGroups * NTG) >> 5, lane = threadIdx.x & 31;
+        // copies of unit k into its stage (q located at k)
+        auto issue = [&](const Pos &q, int k) {
+            const int st = k % ns;
+            if (q.l < 0) {
+                const int n = lv.coarse_m * n2, rpu = lv.coarse_rpu;
+                tc::fence_async_smem();
+                if (lane == 0) {
+                    const uint32_t bytes = (uint32_t)((size_t)rpu * n * sizeof(T));
+                    tc::mbar_arrive_expect_tx(&s_bar[st], bytes);
+                    tc::bulk_copy_g2s(stage_slice(st), G + (size_t)q.item * rpu * n, bytes, &s_bar[st]);
+                }
+            } else {
+                const BcrItem itq = items[lv.off[q.l] + q.item];
+                if (rhs_staged(q, k) && lane == 0) {
+                    // the rhs copies join the phase before stage_unit_bulk's arrival
+                    const uint32_t rb = (uint32_t)(n2 * sizeof(T));
+                    tc::mbar_expect_tx(&s_bar[st], RC * rb);
+                    for (int rc = 0; rc < RC; ++rc)
+                        tc::bulk_copy_g2s(stage_rhs(st) + rc * n2,
+                                          rhs + (size_t)(q.ch * RC + rc) * rstride + (size_t)itq.cell * n2, rb,
+                                          &s_bar[st]);
+                }
+                stage_unit_bulk<T>(A, Bc, Cc, itq, q.sl, q.S, phase_bwd(q.ph), N, stage_slice(st), stage_cpl(st),
+                                   &s_bar[st]);
+            }
+            __syncwarp();
+            if (lane == 0) *(volatile int *)&s_fills[st] = k / ns + 1;
+        };
+        if (sw == 0) {  // factors, couplings and G are not written by the previous kernel
+            Pos q{0, 0, 0, 0, 0, 0, 0, false};
+            for (int k = 0; k < ns; ++k) {
+                locate(q, blockIdx.x + k * (int)gridDim.x);
+                if (q.valid) issue(q, k);
+            }
+        }
+        tc::grid_dependency_wait();  // later copies may carry the previous kernel's right-hand sides
+        Pos cur{0, 0, 0, 0, 0, 0, 0, false}, nxt{0, 0, 0, 0, 0, 0, 0, false};
+        int k = sw;
+        for (;; k += kSolveGroups) {
+            locate(cur, blockIdx.x + k * (int)gridDim.x);
+            if (!cur.valid) break;
+            gbar_sync(3 + k % ns + ns * sw, kHandoff);  // group sw is done with unit k
+            if (*(volatile int *)&s_stop) break;
+            if (lane == 0) {
+                int *sig[3] = {nullptr, nullptr, nullptr};
+                if (cur.l < 0) {
+                    sig[0] = done + (((cur.item * lv.coarse_rpu) / n2) << cl);
+                } else {
+                    const BcrItem it = items[lv.off[cur.l] + cur.item];
+                    int *cnt_c = cnt + (size_t)cur.ch * sumK, *done_c = done + (size_t)cur.ch * sumK;
+                    const int nr = n2 / cur.S, row0 = cur.sl * nr;
+                    if (!phase_bwd(cur.ph)) {
+                        if (it.right >= 0 && row0 + nr == n2) sig[0] = cnt_c + it.right;
+                        if (it.left >= 0 && row0 == 0) sig[1] = cnt_c + it.left;
+                        if (it.left < 0) sig[2] = done_c + it.cell;
+                    } else {
+                        sig[0] = done_c + it.cell;
+                    }
+                }
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (sig[q]) atomicAdd(sig[q], 1);
+            }
+            __syncwarp();
+            // then the stage is refilled (the signal first: the dependency chain of the
+            // narrow levels waits on it, the ring has n_stages - 1 other units in flight)
+            locate(nxt, blockIdx.x + (k + ns) * (int)gridDim.x);
+            if (nxt.valid) issue(nxt, k + ns);
+        }
+        // no copy may still be landing when the block exits: wait (bounded) for each
+        // stage's latest fill (at once if it has landed; it is pending only after a stop)
+        for (int st = 0; st < ns; ++st) {
+            const int f = *(volatile int *)&s_fills[st];
+            if (f > 0) tc::mbar_wait(&s_bar[st], (uint32_t)(f - 1) & 1u);
+        }
+        return;
     }
+    // ---- compute groups
+    const int grp = threadIdx.x / NTG;
+    const Group gr{(int)threadIdx.x - grp * NTG, 1 + grp};
+    T *smg = sm + grp * base;
     tc::grid_dependency_wait();  // the right-hand sides come from the previous kernel
-    while (cur.valid) {
-        const BcrItem it = it_nx;
-        Pos nxt = cur;
-        locate(nxt, gidx + gridDim.x);
-        if (nxt.valid && nxt.l >= 0) it_nx = items[lv.off[nxt.l] + nxt.item];  // arrives while this unit runs
-        T *cb = cb0 ? cb0 + parity * 2 * hh : nullptr, *cb_next = cb0 ? cb0 + (parity ^ 1) * 2 * hh : nullptr;
+    Pos cur{0, 0, 0, 0, 0, 0, 0, false};
+    for (int k = grp;; k += kSolveGroups) {
+        locate(cur, blockIdx.x + k * (int)gridDim.x);
+        if (!cur.valid) break;
+        const int st = k % ns;
+        const uint32_t parity = (uint32_t)(k / ns) & 1u;
+        T *As = stage_slice(st), *cb = stage_cpl(st);
+        // bounded; a group whose copies never land records the error and stops (the
+        // units left are then timed out by their consumers)
         auto wait_copies = [&]() {
-            // bounded; a block whose copies never land records the error and stops
-            // issuing (its remaining units are left to time out in their consumers)
-            stalled = __syncthreads_or(!tc::mbar_wait(&s_bar, parity)) != 0;
-            if (stalled && threadIdx.x == 0) atomicExch(err, 1);
+            bool ok = true;
+            if (*(volatile int *)&s_fills[st] <= k / ns) {  // the fill has not been issued yet
+                const unsigned long long t0 = tc::global_ns();
+                while (*(volatile int *)&s_fills[st] <= k / ns)
+                    if (tc::global_ns() - t0 > tc::kWaitNs) {
+                        ok = false;
+                        break;
+                    }
+            }
+            if (ok) ok = tc::mbar_wait(&s_bar[st], parity);
+            const bool stalled = gbar_or(gr.bar, NTG, !ok);
+            if (stalled && gr.gt == 0) {
+                atomicExch(err, 1);
+                s_stop = 1;
+            }
+            return !stalled;
         };
-        auto next_copy = [&]() {
-            if (nxt.valid && !stalled && threadIdx.x >= NT - 32) stage(nxt, it_nx, cb_next);
-        };
+        bool ok;
         if (cur.l < 0) {
-            // the coarse area of this unit's parity holds r_c (coarse units take no couplings)
-            flow_coarse_unit<T, NT>(cur.item, lv, rhs, Y, N, cb, As, cnt, done, err, wait_copies, next_copy);
+            // the stage's coupling area holds r_c (coarse units take no couplings)
+            ok = ring_coarse_unit<T, NTG>(cur.item, lv, rhs, Y, N, cb, As, cnt, err, limit, gr, wait_copies);
         } else {
+            const BcrItem it = items[lv.off[cur.l] + cur.item];
             const bool bwd = phase_bwd(cur.ph);
             const T *mB, *mC;
             unit_coupling_sources(it, cur.sl, cur.S, bwd, N, Bc, Cc, mB, mC);
@@ -2463,10 +2637,8 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                 mB = mB ? cb : nullptr;
                 mC = mC ? cb + hh : nullptr;
             }
-            const int S = cur.S, sl = cur.sl, ch = cur.ch;
-            const int r0 = ch * RC, nrc = min(RC, R - r0);
-            int *cnt_c = cnt + (size_t)ch * sumK, *done_c = done + (size_t)ch * sumK;
-            const int n2 = 2 * N, nr = n2 / S, row0 = sl * nr;
+            const int r0 = cur.ch * RC, nrc = min(RC, R - r0);
+            const int *cnt_c = cnt + (size_t)cur.ch * sumK, *done_c = done + (size_t)cur.ch * sumK;
             FlowSync fs{};
             fs.err = err;
             fs.limit = limit;
@@ -2478,11 +2650,9 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                     fs.wait0 = cnt_c + it.cell;
                     fs.want0 = want;
                 }
-                if (it.right >= 0 && row0 + nr == n2) fs.sig0 = cnt_c + it.right;
-                if (it.left >= 0 && row0 == 0) fs.sig1 = cnt_c + it.left;
-                if (it.left < 0) fs.sig2 = done_c + it.cell;
-                flow_fwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, rhs, Y, N, sumK, sm, As, &fs, wait_copies,
-                                           next_copy);
+                ok = ring_fwd_unit<T, NTG, RC>(mB, mC, it, r0, nrc, cur.sl, cur.S, rhs, Y, N, sumK, smg, As,
+                                               rhs_staged(cur, k) ? stage_rhs(st) : (const T *)nullptr, &fs, gr,
+                                               wait_copies);
             } else {
                 const int step = 1 << it.level;
                 fs.wait0 = done_c + it.left;
@@ -2491,19 +2661,13 @@ __global__ void __launch_bounds__(NT, 2) k_bcr_solve_flow_s(const T *__restrict_
                     fs.wait1 = done_c + it.right;
                     fs.want1 = done_want(bcr_cell_level(it.local + step, nl));
                 }
-                fs.sig0 = done_c + it.cell;
-                flow_bwd_unit_s<T, NT, RC>(mB, mC, it, r0, nrc, sl, S, Y, N, sumK, sm, As, &fs, wait_copies,
-                                           next_copy);
+                ok = ring_bwd_unit<T, NTG, RC>(mB, mC, it, r0, nrc, cur.sl, cur.S, Y, N, sumK, smg, As, &fs, gr,
+                                               wait_copies);
             }
         }
-        if (stalled) {
-            // no copy may still be landing when the block exits: wait once more (bounded)
-            tc::mbar_wait(&s_bar, parity);
-            break;
-        }
-        cur = nxt;
-        gidx += gridDim.x;
-        parity ^= 1u;
+        // every thread of the group has written and read what the unit needs before the handoff
+        handoff_arrive(3 + st + ns * grp, kHandoff);
+        if (!ok) break;
     }
 }
 
