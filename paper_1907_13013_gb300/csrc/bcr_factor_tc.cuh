@@ -88,7 +88,8 @@ struct Smem {
     static constexpr uint32_t red = iperm + kN2 * 4;                     // 4 doubles
     static constexpr uint32_t bars = red + 4 * 8;                        // 3 mbarriers
     static constexpr uint32_t tslot = bars + 3 * 8;
-    static constexpr uint32_t used = tslot + 8;
+    static constexpr uint32_t next = tslot + 4;                          // the item taken from the queue
+    static constexpr uint32_t used = next + 4;
     // at least this much per CTA, so that no more than 4 CTAs share an SM (4 x 128
     // TMEM columns)
     static constexpr uint32_t total = used > 48 * 1024 ? used : 48 * 1024;
@@ -395,7 +396,11 @@ __device__ __forceinline__ void warp_mm32(const float *M, int ldm, const float *
 }  // namespace tcf
 
 // The factorization dataflow of k_bcr_factor_flow with tensor-core inversions (FP32,
-// 2N = 128): one 128-thread CTA per item at a time, up to 4 CTAs per SM. An item
+// 2N = 128): one 128-thread CTA per item at a time, up to 4 CTAs per SM. CTAs take
+// the items in their order (levels ascending, roots last) from a work queue (*queue,
+// zero at launch): every item a CTA waits for has a lower index and was taken by a
+// CTA that is already running, so the launch needs no co-residency guarantee (it is
+// an ordinary launch, not a cooperative one). An item
 // stages the parts of its block that no lower level updates into TMEM before it
 // waits for its counter, then the two updated chunks; its coupling blocks arrive by
 // bulk copy during the inversion, and the Schur updates of its kept neighbours are
@@ -408,7 +413,8 @@ __global__ void __launch_bounds__(tcf::kThreads, 4) k_bcr_factor_tc(float *__res
                                                                      const BcrItem *__restrict__ items, int n_items,
                                                                      float *__restrict__ Bc, float *__restrict__ Cc,
                                                                      unsigned long long *__restrict__ growth,
-                                                                     int *__restrict__ status, int *cnt, int *err) {
+                                                                     int *__restrict__ status, int *cnt, int *err,
+                                                                     int *queue) {
     using namespace tcf;
     extern __shared__ __align__(128) unsigned char smem_ftc[];
     unsigned char *sm = smem_ftc;
@@ -434,7 +440,12 @@ __global__ void __launch_bounds__(tcf::kThreads, 4) k_bcr_factor_tc(float *__res
     const uint32_t trow = tmem + ((uint32_t)(32 * w) << 16);
     const unsigned limit = flow_spin_limit(err);
     uint32_t pa = 0, pb = 0, pc = 0;
-    for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+    int *s_next = reinterpret_cast<int *>(sm + Smem::next);
+    for (;;) {
+        if (t == 0) *s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int ii = *s_next;
+        if (ii >= n_items) break;
         const BcrItem it = items[ii];
         float *Ag = A + (size_t)it.cell * kN2 * kN2;
         int *iperm = reinterpret_cast<int *>(sm + Smem::iperm);

@@ -562,12 +562,11 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         int n_items = lv.off[g.n_levels] + lv.n_roots;
         unsigned long long *growth = ctx->d_growth;
         int *status = ctx->d_status, *cnt = ctx->d_factor_cnt, *err = ctx->d_dev_err;
-        void *args[] = {(void *)&A,      (void *)&items,  (void *)&n_items, (void *)&Bc, (void *)&Cc,
-                        (void *)&growth, (void *)&status, (void *)&cnt,     (void *)&err};
-        CK(cudaMemsetAsync(cnt, 0, (size_t)g.sumK * sizeof(int), st));
+        int *queue = ctx->d_factor_cnt + g.sumK;  // the work queue's next item
+        CK(cudaMemsetAsync(cnt, 0, ((size_t)g.sumK + 1) * sizeof(int), st));
         Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
-        CK(cudaLaunchCooperativeKernel((const void *)k_bcr_factor_tc, dim3(ctx->factor_tc_grid),
-                                       dim3(tcf::kThreads), args, tcf::Smem::total, st));
+        k_bcr_factor_tc<<<ctx->factor_tc_grid, tcf::kThreads, tcf::Smem::total, st>>>(A, items, n_items, Bc, Cc,
+                                                                                    growth, status, cnt, err, queue);
     } else if (ctx->factor_grid[e] > 0) {
         // every level and the roots in one cooperative launch (dataflow between items)
         const LevelTable &lv = ctx->lvt[e];
@@ -1405,7 +1404,7 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             ctx->flow_n = (size_t)nchunk * g.sumK;
             CK(dalloc(ctx, &ctx->d_flow, 4 * ctx->flow_n));
             CK(cudaMemset(ctx->d_flow, 0, 4 * ctx->flow_n * sizeof(int)));
-            CK(dalloc(ctx, &ctx->d_factor_cnt, (size_t)g.sumK));
+            CK(dalloc(ctx, &ctx->d_factor_cnt, (size_t)g.sumK + 1));  // + the tensor-core factorization's queue
         }
         CK(dalloc(ctx, &ctx->d_growth, 1));
         CK(dalloc(ctx, &ctx->d_status, 1));
@@ -1486,11 +1485,15 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
             }
             if (2 * g.N == tcf::kN2 && ctx->precision == FPSA_PRECISION_MIXED) {
                 // up to 4 CTAs per SM (4 x 128 TMEM columns), as occupancy allows
-                int fper = 0;
+                // 4 CTAs per SM (the shared memory of each admits no more, so their 4 x 128
+                // TMEM columns fit; the runtime's occupancy estimate for kernels that allocate
+                // tensor memory is one CTA per SM, so it is not consulted: the launch is not
+                // cooperative and takes its items from a queue)
                 CK(raise_smem_limit((const void *)k_bcr_factor_tc, (int)tcf::Smem::total));
-                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, k_bcr_factor_tc, tcf::kThreads,
-                                                                 tcf::Smem::total));
-                ctx->factor_tc_grid = std::min(fper, 4) * nsm;
+                CK(cudaFuncSetAttribute((const void *)k_bcr_factor_tc,
+                                        cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+                ctx->factor_tc_grid = 4 * nsm;
             }
             for (int e = 0; e < 2; ++e) {
                 LevelTable &lv = ctx->lvt[e];
