@@ -51,7 +51,8 @@ TOL = 1e-10
 # kernel on this workload, measured by ncu for each row-slice cap of the BCR solve (the
 # launch shape that changes its units; one block per SM), keyed by (kernel, precision,
 # solve_max_slices). A shape missing here reports traffic null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("k_bcr_solve_flow_s", "mixed", 1): 224.14e6, ("k_bcr_solve_flow_s", "mixed", 2): 223.64e6,
+               ("k_bcr_solve_flow_s", "mixed", 4): 222.42e6}
 
 
 def dist_env():
