@@ -229,6 +229,106 @@ def cpu_baseline_all_cores(laplacian):
                                                                      max(secs))}
 
 
+def balance_defect(p, phi, r, tab):
+    """Particle balance of the converged LD solution for right-hand side r: |emission -
+    absorption - leakage| / emission (exact for the discrete solution; tab = the S_N tables)."""
+    mu, w, M = tab["mu"], tab["w"], tab["M"]
+    pos, neg = mu > 0, mu < 0
+    jr = (w[pos] * mu[pos]) @ (M[pos] @ phi[r, -1, 1])
+    jl = (w[neg] * -mu[neg]) @ (M[neg] @ phi[r, 0, 0])
+    h, Q = p["h"], p["Q"][r]
+    sa = p["sigma_t"] - p["sigma_s"][:, 0]
+    emission = np.sum(h * (Q[:, 0, 0] + Q[:, 1, 0]) / 2)
+    absorption = np.sum(sa * h * (phi[r, :, 0, 0] + phi[r, :, 1, 0]) / 2)
+    return float(abs(emission - absorption - jl - jr) / emission)
+
+
+def scale_secondary(binding, inputs, dev, stream, hbm, precisions):
+    """The Scale workload at full size (K = 20000, S256, L = 255, HG g = 0.99, c = 0.9999,
+    64 seeded sources): one set_xs and one solve per (precision, method), FPSA-SI and
+    GMRES(30) right-preconditioned by the FP solve, timed by the host clock around both,
+    with CUDA events around every launch (the library's profiler) for the per-kernel
+    times; the particle balance of the converged flux for 3 of the right-hand sides."""
+    import torch
+    p = inputs.scale_slab()
+    K, N, L, R = p["h"].size, p["N"], p["L"], p["Q"].shape[0]
+    tab = binding.tables(N, L, "mpd")
+    out = {"workload": "scale_slab: 1 cm, K=20000, S256, L=255, HG g=0.99, c=0.9999, sigma_t=100, "
+                       "64 rhs Q~U[0,1), vacuum, MPD, tol 1e-10", "solves": {}}
+    d_st = torch.tensor(p["sigma_t"], device=dev)
+    d_ss = torch.tensor(p["sigma_s"], device=dev)
+    d_q = torch.tensor(p["Q"], device=dev)
+    phi = torch.zeros((R, K, 2, L + 1), dtype=torch.float64, device=dev)
+    for prec in precisions:
+        ctx = binding.Context([K], p["h"], N, L, n_rhs=R, laplacian="mpd", precision=prec, device=dev.index,
+                              stream=stream.cuda_stream)
+        for meth, kw in (("fpsa", {}), ("gmres", {"restart": 30})):
+            ctx.profile_enable(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.set_xs(d_st, d_ss, d_q)
+            _, st = ctx.solve(meth, tol=TOL, max_iterations=400, raise_on_notconv=False, out=phi, **kw)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            prof = ctx.profile_read()
+            ph = phi.cpu().numpy()
+            phases = {k: v for k, v in prof.items() if v["timed"]}
+            dom = max(phases, key=lambda k: phases[k]["ms"])
+            per = phases[dom]["ms"] / phases[dom]["timed"]
+            esize = 4 if prec == "mixed" else 8
+            n2 = 2 * N
+            if dom == "bcr_solve":
+                # the factors once per solve (every eliminated cell: A^{-1} forward, its inflow
+                # columns backward, two couplings), whatever the number of right-hand sides
+                byt = esize * K * (n2 * n2 + n2 * N + 2 * (N // 2) ** 2)
+                roof = {"kernel": "k_bcr_solve_flow", "bound": "hbm", "achieved": byt / (per * 1e-3) / 1e9,
+                        "peak": hbm, "unit": "GB/s", "algorithmic_bytes": byt}
+            elif dom == "contract":
+                # 2 N (L+1) flop per column, K x 2 columns per rhs, 64 rhs, per contraction launch
+                fl = 2.0 * N * (L + 1) * 2 * K * R
+                roof = {"kernel": "contractions (SIMT)", "bound": "alu", "achieved": fl / (per * 1e-3) / 1e12,
+                        "peak": 74.0 if esize == 4 else 1.20, "unit": "TFLOP/s",
+                        "peak_source": "FP32 / FP64 FMA-chain probe on GB300 (74 / 1.20 TFLOP/s)"}
+            else:
+                roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s"}
+            if roof.get("achieved") is not None:
+                roof["frac"] = roof["achieved"] / roof["peak"]
+            roof["avg_launch_ms"] = per
+            out["solves"]["%s_%s" % (prec, meth)] = {
+                "value": 1.0 / wall, "unit": "solves/s (64 rhs each)", "wall_s": wall, "setup_ms": st["setup_ms"],
+                "solve_ms": st["solve_ms"], "iterations": st["iterations"], "outer_iterations": st["outer_iterations"],
+                "sweeps": st["sweeps"], "status": st["status"],
+                "cell_angles_per_s": st["cell_angles"] / wall,
+                "profile_ms": {k: round(v["ms"], 1) for k, v in phases.items()}, "roofline": roof,
+                "balance_defect_max_rhs_0_17_63": max(balance_defect(p, ph, r, tab) for r in (0, 17, 63))}
+        ctx.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def batching_secondary(binding, inputs, n_slabs):
+    """The first n_slabs of the seeded 4096-slab Batching recipe through the batch driver
+    (groups by (N, L) on concurrent streams, memory-bounded waves): wall time of context
+    creation, upload, assembly, factorization and solve, after one untimed run."""
+    import torch
+    from paper_1907_13013_gb300 import batch
+    probs = inputs.batch_slabs(n_slabs, seed=0)
+    batch.BatchSolver(probs, precision="mixed", laplacian="wfd").solve(tol=TOL, max_iterations=200)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phis, stats = batch.BatchSolver(probs, precision="mixed", laplacian="wfd").solve(tol=TOL, max_iterations=200)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    cells = sum(q["h"].size for q in probs)
+    by_n = {}
+    for q in probs:
+        by_n[q["N"]] = by_n.get(q["N"], 0) + 1
+    return {"workload": "batch_slabs(%d, seed=0): the first %d of the seeded 4096-slab recipe (K ~ U{100..5000}, "
+                        "N in {16,32,64,128}, L = N-1, two HG regions), mixed WFD, tol 1e-10" % (n_slabs, n_slabs),
+            "value": n_slabs / wall, "unit": "slabs/s", "wall_s": wall, "cells": int(cells),
+            "slabs_per_N": {str(k): v for k, v in sorted(by_n.items())}, "waves": len(stats)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +342,9 @@ def main():
     ap.add_argument("--tune", default="auto", choices=["library", "auto"],
                     help="launch shapes: the library's own, or those fpsa_autotune picks on this workload "
                          "(before the warm-up, outside the timed region)")
+    ap.add_argument("--no-scale", action="store_true", help="skip the full-size Scale workload line")
+    ap.add_argument("--scale-fp64", action="store_true", help="add the FP64 forms to the Scale line (minutes)")
+    ap.add_argument("--batch-slabs", type=int, default=256, help="Batching line: slabs of the recipe (0: skip)")
     ap.add_argument("--solve-slices", type=int, default=0, choices=[0, 1, 2, 4],
                     help="row-slice cap of the BCR solve after tuning (0: keep the tuned / library value)")
     args = ap.parse_args()
@@ -407,6 +510,13 @@ def main():
                                "setup_ms": st2["setup_ms"], "solve_ms": st2["solve_ms"],
                                "max_rel_err_vs_oracle": err2, "tuning": c2.get_tuning()}
             c2.close()
+
+    if not args.no_secondary and rank == 0 and world == 1:
+        if not args.no_scale:
+            secondary["scale"] = scale_secondary(binding, inputs, dev, stream, hbm,
+                                                 ("mixed", "fp64") if args.scale_fp64 else ("mixed",))
+        if args.batch_slabs > 0:
+            secondary["batching"] = batching_secondary(binding, inputs, args.batch_slabs)
 
     value = whole_job_rate(world, args.steps, ms)
     h2d = 8 * (K + K * (L + 1) + 2 * K * (L + 1))
