@@ -123,7 +123,8 @@ struct fpsa_ctx {
     PathBuffers<double> p64;  // FP64 path; for MIXED: FP64 tables, psi (refined iterate), phi
     PathBuffers<float> p32;   // MIXED: the FP32 inner FPSA solve
     // tensor-core contractions of the FP32 inner solve
-    bool tc_able = false;               // N multiple of 16, 16 <= N <= 128
+    bool tc_able = false;               // N multiple of 16, 16 <= N <= 128, or tc_big
+    bool tc_big = false;                // N multiple of 32 in (128, 256]: operators streamed
     unsigned char *d_tc_ops = nullptr;  // D_hi, D_lo, M_hi, M_lo (BF16, core-matrix layout)
     // [0]: a bounded device wait ran out (tensor-core or BCR dataflow); [1]: the polls a
     // BCR dataflow wait makes before it gives up (fpsa_set_limits)
@@ -479,13 +480,16 @@ int invert_level(fpsa_ctx *ctx, PathBuffers<T> &p, const BcrItem *items, int ni,
 // K-major core-matrix layout (Op_D[l][n] = D[l][n], Op_M[n][l] = M[n][l]).
 int setup_tc(fpsa_ctx *ctx) {
     const int N = ctx->geo.N;
-    ctx->tc_able = (N % 16 == 0) && N >= 16 && N <= 128;
+    // N <= 128: the operators stay in shared memory; N in (128, 256], a multiple of 32:
+    // they are streamed in K-chunks (chunk-major layout)
+    ctx->tc_big = N > 128 && N <= 256 && N % tc::kChunkK == 0;
+    ctx->tc_able = ((N % 16 == 0) && N >= 16 && N <= 128) || ctx->tc_big;
     if (!ctx->tc_able) return FPSA_OK;
     const size_t nn = (size_t)N * N;
     std::vector<__nv_bfloat16> ops(4 * nn);
     for (int o = 0; o < N; ++o)
         for (int k = 0; k < N; ++k) {
-            const size_t off = tc::kmajor_offset(o, k, N) / 2;
+            const size_t off = (ctx->tc_big ? tc::chunk_offset(o, k, N) : tc::kmajor_offset(o, k, N)) / 2;
             const float d = (float)ctx->tab.D[(size_t)o * N + k];
             const float m = (float)ctx->tab.M[(size_t)o * N + k];
             const __nv_bfloat16 dh = __float2bfloat16_rn(d), mh = __float2bfloat16_rn(m);
@@ -496,13 +500,21 @@ int setup_tc(fpsa_ctx *ctx) {
         }
     CK(dalloc(ctx, &ctx->d_tc_ops, 4 * nn * sizeof(__nv_bfloat16)));
     CK(cudaMemcpy(ctx->d_tc_ops, ops.data(), ops.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (ctx->tc_big) {
+        const int smem = (int)tc::BigPlan::make(N).total;
+        CK(raise_smem_limit((const void *)k_tc_fp_rhs_big, smem));
+        CK(raise_smem_limit((const void *)k_tc_update_scatter_big, smem));
+        ctx->tc_grid = nsm;  // one CTA per SM (its shared memory)
+        return FPSA_OK;
+    }
     const int smem = (int)tc::Plan::make(N).total;
     CK(raise_smem_limit((const void *)k_tc_fp_rhs, smem));
     CK(raise_smem_limit((const void *)k_tc_update_scatter, smem));
     CK(raise_smem_limit((const void *)k_tc_fp_rhs_tile, smem));
     CK(raise_smem_limit((const void *)k_tc_update_scatter_tile, smem));
-    int nsm = 0, per_sm = 0;
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_update_scatter, 128, smem));
     ctx->tc_grid = std::max(1, std::min(per_sm, 2)) * nsm;
     return FPSA_OK;
@@ -853,13 +865,15 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     const double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
     int krylov = 0;
     if (o.contraction == 2 && !ctx->tc_able)
-        return fail(ctx, FPSA_ENOTSUP, "tensor-core contractions need N a multiple of 16 and <= 128");
+        return fail(ctx, FPSA_ENOTSUP,
+                    "tensor-core contractions need N a multiple of 16 and <= 128, or a multiple of 32 and <= 256");
     const bool use_tc = ctx->tc_able && o.contraction != 1 && !gmres;
     const TcOps tcops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
     const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
     const int tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
-    const size_t tc_smem = tc::Plan::make(N).total;
-    const bool tc_full = tc::Plan::make(N).full;
+    const bool tc_big = ctx->tc_big;
+    const size_t tc_smem = tc_big ? tc::BigPlan::make(N).total : tc::Plan::make(N).total;
+    const bool tc_full = !tc_big && tc::Plan::make(N).full;
     CK(cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), st));
 
     CK(cudaMemsetAsync(p.phi, 0, nang * sizeof(double), st));
@@ -949,7 +963,11 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             if (fpsa) {
                 {
                     Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                    if (use_tc && tc_full)
+                    if (use_tc && tc_big)
+                        CK(launch_pdl(k_tc_fp_rhs_big, dim3(tc_blocks), dim3(128), tc_smem, st, (const float *)f.psi,
+                                      (const float *)f.phi, f.phi_half, (const float *)f.sigma_s,
+                                      (const double *)ctx->d_h, tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err));
+                    else if (use_tc && tc_full)
                         CK(launch_pdl(k_tc_fp_rhs_tile, dim3(tc_blocks), dim3(128), tc_smem, st, (const float *)f.psi,
                                       (const float *)f.phi, f.phi_half, (const float *)f.sigma_s,
                                       (const double *)ctx->d_h, tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err));
@@ -967,7 +985,11 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             }
             if (j < inner_k) {
                 Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                if (use_tc && tc_full)
+                if (use_tc && tc_big)
+                    CK(launch_pdl(k_tc_update_scatter_big, dim3(tc_blocks), dim3(128), tc_smem, st, vin, base, f.phi,
+                                  (const float *)f.sigma_s, tcops, f.q, (const float *)f.qang, N, g.sumK, g.R,
+                                  ctx->d_dev_err));
+                else if (use_tc && tc_full)
                     CK(launch_pdl(k_tc_update_scatter_tile, dim3(tc_blocks), dim3(128), tc_smem, st, vin, base, f.phi,
                                   (const float *)f.sigma_s, tcops, f.q, (const float *)f.qang, N, g.sumK, g.R,
                                   ctx->d_dev_err));

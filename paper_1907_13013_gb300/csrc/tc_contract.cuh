@@ -643,4 +643,287 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter_tile(const float *__r
     tc_cta_teardown(s, N);
 }
 
+// ---------------------------------------------------------------------------
+// Streamed-operator variants for N > 128 (N a multiple of 32, at most 256): the
+// operators (2 N^2 BF16 values each, split hi / lo) no longer fit shared memory next
+// to the column tile, so each GEMM streams them through two buffers in K-chunks of
+// 32 (an operator is stored chunk-major in global memory, [N / 32 chunks][N rows][32]
+// in the K-major core-matrix layout, so a chunk is one bulk copy; the operators are
+// shared by every tile and stay in L2). The column tile (the A operand, 128 x N) and
+// the staged global I/O are as in k_tc_fp_rhs / k_tc_update_scatter; the accumulator
+// is N FP32 columns of TMEM (M = 128, N = 256 per instruction).
+// ---------------------------------------------------------------------------
+namespace tc {
+constexpr int kChunkK = 32;
+// byte offset of element (row, k) of an N x N operator in the chunk-major layout
+__host__ __device__ __forceinline__ uint32_t chunk_offset(int row, int k, int N) {
+    return (uint32_t)(k / kChunkK) * (uint32_t)N * kChunkK * 2u + kmajor_offset(row, k % kChunkK, kChunkK);
+}
+// Shared-memory plan of a streamed CTA: x_hi, x_lo (128 x N BF16 each), two chunk
+// buffers of hi + lo (N x 32 BF16 each), three staging buffers, 6 mbarriers, tmem slot.
+struct BigPlan {
+    uint32_t x_bytes, chunk_bytes, total;
+    __host__ __device__ static BigPlan make(int N) {
+        BigPlan p;
+        p.x_bytes = 128u * N * 2;
+        p.chunk_bytes = (uint32_t)N * kChunkK * 2;  // one part (hi or lo) of one chunk
+        p.total = 2 * p.x_bytes + 4 * p.chunk_bytes + 3 * kStageBytes + 64;
+        return p;
+    }
+};
+}  // namespace tc
+
+struct TcBig {
+    unsigned char *x_hi, *x_lo, *ch[2];  // ch[b]: hi then lo of buffer b
+    float *stA, *stB, *stC;
+    uint64_t *full, *empty, *bar_mma;    // full[2], empty[2]
+    uint32_t *tmem_slot;
+    uint32_t tmem, mma_phase;
+    uint32_t fills[2], uses[2];          // completed phases per buffer (thread 0's view)
+};
+
+__device__ __forceinline__ void tc_big_setup(TcBig &s, unsigned char *smem, int N) {
+    const tc::BigPlan pl = tc::BigPlan::make(N);
+    s.x_hi = smem;
+    s.x_lo = smem + pl.x_bytes;
+    s.ch[0] = smem + 2 * pl.x_bytes;
+    s.ch[1] = s.ch[0] + 2 * pl.chunk_bytes;
+    s.stA = reinterpret_cast<float *>(s.ch[1] + 2 * pl.chunk_bytes);
+    s.stB = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s.stA) + tc::kStageBytes);
+    s.stC = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s.stB) + tc::kStageBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(s.stC) + tc::kStageBytes);
+    s.full = bars;
+    s.empty = bars + 2;
+    s.bar_mma = bars + 4;
+    s.tmem_slot = reinterpret_cast<uint32_t *>(bars + 5);
+    s.mma_phase = 0;
+    s.fills[0] = s.fills[1] = s.uses[0] = s.uses[1] = 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 5; ++i) tc::mbar_init(bars + i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(s.tmem_slot, tc::tmem_cols_for(N));
+        tc::tmem_relinquish();
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    s.tmem = *s.tmem_slot;
+}
+
+// Out = X Op^T over K = N with the tile in x_hi / x_lo and the operator (hi, lo:
+// chunk-major in global memory) streamed chunk by chunk; returns false on a timeout.
+// Thread 0 runs the pipeline: chunk c + 2 is requested once the MMAs of chunk c have
+// completed (the buffer's empty barrier); every wait is bounded.
+__device__ __forceinline__ bool tc_gemm_streamed(TcBig &s, const unsigned char *op_hi, const unsigned char *op_lo,
+                                                 int N, int *err) {
+    tc::fence_async_smem();  // the tile's st.shared must be visible to the tensor core
+    tc::tc_fence_before();
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        tc::tc_fence_after();
+        const int nch = N / tc::kChunkK;
+        const uint32_t cb = (uint32_t)N * tc::kChunkK * 2;
+        auto request = [&](int c) {
+            const int b = c & 1;
+            tc::mbar_arrive_expect_tx(&s.full[b], 2 * cb);
+            tc::bulk_copy_g2s(s.ch[b], op_hi + (size_t)c * cb, cb, &s.full[b]);
+            tc::bulk_copy_g2s(s.ch[b] + cb, op_lo + (size_t)c * cb, cb, &s.full[b]);
+        };
+        request(0);
+        if (nch > 1) request(1);
+        const uint32_t idesc = tc::idesc_bf16(128, N);
+        const uint32_t xh = tc::smem_u32(s.x_hi), xl = tc::smem_u32(s.x_lo);
+        const uint32_t sbo_x = (uint32_t)N * 16, sbo_b = tc::kChunkK * 16;
+        int issued = nch > 1 ? 2 : 1;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int b = c & 1;
+            ok = tc::mbar_wait(&s.full[b], s.fills[b] & 1u);
+            if (!ok) break;
+            ++s.fills[b];
+            tc::tc_fence_after();
+            const uint32_t oh = tc::smem_u32(s.ch[b]), ol = oh + cb;
+            for (int j = 0; j < tc::kChunkK / 16; ++j) {
+                const uint32_t ka = 256u * (uint32_t)(c * (tc::kChunkK / 16) + j), kb = 256u * (uint32_t)j;
+                const uint64_t a_hi = tc::smem_desc(xh + ka, 128, sbo_x), a_lo = tc::smem_desc(xl + ka, 128, sbo_x);
+                const uint64_t b_hi = tc::smem_desc(oh + kb, 128, sbo_b), b_lo = tc::smem_desc(ol + kb, 128, sbo_b);
+                tc::mma_bf16(s.tmem, a_hi, b_hi, idesc, (c > 0 || j > 0) ? 1u : 0u);
+                tc::mma_bf16(s.tmem, a_hi, b_lo, idesc, 1u);
+                tc::mma_bf16(s.tmem, a_lo, b_hi, idesc, 1u);
+            }
+            tc::mma_commit(&s.empty[b]);
+            if (issued < nch) {  // the buffer is refilled once its MMAs have read it
+                ok = tc::mbar_wait(&s.empty[b], s.uses[b] & 1u);
+                ++s.uses[b];
+                if (!ok) break;
+                request(issued++);
+            } else {
+                ++s.uses[b];  // this phase is waited for (if at all) by the drain below
+            }
+        }
+        tc::mma_commit(s.bar_mma);
+        if (!ok) {
+            // no copy may still be landing: wait (bounded) for every requested chunk
+            for (int b = 0; b < 2; ++b)
+                while (s.fills[b] < (uint32_t)((issued - b + 1) / 2)) {
+                    if (!tc::mbar_wait(&s.full[b], s.fills[b] & 1u)) break;
+                    ++s.fills[b];
+                }
+        }
+    }
+    ok = __syncthreads_and(ok) != 0;
+    // every MMA issued has completed before the accumulator is read or the CTA ends (bounded)
+    const bool done = tc::mbar_wait(s.bar_mma, s.mma_phase);
+    s.mma_phase ^= 1u;
+    tc::tc_fence_after();
+    ok = __syncthreads_and(ok && done) != 0;
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    return ok;
+}
+
+__device__ __forceinline__ void tc_big_teardown(TcBig &s, int N) {
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(s.tmem, tc::tmem_cols_for(N));
+}
+
+// k_tc_fp_rhs with streamed operators (N > 128).
+__global__ void __launch_bounds__(128) k_tc_fp_rhs_big(const float *__restrict__ psi_half,
+                                                       const float *__restrict__ phi, float *__restrict__ phi_half,
+                                                       const float *__restrict__ sigma_s,
+                                                       const double *__restrict__ h, TcOps ops,
+                                                       float *__restrict__ rhs, int N, int sumK, int R, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcBig s;
+    tc_big_setup(s, smem_tc, N);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
+    const int t = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    const size_t opb = (size_t)N * N * 2;  // bytes of one part of one operator
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const bool live = t < ncols;
+        const int g = (j0 + t) >> 1;
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
+        const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(s.stA, psi_half + cb, N, ncols, k0);
+            __syncthreads();
+            float v[16];
+            tc::row_get16(s.stA, t, v);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
+        }
+        if (!(ok = tc_gemm_streamed(s, ops.D, ops.D + opb, N, err))) break;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(s.stA, phi + cb, N, ncols, k0);
+            tc::stage_in(s.stB, sig, N, ncell, k0);
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            __syncthreads();
+            float ph[16], sg[16], v[16];
+            tc::row_get16(s.stA, t, ph);
+            tc::row_get16(s.stB, t >> 1, sg);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = live ? sg[i] * (a[i] - ph[i]) : 0.f;
+            tc::row_put16(s.stC, t, a);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
+            tc::stage_out(s.stC, phi_half + cb, N, ncols, k0);
+        }
+        if (!(ok = tc_gemm_streamed(s, ops.M, ops.M + opb, N, err))) break;
+        const float w = live ? (float)(h[g] / 6.0) : 0.f;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            float a[16], o[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);  // r at the other node
+                o[i] = w * (2.f * a[i] + other);
+            }
+            __syncthreads();  // stC of the previous chunk has been written out
+            tc::row_put16(s.stC, t, o);
+            __syncthreads();
+            tc::stage_out(s.stC, rhs + cb, N, ncols, k0);
+        }
+    }
+    tc_big_teardown(s, N);
+}
+
+// k_tc_update_scatter with streamed operators (N > 128).
+__global__ void __launch_bounds__(128) k_tc_update_scatter_big(const float *__restrict__ v_in,
+                                                               const float *__restrict__ phi_base,
+                                                               float *__restrict__ phi,
+                                                               const float *__restrict__ sigma_s, TcOps ops,
+                                                               float *__restrict__ q, const float *__restrict__ qang,
+                                                               int N, int sumK, int R, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcBig s;
+    tc_big_setup(s, smem_tc, N);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
+    const int t = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    const size_t opb = (size_t)N * N * 2;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const bool live = t < ncols;
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
+        const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(s.stA, v_in + cb, N, ncols, k0);
+            __syncthreads();
+            float v[16];
+            tc::row_get16(s.stA, t, v);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
+        }
+        if (!(ok = tc_gemm_streamed(s, ops.D, ops.D + opb, N, err))) break;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            if (phi_base) tc::stage_in(s.stA, phi_base + cb, N, ncols, k0);
+            tc::stage_in(s.stB, sig, N, ncell, k0);
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            __syncthreads();
+            float pb[16], sg[16], v[16];
+            if (phi_base) tc::row_get16(s.stA, t, pb);
+            tc::row_get16(s.stB, t >> 1, sg);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                a[i] += phi_base ? pb[i] : 0.f;
+                v[i] = live ? sg[i] * a[i] : 0.f;
+            }
+            tc::row_put16(s.stC, t, a);
+            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
+            __syncthreads();
+            tc::stage_out(s.stC, phi + cb, N, ncols, k0);
+        }
+        if (!(ok = tc_gemm_streamed(s, ops.M, ops.M + opb, N, err))) break;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            if (qang) tc::stage_in(s.stA, qang + cb, N, ncols, k0);
+            float a[16];
+            tc::tmem_ld16(s.tmem + lane_base + k0, a);
+            __syncthreads();
+            if (qang) {
+                float qa[16];
+                tc::row_get16(s.stA, t, qa);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a[i] += qa[i];
+            }
+            tc::row_put16(s.stC, t, a);
+            __syncthreads();
+            tc::stage_out(s.stC, q + cb, N, ncols, k0);
+        }
+    }
+    tc_big_teardown(s, N);
+}
+
 }  // namespace fpsa
