@@ -98,7 +98,8 @@ typedef struct {
     double inner_tol;         /* MIXED, GMRES: relative residual target of each FP32 inner
                                  GMRES solve (0 = default 1e-5); unused otherwise */
     int32_t check_every;      /* test convergence every this many iterations (0 = 1) */
-    int32_t contraction;      /* MIXED inner SI / FPSA contractions: 0 = auto (tensor cores when N is a
+    int32_t contraction;      /* MIXED inner contractions (SI, FPSA and the inner GMRES solves of
+                                 GMRES-IR): 0 = auto (tensor cores when N is a
                                  multiple of 16 and <= 128, or a multiple of 32 and <= 256), 1 = SIMT
                                  FP32, 2 = tensor cores (tcgen05, split BF16 x3; FPSA_ENOTSUP if N
                                  does not qualify) */

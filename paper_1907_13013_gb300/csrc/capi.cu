@@ -125,6 +125,7 @@ struct fpsa_ctx {
     // tensor-core contractions of the FP32 inner solve
     bool tc_able = false;               // N multiple of 16, 16 <= N <= 128, or tc_big
     bool tc_big = false;                // N multiple of 32 in (128, 256]: operators streamed
+    bool gm_use_tc = false;             // this solve's GMRES contractions on tensor cores (MIXED)
     unsigned char *d_tc_ops = nullptr;  // D_hi, D_lo, M_hi, M_lo (BF16, core-matrix layout)
     // [0]: a bounded device wait ran out (tensor-core or BCR dataflow); [1]: the polls a
     // BCR dataflow wait makes before it gives up (fpsa_set_limits)
@@ -506,6 +507,8 @@ int setup_tc(fpsa_ctx *ctx) {
         const int smem = (int)tc::BigPlan::make(N).total;
         CK(raise_smem_limit((const void *)k_tc_fp_rhs_big, smem));
         CK(raise_smem_limit((const void *)k_tc_update_scatter_big, smem));
+        CK(raise_smem_limit((const void *)k_tc_fp_rhs_moments<true>, smem));
+        CK(raise_smem_limit((const void *)k_tc_moments_axpy<true>, smem));
         ctx->tc_grid = nsm;  // one CTA per SM (its shared memory)
         return FPSA_OK;
     }
@@ -514,6 +517,8 @@ int setup_tc(fpsa_ctx *ctx) {
     CK(raise_smem_limit((const void *)k_tc_update_scatter, smem));
     CK(raise_smem_limit((const void *)k_tc_fp_rhs_tile, smem));
     CK(raise_smem_limit((const void *)k_tc_update_scatter_tile, smem));
+    CK(raise_smem_limit((const void *)k_tc_fp_rhs_moments<false>, smem));
+    CK(raise_smem_limit((const void *)k_tc_moments_axpy<false>, smem));
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_update_scatter, 128, smem));
     ctx->tc_grid = std::max(1, std::min(per_sm, 2)) * nsm;
@@ -867,7 +872,8 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     if (o.contraction == 2 && !ctx->tc_able)
         return fail(ctx, FPSA_ENOTSUP,
                     "tensor-core contractions need N a multiple of 16 and <= 128, or a multiple of 32 and <= 256");
-    const bool use_tc = ctx->tc_able && o.contraction != 1 && !gmres;
+    const bool use_tc = ctx->tc_able && o.contraction != 1;
+    ctx->gm_use_tc = use_tc;  // the inner GMRES solves of GMRES-IR too
     const TcOps tcops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
     const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
     const int tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
@@ -1122,35 +1128,115 @@ int gm_combine(fpsa_ctx *ctx, T *y, const std::vector<double> *alpha, const T *V
     return FPSA_OK;
 }
 
+// The GMRES operator's contractions, on tensor cores for the FP32 inner solve of
+// GMRES-IR when ctx->gm_use_tc (set per solve from the options), else SIMT:
+//   gm_fp_rhs:  rhs = m (x) M Sigma v
+//   gm_update:  out = base + D y;  q = M Sigma out
+//   gm_axpy:    out = base + sign D psi  (base may be NULL or alias out)
+template <typename T>
+int gm_fp_rhs(fpsa_ctx *ctx, PathBuffers<T> &p, const T *v, T *rhs) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N;
+    cudaStream_t st = ctx->stream;
+    Launch L_(ctx, FPSA_PHASE_CONTRACT);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (ctx->gm_use_tc) {
+            const TcOps ops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
+            const int blocks = std::max(1, std::min(((2 * g.sumK + 127) / 128) * g.R, ctx->tc_grid));
+            if (ctx->tc_big)
+                CK(launch_pdl(k_tc_fp_rhs_moments<true>, dim3(blocks), dim3(128), (size_t)tc::BigPlan::make(N).total, st,
+                              (const float *)v, (const float *)p.sigma_s, (const double *)ctx->d_h, ops, (float *)rhs, N,
+                              g.sumK, g.R, ctx->d_dev_err));
+            else
+                CK(launch_pdl(k_tc_fp_rhs_moments<false>, dim3(blocks), dim3(128), (size_t)tc::Plan::make(N).total, st,
+                              (const float *)v, (const float *)p.sigma_s, (const double *)ctx->d_h, ops, (float *)rhs, N,
+                              g.sumK, g.R, ctx->d_dev_err));
+            return FPSA_OK;
+        }
+    }
+    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    k_fp_rhs_moments<T><<<cgrid, kContractThreads, contract_smem<T>(N), st>>>(v, p.sigma_s, ctx->d_h, p.MT, rhs, N,
+                                                                               g.sumK);
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
+template <typename T>
+int gm_update(fpsa_ctx *ctx, PathBuffers<T> &p, const T *y, const T *base, T *out) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N;
+    cudaStream_t st = ctx->stream;
+    Launch L_(ctx, FPSA_PHASE_CONTRACT);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (ctx->gm_use_tc) {
+            const TcOps ops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
+            const int blocks = std::max(1, std::min(((2 * g.sumK + 127) / 128) * g.R, ctx->tc_grid));
+            const float *qnull = nullptr;
+            if (ctx->tc_big)
+                CK(launch_pdl(k_tc_update_scatter_big, dim3(blocks), dim3(128), (size_t)tc::BigPlan::make(N).total,
+                              st, (const float *)y, (const float *)base, (float *)out, (const float *)p.sigma_s, ops,
+                              (float *)p.q, qnull, N, g.sumK, g.R, ctx->d_dev_err));
+            else if (tc::Plan::make(N).full)
+                CK(launch_pdl(k_tc_update_scatter_tile, dim3(blocks), dim3(128), (size_t)tc::Plan::make(N).total, st,
+                              (const float *)y, (const float *)base, (float *)out, (const float *)p.sigma_s, ops,
+                              (float *)p.q, qnull, N, g.sumK, g.R, ctx->d_dev_err));
+            else
+                CK(launch_pdl(k_tc_update_scatter, dim3(blocks), dim3(128), (size_t)tc::Plan::make(N).total, st,
+                              (const float *)y, (const float *)base, (float *)out, (const float *)p.sigma_s, ops,
+                              (float *)p.q, qnull, N, g.sumK, g.R, ctx->d_dev_err));
+            return FPSA_OK;
+        }
+    }
+    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    k_update_scatter<T><<<cgrid, kContractThreads, contract_smem<T>(N), st>>>(
+        y, base, out, p.sigma_s, (const T *)nullptr, p.DT, p.MT, p.q, ctx->d_cell_inst, g.B,
+        (unsigned long long *)nullptr, N, g.sumK, (const T *)nullptr);
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
+template <typename T>
+int gm_axpy(fpsa_ctx *ctx, PathBuffers<T> &p, const T *psi, const T *base, T sign, T *out) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N;
+    cudaStream_t st = ctx->stream;
+    Launch L_(ctx, FPSA_PHASE_CONTRACT);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (ctx->gm_use_tc) {
+            const TcOps ops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
+            const int blocks = std::max(1, std::min(((2 * g.sumK + 127) / 128) * g.R, ctx->tc_grid));
+            if (ctx->tc_big)
+                CK(launch_pdl(k_tc_moments_axpy<true>, dim3(blocks), dim3(128), (size_t)tc::BigPlan::make(N).total, st,
+                              (const float *)psi, (const float *)base, (float)sign, ops, (float *)out, N, g.sumK, g.R,
+                              ctx->d_dev_err));
+            else
+                CK(launch_pdl(k_tc_moments_axpy<false>, dim3(blocks), dim3(128), (size_t)tc::Plan::make(N).total, st,
+                              (const float *)psi, (const float *)base, (float)sign, ops, (float *)out, N, g.sumK, g.R,
+                              ctx->d_dev_err));
+            return FPSA_OK;
+        }
+    }
+    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    k_moments_axpy<T><<<cgrid, kContractThreads, contract_smem<T>(N), st>>>(psi, base, sign, p.DT, out, N, g.sumK);
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
 // out = (I - T)(I + C) v  (out may not alias v)
 template <typename T>
 int gm_apply(fpsa_ctx *ctx, PathBuffers<T> &p, const T *v, T *out) {
     const Geometry &g = ctx->geo;
     const int N = g.N;
     cudaStream_t st = ctx->stream;
-    const size_t csm = contract_smem<T>(N);
-    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
-    {
-        Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_fp_rhs_moments<T><<<cgrid, kContractThreads, csm, st>>>(v, p.sigma_s, ctx->d_h, p.MT, p.rhs, N, g.sumK);
-    }
-    int rc = bcr_solve(ctx, p, p.rhs);
+    int rc = gm_fp_rhs(ctx, p, v, p.rhs);
     if (rc) return rc;
-    {
-        Launch L_(ctx, FPSA_PHASE_CONTRACT);  // out = z = v + D upsilon;  q = M Sigma z
-        k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.ybuf, v, out, p.sigma_s, (const T *)nullptr, p.DT,
-                                                                  p.MT, p.q, ctx->d_cell_inst, g.B,
-                                                                  (unsigned long long *)nullptr, N, g.sumK,
-                                                                  (const T *)nullptr);
-    }
+    rc = bcr_solve(ctx, p, p.rhs);
+    if (rc) return rc;
+    rc = gm_update(ctx, p, (const T *)p.ybuf, v, out);  // out = z = v + D upsilon;  q = M Sigma z
+    if (rc) return rc;
     rc = sweep(ctx, p, p.q, p.psi, (const T *)nullptr);
     if (rc) return rc;
-    {
-        Launch L_(ctx, FPSA_PHASE_CONTRACT);  // out = z - D psi
-        k_moments_axpy<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, out, T(-1), p.DT, out, N, g.sumK);
-    }
-    CK(cudaGetLastError());
-    return FPSA_OK;
+    return gm_axpy(ctx, p, (const T *)p.psi, (const T *)out, T(-1), out);  // out = z - D psi
 }
 
 // GMRES(m) with right FPSA preconditioning in precision T, batched over (rhs, instance)
@@ -1181,11 +1267,8 @@ int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, 
     }
     rc = sweep(ctx, p, p.q, p.psi, inc);
     if (rc) return rc;
-    {
-        Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_moments_axpy<T><<<cgrid, kContractThreads, csm, st>>>(p.psi, (const T *)nullptr, T(1), p.DT, b, N, g.sumK);
-    }
-    CK(cudaGetLastError());
+    rc = gm_axpy(ctx, p, (const T *)p.psi, (const T *)nullptr, T(1), b);
+    if (rc) return rc;
     std::vector<double> dots, bnorm(nsys), coef, alpha(nsys), c1(nsys, 1.0);
     rc = gm_dots(ctx, b, 1, b, dots);
     if (rc) return rc;
@@ -1286,20 +1369,12 @@ int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, 
         if (worst < tol) { status = FPSA_OK; break; }
     }
     // phi = (I + C) u
-    {
-        Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_fp_rhs_moments<T><<<cgrid, kContractThreads, csm, st>>>(u, p.sigma_s, ctx->d_h, p.MT, p.rhs, N, g.sumK);
-    }
+    rc = gm_fp_rhs(ctx, p, (const T *)u, p.rhs);
+    if (rc) return rc;
     rc = bcr_solve(ctx, p, p.rhs);
     if (rc) return rc;
-    {
-        Launch L_(ctx, FPSA_PHASE_CONTRACT);
-        k_update_scatter<T><<<cgrid, kContractThreads, csm, st>>>(p.ybuf, u, p.phi, p.sigma_s, (const T *)nullptr, p.DT,
-                                                                  p.MT, p.q, ctx->d_cell_inst, g.B,
-                                                                  (unsigned long long *)nullptr, N, g.sumK,
-                                                                  (const T *)nullptr);
-    }
-    CK(cudaGetLastError());
+    rc = gm_update(ctx, p, (const T *)p.ybuf, (const T *)u, p.phi);
+    if (rc) return rc;
     return status;
 }
 

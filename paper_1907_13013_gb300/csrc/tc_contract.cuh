@@ -926,4 +926,138 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter_big(const float *__re
     tc_big_teardown(s, N);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core contractions of the GMRES operator (the FP32 inner solve of GMRES-IR),
+// one GEMM each, with the operators either in shared memory (N <= 128) or streamed
+// (N > 128); TcEngine picks the form at compile time.
+//   k_tc_fp_rhs_moments:  rhs = m (x) M Sigma v      (v: moments)
+//   k_tc_moments_axpy:    out = base + sign D psi   (base may be NULL or alias out)
+// ---------------------------------------------------------------------------
+template <bool kBig>
+struct TcEngine {
+    TcCta a;
+    TcBig b;
+    float *stA, *stB, *stC;
+    unsigned char *x_hi, *x_lo;
+    uint32_t tmem;
+    __device__ __forceinline__ bool setup(unsigned char *smem, const TcOps &ops, int N, int *err) {
+        bool ok = true;
+        if constexpr (kBig) {
+            tc_big_setup(b, smem, N);
+            stA = b.stA; stB = b.stB; stC = b.stC; x_hi = b.x_hi; x_lo = b.x_lo; tmem = b.tmem;
+        } else {
+            ok = tc_cta_setup(a, smem, ops, N, err);
+            stA = a.stA; stB = a.stB; stC = a.stC; x_hi = a.x_hi; x_lo = a.x_lo; tmem = a.tmem;
+        }
+        return ok;
+    }
+    __device__ __forceinline__ bool gemm(const TcOps &ops, bool use_d, int N, int *err) {
+        if constexpr (kBig) {
+            const unsigned char *o = use_d ? ops.D : ops.M;
+            return tc_gemm_streamed(b, o, o + (size_t)N * N * 2, N, err);
+        } else {
+            return tc_gemm(a, use_d ? a.opD_hi : a.opM_hi, use_d ? a.opD_lo : a.opM_lo, N, err);
+        }
+    }
+    __device__ __forceinline__ void teardown(int N) {
+        if constexpr (kBig) tc_big_teardown(b, N);
+        else tc_cta_teardown(a, N);
+    }
+};
+
+template <bool kBig>
+__global__ void __launch_bounds__(128) k_tc_fp_rhs_moments(const float *__restrict__ v,
+                                                           const float *__restrict__ sigma_s,
+                                                           const double *__restrict__ h, TcOps ops,
+                                                           float *__restrict__ rhs, int N, int sumK, int R, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcEngine<kBig> e;
+    bool ok = e.setup(smem_tc, ops, N, err);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
+    const int t = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const bool live = t < ncols;
+        const int g = (j0 + t) >> 1;
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
+        const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
+        // A = Sigma v
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(e.stA, v + cb, N, ncols, k0);
+            tc::stage_in(e.stB, sig, N, ncell, k0);
+            __syncthreads();
+            float vv[16], sg[16], a[16];
+            tc::row_get16(e.stA, t, vv);
+            tc::row_get16(e.stB, t >> 1, sg);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] = live ? sg[i] * vv[i] : 0.f;
+            tc::store_split_row16(e.x_hi, e.x_lo, t, k0, a, N);
+            __syncthreads();
+        }
+        if (!(ok = e.gemm(ops, false, N, err))) break;
+        // rhs = m (x) r: node partner is the adjacent lane (column j ^ 1)
+        const float w = live ? (float)(h[g] / 6.0) : 0.f;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            float a[16], o[16];
+            tc::tmem_ld16(e.tmem + lane_base + k0, a);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);
+                o[i] = w * (2.f * a[i] + other);
+            }
+            __syncthreads();  // stC of the previous chunk has been written out
+            tc::row_put16(e.stC, t, o);
+            __syncthreads();
+            tc::stage_out(e.stC, rhs + cb, N, ncols, k0);
+        }
+    }
+    e.teardown(N);
+}
+
+template <bool kBig>
+__global__ void __launch_bounds__(128) k_tc_moments_axpy(const float *__restrict__ psi, const float *base, float sign,
+                                                         TcOps ops, float *out, int N, int sumK, int R, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    TcEngine<kBig> e;
+    bool ok = e.setup(smem_tc, ops, N, err);
+    tc::grid_dependency_wait();  // the inputs come from the previous kernel
+    const int t = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+    const int tiles_per_r = (2 * sumK + 127) / 128;
+    const int ntiles = tiles_per_r * R;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
+        const int ncols = min(128, 2 * sumK - j0);
+        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            tc::stage_in(e.stA, psi + cb, N, ncols, k0);
+            __syncthreads();
+            float vv[16];
+            tc::row_get16(e.stA, t, vv);
+            tc::store_split_row16(e.x_hi, e.x_lo, t, k0, vv, N);
+            __syncthreads();
+        }
+        if (!(ok = e.gemm(ops, true, N, err))) break;
+        // out = base + sign D psi (base read chunk by chunk before out is written: it may alias)
+        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+            if (base) tc::stage_in(e.stA, base + cb, N, ncols, k0);
+            float a[16];
+            tc::tmem_ld16(e.tmem + lane_base + k0, a);
+            __syncthreads();
+            float bs[16];
+            if (base) tc::row_get16(e.stA, t, bs);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] = (base ? bs[i] : 0.f) + sign * a[i];
+            tc::row_put16(e.stC, t, a);
+            __syncthreads();
+            tc::stage_out(e.stC, out + cb, N, ncols, k0);
+        }
+    }
+    e.teardown(N);
+}
+
 }  // namespace fpsa
