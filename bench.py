@@ -281,7 +281,14 @@ def scale_secondary(binding, inputs, dev, stream, hbm, precisions):
                 # the factors once per solve (every eliminated cell: A^{-1} forward, its inflow
                 # columns backward, two couplings), whatever the number of right-hand sides
                 byt = esize * K * (n2 * n2 + n2 * N + 2 * (N // 2) ** 2)
-                roof = {"kernel": "k_bcr_solve_flow", "bound": "hbm", "achieved": byt / (per * 1e-3) / 1e9,
+                kname = "k_bcr_solve_flow"
+                if ctx.get_tuning()["solve_engine"] == 2:
+                    # tensor-core solve: the split factors (4 bytes an element) once per tile of
+                    # 64 right-hand sides, and the vector passes (rhs read and Y written forward,
+                    # Y read and written backward) of every right-hand side
+                    kname = "k_bcr_solve_tc"
+                    byt = K * (-(-R // 64) * 4 * (n2 * n2 + n2 * N + 4 * (N // 2) ** 2) + 4 * R * 4 * n2)
+                roof = {"kernel": kname, "bound": "hbm", "achieved": byt / (per * 1e-3) / 1e9,
                         "peak": hbm, "unit": "GB/s", "algorithmic_bytes": byt}
             elif dom == "contract":
                 # 2 N (L+1) flop per column, K x 2 columns per rhs, 64 rhs, per contraction launch

@@ -239,6 +239,18 @@ typedef struct {
                                        0 = tensor cores where they apply, else SIMT. Factors
                                        differ by rounding only (the pivots are chosen in FP32
                                        either way) */
+    int32_t solve_engine;           /* BCR solve (the FP solve of every iteration; the
+                                       factorization itself is unchanged): 1 = the dataflow
+                                       solve on the FP32/FP64 cores (right-hand sides 8 at a
+                                       time), 2 = tensor cores (each unit one split-BF16 tcgen05
+                                       GEMM of A^{-1} by 64 right-hand sides, so every factor
+                                       is read once per 64 of them; only for FP32 factors
+                                       (MIXED) with 2N a multiple of 128 up to 512 and at least
+                                       16 right-hand sides, else FPSA_ENOTSUP; such a context
+                                       keeps a second, split copy of its factors, the same
+                                       size as the FP32 ones); 0 = tensor cores where they
+                                       apply, else the dataflow solve. Solutions differ by
+                                       rounding only */
 } fpsa_tuning;
 
 /* The shapes in effect (zero fields resolved to the values used). */

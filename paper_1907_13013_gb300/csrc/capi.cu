@@ -22,6 +22,7 @@
 #include "tc_contract.cuh"
 #include "bcr_large.cuh"
 #include "bcr_factor_tc.cuh"
+#include "bcr_solve_tc.cuh"
 #include "gmres.cuh"
 
 using namespace fpsa;
@@ -100,6 +101,12 @@ struct fpsa_ctx {
     fpsa_tuning tuning = {};         // requested launch shapes (0: the library's choice)
     int factor_grid[2] = {0, 0};     // cooperative dataflow factorization grid (0: per-level launches)
     int factor_tc_grid = 0;          // grid of the tensor-core factorization (FP32, 2N = 128), 0: unavailable
+    // tensor-core BCR solve (FP32 factors, 2N a multiple of 128 up to 512, R >= 16)
+    int tcs_rt = 0;                  // right-hand sides per unit; 0: unavailable
+    int tcs_grid = 0;                // two CTAs per SM
+    unsigned char *d_tcs_A = nullptr;  // the factors split to BF16 hi / lo in the core-matrix layout
+    float *d_tcs_g = nullptr;        // per-CTA backward coupling vectors
+    int *d_tcs_queue = nullptr;      // unit counters, one per parity of d_flow
     unsigned long long *d_conv = nullptr, *d_growth = nullptr;
     int *d_status = nullptr;
     double *d_result = nullptr;
@@ -310,6 +317,16 @@ const void *coop_kernel(int RC, int N) {
         case 4: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 4>;
         case 2: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 2>;
         default: return (const void *)k_bcr_solve_flow<T, kSolveThreads, 1>;
+    }
+}
+
+// the tensor-core solve for RT right-hand sides per unit
+const void *tcs_kernel(int RT) {
+    switch (RT) {
+        case 16: return (const void *)k_bcr_solve_tc<16>;
+        case 32: return (const void *)k_bcr_solve_tc<32>;
+        case 48: return (const void *)k_bcr_solve_tc<48>;
+        default: return (const void *)k_bcr_solve_tc<64>;
     }
 }
 
@@ -619,6 +636,12 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
         if (rc) return rc;
     }
     CK(cudaGetLastError());
+    if (e == 0 && ctx->d_tcs_A) {  // the factors once more, split for the tensor-core solve
+        Launch L_(ctx, FPSA_PHASE_BCR_INVERT);
+        tcs::k_bcr_factor_split<<<(unsigned)((size_t)g.sumK * (2 * N / tcs::kK)), 256, 0, st>>>(
+            reinterpret_cast<const float *>(p.A), ctx->d_tcs_A, 2 * N);
+        CK(cudaGetLastError());
+    }
     if (p.G) {
         const LevelTable &lv = ctx->lvt[sizeof(T) == 8 ? 1 : 0];
         const int n = lv.coarse_m * 2 * N;
@@ -704,8 +727,37 @@ void plan_solve_shape(fpsa_ctx *ctx) {
 // launch (forward levels, roots, backward levels); the solution is left in p.ybuf.
 // No memset precedes it (its counters were zeroed by the previous solve), so it can
 // be launched as a programmatic dependent of the kernel before it.
+// The tensor-core solve (k_bcr_solve_tc): an ordinary launch of two CTAs per SM
+// that takes its units from a queue; counters as the cooperative solve's.
+int bcr_solve_tc(fpsa_ctx *ctx, PathBuffers<float> &p, float *rhs) {
+    const Geometry &g = ctx->geo;
+    const size_t n = ctx->flow_n;
+    int *cnt = ctx->d_flow + 2 * n * ctx->flow_parity, *done = cnt + n;
+    int *zero_next = ctx->d_flow + 2 * n * (1 - ctx->flow_parity);
+    int *queue = ctx->d_tcs_queue + ctx->flow_parity, *queue_next = ctx->d_tcs_queue + (1 - ctx->flow_parity);
+    ctx->flow_parity ^= 1;
+    const int RT = ctx->tcs_rt;
+    const size_t smem = tcs::Plan::make(2 * g.N, RT).total;
+    Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
+    auto go = [&](auto kern) {
+        return launch_pdl(kern, dim3(ctx->tcs_grid), dim3(tcs::kThreads), smem, ctx->stream,
+                          (const unsigned char *)ctx->d_tcs_A, (const float *)p.Bc, (const float *)p.Cc,
+                          (const BcrItem *)ctx->d_items_all, ctx->lvt[0], rhs, p.ybuf, ctx->d_tcs_g, g.N, g.sumK,
+                          g.R, cnt, done, queue, ctx->d_dev_err, zero_next, (long long)(2 * n), queue_next);
+    };
+    switch (RT) {
+        case 16: CK(go(k_bcr_solve_tc<16>)); break;
+        case 32: CK(go(k_bcr_solve_tc<32>)); break;
+        case 48: CK(go(k_bcr_solve_tc<48>)); break;
+        default: CK(go(k_bcr_solve_tc<64>)); break;
+    }
+    return FPSA_OK;
+}
+
 template <typename T>
 int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
+    if constexpr (sizeof(T) == sizeof(float))
+        if (ctx->tcs_rt && ctx->tuning.solve_engine != 1) return bcr_solve_tc(ctx, p, rhs);
     const Geometry &g = ctx->geo;
     int N = g.N, sumK = g.sumK, R = g.R;
     const BcrItem *items = ctx->d_items_all;
@@ -1592,6 +1644,19 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
                                         (int)cudaSharedmemCarveoutMaxShared));
                 ctx->factor_tc_grid = 4 * nsm;
             }
+            if (ctx->precision == FPSA_PRECISION_MIXED && tcs::applies(2 * g.N, g.R)) {
+                // the tensor-core BCR solve: a split copy of the factors, two CTAs per SM
+                ctx->tcs_rt = tcs::rhs_tile(g.R);
+                ctx->tcs_grid = 2 * nsm;
+                CK(dalloc(ctx, &ctx->d_tcs_A, (size_t)g.sumK * tcs::cell_bytes(2 * g.N)));
+                CK(dalloc(ctx, &ctx->d_tcs_g, (size_t)ctx->tcs_grid * ctx->tcs_rt * g.N));
+                CK(dalloc(ctx, &ctx->d_tcs_queue, 2));
+                CK(cudaMemset(ctx->d_tcs_queue, 0, 2 * sizeof(int)));
+                const void *k = tcs_kernel(ctx->tcs_rt);
+                CK(raise_smem_limit(k, (int)tcs::Plan::make(2 * g.N, ctx->tcs_rt).total));
+                CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+            }
             for (int e = 0; e < 2; ++e) {
                 LevelTable &lv = ctx->lvt[e];
                 lv.n_levels = g.n_levels;
@@ -1875,6 +1940,7 @@ int fpsa_get_tuning(const fpsa_ctx *ctx, fpsa_tuning *out) {
     out->solve_blocks_per_sm = ctx->coop_grid[e] / std::max(1, ctx->n_sm);
     out->solve_max_slices = ctx->tuning.solve_max_slices > 0 ? ctx->tuning.solve_max_slices : 4;
     out->factor_engine = (ctx->factor_tc_grid > 0 && ctx->tuning.factor_engine != 1) ? 2 : 1;
+    out->solve_engine = (ctx->tcs_rt > 0 && ctx->tuning.solve_engine != 1) ? 2 : 1;
     return FPSA_OK;
 }
 
@@ -1891,6 +1957,11 @@ int fpsa_set_tuning(fpsa_ctx *ctx, const fpsa_tuning *t) {
     if (r.factor_engine < 0 || r.factor_engine > 2) return fail(ctx, FPSA_EINVAL, "factor_engine not 0, 1 or 2");
     if (r.factor_engine == 2 && ctx->factor_tc_grid == 0)
         return fail(ctx, FPSA_ENOTSUP, "tensor-core factorization needs FP32 factors (MIXED) with 2N = 128");
+    if (r.solve_engine < 0 || r.solve_engine > 2) return fail(ctx, FPSA_EINVAL, "solve_engine not 0, 1 or 2");
+    if (r.solve_engine == 2 && ctx->tcs_rt == 0)
+        return fail(ctx, FPSA_ENOTSUP,
+                    "tensor-core BCR solve needs FP32 factors (MIXED), 2N a multiple of 128 up to 512 and at least "
+                    "16 right-hand sides");
     // the segment maps were allocated for the smallest cells-per-thread (most segments)
     const int cmin = sweep_cells_per_thread(ctx->geo);
     ctx->sweep_cpt = std::max(cmin, r.sweep_cells_per_thread);
@@ -1945,7 +2016,7 @@ int fpsa_autotune(fpsa_ctx *ctx, const fpsa_opts *opts, int32_t repeats, fpsa_tu
     const int bmax = std::min(4, ctx->solve_per_sm[ctx->precision == FPSA_PRECISION_FP64 ? 1 : 0]);
     for (int b = 1; b <= bmax; ++b)
         for (int s = 1; s <= 4; s *= 2) {
-            const fpsa_tuning t{0, b, s, saved.factor_engine};
+            const fpsa_tuning t{0, b, s, saved.factor_engine, saved.solve_engine};
             double ms = 0.0;
             const int rc = trial(t, ms);
             if (rc != FPSA_OK) return give_up(rc);

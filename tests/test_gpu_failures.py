@@ -101,3 +101,22 @@ def test_limits_reject_negative_values(binding, slab):
             ctx.set_limits(*args)
         assert e.value.code == binding.EINVAL
     ctx.close()
+
+
+def test_tensor_core_solve_wait_runs_out_then_context_recovers(binding):
+    # 16 right-hand sides, 2N = 128: the tensor-core BCR solve, whose units take their
+    # work from a queue and give up their waits at once when another has recorded one
+    p = inputs.random_slab(300, 64, 63, seed=778, kernel="srk", thick=(2, 200), c=(0.7, 0.995), nrhs=16)
+    ctx = binding.context_for(p, laplacian="wfd", precision="mixed")
+    assert ctx.get_tuning()["solve_engine"] == 2
+    ctx.set_limits(wait_polls=1)
+    with pytest.raises(binding.FpsaError) as e:
+        ctx.solve("fpsa", tol=1e-13, max_iterations=500)
+    assert e.value.code == binding.ETIMEOUT
+    ctx.set_limits()
+    phi, st = ctx.solve("fpsa", tol=1e-13, max_iterations=500)
+    ctx.close()
+    for r in (0, 15):
+        ref = oit.direct_solve(dict(p, Q=p["Q"][r]))
+        err = np.abs(phi[r] - ref).max() / np.abs(ref[..., 0]).max()
+        assert err < 1e-9, (r, err)
