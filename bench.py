@@ -243,7 +243,7 @@ def balance_defect(p, phi, r, tab):
     return float(abs(emission - absorption - jl - jr) / emission)
 
 
-def scale_secondary(binding, inputs, dev, stream, hbm, precisions):
+def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions):
     """The Scale workload at full size (K = 20000, S256, L = 255, HG g = 0.99, c = 0.9999,
     64 seeded sources): one set_xs and one solve per (precision, method), FPSA-SI and
     GMRES(30) right-preconditioned by the FP solve, timed by the host clock around both,
@@ -290,12 +290,28 @@ def scale_secondary(binding, inputs, dev, stream, hbm, precisions):
                     byt = K * (-(-R // 64) * 4 * (n2 * n2 + n2 * N + 4 * (N // 2) ** 2) + 4 * R * 4 * n2)
                 roof = {"kernel": kname, "bound": "hbm", "achieved": byt / (per * 1e-3) / 1e9,
                         "peak": hbm, "unit": "GB/s", "algorithmic_bytes": byt}
+            elif dom == "contract" and prec == "mixed":
+                # tensor-core contractions, split BF16 with three products: an N x N GEMM over
+                # every column (K x 2 per rhs) is 3 x 2 N^2 flop a column; FPSA-SI launches two
+                # such GEMMs per contraction launch, a GMRES operator four in three launches
+                gemms = 2.0 if meth == "fpsa" else 4.0 / 3.0
+                fl = gemms * 3 * 2.0 * N * N * 2 * K * R
+                roof = {"kernel": "k_tc_*_big (tensor-core contractions)", "bound": "tensor",
+                        "achieved": fl / (per * 1e-3) / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"}
             elif dom == "contract":
                 # 2 N (L+1) flop per column, K x 2 columns per rhs, 64 rhs, per contraction launch
                 fl = 2.0 * N * (L + 1) * 2 * K * R
                 roof = {"kernel": "contractions (SIMT)", "bound": "alu", "achieved": fl / (per * 1e-3) / 1e12,
-                        "peak": 74.0 if esize == 4 else 1.20, "unit": "TFLOP/s",
-                        "peak_source": "FP32 / FP64 FMA-chain probe on GB300 (74 / 1.20 TFLOP/s)"}
+                        "peak": 1.20, "unit": "TFLOP/s", "peak_source": "FP64 FMA-chain probe on GB300 (1.20 TFLOP/s)"}
+            elif dom == "residual" and prec == "mixed":
+                # the FP64 refinement residual: both contractions fold the mirror ordinates, N^2
+                # FP64 multiply-adds per column; a refinement step launches the residual and the
+                # accumulation of the correction, so the phase's launches are two per step
+                fl = 2.0 * N * N * 2 * K * R / 2
+                roof = {"kernel": "k_mixed_residual", "bound": "alu", "achieved": fl / (per * 1e-3) / 1e12,
+                        "peak": 1.20, "unit": "TFLOP/s", "peak_source": "FP64 FMA-chain probe on GB300 (1.20 TFLOP/s)",
+                        "note": "achieved over the residual phase's launch pairs (residual + accumulation)"}
             else:
                 roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s"}
             if roof.get("achieved") is not None:
@@ -521,6 +537,7 @@ def main():
     if not args.no_secondary and rank == 0 and world == 1:
         if not args.no_scale:
             secondary["scale"] = scale_secondary(binding, inputs, dev, stream, hbm,
+                                                 peaks.get("bf16_tflops_sustained", 1676.4),
                                                  ("mixed", "fp64") if args.scale_fp64 else ("mixed",))
         if args.batch_slabs > 0:
             secondary["batching"] = batching_secondary(binding, inputs, args.batch_slabs)

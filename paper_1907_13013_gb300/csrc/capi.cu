@@ -124,7 +124,6 @@ struct fpsa_ctx {
     unsigned char *gm_V = nullptr, *gm_u = nullptr, *gm_w = nullptr, *gm_b = nullptr;
     double *gm_partial = nullptr, *gm_dots = nullptr, *gm_coef = nullptr, *gm_alpha = nullptr;
     long long *gm_seg_begin = nullptr, *gm_seg_end = nullptr;
-    int32_t *gm_col_sys = nullptr;
     int gm_nchunks = 0;
 
     PathBuffers<double> p64;  // FP64 path; for MIXED: FP64 tables, psi (refined iterate), phi
@@ -1102,9 +1101,7 @@ int gmres_alloc(fpsa_ctx *ctx, int m) {
         CK(dalloc(ctx, &ctx->gm_b, n * es));
         CK(dalloc(ctx, &ctx->gm_seg_begin, nsys));
         CK(dalloc(ctx, &ctx->gm_seg_end, nsys));
-        CK(dalloc(ctx, &ctx->gm_col_sys, (size_t)g.R * g.sumK * 2));
         std::vector<long long> sb(nsys), se(nsys);
-        std::vector<int32_t> cs((size_t)g.R * g.sumK * 2);
         long long maxlen = 0;
         for (int r = 0; r < g.R; ++r)
             for (int b = 0; b < g.B; ++b) {
@@ -1112,12 +1109,9 @@ int gmres_alloc(fpsa_ctx *ctx, int m) {
                 sb[s] = ((long long)r * g.sumK + g.off[b]) * 2 * g.N;
                 se[s] = sb[s] + (long long)g.K[b] * 2 * g.N;
                 maxlen = std::max(maxlen, se[s] - sb[s]);
-                for (int c = 0; c < g.K[b]; ++c)
-                    for (int a = 0; a < 2; ++a) cs[((size_t)r * g.sumK + g.off[b] + c) * 2 + a] = s;
             }
         CK(cudaMemcpy(ctx->gm_seg_begin, sb.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->gm_seg_end, se.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(ctx->gm_col_sys, cs.data(), cs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         ctx->gm_nchunks = (int)((maxlen + kDotChunk - 1) / kDotChunk);
     }
     if (ctx->gm_partial) {
@@ -1143,7 +1137,7 @@ int gm_dots(fpsa_ctx *ctx, const T *V, int nv, const T *w, std::vector<double> &
     cudaStream_t st = ctx->stream;
     {
         Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
-        k_seg_dots<T><<<dim3(ctx->gm_nchunks, nsys), 256, 0, st>>>(V, n, nv, w, ctx->gm_seg_begin, ctx->gm_seg_end,
+        k_seg_dots<T><<<dim3(ctx->gm_nchunks, nsys), kDotThreads, 0, st>>>(V, n, nv, w, ctx->gm_seg_begin, ctx->gm_seg_end,
                                                                    ctx->gm_nchunks, ctx->gm_partial);
     }
     {
@@ -1160,11 +1154,13 @@ int gm_dots(fpsa_ctx *ctx, const T *V, int nv, const T *w, std::vector<double> &
     return FPSA_OK;
 }
 
-// y = alpha_s y + sum_i coef[s][i] V_i (alpha NULL: y = sum ...), coefficients from the host.
+// y = alpha_s x + sum_i coef[s][i] V_i (alpha NULL: y = sum ...; x NULL: x = y),
+// coefficients from the host.
 template <typename T>
 int gm_combine(fpsa_ctx *ctx, T *y, const std::vector<double> *alpha, const T *V, int nv,
-               const std::vector<double> &coef) {
+               const std::vector<double> &coef, const T *x = nullptr) {
     const Geometry &g = ctx->geo;
+    const int nsys = g.R * g.B;
     const size_t n = (size_t)g.R * g.sumK * 2 * g.N;
     cudaStream_t st = ctx->stream;
     if (nv) CK(cudaMemcpyAsync(ctx->gm_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1172,8 +1168,9 @@ int gm_combine(fpsa_ctx *ctx, T *y, const std::vector<double> *alpha, const T *V
         CK(cudaMemcpyAsync(ctx->gm_alpha, alpha->data(), alpha->size() * sizeof(double), cudaMemcpyHostToDevice, st));
     {
         Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
-        k_seg_combine<T><<<4 * 152, 256, 0, st>>>(y, alpha ? ctx->gm_alpha : nullptr, V, n, nv, ctx->gm_coef,
-                                                  ctx->gm_col_sys, g.N, n);
+        k_seg_combine<T><<<dim3(ctx->gm_nchunks, nsys), kDotThreads, 0, st>>>(
+            y, alpha ? ctx->gm_alpha : nullptr, x ? x : y, V, n, nv, ctx->gm_coef, ctx->gm_seg_begin,
+            ctx->gm_seg_end);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));  // the host vectors are reused right away
@@ -1331,14 +1328,15 @@ int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, 
     int status = FPSA_ENOTCONV;
     while (it < max_it) {
         // r = b - A' u  (u = 0 on the first cycle)
-        CK(cudaMemcpyAsync(V, b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
         if (it > 0) {
             rc = gm_apply(ctx, p, u, w);
             if (rc) return rc;
             ++sweeps;
             std::vector<double> one(nsys, -1.0);
-            rc = gm_combine(ctx, V, &c1, w, 1, one);  // V_0 = b - A' u
+            rc = gm_combine(ctx, V, &c1, w, 1, one, (const T *)b);  // V_0 = b - A' u
             if (rc) return rc;
+        } else {
+            CK(cudaMemcpyAsync(V, b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
         }
         rc = gm_dots(ctx, V, 1, V, dots);
         if (rc) return rc;
@@ -1403,8 +1401,7 @@ int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, 
             if (!std::isfinite(worst)) return fail(ctx, FPSA_ENONFINITE, "non-finite GMRES residual");
             if (worst < tol) break;
             if (j + 1 < m) {  // V_{j+1} = w / h_{j+1,j}
-                CK(cudaMemcpyAsync(V + (size_t)(j + 1) * n, w, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
-                rc = gm_combine(ctx, V + (size_t)(j + 1) * n, &alpha, V, 0, coef);
+                rc = gm_combine(ctx, V + (size_t)(j + 1) * n, &alpha, V, 0, coef, (const T *)w);
                 if (rc) return rc;
             }
         }
