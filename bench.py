@@ -243,18 +243,19 @@ def balance_defect(p, phi, r, tab):
     return float(abs(emission - absorption - jl - jr) / emission)
 
 
-def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions):
-    """The Scale workload at full size (K = 20000, S256, L = 255, HG g = 0.99, c = 0.9999,
+def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions, K=20000, methods=("fpsa", "gmres")):
+    """The Scale workload (full size: K = 20000, S256, L = 255, HG g = 0.99, c = 0.9999,
     64 seeded sources): one set_xs and one solve per (precision, method), FPSA-SI and
     GMRES(30) right-preconditioned by the FP solve, timed by the host clock around both,
     with CUDA events around every launch (the library's profiler) for the per-kernel
-    times; the particle balance of the converged flux for 3 of the right-hand sides."""
+    times; the particle balance of the converged flux for 3 of the right-hand sides.
+    A smaller K (same recipe) serves the ncu captures of its kernels."""
     import torch
-    p = inputs.scale_slab()
+    p = inputs.scale_slab(K=K)
     K, N, L, R = p["h"].size, p["N"], p["L"], p["Q"].shape[0]
     tab = binding.tables(N, L, "mpd")
-    out = {"workload": "scale_slab: 1 cm, K=20000, S256, L=255, HG g=0.99, c=0.9999, sigma_t=100, "
-                       "64 rhs Q~U[0,1), vacuum, MPD, tol 1e-10", "solves": {}}
+    out = {"workload": "scale_slab: 1 cm, K=%d, S256, L=255, HG g=0.99, c=0.9999, sigma_t=100, "
+                       "64 rhs Q~U[0,1), vacuum, MPD, tol 1e-10" % K, "solves": {}}
     d_st = torch.tensor(p["sigma_t"], device=dev)
     d_ss = torch.tensor(p["sigma_s"], device=dev)
     d_q = torch.tensor(p["Q"], device=dev)
@@ -262,7 +263,7 @@ def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions):
     for prec in precisions:
         ctx = binding.Context([K], p["h"], N, L, n_rhs=R, laplacian="mpd", precision=prec, device=dev.index,
                               stream=stream.cuda_stream)
-        for meth, kw in (("fpsa", {}), ("gmres", {"restart": 30})):
+        for meth, kw in [m for m in (("fpsa", {}), ("gmres", {"restart": 30})) if m[0] in methods]:
             ctx.profile_enable(True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -323,16 +324,19 @@ def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions):
                 "sweeps": st["sweeps"], "status": st["status"],
                 "cell_angles_per_s": st["cell_angles"] / wall,
                 "profile_ms": {k: round(v["ms"], 1) for k, v in phases.items()}, "roofline": roof,
-                "balance_defect_max_rhs_0_17_63": max(balance_defect(p, ph, r, tab) for r in (0, 17, 63))}
+                "balance_defect_max_rhs_0_17_63": max(balance_defect(p, ph, r, tab) for r in (0, 17, R - 1))}
         ctx.close()
         torch.cuda.empty_cache()
     return out
 
 
-def batching_secondary(binding, inputs, n_slabs):
+def batching_secondary(binding, inputs, n_slabs, hbm):
     """The first n_slabs of the seeded 4096-slab Batching recipe through the batch driver
     (groups by (N, L) on concurrent streams, memory-bounded waves): wall time of context
-    creation, upload, assembly, factorization and solve, after one untimed run."""
+    creation, upload, assembly, factorization and solve, after one untimed run; the
+    particle balance of every converged slab; then one more pass with CUDA events around
+    every launch (the library's profiler), its groups one after another, for the roofline
+    of the BCR solve (the dominant kernel) of the largest-N group."""
     import torch
     from paper_1907_13013_gb300 import batch
     probs = inputs.batch_slabs(n_slabs, seed=0)
@@ -346,10 +350,39 @@ def batching_secondary(binding, inputs, n_slabs):
     by_n = {}
     for q in probs:
         by_n[q["N"]] = by_n.get(q["N"], 0) + 1
+    tabs = {}
+    defect = 0.0
+    for q, ph in zip(probs, phis):
+        if q["N"] not in tabs:
+            tabs[q["N"]] = binding.tables(q["N"], q["L"], "wfd")
+        qq = dict(q, Q=q["Q"][None])
+        defect = max(defect, balance_defect(qq, np.asarray(ph)[None], 0, tabs[q["N"]]))
+    # profiled pass: groups one at a time (max_streams=1), so the event pairs time each
+    # kernel alone
+    _, pst = batch.BatchSolver(probs, precision="mixed", laplacian="wfd", max_streams=1,
+                               profile=True).solve(tol=TOL, max_iterations=200)
+    nmax = max(by_n)
+    roof = None
+    grp = [w for w in pst if w["N"] == nmax]
+    if grp:
+        ms = sum(w["profile"]["bcr_solve"]["ms"] for w in grp)
+        nl = sum(w["profile"]["bcr_solve"]["timed"] for w in grp)
+        # one BCR solve reads, for every cell of the group: A^{-1} ((2N)^2 forward), its
+        # 2N x N inflow columns (backward) and two N/2 x N/2 couplings, FP32
+        byt_per_solve = [4 * w["cells"] * ((2 * nmax) ** 2 + 2 * nmax * nmax + 2 * (nmax // 2) ** 2) for w in grp]
+        solves = [w["profile"]["bcr_solve"]["timed"] for w in grp]
+        byt = sum(b * n for b, n in zip(byt_per_solve, solves))
+        achieved = byt / (ms * 1e-3) / 1e9
+        roof = {"kernel": "k_bcr_solve_flow (N = %d group, 2N = %d)" % (nmax, 2 * nmax), "bound": "hbm",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "avg_launch_ms": ms / max(nl, 1), "algorithmic_bytes_per_launch": byt / max(nl, 1),
+                "phase_ms": {k: round(sum(w["profile"][k]["ms"] for w in grp), 1) for k in grp[0]["profile"]
+                             if grp[0]["profile"][k]["timed"]}}
     return {"workload": "batch_slabs(%d, seed=0): the first %d of the seeded 4096-slab recipe (K ~ U{100..5000}, "
                         "N in {16,32,64,128}, L = N-1, two HG regions), mixed WFD, tol 1e-10" % (n_slabs, n_slabs),
             "value": n_slabs / wall, "unit": "slabs/s", "wall_s": wall, "cells": int(cells),
-            "slabs_per_N": {str(k): v for k, v in sorted(by_n.items())}, "waves": len(stats)}
+            "slabs_per_N": {str(k): v for k, v in sorted(by_n.items())}, "waves": len(stats),
+            "balance_defect_max": defect, "roofline": roof}
 
 
 def main():
@@ -367,6 +400,9 @@ def main():
                          "(before the warm-up, outside the timed region)")
     ap.add_argument("--no-scale", action="store_true", help="skip the full-size Scale workload line")
     ap.add_argument("--scale-fp64", action="store_true", help="add the FP64 forms to the Scale line (minutes)")
+    ap.add_argument("--scale-only", type=int, default=0, metavar="K",
+                    help="run only the Scale recipe with K cells (mixed FPSA-SI and GMRES(30)) and print its "
+                         "line: the small case of the Scale kernels' ncu captures")
     ap.add_argument("--batch-slabs", type=int, default=256, help="Batching line: slabs of the recipe (0: skip)")
     ap.add_argument("--solve-slices", type=int, default=0, choices=[0, 1, 2, 4],
                     help="row-slice cap of the BCR solve after tuning (0: keep the tuned / library value)")
@@ -388,6 +424,15 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_1907_13013_gb300 import binding, inputs
+
+    if args.scale_only:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        out = scale_secondary(binding, inputs, dev, torch.cuda.current_stream(), peaks.get("hbm_gbs", 6800.0),
+                              peaks.get("bf16_tflops_sustained", 1676.4), ("mixed",), K=args.scale_only)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
 
     p = inputs.precision_srk_slab()
     K, N, L = p["h"].size, p["N"], p["L"]
@@ -540,7 +585,7 @@ def main():
                                                  peaks.get("bf16_tflops_sustained", 1676.4),
                                                  ("mixed", "fp64") if args.scale_fp64 else ("mixed",))
         if args.batch_slabs > 0:
-            secondary["batching"] = batching_secondary(binding, inputs, args.batch_slabs)
+            secondary["batching"] = batching_secondary(binding, inputs, args.batch_slabs, hbm)
 
     value = whole_job_rate(world, args.steps, ms)
     h2d = 8 * (K + K * (L + 1) + 2 * K * (L + 1))

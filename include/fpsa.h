@@ -233,12 +233,15 @@ typedef struct {
     int32_t solve_max_slices;       /* BCR solve: most row slices one block-row of a level is
                                        split into, 1, 2 or 4 */
     int32_t factor_engine;          /* BCR factorization of the next fpsa_set_xs: 1 = SIMT
-                                       Gauss-Jordan, 2 = tensor cores (blocked Gauss-Jordan with
-                                       tcgen05 trailing updates in split BF16; only for FP32
-                                       factors (MIXED) with 2N = 128, else FPSA_ENOTSUP);
-                                       0 = tensor cores where they apply, else SIMT. Factors
-                                       differ by rounding only (the pivots are chosen in FP32
-                                       either way) */
+                                       Gauss-Jordan (and SIMT block GEMMs), 2 = tensor cores
+                                       (only for FP32 factors (MIXED), else FPSA_ENOTSUP:
+                                       2N = 128, blocked Gauss-Jordan with tcgen05 trailing
+                                       updates in split BF16; 2N = 256 or 512, the recursive
+                                       block inversion's h x h products as tcgen05 split-BF16
+                                       GEMMs, its 128 x 128 leaves by Gauss-Jordan); 0 = tensor
+                                       cores where they apply, else SIMT. Factors differ by
+                                       rounding only (the pivots are chosen in FP32 either
+                                       way) */
     int32_t solve_engine;           /* BCR solve (the FP solve of every iteration; the
                                        factorization itself is unchanged): 1 = the dataflow
                                        solve on the FP32/FP64 cores (right-hand sides 8 at a

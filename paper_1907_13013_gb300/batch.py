@@ -102,17 +102,20 @@ class BatchSolver:
     """Solve a list of problem dicts (see inputs.py; single right-hand side each)."""
 
     def __init__(self, problems, precision="mixed", laplacian="wfd", budget_bytes=32 << 30, device=0,
-                 max_streams=4, tuning=None):
+                 max_streams=4, tuning=None, profile=False):
         """tuning: None (the library's launch shapes), or a TuningCache: each wave takes
         the cached shapes of its key; keys missing from the cache are searched first, one
         wave at a time with nothing else on the GPU (fpsa_autotune times whole solves, so
-        concurrent waves would distort each other's timings), then every wave runs."""
+        concurrent waves would distort each other's timings), then every wave runs.
+        profile: time every launch of each wave's solve with the library's profiler (CUDA
+        event pairs) and return the per-kernel-class times in the wave's stats."""
         self.problems = list(problems)
         self.precision, self.laplacian = precision, laplacian
         self.device = device
         self.waves = plan_waves(self.problems, budget_bytes, precision)
         self.max_streams = max_streams
         self.tuning = tuning
+        self.profile = profile
 
     def _key(self, wave, method):
         N, L, idx = wave
@@ -155,15 +158,19 @@ class BatchSolver:
                 ctx.set_tuning(self.tuning.get(key))
                 source = "search" if key in searched else "cache"
             tuned = ctx.get_tuning()
+            if self.profile:
+                ctx.profile_enable(True)
             phi, st = ctx.solve(**solve_kw)
+            prof = ctx.profile_read() if self.profile else None
             ctx.close()
         out, off = {}, 0
         for i, p in zip(idx, probs):
             K = p["h"].size
             out[i] = phi[0, off:off + K]
             off += K
+        extra = {"profile": prof} if prof is not None else {}
         return out, dict(st, N=N, instances=len(idx), cells=int(sum(p["h"].size for p in probs)),
-                         tuning=tuned, tuning_source=source)
+                         tuning=tuned, tuning_source=source, **extra)
 
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, **kw):
         """Returns (list of phi [K][2][L+1] per problem, list of per-wave stats)."""

@@ -21,6 +21,7 @@
 #include "kernels.cuh"
 #include "tc_contract.cuh"
 #include "bcr_large.cuh"
+#include "bgemm_tc.cuh"
 #include "bcr_factor_tc.cuh"
 #include "bcr_solve_tc.cuh"
 #include "gmres.cuh"
@@ -101,6 +102,7 @@ struct fpsa_ctx {
     fpsa_tuning tuning = {};         // requested launch shapes (0: the library's choice)
     int factor_grid[2] = {0, 0};     // cooperative dataflow factorization grid (0: per-level launches)
     int factor_tc_grid = 0;          // grid of the tensor-core factorization (FP32, 2N = 128), 0: unavailable
+    bool bgemm_tc_able = false;      // FP32, 2N = 256 or 512: recursive inversion's GEMMs on tensor cores
     // tensor-core BCR solve (FP32 factors, 2N a multiple of 128 up to 512, R >= 16)
     int tcs_rt = 0;                  // right-hand sides per unit; 0: unavailable
     int tcs_grid = 0;                // two CTAs per SM
@@ -419,6 +421,31 @@ int alloc_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     return FPSA_OK;
 }
 
+// Does the recursive inversion of this context run its block GEMMs on the tensor
+// cores? (FP32 factors with 2N = 256 or 512, unless the SIMT engine is requested.)
+bool bgemm_on_tc(const fpsa_ctx *ctx) { return ctx->bgemm_tc_able && ctx->tuning.factor_engine != 1; }
+
+// C = alpha A B + beta C for the h x h blocks of a batch of ne items: tcgen05 split
+// BF16 GEMMs for FP32 blocks with h = 128 or 256 where the context allows it, else
+// the SIMT kernel.
+template <typename T>
+void bgemm(fpsa_ctx *ctx, int h, T alpha, BMat<T> A, BMat<T> B, T beta, BMat<T> C, const BcrItem *items, int ne) {
+    cudaStream_t st = ctx->stream;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (bgemm_on_tc(ctx) && (h == 128 || h == 256)) {
+            if (h == 256)
+                k_bgemm_tc<256><<<dim3(2, ne), bgt::kThreads, bgt::smem_bytes(256), st>>>(alpha, A, B, beta, C,
+                                                                                          items, ctx->d_dev_err);
+            else
+                k_bgemm_tc<128><<<dim3(1, ne), bgt::kThreads, bgt::smem_bytes(128), st>>>(alpha, A, B, beta, C,
+                                                                                          items, ctx->d_dev_err);
+            return;
+        }
+    }
+    const dim3 gg((h + 63) / 64, (h + 63) / 64, ne);
+    k_bgemm<T><<<gg, 256, 0, st>>>(h, alpha, A, B, beta, C, items);
+}
+
 // In-place inverse (row-major) of the n x n blocks M of a batch of ne items,
 // recursing by block Schur complements down to CTA-sized blocks.
 template <typename T>
@@ -438,17 +465,16 @@ int invert_inplace(fpsa_ctx *ctx, PathBuffers<T> &p, BMat<T> M, int n, const Bcr
         const BMat<T> A11 = M.sub(0, 0), A12 = M.sub(0, h), A21 = M.sub(h, 0), A22 = M.sub(h, h);
         T *s = p.inv_scratch[depth];
         const BMat<T> X{s, (long long)h * h, h, 0}, Y{s + (size_t)kLargeChunk * h * h, (long long)h * h, h, 0};
-        const dim3 gg((h + 63) / 64, (h + 63) / 64, ne);
         int rc = invert_inplace(ctx, p, A11, h, items, ne, depth + 1);  // A11 <- P
         if (rc) return rc;
-        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(1), A11, A12, T(0), X, items);    // X = P A12
-        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(1), A21, A11, T(0), Y, items);    // Y = A21 P
-        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), A21, X, T(1), A22, items);   // A22 <- S = A22 - A21 X
-        rc = invert_inplace(ctx, p, A22, h, items, ne, depth + 1);            // A22 <- Q = S^{-1}
+        bgemm(ctx, h, T(1), A11, A12, T(0), X, items, ne);    // X = P A12
+        bgemm(ctx, h, T(1), A21, A11, T(0), Y, items, ne);    // Y = A21 P
+        bgemm(ctx, h, T(-1), A21, X, T(1), A22, items, ne);   // A22 <- S = A22 - A21 X
+        rc = invert_inplace(ctx, p, A22, h, items, ne, depth + 1);  // A22 <- Q = S^{-1}
         if (rc) return rc;
-        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), X, A22, T(0), A12, items);   // A12 <- -X Q
-        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), A22, Y, T(0), A21, items);   // A21 <- -Q Y
-        k_bgemm<T><<<gg, 256, 0, st>>>(h, T(-1), X, A21, T(1), A11, items);   // A11 <- P - X A21
+        bgemm(ctx, h, T(-1), X, A22, T(0), A12, items, ne);   // A12 <- -X Q
+        bgemm(ctx, h, T(-1), A22, Y, T(0), A21, items, ne);   // A21 <- -Q Y
+        bgemm(ctx, h, T(-1), X, A21, T(1), A11, items, ne);   // A11 <- P - X A21
     }
     CK(cudaGetLastError());
     return FPSA_OK;
@@ -1641,6 +1667,14 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
                                         (int)cudaSharedmemCarveoutMaxShared));
                 ctx->factor_tc_grid = 4 * nsm;
             }
+            if ((2 * g.N == 256 || 2 * g.N == 512) && ctx->precision == FPSA_PRECISION_MIXED) {
+                // the recursive block inversion's GEMMs (h = 128, 256) on the tensor cores:
+                // two (h = 256) or three (h = 128) CTAs per SM by shared memory, so their
+                // tensor-memory columns always fit
+                CK(raise_smem_limit((const void *)k_bgemm_tc<256>, (int)bgt::smem_bytes(256)));
+                CK(raise_smem_limit((const void *)k_bgemm_tc<128>, (int)bgt::smem_bytes(128)));
+                ctx->bgemm_tc_able = true;
+            }
             if (ctx->precision == FPSA_PRECISION_MIXED && tcs::applies(2 * g.N, g.R)) {
                 // the tensor-core BCR solve: a split copy of the factors, two CTAs per SM
                 ctx->tcs_rt = tcs::rhs_tile(g.R);
@@ -1936,7 +1970,7 @@ int fpsa_get_tuning(const fpsa_ctx *ctx, fpsa_tuning *out) {
     out->sweep_cells_per_thread = ctx->sweep_cpt;
     out->solve_blocks_per_sm = ctx->coop_grid[e] / std::max(1, ctx->n_sm);
     out->solve_max_slices = ctx->tuning.solve_max_slices > 0 ? ctx->tuning.solve_max_slices : 4;
-    out->factor_engine = (ctx->factor_tc_grid > 0 && ctx->tuning.factor_engine != 1) ? 2 : 1;
+    out->factor_engine = ((ctx->factor_tc_grid > 0 || ctx->bgemm_tc_able) && ctx->tuning.factor_engine != 1) ? 2 : 1;
     out->solve_engine = (ctx->tcs_rt > 0 && ctx->tuning.solve_engine != 1) ? 2 : 1;
     return FPSA_OK;
 }
@@ -1952,8 +1986,8 @@ int fpsa_set_tuning(fpsa_ctx *ctx, const fpsa_tuning *t) {
     if (r.solve_max_slices != 0 && r.solve_max_slices != 1 && r.solve_max_slices != 2 && r.solve_max_slices != 4)
         return fail(ctx, FPSA_EINVAL, "solve_max_slices not 0, 1, 2 or 4");
     if (r.factor_engine < 0 || r.factor_engine > 2) return fail(ctx, FPSA_EINVAL, "factor_engine not 0, 1 or 2");
-    if (r.factor_engine == 2 && ctx->factor_tc_grid == 0)
-        return fail(ctx, FPSA_ENOTSUP, "tensor-core factorization needs FP32 factors (MIXED) with 2N = 128");
+    if (r.factor_engine == 2 && ctx->factor_tc_grid == 0 && !ctx->bgemm_tc_able)
+        return fail(ctx, FPSA_ENOTSUP, "tensor-core factorization needs FP32 factors (MIXED) with 2N = 128, 256 or 512");
     if (r.solve_engine < 0 || r.solve_engine > 2) return fail(ctx, FPSA_EINVAL, "solve_engine not 0, 1 or 2");
     if (r.solve_engine == 2 && ctx->tcs_rt == 0)
         return fail(ctx, FPSA_ENOTSUP,

@@ -1,5 +1,6 @@
-"""The BCR factorization with tensor-core inversions (FP32 factors, 2N = 128: blocked
-Gauss-Jordan with tcgen05 trailing updates in split BF16) against the SIMT
+"""The BCR factorization with tensor-core inversions (FP32 factors; 2N = 128: blocked
+Gauss-Jordan with tcgen05 trailing updates in split BF16; 2N = 256 and 512: the
+recursive block inversion's GEMMs as tcgen05 split-BF16 products) against the SIMT
 factorization and the FP64 oracle, through the C ABI.
 
 The factors are the FP correction's preconditioner inside the mixed-precision
@@ -68,6 +69,41 @@ def test_tensor_core_factorization_matches_simt_and_oracle(binding, case, laplac
     assert abs(st_tc["outer_iterations"] - st_si["outer_iterations"]) <= 1, (st_tc, st_si)
     g_tc, g_si = st_tc["pivot_growth"], st_si["pivot_growth"]
     assert g_tc > 0 and abs(g_tc - g_si) <= 1e-3 * g_si, (g_tc, g_si)
+    off = 0
+    for p in probs:
+        K = p["h"].size
+        ref = oit.direct_solve(p)
+        assert relerr(phi_tc[off:off + K], ref) < TOL, (case, relerr(phi_tc[off:off + K], ref))
+        assert relerr(phi_si[off:off + K], ref) < TOL
+        off += K
+
+
+# 2N = 256 and 512: the recursive block inversion (128 x 128 leaves by Gauss-Jordan)
+# with its block GEMMs on the tensor cores (engine 2) or the FP32 cores (engine 1)
+LARGE_CASES = {
+    "n128_single": lambda: [inputs.random_slab(301, 128, 127, seed=650, kernel="srk", thick=(5, 500),
+                                               c=(0.8, 0.999))],
+    "n128_batch": lambda: [inputs.random_slab(K, 128, 100, seed=651 + K, kernel="hg", thick=(2, 200),
+                                              c=(0.6, 0.995)) for K in (1, 5, 130)],
+    "n256_single": lambda: [inputs.random_slab(61, 256, 255, seed=660, kernel="hg", thick=(5, 500),
+                                               c=(0.8, 0.999))],
+    "n256_reflective": lambda: [dict(inputs.random_slab(33, 256, 200, seed=661, kernel="srk", thick=(2, 200),
+                                                        c=(0.7, 0.995)), bc=("vacuum", "reflective"))],
+}
+
+
+@pytest.mark.parametrize("case", sorted(LARGE_CASES))
+def test_tensor_core_block_gemms_match_simt_and_oracle(binding, case):
+    probs = LARGE_CASES[case]()
+    phi_tc, st_tc = solve_with(binding, probs, 2, "mpd")
+    phi_si, st_si = solve_with(binding, probs, 1, "mpd")
+    assert st_tc["status"] == 0 and st_si["status"] == 0
+    assert abs(st_tc["outer_iterations"] - st_si["outer_iterations"]) <= 1, (st_tc, st_si)
+    # the growth max|A| max|A^{-1}| of both engines: each split-BF16 product carries about
+    # 2^-15 of relative error, amplified through the Schur complements of two levels of
+    # recursion (2N = 512) to a few 1e-3 of the largest inverse entry
+    g_tc, g_si = st_tc["pivot_growth"], st_si["pivot_growth"]
+    assert g_tc > 0 and abs(g_tc - g_si) <= 1e-2 * g_si, (g_tc, g_si)
     off = 0
     for p in probs:
         K = p["h"].size

@@ -470,6 +470,72 @@ def test_batching_workload_reduced(binding):
         assert relerr(phis[i], ref) < TOL, (i, p["N"], p["h"].size)
 
 
+def window_residual(p, phi, cells):
+    """Residual of the discrete LD transport equations (the oracle's L_h - S_h and m q,
+    Eq. trop) at the given cells, relative to the largest |L_h - S_h| |psi| + |m q| of
+    the window: each cell is checked on the 3-cell window around it, whose rows for
+    the middle cell are exactly the full slab's (psi = M phi is exact for L = N - 1).
+    A perturbation of phi by 1e-9 of max|phi_0| (the parity bound) raises this measure
+    to about 2e-7 on the Batching recipe; the converged solution gives about 1e-15."""
+    from oracle import transport as tr
+    N, L = p["N"], p["L"]
+    mu, w, D, M = oit.tables(N, L)
+    K = p["h"].size
+    worst = 0.0
+    for i in cells:
+        a, b = max(i - 1, 0), min(i + 2, K)
+        sub = dict(p, h=p["h"][a:b], sigma_t=p["sigma_t"][a:b], sigma_s=p["sigma_s"][a:b], Q=p["Q"][a:b],
+                   bc="vacuum")
+        A = oit.transport_matrix(sub, mu, w)
+        psi = np.einsum("nl,kal->kan", M, phi[a:b]).ravel()
+        bv = tr.mass_weight(sub["h"], oit.scattering_source(M, np.zeros_like(sub["sigma_s"]),
+                                                            np.zeros_like(phi[a:b]), sub["Q"])).ravel()
+        r = A @ psi - bv
+        scale = abs(A) @ np.abs(psi) + np.abs(bv)
+        rows = slice((i - a) * 2 * N, (i - a + 1) * 2 * N)
+        worst = max(worst, float(np.max(np.abs(r[rows])) / np.max(scale)))
+    return worst
+
+
+def test_batching_recipe_full_size_sampled(binding):
+    """The first 128 slabs of the seeded 4096-slab Batching recipe (K up to 5000, every N)
+    through the batch driver at the bench's tolerance: for each N its largest slab and
+    one more, the LD equations at the edges, the region boundary and seeded interior
+    cells (window_residual), the particle balance of every slab, and the oracle's
+    direct solution for each N's smallest slab."""
+    from paper_1907_13013_gb300 import batch
+    probs = inputs.batch_slabs(128, seed=0)
+    phis, stats = batch.BatchSolver(probs, precision="mixed", laplacian="wfd").solve(tol=1e-10, max_iterations=200)
+    assert all(s["status"] == 0 for s in stats)
+    rng = np.random.default_rng(5)
+    tabs = {}
+    for N in (16, 32, 64, 128):
+        idx = [i for i, p in enumerate(probs) if p["N"] == N]
+        assert idx
+        by_k = sorted(idx, key=lambda i: probs[i]["h"].size)
+        for i in (by_k[-1], by_k[len(by_k) // 2]):
+            p = probs[i]
+            K = p["h"].size
+            cells = [0, K - 1, K // 2 - 1, K // 2] + [int(x) for x in rng.integers(1, K - 1, 3)]
+            res = window_residual(p, np.asarray(phis[i]), cells)
+            assert res < 1e-7, (N, K, res)
+        small = by_k[0]
+        if probs[small]["h"].size <= 1200:
+            ref = oit.direct_solve(probs[small])
+            assert relerr(np.asarray(phis[small]), ref) < TOL, (N, probs[small]["h"].size)
+        if N not in tabs:
+            tabs[N] = binding.tables(N, N - 1, "wfd")
+    for p, phi in zip(probs, phis):
+        mu, w, M = tabs[p["N"]]["mu"], tabs[p["N"]]["w"], tabs[p["N"]]["M"]
+        phi = np.asarray(phi)
+        jr = (w[mu > 0] * mu[mu > 0]) @ (M[mu > 0] @ phi[-1, 1])
+        jl = (w[mu < 0] * -mu[mu < 0]) @ (M[mu < 0] @ phi[0, 0])
+        sa = p["sigma_t"] - p["sigma_s"][:, 0]
+        emission = np.sum(p["h"] * (p["Q"][:, 0, 0] + p["Q"][:, 1, 0]) / 2)
+        absorption = np.sum(sa * p["h"] * (phi[:, 0, 0] + phi[:, 1, 0]) / 2)
+        assert abs(emission - absorption - jl - jr) < 1e-9 * emission
+
+
 # ---------------------------------------------------------------------------
 # FPSA-preconditioned GMRES(m) (FP64), against the oracle's GMRES and direct solve.
 # ---------------------------------------------------------------------------
