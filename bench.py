@@ -330,22 +330,34 @@ def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions, K=20000
     return out
 
 
-def batching_secondary(binding, inputs, n_slabs, hbm):
+def batching_secondary(binding, inputs, n_slabs, hbm, mode="graph"):
     """The first n_slabs of the seeded 4096-slab Batching recipe through the batch driver
-    (groups by (N, L) on concurrent streams, memory-bounded waves): wall time of context
-    creation, upload, assembly, factorization and solve, after one untimed run; the
+    (groups by (N, L), memory-bounded waves; each round of waves, one per N, solved as
+    one CUDA graph launch): wall time of context creation, upload, assembly,
+    factorization and solve, after one untimed run (and the same with the waves solved
+    from host threads on concurrent streams, for comparison); the
     particle balance of every converged slab; then one more pass with CUDA events around
     every launch (the library's profiler), its groups one after another, for the roofline
     of the BCR solve (the dominant kernel) of the largest-N group."""
     import torch
     from paper_1907_13013_gb300 import batch
     probs = inputs.batch_slabs(n_slabs, seed=0)
-    batch.BatchSolver(probs, precision="mixed", laplacian="wfd").solve(tol=TOL, max_iterations=200)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    phis, stats = batch.BatchSolver(probs, precision="mixed", laplacian="wfd").solve(tol=TOL, max_iterations=200)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+
+    def run(graph):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = batch.BatchSolver(probs, precision="mixed", laplacian="wfd", graph=graph).solve(tol=TOL,
+                                                                                            max_iterations=200)
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    graph = mode == "graph"
+    run(graph)  # untimed
+    (phis, stats), wall = run(graph)
+    # the same slabs with every wave's solve driven from its own host thread and stream
+    (phis_t, _), wall_t = run(False) if graph else ((phis, stats), wall)
+    agree = max(float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)[..., 0]).max())
+                for a, b in zip(phis, phis_t))
     cells = sum(q["h"].size for q in probs)
     by_n = {}
     for q in probs:
@@ -381,6 +393,10 @@ def batching_secondary(binding, inputs, n_slabs, hbm):
     return {"workload": "batch_slabs(%d, seed=0): the first %d of the seeded 4096-slab recipe (K ~ U{100..5000}, "
                         "N in {16,32,64,128}, L = N-1, two HG regions), mixed WFD, tol 1e-10" % (n_slabs, n_slabs),
             "value": n_slabs / wall, "unit": "slabs/s", "wall_s": wall, "cells": int(cells),
+            "mode": ("one CUDA graph launch per round of waves (every N's refinement loop a device-side while node)"
+                     if graph else "every wave's solve from its own host thread and stream"),
+            "graph_rounds": 1 + max(s.get("graph_round", 0) for s in stats) if graph else None,
+            "threads_value": n_slabs / wall_t, "threads_vs_graph_max_rel_diff": agree,
             "slabs_per_N": {str(k): v for k, v in sorted(by_n.items())}, "waves": len(stats),
             "balance_defect_max": defect, "roofline": roof}
 
@@ -400,6 +416,11 @@ def main():
                          "(before the warm-up, outside the timed region)")
     ap.add_argument("--no-scale", action="store_true", help="skip the full-size Scale workload line")
     ap.add_argument("--scale-fp64", action="store_true", help="add the FP64 forms to the Scale line (minutes)")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="B",
+                    help="run only the Batching line on the first B slabs of the recipe and print it: the small "
+                         "case of the Batching kernels' ncu captures")
+    ap.add_argument("--batch-mode", default="graph", choices=["graph", "threads"],
+                    help="Batching line: one CUDA graph per round of waves, or the waves from host threads")
     ap.add_argument("--scale-only", type=int, default=0, metavar="K",
                     help="run only the Scale recipe with K cells (mixed FPSA-SI and GMRES(30)) and print its "
                          "line: the small case of the Scale kernels' ncu captures")
@@ -425,9 +446,15 @@ def main():
         dist.barrier()
     from paper_1907_13013_gb300 import binding, inputs
 
-    if args.scale_only:
+    if args.scale_only or args.batch_only:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if args.batch_only:
+        out = batching_secondary(binding, inputs, args.batch_only, peaks.get("hbm_gbs", 6800.0), args.batch_mode)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    if args.scale_only:
         out = scale_secondary(binding, inputs, dev, torch.cuda.current_stream(), peaks.get("hbm_gbs", 6800.0),
                               peaks.get("bf16_tflops_sustained", 1676.4), ("mixed",), K=args.scale_only)
         if rank == 0:
@@ -585,7 +612,7 @@ def main():
                                                  peaks.get("bf16_tflops_sustained", 1676.4),
                                                  ("mixed", "fp64") if args.scale_fp64 else ("mixed",))
         if args.batch_slabs > 0:
-            secondary["batching"] = batching_secondary(binding, inputs, args.batch_slabs, hbm)
+            secondary["batching"] = batching_secondary(binding, inputs, args.batch_slabs, hbm, args.batch_mode)
 
     value = whole_job_rate(world, args.steps, ms)
     h2d = 8 * (K + K * (L + 1) + 2 * K * (L + 1))

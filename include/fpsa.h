@@ -192,6 +192,30 @@ int fpsa_set_incident(fpsa_ctx *ctx, const double *psi_inc, int32_t mem);
 int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *phi0,
                int32_t mem, fpsa_stats *stats);
 
+/* Solve the problems of n contexts together as ONE launch of a CUDA graph: the
+ * Batching pattern, where slabs of different orders N (one context per (N, L)
+ * group) are solved at once. Every context must be MIXED precision, on the same
+ * device, after a successful fpsa_set_xs; methods SI or FPSA (Eqs. trsi; predict,
+ * correct, iterate). The graph holds, per context, the start of its FP64
+ * refinement (zero state, first residual) and a device-side while loop whose body
+ * is one refinement step (inner_iterations FP32 iterations, default 4, the FP64
+ * accumulation and residual) and whose test is the stopping rule of fpsa_solve
+ * (relative change of phi_0 below tol, or max_iterations refinement steps, or a
+ * bounded wait that ran out, or a non-finite change), evaluated on the GPU; the
+ * contexts' loops are independent branches of the graph and run concurrently. The
+ * inner iteration count is fixed (fpsa_solve shortens the confirming step to one
+ * inner iteration), so a context may take one step more than fpsa_solve would;
+ * the iterates differ by rounding order only. The kernels are launched without
+ * programmatic dependent launch inside the graph. phi[i]: output [R][sumK][2][L+1]
+ * of context i, of kind mem (no phi0: every solve starts from zero). stats: NULL
+ * or an array of n (solve_ms is the wall time of the whole call). The graph is
+ * built, run and destroyed inside the call; it allocates a stream and the graph.
+ * Returns the first failing status (each stats[i].status tells which), FPSA_ENOTSUP
+ * if this CUDA driver refuses the graph (e.g. a conditional node). Contexts must not
+ * be used by other threads during the call. */
+int fpsa_solve_batch(fpsa_ctx *const *ctxs, int32_t n, const fpsa_opts *opts, double *const *phi,
+                     int32_t mem, fpsa_stats *stats);
+
 /* Sensitivities of an objective J of the converged solution with respect to every
  * per-cell sigma_t and sigma_s,l, by implicit differentiation of the discrete
  * fixed point (the paper has no adjoint; the system is Eq. trop in LD / S_N form,

@@ -102,13 +102,17 @@ class BatchSolver:
     """Solve a list of problem dicts (see inputs.py; single right-hand side each)."""
 
     def __init__(self, problems, precision="mixed", laplacian="wfd", budget_bytes=32 << 30, device=0,
-                 max_streams=4, tuning=None, profile=False):
+                 max_streams=4, tuning=None, profile=False, graph=False):
         """tuning: None (the library's launch shapes), or a TuningCache: each wave takes
         the cached shapes of its key; keys missing from the cache are searched first, one
         wave at a time with nothing else on the GPU (fpsa_autotune times whole solves, so
         concurrent waves would distort each other's timings), then every wave runs.
         profile: time every launch of each wave's solve with the library's profiler (CUDA
-        event pairs) and return the per-kernel-class times in the wave's stats."""
+        event pairs) and return the per-kernel-class times in the wave's stats.
+        graph: solve in rounds, each holding one wave of every (N, L) group, as ONE launch
+        of a CUDA graph per round (fpsa_solve_batch: every group's refinement loop a
+        device-side while node, the groups concurrent branches); MIXED precision, SI or
+        FPSA. Contexts are still created and factorized on concurrent streams first."""
         self.problems = list(problems)
         self.precision, self.laplacian = precision, laplacian
         self.device = device
@@ -116,6 +120,9 @@ class BatchSolver:
         self.max_streams = max_streams
         self.tuning = tuning
         self.profile = profile
+        self.graph = graph
+        if graph and precision != "mixed":
+            raise ValueError("graph batches need precision='mixed'")
 
     def _key(self, wave, method):
         N, L, idx = wave
@@ -172,12 +179,63 @@ class BatchSolver:
         return out, dict(st, N=N, instances=len(idx), cells=int(sum(p["h"].size for p in probs)),
                          tuning=tuned, tuning_source=source, **extra)
 
+    def rounds(self):
+        """Graph mode: lists of waves, the r-th wave of every (N, L) group in round r."""
+        by_group = {}
+        for w in self.waves:
+            by_group.setdefault((w[0], w[1]), []).append(w)
+        n = max(len(v) for v in by_group.values())
+        return [[v[r] for v in by_group.values() if r < len(v)] for r in range(n)]
+
+    def _prepare_wave(self, wave, method, searched):
+        import torch
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(device=self.device)
+        with torch.cuda.stream(stream):
+            ctx = self._context(wave, stream)
+            source = "library"
+            if self.tuning is not None:
+                key = self._key(wave, method)
+                ctx.set_tuning(self.tuning.get(key))
+                source = "search" if key in searched else "cache"
+        return ctx, stream, source
+
+    def _solve_graph(self, solve_kw, searched):
+        results = [None] * len(self.problems)
+        stats = []
+        kw = {k: v for k, v in solve_kw.items() if k in ("method", "tol", "max_iterations", "inner_iterations",
+                                                        "contraction")}
+        with cf.ThreadPoolExecutor(max_workers=self.max_streams) as ex:
+            for r, rnd in enumerate(self.rounds()):
+                prepared = list(ex.map(lambda w: self._prepare_wave(w, solve_kw.get("method", "fpsa"), searched),
+                                       rnd))
+                ctxs = [c for c, _, _ in prepared]
+                try:
+                    phis, sts = binding.solve_batch(ctxs, **kw)
+                    for (N, L, idx), phi, st, (ctx, _, source) in zip(rnd, phis, sts, prepared):
+                        off = 0
+                        for i in idx:
+                            K = self.problems[i]["h"].size
+                            results[i] = phi[0, off:off + K]
+                            off += K
+                        stats.append(dict(st, N=N, instances=len(idx), cells=int(off), tuning=ctx.get_tuning(),
+                                          tuning_source=source, graph_round=r))
+                finally:
+                    for c in ctxs:
+                        c.close()
+        return results, stats
+
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, **kw):
         """Returns (list of phi [K][2][L+1] per problem, list of per-wave stats)."""
         solve_kw = dict(method=method, tol=tol, max_iterations=max_iterations, **kw)
         results = [None] * len(self.problems)
         stats = []
         searched = self._search(solve_kw) if self.tuning is not None else set()
+        if self.graph:
+            results, stats = self._solve_graph(solve_kw, searched)
+            if self.tuning is not None:
+                self.tuning.save()
+            return results, stats
         with cf.ThreadPoolExecutor(max_workers=self.max_streams) as ex:
             for out, st in ex.map(lambda w: self._run_wave(w, solve_kw, searched), self.waves):
                 for i, phi in out.items():

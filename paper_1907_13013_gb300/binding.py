@@ -125,6 +125,9 @@ def load():
     lib.fpsa_set_limits.restype = ctypes.c_int
     lib.fpsa_sweep_noalloc.argtypes = [i32, i32, dp, dp, dp, dp, vp]
     lib.fpsa_sweep_noalloc.restype = ctypes.c_int
+    lib.fpsa_solve_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(FpsaOpts), ctypes.POINTER(dp), i32,
+                                     ctypes.POINTER(FpsaStats)]
+    lib.fpsa_solve_batch.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -348,6 +351,27 @@ def sweep_noalloc(N, h, sigma_t, q, psi, stream=None):
     if rc != OK:
         raise FpsaError(rc, "fpsa_sweep_noalloc (N=%d, K=%d)" % (N, K))
     return psi
+
+
+def solve_batch(contexts, method="fpsa", tol=1e-10, max_iterations=10000, inner_iterations=0,
+                contraction="auto", raise_on_notconv=True):
+    """fpsa_solve_batch: the MIXED solves of several contexts (e.g. the (N, L) groups of a
+    batch of slabs) as one CUDA graph launch. Returns ([phi per context, numpy
+    [R][sumK][2][L+1]], [stats dict per context])."""
+    lib = load()
+    n = len(contexts)
+    outs = [np.zeros((c.R, c.sumK, 2, c.L + 1)) for c in contexts]
+    handles = (ctypes.c_void_p * n)(*[c._h.value for c in contexts])
+    ptrs = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+    st = (FpsaStats * n)()
+    o = FpsaOpts(METHOD[method], int(max_iterations), float(tol), int(inner_iterations), 0.0, 1,
+                 CONTRACTION[contraction], 0)
+    rc = lib.fpsa_solve_batch(handles, n, ctypes.byref(o), ptrs, MEM_HOST, st)
+    stats = [s.as_dict() for s in st]
+    if rc != OK and not (rc == ENOTCONV and not raise_on_notconv):
+        bad = next((i for i, s in enumerate(stats) if s["status"] != OK), 0)
+        raise FpsaError(rc, "fpsa_solve_batch: " + lib.fpsa_last_error(handles[bad]).decode())
+    return outs, stats
 
 
 def _bc_array(bc, B):

@@ -112,6 +112,7 @@ struct fpsa_ctx {
     unsigned long long *d_conv = nullptr, *d_growth = nullptr;
     int *d_status = nullptr;
     double *d_result = nullptr;
+    int *d_steps = nullptr;      // refinement steps taken by a batch graph's loop
     double *h_result = nullptr;  // pinned
 
     // adjoint
@@ -678,6 +679,10 @@ int setup_path(fpsa_ctx *ctx, PathBuffers<T> &p, bool full) {
     return FPSA_OK;
 }
 
+// Set while a batch graph is captured on this thread: kernels are launched without the
+// programmatic-dependent-launch attribute (plain graph edges between them).
+thread_local bool g_plain_launch = false;
+
 // Launch with programmatic dependent launch allowed: the kernel's blocks may be
 // scheduled while the previous kernel in the stream drains, and the kernel waits
 // for it (griddepcontrol.wait, before touching its outputs or overwriting its
@@ -693,7 +698,7 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr.val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = g_plain_launch ? 0 : 1;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
@@ -802,6 +807,20 @@ int bcr_solve(fpsa_ctx *ctx, PathBuffers<T> &p, T *rhs) {
     const int RC = solve_rc(R);
     const void *kern = coop_kernel<T>(RC, N);
     Launch L_(ctx, FPSA_PHASE_BCR_SOLVE);
+    if (g_plain_launch) {  // captured into a batch graph: a cooperative kernel node
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(solve_threads<T>(N));
+        cfg.dynamicSmemBytes = solve_smem<T>(N, RC);
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeCooperative;
+        attr.val.cooperative = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelExC(&cfg, kern, args));
+        return FPSA_OK;
+    }
     if (ctx->solve_pdl) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
@@ -931,6 +950,130 @@ template <typename T>
 int gmres_core(fpsa_ctx *ctx, PathBuffers<T> &p, int m, double tol, int max_it, const T *Qm, const T *Qa,
                const T *inc, int &it, int &sweeps, double &worst);
 
+// Launch plan of the MIXED path's inner contractions (tensor cores or SIMT FP32).
+struct MixedPlan {
+    dim3 cgrid;
+    size_t ncol, nang;
+    bool use_tc, tc_big, tc_full;
+    TcOps tcops;
+    int tc_blocks;
+    size_t tc_smem;
+};
+
+int mixed_plan(fpsa_ctx *ctx, const fpsa_opts &o, MixedPlan &mp) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N;
+    if (o.contraction == 2 && !ctx->tc_able)
+        return fail(ctx, FPSA_ENOTSUP,
+                    "tensor-core contractions need N a multiple of 16 and <= 128, or a multiple of 32 and <= 256");
+    mp.cgrid = dim3((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    mp.ncol = (size_t)g.R * g.sumK * 2;
+    mp.nang = mp.ncol * N;
+    mp.use_tc = ctx->tc_able && o.contraction != 1;
+    mp.tcops = TcOps{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
+    const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
+    mp.tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
+    mp.tc_big = ctx->tc_big;
+    mp.tc_smem = mp.tc_big ? tc::BigPlan::make(N).total : tc::Plan::make(N).total;
+    mp.tc_full = !mp.tc_big && tc::Plan::make(N).full;
+    return FPSA_OK;
+}
+
+// The FP64 residual of a refinement step: phi = D psi64, the convergence maxima, the
+// residual source of the next inner solve (k_mixed_residual), then the relative change
+// of phi_0 into d_result (k_conv_finalize).
+int mixed_residual_launch(fpsa_ctx *ctx, const MixedPlan &mp, const double *Qm, const double *Qa, const double *inc,
+                          bool gmres) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N;
+    cudaStream_t st = ctx->stream;
+    PathBuffers<double> &p = ctx->p64;
+    PathBuffers<float> &f = ctx->p32;
+    {
+        Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+        CK(launch_pdl(k_mixed_residual, mp.cgrid, dim3(kContractThreads), contract_smem<double>(N), st, p.psi, p.phi,
+                      p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst, ctx->d_off,
+                      ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc, ctx->d_bc,
+                      gmres ? (float *)nullptr : f.q, gmres ? (float *)nullptr : f.phi));
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
+        CK(launch_pdl(k_conv_finalize, dim3(1), dim3(256), 0, st, ctx->d_conv, g.R * g.B, ctx->d_result));
+    }
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
+// inner_k FP32 FPSA (fpsa) or SI iterations of the correction equation from zero
+// (f.phi = 0 and f.q = f.qang were written by the residual kernel), then
+// psi64 += dpsi (FP64). Adds the sweeps launched to `sweeps`.
+int mixed_inner_launch(fpsa_ctx *ctx, const MixedPlan &mp, int inner_k, bool fpsa, int &sweeps) {
+    const Geometry &g = ctx->geo;
+    const int N = g.N;
+    cudaStream_t st = ctx->stream;
+    PathBuffers<double> &p = ctx->p64;
+    PathBuffers<float> &f = ctx->p32;
+    const dim3 cgrid = mp.cgrid;
+    const bool use_tc = mp.use_tc, tc_big = mp.tc_big, tc_full = mp.tc_full;
+    const int tc_blocks = mp.tc_blocks;
+    const size_t tc_smem = mp.tc_smem;
+    const TcOps tcops = mp.tcops;
+    for (int j = 1; j <= inner_k; ++j) {
+        int rcs = sweep(ctx, f, f.q, f.psi, (const float *)nullptr);
+        if (rcs) return rcs;
+        ++sweeps;
+        const float *vin = f.psi, *base = nullptr;
+        if (fpsa) {
+            {
+                Launch L_(ctx, FPSA_PHASE_CONTRACT);
+                if (use_tc && tc_big)
+                    CK(launch_pdl(k_tc_fp_rhs_big, dim3(tc_blocks), dim3(128), tc_smem, st, (const float *)f.psi,
+                                  (const float *)f.phi, f.phi_half, (const float *)f.sigma_s,
+                                  (const double *)ctx->d_h, tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err));
+                else if (use_tc && tc_full)
+                    CK(launch_pdl(k_tc_fp_rhs_tile, dim3(tc_blocks), dim3(128), tc_smem, st, (const float *)f.psi,
+                                  (const float *)f.phi, f.phi_half, (const float *)f.sigma_s,
+                                  (const double *)ctx->d_h, tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err));
+                else if (use_tc)
+                    k_tc_fp_rhs<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h,
+                                                                 tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err);
+                else
+                    k_fp_rhs<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
+                        f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h, f.DT, f.MT, f.rhs, N, g.sumK);
+            }
+            int rc = bcr_solve(ctx, f, f.rhs);
+            if (rc) return rc;
+            vin = f.ybuf;
+            base = f.phi_half;
+        }
+        if (j < inner_k) {
+            Launch L_(ctx, FPSA_PHASE_CONTRACT);
+            if (use_tc && tc_big)
+                CK(launch_pdl(k_tc_update_scatter_big, dim3(tc_blocks), dim3(128), tc_smem, st, vin, base, f.phi,
+                              (const float *)f.sigma_s, tcops, f.q, (const float *)f.qang, N, g.sumK, g.R,
+                              ctx->d_dev_err));
+            else if (use_tc && tc_full)
+                CK(launch_pdl(k_tc_update_scatter_tile, dim3(tc_blocks), dim3(128), tc_smem, st, vin, base, f.phi,
+                              (const float *)f.sigma_s, tcops, f.q, (const float *)f.qang, N, g.sumK, g.R,
+                              ctx->d_dev_err));
+            else if (use_tc)
+                k_tc_update_scatter<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops, f.q,
+                                                                     f.qang, N, g.sumK, g.R, ctx->d_dev_err);
+            else
+                k_update_scatter<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
+                    vin, base, f.phi, f.sigma_s, (const float *)nullptr, f.DT, f.MT, f.q, ctx->d_cell_inst, g.B,
+                    (unsigned long long *)nullptr, N, g.sumK, f.qang);
+        }
+    }
+    {
+        Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+        CK(launch_pdl(k_mixed_accumulate, dim3(4 * 152), dim3(256), 0, st, p.psi, (const float *)f.psi,
+                      fpsa ? (const float *)f.ybuf : (const float *)nullptr, mp.nang));
+    }
+    CK(cudaGetLastError());
+    return FPSA_OK;
+}
+
 int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, double *phi_out, fpsa_stats &stats,
                 const double *Qm, const double *Qa, const double *inc) {
     const Geometry &g = ctx->geo;
@@ -938,25 +1081,18 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     cudaStream_t st = ctx->stream;
     PathBuffers<double> &p = ctx->p64;
     PathBuffers<float> &f = ctx->p32;
-    const size_t ncol = (size_t)g.R * g.sumK * 2, nang = ncol * N;
-    const dim3 cgrid((g.sumK + kContractCells - 1) / kContractCells, g.R);
+    MixedPlan mp;
+    int rcp = mixed_plan(ctx, o, mp);
+    if (rcp) return rcp;
+    const size_t ncol = mp.ncol, nang = mp.nang;
+    const dim3 cgrid = mp.cgrid;
     const int inner = o.inner_iterations > 0 ? o.inner_iterations : 4;
     const bool fpsa = o.method == FPSA_METHOD_FPSA, gmres = o.method == FPSA_METHOD_GMRES;
     const int m = o.restart > 0 ? o.restart : 30;
     const int inner_cap = o.inner_iterations > 0 ? o.inner_iterations : m;
     const double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
     int krylov = 0;
-    if (o.contraction == 2 && !ctx->tc_able)
-        return fail(ctx, FPSA_ENOTSUP,
-                    "tensor-core contractions need N a multiple of 16 and <= 128, or a multiple of 32 and <= 256");
-    const bool use_tc = ctx->tc_able && o.contraction != 1;
-    ctx->gm_use_tc = use_tc;  // the inner GMRES solves of GMRES-IR too
-    const TcOps tcops{ctx->d_tc_ops, ctx->d_tc_ops + 2 * (size_t)N * N * sizeof(__nv_bfloat16)};
-    const int tc_tiles = ((2 * g.sumK + 127) / 128) * g.R;
-    const int tc_blocks = std::max(1, std::min(tc_tiles, ctx->tc_grid));
-    const bool tc_big = ctx->tc_big;
-    const size_t tc_smem = tc_big ? tc::BigPlan::make(N).total : tc::Plan::make(N).total;
-    const bool tc_full = !tc_big && tc::Plan::make(N).full;
+    ctx->gm_use_tc = mp.use_tc;  // the inner GMRES solves of GMRES-IR too
     CK(cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), st));
 
     CK(cudaMemsetAsync(p.phi, 0, nang * sizeof(double), st));
@@ -973,18 +1109,8 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     double e = INFINITY, e_prev = INFINITY;
     int outer = 0, sweeps = 0;
     for (outer = 1; outer <= o.max_iterations + 1; ++outer) {
-        {
-            Launch L_(ctx, FPSA_PHASE_RESIDUAL);
-            CK(launch_pdl(k_mixed_residual, cgrid, dim3(kContractThreads), contract_smem<double>(N), st, p.psi, p.phi,
-                          p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst, ctx->d_off,
-                          ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc, ctx->d_bc,
-                          gmres ? (float *)nullptr : f.q, gmres ? (float *)nullptr : f.phi));
-        }
-        {
-            Launch L_(ctx, FPSA_PHASE_CONVERGENCE);
-            CK(launch_pdl(k_conv_finalize, dim3(1), dim3(256), 0, st, ctx->d_conv, g.R * g.B, ctx->d_result));
-        }
-        CK(cudaGetLastError());
+        int rcr = mixed_residual_launch(ctx, mp, Qm, Qa, inc, gmres);
+        if (rcr) return rcr;
         CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1037,60 +1163,8 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
             if (e * r / (1.0 - r) < o.tol) inner_k = 1;
         }
         e_prev = e;
-        // f.phi = 0 and f.q = f.qang were written by the residual kernel
-        for (int j = 1; j <= inner_k; ++j) {
-            int rcs = sweep(ctx, f, f.q, f.psi, (const float *)nullptr);
-            if (rcs) return rcs;
-            ++sweeps;
-            const float *vin = f.psi, *base = nullptr;
-            if (fpsa) {
-                {
-                    Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                    if (use_tc && tc_big)
-                        CK(launch_pdl(k_tc_fp_rhs_big, dim3(tc_blocks), dim3(128), tc_smem, st, (const float *)f.psi,
-                                      (const float *)f.phi, f.phi_half, (const float *)f.sigma_s,
-                                      (const double *)ctx->d_h, tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err));
-                    else if (use_tc && tc_full)
-                        CK(launch_pdl(k_tc_fp_rhs_tile, dim3(tc_blocks), dim3(128), tc_smem, st, (const float *)f.psi,
-                                      (const float *)f.phi, f.phi_half, (const float *)f.sigma_s,
-                                      (const double *)ctx->d_h, tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err));
-                    else if (use_tc)
-                        k_tc_fp_rhs<<<tc_blocks, 128, tc_smem, st>>>(f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h,
-                                                                     tcops, f.rhs, N, g.sumK, g.R, ctx->d_dev_err);
-                    else
-                        k_fp_rhs<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
-                            f.psi, f.phi, f.phi_half, f.sigma_s, ctx->d_h, f.DT, f.MT, f.rhs, N, g.sumK);
-                }
-                int rc = bcr_solve(ctx, f, f.rhs);
-                if (rc) return rc;
-                vin = f.ybuf;
-                base = f.phi_half;
-            }
-            if (j < inner_k) {
-                Launch L_(ctx, FPSA_PHASE_CONTRACT);
-                if (use_tc && tc_big)
-                    CK(launch_pdl(k_tc_update_scatter_big, dim3(tc_blocks), dim3(128), tc_smem, st, vin, base, f.phi,
-                                  (const float *)f.sigma_s, tcops, f.q, (const float *)f.qang, N, g.sumK, g.R,
-                                  ctx->d_dev_err));
-                else if (use_tc && tc_full)
-                    CK(launch_pdl(k_tc_update_scatter_tile, dim3(tc_blocks), dim3(128), tc_smem, st, vin, base, f.phi,
-                                  (const float *)f.sigma_s, tcops, f.q, (const float *)f.qang, N, g.sumK, g.R,
-                                  ctx->d_dev_err));
-                else if (use_tc)
-                    k_tc_update_scatter<<<tc_blocks, 128, tc_smem, st>>>(vin, base, f.phi, f.sigma_s, tcops, f.q,
-                                                                         f.qang, N, g.sumK, g.R, ctx->d_dev_err);
-                else
-                    k_update_scatter<float><<<cgrid, kContractThreads, contract_smem<float>(N), st>>>(
-                        vin, base, f.phi, f.sigma_s, (const float *)nullptr, f.DT, f.MT, f.q, ctx->d_cell_inst, g.B,
-                        (unsigned long long *)nullptr, N, g.sumK, f.qang);
-            }
-        }
-        {
-            Launch L_(ctx, FPSA_PHASE_RESIDUAL);
-            CK(launch_pdl(k_mixed_accumulate, dim3(4 * 152), dim3(256), 0, st, p.psi, (const float *)f.psi,
-                          fpsa ? (const float *)f.ybuf : (const float *)nullptr, nang));
-        }
-        CK(cudaGetLastError());
+        int rci = mixed_inner_launch(ctx, mp, inner_k, fpsa, sweeps);
+        if (rci) return rci;
     }
     stats.iterations = gmres ? krylov : sweeps;
     stats.outer_iterations = std::min(outer, o.max_iterations + 1);
@@ -1480,6 +1554,127 @@ int solve_gmres(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
 
 }  // namespace
 
+// One device-side loop test of a batch graph (Eq. iterate): after a refinement step's
+// residual, count the step and keep looping while the relative change of phi_0 is at
+// least tol, no bounded wait ran out, the change is finite and fewer than max_steps
+// corrections were made.
+__global__ void k_batch_cond(cudaGraphConditionalHandle handle, const double *__restrict__ e,
+                             const int *__restrict__ err, int *__restrict__ steps, double tol, int max_steps) {
+    if (threadIdx.x == 0) {
+        const int s = ++*steps;
+        const double v = *e;
+        const bool go = *err == 0 && !isnan(v) && !(v < tol) && s < max_steps;
+        cudaGraphSetConditional(handle, go ? 1u : 0u);
+    }
+}
+
+// Capture one context's MIXED solve into graph G as a prologue node (zero state,
+// first residual) followed by a while node whose body is one refinement step
+// (inner FP32 iterations, accumulation, residual, loop test). Launches go to the
+// capture stream cs; the context's own stream and profiler are restored afterwards.
+int capture_mixed_loop(fpsa_ctx *ctx, const MixedPlan &mp, const fpsa_opts &o, int inner, cudaGraph_t G,
+                       cudaStream_t cs) {
+    const Geometry &g = ctx->geo;
+    PathBuffers<double> &p = ctx->p64;
+    const bool fpsa = o.method == FPSA_METHOD_FPSA;
+    const double *inc = ctx->has_inc ? ctx->d_inc : nullptr;
+    cudaStream_t own = ctx->stream;
+    const bool prof = ctx->prof_on;
+    ctx->stream = cs;
+    ctx->prof_on = false;
+    g_plain_launch = true;
+    int rc = FPSA_OK;
+    cudaGraph_t pg = nullptr;
+    cudaGraphNode_t pnode = nullptr, wnode = nullptr;
+    auto restore = [&]() {
+        ctx->stream = own;
+        ctx->prof_on = prof;
+        g_plain_launch = false;
+    };
+    auto end_capture_on_error = [&]() {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        (void)cudaGetLastError();
+    };
+    // prologue: zero state, first residual (its change is never tested: no phi0)
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        restore();
+        return fail(ctx, FPSA_ECUDA, "batch graph: stream capture refused");
+    }
+    int sw = 0;
+    if (cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int), cs) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_steps, 0, sizeof(int), cs) != cudaSuccess ||
+        cudaMemsetAsync(p.phi, 0, mp.nang * sizeof(double), cs) != cudaSuccess ||
+        cudaMemsetAsync(p.psi, 0, mp.nang * sizeof(double), cs) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_conv, 0, (size_t)g.R * g.B * 2 * sizeof(unsigned long long), cs) != cudaSuccess) {
+        end_capture_on_error();
+        restore();
+        return fail(ctx, FPSA_ECUDA, "batch graph: capture of the prologue failed");
+    }
+    rc = mixed_residual_launch(ctx, mp, p.Q, nullptr, inc, false);
+    if (rc) {
+        end_capture_on_error();
+        restore();
+        return rc;
+    }
+    if (cudaStreamEndCapture(cs, &pg) != cudaSuccess || !pg) {
+        (void)cudaGetLastError();
+        restore();
+        return fail(ctx, FPSA_ECUDA, "batch graph: capture of the prologue failed");
+    }
+    cudaGraphConditionalHandle handle;
+    cudaGraphNodeParams cp = {};
+    bool ok = cudaGraphAddChildGraphNode(&pnode, G, nullptr, 0, pg) == cudaSuccess;
+    cudaGraphDestroy(pg);
+    ok = ok && cudaGraphConditionalHandleCreate(&handle, G, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&wnode, G, &pnode, nullptr, 1, &cp) == cudaSuccess;
+    }
+    if (!ok || cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        (void)cudaGetLastError();
+        restore();
+        return fail(ctx, FPSA_ENOTSUP, "batch graph: conditional while node refused");
+    }
+    // body: the BCR solves alternate their counter halves; with an odd number of them per
+    // step the first one's half is zeroed at the top of the step (it is otherwise zeroed
+    // by the step before)
+    if (fpsa && inner % 2 == 1) {
+        const int par = ctx->flow_parity;
+        ok = cudaMemsetAsync(ctx->d_flow + 2 * ctx->flow_n * par, 0, 2 * ctx->flow_n * sizeof(int), cs) == cudaSuccess;
+        if (ctx->d_tcs_queue) ok = ok && cudaMemsetAsync(ctx->d_tcs_queue + par, 0, sizeof(int), cs) == cudaSuccess;
+        if (!ok) {
+            end_capture_on_error();
+            restore();
+            return fail(ctx, FPSA_ECUDA, "batch graph: capture of the loop body failed");
+        }
+    }
+    rc = mixed_inner_launch(ctx, mp, inner, fpsa, sw);
+    if (!rc) rc = mixed_residual_launch(ctx, mp, p.Q, nullptr, inc, false);
+    if (!rc) {
+        k_batch_cond<<<1, 32, 0, cs>>>(handle, ctx->d_result, ctx->d_dev_err, ctx->d_steps, o.tol, o.max_iterations);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(ctx, FPSA_ECUDA, "batch graph: loop test launch failed");
+    }
+    if (rc) {
+        end_capture_on_error();
+        restore();
+        return rc;
+    }
+    cudaGraph_t body_out = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &body_out);
+    restore();
+    if (ce != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, FPSA_ENOTSUP, std::string("batch graph: loop body capture failed: ") + cudaGetErrorString(ce));
+    }
+    return FPSA_OK;
+}
+
 extern "C" {
 
 const char *fpsa_strerror(int code) {
@@ -1581,6 +1776,7 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         CK(dalloc(ctx, &ctx->d_growth, 1));
         CK(dalloc(ctx, &ctx->d_status, 1));
         CK(dalloc(ctx, &ctx->d_result, 2));
+        CK(dalloc(ctx, &ctx->d_steps, 1));
         CK(cudaMallocHost(&ctx->h_result, 2 * sizeof(double)));
         CK(cudaMemcpy(ctx->d_off, g.off.data(), g.B * sizeof(int32_t), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_K, g.K.data(), g.B * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -1878,6 +2074,125 @@ int fpsa_solve(fpsa_ctx *ctx, const fpsa_opts *opts, double *phi, const double *
     s.cell_angles = (double)ctx->geo.sumK * ctx->geo.N * ctx->geo.R * s.sweeps;
     if (stats) *stats = s;
     return rc;
+}
+
+int fpsa_solve_batch(fpsa_ctx *const *ctxs, int32_t n, const fpsa_opts *opts, double *const *phi, int32_t mem,
+                     fpsa_stats *stats) {
+    if (!ctxs || n < 1) return FPSA_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return FPSA_EINVAL;
+    fpsa_ctx *c0 = ctxs[0];
+    if (!phi) return fail(c0, FPSA_EINVAL, "null phi array");
+    if (mem != FPSA_MEM_HOST && mem != FPSA_MEM_DEVICE) return fail(c0, FPSA_EINVAL, "bad mem kind");
+    fpsa_opts o{FPSA_METHOD_FPSA, 10000, 1e-10, 0, 0.0, 1, 0, 0};
+    if (opts) o = *opts;
+    if (o.method != FPSA_METHOD_SI && o.method != FPSA_METHOD_FPSA)
+        return fail(c0, FPSA_ENOTSUP, "fpsa_solve_batch: method must be SI or FPSA");
+    if (o.max_iterations < 1 || !(o.tol >= 0.0)) return fail(c0, FPSA_EINVAL, "bad max_iterations / tol");
+    for (int i = 0; i < n; ++i) {
+        fpsa_ctx *c = ctxs[i];
+        if (!phi[i]) return fail(c, FPSA_EINVAL, "null phi");
+        if (c->precision != FPSA_PRECISION_MIXED)
+            return fail(c, FPSA_ENOTSUP, "fpsa_solve_batch: MIXED precision contexts only");
+        if (c->device != c0->device) return fail(c, FPSA_EINVAL, "fpsa_solve_batch: contexts on different devices");
+        if (!c->xs_ready) return fail(c, FPSA_ESTATE, "fpsa_set_xs must succeed before fpsa_solve_batch");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(c, FPSA_EINVAL, "fpsa_solve_batch: a context appears twice");
+    }
+    fpsa_ctx *ctx = c0;  // error messages of CUDA failures go to the first context
+    CK(cudaSetDevice(c0->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    const int inner = o.inner_iterations > 0 ? o.inner_iterations : 4;
+    std::vector<MixedPlan> plans(n);
+    for (int i = 0; i < n; ++i) {
+        ctxs[i]->fwd_ready = false;
+        int rc = mixed_plan(ctxs[i], o, plans[i]);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(ctxs[i]->stream));  // earlier work of every context is done
+    }
+    cudaStream_t cs = nullptr;
+    cudaGraph_t G = nullptr;
+    cudaGraphExec_t X = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    auto cleanup = [&]() {
+        if (X) cudaGraphExecDestroy(X);
+        if (G) cudaGraphDestroy(G);
+        if (cs) cudaStreamDestroy(cs);
+    };
+#define CKB(x)                                                                             \
+    do {                                                                                   \
+        cudaError_t e_ = (x);                                                              \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaStreamSynchronize(cs);                                                     \
+            cleanup();                                                                     \
+            return fail(c0, FPSA_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                  \
+    } while (0)
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) {
+        cleanup();
+        return fail(c0, FPSA_ECUDA, "cudaGraphCreate failed");
+    }
+    for (int i = 0; i < n; ++i) {
+        int rc = capture_mixed_loop(ctxs[i], plans[i], o, inner, G, cs);
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+    }
+    cudaError_t ce = cudaGraphInstantiate(&X, G, 0);
+    if (ce != cudaSuccess) {
+        (void)cudaGetLastError();
+        cleanup();
+        return fail(c0, FPSA_ENOTSUP, std::string("batch graph instantiation failed: ") + cudaGetErrorString(ce));
+    }
+    ce = cudaGraphLaunch(X, cs);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
+    if (ce != cudaSuccess) {
+        cleanup();
+        return fail(c0, FPSA_ECUDA, std::string("batch graph launch failed: ") + cudaGetErrorString(ce));
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int worst = FPSA_OK;
+    for (int i = 0; i < n; ++i) {
+        fpsa_ctx *c = ctxs[i];
+        const Geometry &g = c->geo;
+        double e = 0.0;
+        int err = 0, steps = 0;
+        CKB(cudaMemcpy(&e, c->d_result, sizeof(double), cudaMemcpyDeviceToHost));
+        CKB(cudaMemcpy(&err, c->d_dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+        CKB(cudaMemcpy(&steps, c->d_steps, sizeof(int), cudaMemcpyDeviceToHost));
+        int status = FPSA_OK;
+        if (err) status = fail(c, FPSA_ETIMEOUT, "a bounded device wait ran out (tensor-core contraction or BCR dataflow)");
+        else if (std::isnan(e)) status = fail(c, FPSA_ENONFINITE, "non-finite iterate in the batch graph");
+        else if (!(e < o.tol))
+            status = fail(c, FPSA_ENOTCONV, "not converged after " + std::to_string(o.max_iterations) + " refinement steps");
+        const size_t ncol = (size_t)g.R * g.sumK * 2;
+        CKB(cudaMemcpy2DAsync(phi[i], g.L1 * sizeof(double), c->p64.phi, g.N * sizeof(double), g.L1 * sizeof(double),
+                             ncol, mem == FPSA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, cs));
+        if (status == FPSA_OK) {
+            CKB(cudaMemcpyAsync(c->d_phi_fwd, c->p64.phi, ncol * g.N * sizeof(double), cudaMemcpyDeviceToDevice, cs));
+            c->fwd_ready = true;
+        }
+        if (stats) {
+            fpsa_stats s{};
+            s.status = status;
+            s.outer_iterations = steps + 1;
+            s.sweeps = steps * inner;
+            s.iterations = s.sweeps;
+            s.rel_change = e;
+            s.setup_ms = c->setup_ms;
+            s.solve_ms = ms;
+            s.pivot_growth = c->pivot_growth;
+            s.cell_angles = (double)g.sumK * g.N * g.R * s.sweeps;
+            stats[i] = s;
+        }
+        if (status != FPSA_OK && worst == FPSA_OK) worst = status;
+    }
+    ce = cudaStreamSynchronize(cs);
+    cleanup();
+    if (ce != cudaSuccess) return fail(c0, FPSA_ECUDA, cudaGetErrorString(ce));
+    return worst;
+#undef CKB
 }
 
 int fpsa_adjoint(fpsa_ctx *ctx, const fpsa_opts *opts, const double *dJ_dphi, double *dJ_dsigma_t,
