@@ -1690,8 +1690,11 @@ __device__ __forceinline__ T group_sum(T v, int G) {
 // BEFORE stage() runs (stage stages the coefficients and ends with a block
 // barrier), so the factor reads overlap the wait for the right-hand side.
 // Each A^{-1} vector is loaded once and used for all RC right-hand sides.
-// Returns the number of k-slices.
-constexpr int kMatvecChunk = 16;
+// Returns the number of k-slices. KC = 8: with 16 the unstaged solve kernels
+// (2N = 256) spilled 236-748 bytes per thread at their 128-register cap, and the
+// spill traffic serialised the factor stream (2.30 against 0.99 ms per solve
+// launch, 0.29 against 0.67 of HBM, on the Batching recipe's N = 128 group).
+constexpr int kMatvecChunk = 8;
 template <typename T, int NT, int RC, typename Stage>
 __device__ __forceinline__ int sliced_matvec(const T *__restrict__ Mt, int n2, int row0, int nr, int nk,
                                              int col_split, int col_off0, int col_off1, const T *coef, int cstride,
