@@ -243,7 +243,8 @@ def balance_defect(p, phi, r, tab):
     return float(abs(emission - absorption - jl - jr) / emission)
 
 
-def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions, K=20000, methods=("fpsa", "gmres")):
+def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions, K=20000, methods=("fpsa", "gmres"),
+                    inner=0):
     """The Scale workload (full size: K = 20000, S256, L = 255, HG g = 0.99, c = 0.9999,
     64 seeded sources): one set_xs and one solve per (precision, method), FPSA-SI and
     GMRES(30) right-preconditioned by the FP solve, timed by the host clock around both,
@@ -263,7 +264,8 @@ def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions, K=20000
     for prec in precisions:
         ctx = binding.Context([K], p["h"], N, L, n_rhs=R, laplacian="mpd", precision=prec, device=dev.index,
                               stream=stream.cuda_stream)
-        for meth, kw in [m for m in (("fpsa", {}), ("gmres", {"restart": 30})) if m[0] in methods]:
+        for meth, kw in [m for m in (("fpsa", {"inner_iterations": inner}), ("gmres", {"restart": 30}))
+                         if m[0] in methods]:
             ctx.profile_enable(True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -419,6 +421,9 @@ def main():
     ap.add_argument("--batch-only", type=int, default=0, metavar="B",
                     help="run only the Batching line on the first B slabs of the recipe and print it: the small "
                          "case of the Batching kernels' ncu captures")
+    ap.add_argument("--scale-inner", type=int, default=0,
+                    help="Scale line: FP32 FPSA iterations per FP64 refinement step (0: the library's default)")
+    ap.add_argument("--scale-methods", default="fpsa,gmres", help="Scale line: methods, comma-separated")
     ap.add_argument("--batch-mode", default="graph", choices=["graph", "threads"],
                     help="Batching line: one CUDA graph per round of waves, or the waves from host threads")
     ap.add_argument("--scale-only", type=int, default=0, metavar="K",
@@ -456,7 +461,8 @@ def main():
         return
     if args.scale_only:
         out = scale_secondary(binding, inputs, dev, torch.cuda.current_stream(), peaks.get("hbm_gbs", 6800.0),
-                              peaks.get("bf16_tflops_sustained", 1676.4), ("mixed",), K=args.scale_only)
+                              peaks.get("bf16_tflops_sustained", 1676.4), ("mixed",), K=args.scale_only,
+                              methods=tuple(args.scale_methods.split(",")), inner=args.scale_inner)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
@@ -610,7 +616,8 @@ def main():
         if not args.no_scale:
             secondary["scale"] = scale_secondary(binding, inputs, dev, stream, hbm,
                                                  peaks.get("bf16_tflops_sustained", 1676.4),
-                                                 ("mixed", "fp64") if args.scale_fp64 else ("mixed",))
+                                                 ("mixed", "fp64") if args.scale_fp64 else ("mixed",),
+                                                 methods=tuple(args.scale_methods.split(",")), inner=args.scale_inner)
         if args.batch_slabs > 0:
             secondary["batching"] = batching_secondary(binding, inputs, args.batch_slabs, hbm, args.batch_mode)
 

@@ -92,9 +92,16 @@ typedef struct {
                                  instance/right-hand side deciding (Eq. iterate);
                                  GMRES in FP64: stop when every (rhs, instance) system has
                                  ||b - (I-T) phi||_2 / ||b||_2 < tol on the moments */
-    int32_t inner_iterations; /* MIXED, SI / FPSA: FP32 iterations per FP64 refinement step
-                                 (0 = default 4); MIXED, GMRES: cap on the FP32 Krylov
-                                 iterations per refinement step (0 = the restart length) */
+    int32_t inner_iterations; /* MIXED, SI / FPSA: FP32 iterations per FP64 refinement step;
+                                 0 = adaptive (FPSA): 4 per step, and where the first step
+                                 shows the FP64 residual taking longer than one inner
+                                 iteration (timed by CUDA events), later steps take as many
+                                 as the observed contraction per inner iteration needs to
+                                 bring the error below tol (at least 4, at most 16, and no
+                                 more than keep a step's reduction above 1e-6, the FP32
+                                 floor); fpsa_solve_batch: 0 = 4 every step. MIXED, GMRES:
+                                 cap on the FP32 Krylov iterations per refinement step
+                                 (0 = the restart length) */
     double inner_tol;         /* MIXED, GMRES: relative residual target of each FP32 inner
                                  GMRES solve (0 = default 1e-5); unused otherwise */
     int32_t check_every;      /* test convergence every this many iterations (0 = 1) */
@@ -278,6 +285,16 @@ typedef struct {
                                        size as the FP32 ones); 0 = tensor cores where they
                                        apply, else the dataflow solve. Solutions differ by
                                        rounding only */
+    int32_t residual_engine;        /* MIXED, the FP64 refinement residual's two contractions
+                                       (phi = D psi, s = M (Sigma phi + Q)): 1 = FP64 FMA
+                                       cores, 2 = tensor cores computing them exactly at FP64
+                                       working accuracy (each column and operator row as a
+                                       56-bit fixed-point number in eight 7-bit BF16 digit
+                                       slices, the 36 digit-pair products summed exactly in
+                                       FP32 and recombined in FP64; N a multiple of 32 up to
+                                       256, else FPSA_ENOTSUP); 0 = tensor cores where they
+                                       apply, else FP64 cores. Results differ by rounding
+                                       only */
 } fpsa_tuning;
 
 /* The shapes in effect (zero fields resolved to the values used). */

@@ -200,15 +200,32 @@ class BatchSolver:
                 source = "search" if key in searched else "cache"
         return ctx, stream, source
 
+    def _round_bytes(self, rnd):
+        return sum(factor_bytes(sum(self.problems[i]["h"].size for i in w[2]), w[0], self.precision) for w in rnd)
+
     def _solve_graph(self, solve_kw, searched):
+        """Rounds of waves, each one graph launch (fpsa_solve_batch, which releases the GIL);
+        the next round's contexts are created and factorized on the pool's streams while
+        the current round's graph runs, when free device memory holds both rounds."""
+        import torch
         results = [None] * len(self.problems)
         stats = []
         kw = {k: v for k, v in solve_kw.items() if k in ("method", "tol", "max_iterations", "inner_iterations",
                                                         "contraction")}
+        method = solve_kw.get("method", "fpsa")
+        rounds = self.rounds()
         with cf.ThreadPoolExecutor(max_workers=self.max_streams) as ex:
-            for r, rnd in enumerate(self.rounds()):
-                prepared = list(ex.map(lambda w: self._prepare_wave(w, solve_kw.get("method", "fpsa"), searched),
-                                       rnd))
+            def start(rnd):
+                return [ex.submit(self._prepare_wave, w, method, searched) for w in rnd]
+
+            pending = start(rounds[0]) if rounds else None
+            for r, rnd in enumerate(rounds):
+                prepared = [f.result() for f in pending]
+                pending = None
+                if r + 1 < len(rounds):
+                    free, _ = torch.cuda.mem_get_info(self.device)
+                    if free > 1.25 * self._round_bytes(rounds[r + 1]) + (4 << 30):
+                        pending = start(rounds[r + 1])
                 ctxs = [c for c, _, _ in prepared]
                 try:
                     phis, sts = binding.solve_batch(ctxs, **kw)
@@ -223,6 +240,8 @@ class BatchSolver:
                 finally:
                     for c in ctxs:
                         c.close()
+                if pending is None and r + 1 < len(rounds):
+                    pending = start(rounds[r + 1])
         return results, stats
 
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, **kw):

@@ -57,7 +57,7 @@ class FpsaStats(ctypes.Structure):
 class FpsaTuning(ctypes.Structure):
     _fields_ = [("sweep_cells_per_thread", ctypes.c_int32), ("solve_blocks_per_sm", ctypes.c_int32),
                 ("solve_max_slices", ctypes.c_int32), ("factor_engine", ctypes.c_int32),
-                ("solve_engine", ctypes.c_int32)]
+                ("solve_engine", ctypes.c_int32), ("residual_engine", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -22,6 +22,7 @@
 #include "tc_contract.cuh"
 #include "bcr_large.cuh"
 #include "bgemm_tc.cuh"
+#include "residual_tc.cuh"
 #include "bcr_factor_tc.cuh"
 #include "bcr_solve_tc.cuh"
 #include "gmres.cuh"
@@ -103,6 +104,8 @@ struct fpsa_ctx {
     int factor_grid[2] = {0, 0};     // cooperative dataflow factorization grid (0: per-level launches)
     int factor_tc_grid = 0;          // grid of the tensor-core factorization (FP32, 2N = 128), 0: unavailable
     bool bgemm_tc_able = false;      // FP32, 2N = 256 or 512: recursive inversion's GEMMs on tensor cores
+    unsigned char *d_res_ops = nullptr;  // MIXED: digit slices of D and M, then their row exponents
+    rtc::Ops res_ops = {};               // (NULL D: the tensor-core residual does not apply)
     // tensor-core BCR solve (FP32 factors, 2N a multiple of 128 up to 512, R >= 16)
     int tcs_rt = 0;                  // right-hand sides per unit; 0: unavailable
     int tcs_grid = 0;                // two CTAs per SM
@@ -113,6 +116,7 @@ struct fpsa_ctx {
     int *d_status = nullptr;
     double *d_result = nullptr;
     int *d_steps = nullptr;      // refinement steps taken by a batch graph's loop
+    cudaEvent_t ad_ev[4] = {};   // MIXED: first residual and first inner step, timed once per solve
     double *h_result = nullptr;  // pinned
 
     // adjoint
@@ -522,6 +526,29 @@ int invert_level(fpsa_ctx *ctx, PathBuffers<T> &p, const BcrItem *items, int ni,
 // Tensor-core operands of the FP32 inner contractions: D and M (as FP32 values)
 // split into BF16 hi / lo, stored as the B operands of Out = X Op^T in the
 // K-major core-matrix layout (Op_D[l][n] = D[l][n], Op_M[n][l] = M[n][l]).
+// Digit slices of D and M for the tensor-core FP64 residual (MIXED, N a multiple of 32
+// up to 256): computed once on the host, layout of rtc::block_offset, exponents after.
+int setup_residual_tc(fpsa_ctx *ctx) {
+    const int N = ctx->geo.N;
+    if (ctx->precision != FPSA_PRECISION_MIXED || !rtc::applies(N)) return FPSA_OK;
+    const size_t nn = (size_t)N * N;
+    const size_t sl = (size_t)(N / rtc::oc_of(N)) * (N / rtc::KC) * rtc::b_block_bytes(N);
+    std::vector<unsigned char> host(2 * sl + 2 * N * sizeof(int32_t));
+    std::vector<double> M(nn);  // M stored [n][l] already: rows n, K = l
+    for (size_t i = 0; i < nn; ++i) M[i] = ctx->tab.M[i];
+    int32_t *eD = reinterpret_cast<int32_t *>(host.data() + 2 * sl), *eM = eD + N;
+    rtc::slice_operator(ctx->tab.D.data(), N, host.data(), eD);
+    rtc::slice_operator(M.data(), N, host.data() + sl, eM);
+    CK(dalloc(ctx, &ctx->d_res_ops, host.size()));
+    CK(cudaMemcpy(ctx->d_res_ops, host.data(), host.size(), cudaMemcpyHostToDevice));
+    ctx->res_ops.D = ctx->d_res_ops;
+    ctx->res_ops.M = ctx->d_res_ops + sl;
+    ctx->res_ops.eD = reinterpret_cast<const int32_t *>(ctx->d_res_ops + 2 * sl);
+    ctx->res_ops.eM = ctx->res_ops.eD + N;
+    CK(raise_smem_limit((const void *)k_mixed_residual_tc, (int)rtc::smem_bytes(N)));
+    return FPSA_OK;
+}
+
 int setup_tc(fpsa_ctx *ctx) {
     const int N = ctx->geo.N;
     // N <= 128: the operators stay in shared memory; N in (128, 256], a multiple of 32:
@@ -989,7 +1016,21 @@ int mixed_residual_launch(fpsa_ctx *ctx, const MixedPlan &mp, const double *Qm, 
     cudaStream_t st = ctx->stream;
     PathBuffers<double> &p = ctx->p64;
     PathBuffers<float> &f = ctx->p32;
-    {
+    // auto: the tensor cores where the 64-cell tiles fill the GPU (one CTA per SM holds all
+    // of its tensor memory); below that the FP64 kernel's finer blocks finish sooner
+    const bool res_tc = ctx->res_ops.D && (ctx->tuning.residual_engine == 2 ||
+                                           (ctx->tuning.residual_engine == 0 &&
+                                            (long long)((g.sumK + 63) / 64) * g.R >= ctx->n_sm));
+    if (res_tc) {
+        Launch L_(ctx, FPSA_PHASE_RESIDUAL);
+        CK(launch_pdl(k_mixed_residual_tc, dim3((g.sumK + 63) / 64, g.R), dim3(rtc::kThreads),
+                      (size_t)rtc::smem_bytes(N), st, (const double *)p.psi, p.phi, (const double *)p.sigma_s, Qm,
+                      ctx->res_ops, (const double *)ctx->d_sigma_t, (const double *)ctx->d_h,
+                      (const double *)ctx->d_mu, (const int32_t *)ctx->d_cell_inst, (const int32_t *)ctx->d_off,
+                      (const int32_t *)ctx->d_K, g.B, ctx->d_conv, f.qang, N, g.sumK, Qa, inc,
+                      (const int32_t *)ctx->d_bc, gmres ? (float *)nullptr : f.q, gmres ? (float *)nullptr : f.phi,
+                      ctx->d_dev_err));
+    } else {
         Launch L_(ctx, FPSA_PHASE_RESIDUAL);
         CK(launch_pdl(k_mixed_residual, mp.cgrid, dim3(kContractThreads), contract_smem<double>(N), st, p.psi, p.phi,
                       p.sigma_s, Qm, p.DT, p.MT, ctx->d_sigma_t, ctx->d_h, ctx->d_mu, ctx->d_cell_inst, ctx->d_off,
@@ -1087,6 +1128,9 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     const size_t ncol = mp.ncol, nang = mp.nang;
     const dim3 cgrid = mp.cgrid;
     const int inner = o.inner_iterations > 0 ? o.inner_iterations : 4;
+    const bool adaptive = o.inner_iterations <= 0;
+    constexpr int kInnerMax = 16;
+    int k_before = 0, k_last = 0;  // inner iterations of the last two steps
     const bool fpsa = o.method == FPSA_METHOD_FPSA, gmres = o.method == FPSA_METHOD_GMRES;
     const int m = o.restart > 0 ? o.restart : 30;
     const int inner_cap = o.inner_iterations > 0 ? o.inner_iterations : m;
@@ -1108,9 +1152,17 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
     int status = FPSA_ENOTCONV;
     double e = INFINITY, e_prev = INFINITY;
     int outer = 0, sweeps = 0;
+    // the adaptive inner count pays only where a residual costs more than an inner
+    // iteration: both are timed once, on the first refinement step (event pairs)
+    bool adaptive_on = false;
+    const bool time_first = adaptive && fpsa;
+    if (time_first && !ctx->ad_ev[0])
+        for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ctx->ad_ev[i]));
     for (outer = 1; outer <= o.max_iterations + 1; ++outer) {
+        if (time_first && outer == 1) CK(cudaEventRecord(ctx->ad_ev[0], st));
         int rcr = mixed_residual_launch(ctx, mp, Qm, Qa, inc, gmres);
         if (rcr) return rcr;
+        if (time_first && outer == 1) CK(cudaEventRecord(ctx->ad_ev[1], st));
         CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1156,15 +1208,48 @@ int solve_mixed(fpsa_ctx *ctx, const fpsa_opts &o, const double *phi0, int mem, 
         // inner FP32 solve of the correction from zero. When the last two refinement
         // changes predict that the remaining error (geometric extrapolation) is already
         // below tol, one inner iteration suffices for the step that confirms it: the
-        // stopping test itself is unchanged.
+        // stopping test itself is unchanged. With the adaptive count (inner_iterations
+        // 0), a step takes as many inner iterations as the observed contraction per
+        // inner iteration needs to bring that error below tol, at most kInnerMax and no
+        // more than keep the step's reduction above the FP32 floor (1e-6): fewer FP64
+        // residuals where they are expensive relative to an inner iteration.
+        // The change e measured now is the size of the previous step's correction, i.e. the
+        // error before that step, so e / e_prev is the contraction of the step before it
+        // (k_before inner iterations) and the error now is e times the contraction of the
+        // previous step (k_last inner iterations).
         int inner_k = inner;
         if (outer > 1 && e_prev > e && e > 0.0) {
             const double r = e / e_prev;
-            if (e * r / (1.0 - r) < o.tol) inner_k = 1;
+            if (!adaptive || k_before == 0) {
+                if (e * r / (1.0 - r) < o.tol) inner_k = 1;
+            } else {
+                const double lrho = std::log(r) / k_before;  // log of the contraction per inner iteration
+                const double err = e * std::exp(lrho * k_last), rk = std::exp(lrho * inner);
+                if (err / (1.0 - rk) < o.tol) {
+                    inner_k = 1;
+                } else {
+                    const int need = (int)std::ceil(std::log(o.tol / err) / lrho);
+                    const int floor32 = (int)std::floor(std::log(1e-6) / lrho);
+                    inner_k = std::max(inner, std::min({need, floor32, kInnerMax}));
+                }
+            }
         }
         e_prev = e;
+        k_before = k_last;
+        k_last = inner_k;
+        if (time_first && outer == 2) {  // the first step's events have completed (synchronised above)
+            float t_res = 0.f, t_step = 0.f;
+            if (cudaEventElapsedTime(&t_res, ctx->ad_ev[0], ctx->ad_ev[1]) == cudaSuccess &&
+                cudaEventElapsedTime(&t_step, ctx->ad_ev[2], ctx->ad_ev[3]) == cudaSuccess)
+                adaptive_on = t_res * inner > t_step;  // residual slower than one inner iteration
+            (void)cudaGetLastError();
+        }
+        if (!adaptive_on && inner_k > inner) inner_k = inner;
+        k_last = inner_k;
+        if (time_first && outer == 1) CK(cudaEventRecord(ctx->ad_ev[2], st));
         int rci = mixed_inner_launch(ctx, mp, inner_k, fpsa, sweeps);
         if (rci) return rci;
+        if (time_first && outer == 1) CK(cudaEventRecord(ctx->ad_ev[3], st));
     }
     stats.iterations = gmres ? krylov : sweeps;
     stats.outer_iterations = std::min(outer, o.max_iterations + 1);
@@ -1701,6 +1786,8 @@ void fpsa_destroy(fpsa_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (void *p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->ad_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
     delete ctx;
@@ -1903,6 +1990,8 @@ int fpsa_create(fpsa_ctx **out, const fpsa_desc *d) {
         int r2 = alloc_path(ctx, ctx->p64, false);
         if (r2) return r2;
         r2 = alloc_path(ctx, ctx->p32, true);
+        if (r2) return r2;
+        r2 = setup_residual_tc(ctx);
         if (r2) return r2;
         return setup_tc(ctx);
     }();
@@ -2287,6 +2376,10 @@ int fpsa_get_tuning(const fpsa_ctx *ctx, fpsa_tuning *out) {
     out->solve_max_slices = ctx->tuning.solve_max_slices > 0 ? ctx->tuning.solve_max_slices : 4;
     out->factor_engine = ((ctx->factor_tc_grid > 0 || ctx->bgemm_tc_able) && ctx->tuning.factor_engine != 1) ? 2 : 1;
     out->solve_engine = (ctx->tcs_rt > 0 && ctx->tuning.solve_engine != 1) ? 2 : 1;
+    out->residual_engine =
+        (ctx->res_ops.D && (ctx->tuning.residual_engine == 2 ||
+                            (ctx->tuning.residual_engine == 0 &&
+                             (long long)((ctx->geo.sumK + 63) / 64) * ctx->geo.R >= ctx->n_sm))) ? 2 : 1;
     return FPSA_OK;
 }
 
@@ -2304,6 +2397,10 @@ int fpsa_set_tuning(fpsa_ctx *ctx, const fpsa_tuning *t) {
     if (r.factor_engine == 2 && ctx->factor_tc_grid == 0 && !ctx->bgemm_tc_able)
         return fail(ctx, FPSA_ENOTSUP, "tensor-core factorization needs FP32 factors (MIXED) with 2N = 128, 256 or 512");
     if (r.solve_engine < 0 || r.solve_engine > 2) return fail(ctx, FPSA_EINVAL, "solve_engine not 0, 1 or 2");
+    if (r.residual_engine < 0 || r.residual_engine > 2)
+        return fail(ctx, FPSA_EINVAL, "residual_engine not 0, 1 or 2");
+    if (r.residual_engine == 2 && !ctx->res_ops.D)
+        return fail(ctx, FPSA_ENOTSUP, "tensor-core residual needs MIXED precision and N a multiple of 32 up to 256");
     if (r.solve_engine == 2 && ctx->tcs_rt == 0)
         return fail(ctx, FPSA_ENOTSUP,
                     "tensor-core BCR solve needs FP32 factors (MIXED), 2N a multiple of 128 up to 512 and at least "
@@ -2362,7 +2459,7 @@ int fpsa_autotune(fpsa_ctx *ctx, const fpsa_opts *opts, int32_t repeats, fpsa_tu
     const int bmax = std::min(4, ctx->solve_per_sm[ctx->precision == FPSA_PRECISION_FP64 ? 1 : 0]);
     for (int b = 1; b <= bmax; ++b)
         for (int s = 1; s <= 4; s *= 2) {
-            const fpsa_tuning t{0, b, s, saved.factor_engine, saved.solve_engine};
+            const fpsa_tuning t{0, b, s, saved.factor_engine, saved.solve_engine, saved.residual_engine};
             double ms = 0.0;
             const int rc = trial(t, ms);
             if (rc != FPSA_OK) return give_up(rc);

@@ -646,60 +646,100 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter_tile(const float *__r
 // ---------------------------------------------------------------------------
 // Streamed-operator variants for N > 128 (N a multiple of 32, at most 256): the
 // operators (2 N^2 BF16 values each, split hi / lo) no longer fit shared memory next
-// to the column tile, so each GEMM streams them through two buffers in K-chunks of
+// to the column tile, so each GEMM streams them through three buffers in K-chunks of
 // 32 (an operator is stored chunk-major in global memory, [N / 32 chunks][N rows][32]
 // in the K-major core-matrix layout, so a chunk is one bulk copy; the operators are
-// shared by every tile and stay in L2). The column tile (the A operand, 128 x N) and
-// the staged global I/O are as in k_tc_fp_rhs / k_tc_update_scatter; the accumulator
-// is N FP32 columns of TMEM (M = 128, N = 256 per instruction).
+// shared by every tile and stay in L2); a buffer is refilled once the MMAs of the
+// chunk before the current one have read it, so two copies stay in flight while a
+// chunk is multiplied. The column tile (the A operand, 128 x N) is split from FP32
+// rows that each thread reads straight from global memory (row t of the tile is the
+// thread's accumulator lane), and every epilogue reads and writes its row the same
+// way, four 16-byte accesses per 16 columns and no block barrier between k-chunks,
+// several k-chunks of loads in flight per thread. The accumulator is N FP32 columns
+// of TMEM (M = 128, N = 256 per instruction).
 // ---------------------------------------------------------------------------
 namespace tc {
 constexpr int kChunkK = 32;
+constexpr int kBigBufs = 3;
 // byte offset of element (row, k) of an N x N operator in the chunk-major layout
 __host__ __device__ __forceinline__ uint32_t chunk_offset(int row, int k, int N) {
     return (uint32_t)(k / kChunkK) * (uint32_t)N * kChunkK * 2u + kmajor_offset(row, k % kChunkK, kChunkK);
 }
-// Shared-memory plan of a streamed CTA: x_hi, x_lo (128 x N BF16 each), two chunk
-// buffers of hi + lo (N x 32 BF16 each), three staging buffers, 6 mbarriers, tmem slot.
+// Shared-memory plan of a streamed CTA: x_hi, x_lo (128 x N BF16 each), three chunk
+// buffers of hi + lo (N x 32 BF16 each), 7 mbarriers, tmem slot.
 struct BigPlan {
     uint32_t x_bytes, chunk_bytes, total;
     __host__ __device__ static BigPlan make(int N) {
         BigPlan p;
         p.x_bytes = 128u * N * 2;
         p.chunk_bytes = (uint32_t)N * kChunkK * 2;  // one part (hi or lo) of one chunk
-        p.total = 2 * p.x_bytes + 4 * p.chunk_bytes + 3 * kStageBytes + 64;
+        p.total = 2 * p.x_bytes + 2 * kBigBufs * p.chunk_bytes + 128;
         return p;
     }
 };
+
+// 16 consecutive floats at p (16-byte aligned) through L2, or zeros.
+__device__ __forceinline__ void ld_row16(const float *p, bool live, float *v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 x = live ? __ldcg(reinterpret_cast<const float4 *>(p) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+}
+__device__ __forceinline__ void st_row16(float *p, const float *v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4 *>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+// Row t of the tile (N floats at src, zeros when not live), scaled elementwise by
+// scale (N floats, NULL: none), split into x_hi / x_lo; 64 columns of loads in flight.
+__device__ __forceinline__ void load_split_row(const float *src, const float *scale, bool live, int N,
+                                               unsigned char *x_hi, unsigned char *x_lo, int t) {
+    for (int k0 = 0; k0 < N; k0 += 64) {
+        float v[4][16], sc[4][16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = live && k0 + 16 * j < N;
+            ld_row16(src + k0 + 16 * j, in, v[j]);
+            if (scale) ld_row16(scale + k0 + 16 * j, in, sc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (k0 + 16 * j >= N) break;
+            if (scale) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[j][i] *= sc[j][i];
+            }
+            store_split_row16(x_hi, x_lo, t, k0 + 16 * j, v[j], N);
+        }
+    }
+}
 }  // namespace tc
 
 struct TcBig {
-    unsigned char *x_hi, *x_lo, *ch[2];  // ch[b]: hi then lo of buffer b
-    float *stA, *stB, *stC;
-    uint64_t *full, *empty, *bar_mma;    // full[2], empty[2]
+    unsigned char *x_hi, *x_lo, *ch[tc::kBigBufs];  // ch[b]: hi then lo of buffer b
+    uint64_t *full, *empty, *bar_mma;               // full[kBigBufs], empty[kBigBufs]
     uint32_t *tmem_slot;
     uint32_t tmem, mma_phase;
-    uint32_t fills[2], uses[2];          // completed phases per buffer (thread 0's view)
+    uint32_t fills[tc::kBigBufs], reqs[tc::kBigBufs], commits[tc::kBigBufs];  // thread 0's view
 };
 
 __device__ __forceinline__ void tc_big_setup(TcBig &s, unsigned char *smem, int N) {
     const tc::BigPlan pl = tc::BigPlan::make(N);
     s.x_hi = smem;
     s.x_lo = smem + pl.x_bytes;
-    s.ch[0] = smem + 2 * pl.x_bytes;
-    s.ch[1] = s.ch[0] + 2 * pl.chunk_bytes;
-    s.stA = reinterpret_cast<float *>(s.ch[1] + 2 * pl.chunk_bytes);
-    s.stB = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s.stA) + tc::kStageBytes);
-    s.stC = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s.stB) + tc::kStageBytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(s.stC) + tc::kStageBytes);
+    for (int b = 0; b < tc::kBigBufs; ++b) {
+        s.ch[b] = smem + 2 * pl.x_bytes + 2 * b * pl.chunk_bytes;
+        s.fills[b] = s.reqs[b] = s.commits[b] = 0;
+    }
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * pl.x_bytes + 2 * tc::kBigBufs * pl.chunk_bytes);
     s.full = bars;
-    s.empty = bars + 2;
-    s.bar_mma = bars + 4;
-    s.tmem_slot = reinterpret_cast<uint32_t *>(bars + 5);
+    s.empty = bars + tc::kBigBufs;
+    s.bar_mma = bars + 2 * tc::kBigBufs;
+    s.tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * tc::kBigBufs + 1);
     s.mma_phase = 0;
-    s.fills[0] = s.fills[1] = s.uses[0] = s.uses[1] = 0;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 5; ++i) tc::mbar_init(bars + i, 1);
+        for (int i = 0; i < 2 * tc::kBigBufs + 1; ++i) tc::mbar_init(bars + i, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (threadIdx.x < 32) {
@@ -713,10 +753,13 @@ __device__ __forceinline__ void tc_big_setup(TcBig &s, unsigned char *smem, int 
 
 // Out = X Op^T over K = N with the tile in x_hi / x_lo and the operator (hi, lo:
 // chunk-major in global memory) streamed chunk by chunk; returns false on a timeout.
-// Thread 0 runs the pipeline: chunk c + 2 is requested once the MMAs of chunk c have
-// completed (the buffer's empty barrier); every wait is bounded.
+// Thread 0 runs the pipeline: chunks 0..2 are requested at once; after the MMAs of
+// chunk c are issued, the buffer of chunk c - 1 is refilled with chunk c + 2 once
+// those earlier MMAs have read it (its empty barrier), so the tensor core is not held
+// up by the copy just requested. Every wait is bounded.
 __device__ __forceinline__ bool tc_gemm_streamed(TcBig &s, const unsigned char *op_hi, const unsigned char *op_lo,
                                                  int N, int *err) {
+    constexpr int NB = tc::kBigBufs;
     tc::fence_async_smem();  // the tile's st.shared must be visible to the tensor core
     tc::tc_fence_before();
     __syncthreads();
@@ -726,19 +769,19 @@ __device__ __forceinline__ bool tc_gemm_streamed(TcBig &s, const unsigned char *
         const int nch = N / tc::kChunkK;
         const uint32_t cb = (uint32_t)N * tc::kChunkK * 2;
         auto request = [&](int c) {
-            const int b = c & 1;
+            const int b = c % NB;
             tc::mbar_arrive_expect_tx(&s.full[b], 2 * cb);
             tc::bulk_copy_g2s(s.ch[b], op_hi + (size_t)c * cb, cb, &s.full[b]);
             tc::bulk_copy_g2s(s.ch[b] + cb, op_lo + (size_t)c * cb, cb, &s.full[b]);
+            ++s.reqs[b];
         };
-        request(0);
-        if (nch > 1) request(1);
+        int issued = 0;
+        while (issued < nch && issued < NB) request(issued++);
         const uint32_t idesc = tc::idesc_bf16(128, N);
         const uint32_t xh = tc::smem_u32(s.x_hi), xl = tc::smem_u32(s.x_lo);
         const uint32_t sbo_x = (uint32_t)N * 16, sbo_b = tc::kChunkK * 16;
-        int issued = nch > 1 ? 2 : 1;
         for (int c = 0; c < nch && ok; ++c) {
-            const int b = c & 1;
+            const int b = c % NB;
             ok = tc::mbar_wait(&s.full[b], s.fills[b] & 1u);
             if (!ok) break;
             ++s.fills[b];
@@ -753,23 +796,26 @@ __device__ __forceinline__ bool tc_gemm_streamed(TcBig &s, const unsigned char *
                 tc::mma_bf16(s.tmem, a_lo, b_hi, idesc, 1u);
             }
             tc::mma_commit(&s.empty[b]);
-            if (issued < nch) {  // the buffer is refilled once its MMAs have read it
-                ok = tc::mbar_wait(&s.empty[b], s.uses[b] & 1u);
-                ++s.uses[b];
+            ++s.commits[b];
+            if (c >= 1 && issued < nch) {  // chunk c - 1 + NB into the buffer of chunk c - 1
+                const int bp = (c - 1) % NB;
+                ok = tc::mbar_wait(&s.empty[bp], (s.commits[bp] - 1u) & 1u);
                 if (!ok) break;
                 request(issued++);
-            } else {
-                ++s.uses[b];  // this phase is waited for (if at all) by the drain below
             }
         }
         tc::mma_commit(s.bar_mma);
-        if (!ok) {
-            // no copy may still be landing: wait (bounded) for every requested chunk
-            for (int b = 0; b < 2; ++b)
-                while (s.fills[b] < (uint32_t)((issued - b + 1) / 2)) {
-                    if (!tc::mbar_wait(&s.full[b], s.fills[b] & 1u)) break;
-                    ++s.fills[b];
+        // every buffer's last commit has landed (its phases stay in step for the next
+        // GEMM), and on a timeout no requested copy is still landing (bounded)
+        for (int b = 0; b < NB; ++b) {
+            if (s.commits[b] > 0 && !tc::mbar_wait(&s.empty[b], (s.commits[b] - 1u) & 1u)) ok = false;
+            while (s.fills[b] < s.reqs[b]) {
+                if (!tc::mbar_wait(&s.full[b], s.fills[b] & 1u)) {
+                    ok = false;
+                    break;
                 }
+                ++s.fills[b];
+            }
         }
     }
     ok = __syncthreads_and(ok) != 0;
@@ -806,50 +852,36 @@ __global__ void __launch_bounds__(128) k_tc_fp_rhs_big(const float *__restrict__
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
-        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const int ncols = min(128, 2 * sumK - j0);
         const bool live = t < ncols;
-        const int g = (j0 + t) >> 1;
-        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
-        const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            tc::stage_in(s.stA, psi_half + cb, N, ncols, k0);
-            __syncthreads();
-            float v[16];
-            tc::row_get16(s.stA, t, v);
-            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
-            __syncthreads();
-        }
+        const int g = live ? (j0 + t) >> 1 : 0;
+        const size_t row = ((size_t)r * sumK * 2 + j0 + t) * N;  // this thread's column of the tile
+        tc::load_split_row(psi_half + row, nullptr, live, N, s.x_hi, s.x_lo, t);
         if (!(ok = tc_gemm_streamed(s, ops.D, ops.D + opb, N, err))) break;
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            tc::stage_in(s.stA, phi + cb, N, ncols, k0);
-            tc::stage_in(s.stB, sig, N, ncell, k0);
-            float a[16];
+        // phi_half = D psi_half; next A = Sigma (phi_half - phi)
+        const float *sig = sigma_s + (size_t)g * N;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16], ph[16], sg[16], v[16];
+            tc::ld_row16(phi + row + k0, live, ph);
+            tc::ld_row16(sig + k0, live, sg);
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
-            __syncthreads();
-            float ph[16], sg[16], v[16];
-            tc::row_get16(s.stA, t, ph);
-            tc::row_get16(s.stB, t >> 1, sg);
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = live ? sg[i] * (a[i] - ph[i]) : 0.f;
-            tc::row_put16(s.stC, t, a);
+            if (live) tc::st_row16(phi_half + row + k0, a);
             tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
-            __syncthreads();
-            tc::stage_out(s.stC, phi_half + cb, N, ncols, k0);
         }
         if (!(ok = tc_gemm_streamed(s, ops.M, ops.M + opb, N, err))) break;
+        // rhs = m (x) r: the node partner is the adjacent lane (column j ^ 1)
         const float w = live ? (float)(h[g] / 6.0) : 0.f;
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+        for (int k0 = 0; k0 < N; k0 += 16) {
             float a[16], o[16];
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);  // r at the other node
+                const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);
                 o[i] = w * (2.f * a[i] + other);
             }
-            __syncthreads();  // stC of the previous chunk has been written out
-            tc::row_put16(s.stC, t, o);
-            __syncthreads();
-            tc::stage_out(s.stC, rhs + cb, N, ncols, k0);
+            if (live) tc::st_row16(rhs + row + k0, o);
         }
     }
     tc_big_teardown(s, N);
@@ -874,53 +906,36 @@ __global__ void __launch_bounds__(128) k_tc_update_scatter_big(const float *__re
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
-        const int ncols = min(128, 2 * sumK - j0), ncell = (ncols + 1) >> 1;
+        const int ncols = min(128, 2 * sumK - j0);
         const bool live = t < ncols;
-        const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
-        const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            tc::stage_in(s.stA, v_in + cb, N, ncols, k0);
-            __syncthreads();
-            float v[16];
-            tc::row_get16(s.stA, t, v);
-            tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
-            __syncthreads();
-        }
+        const int g = live ? (j0 + t) >> 1 : 0;
+        const size_t row = ((size_t)r * sumK * 2 + j0 + t) * N;
+        tc::load_split_row(v_in + row, nullptr, live, N, s.x_hi, s.x_lo, t);
         if (!(ok = tc_gemm_streamed(s, ops.D, ops.D + opb, N, err))) break;
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            if (phi_base) tc::stage_in(s.stA, phi_base + cb, N, ncols, k0);
-            tc::stage_in(s.stB, sig, N, ncell, k0);
-            float a[16];
+        // phi = phi_base + D v (read before written: phi_base may alias phi); next A = Sigma phi
+        const float *sig = sigma_s + (size_t)g * N;
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16], pb[16], sg[16], v[16];
+            tc::ld_row16(phi_base ? phi_base + row + k0 : nullptr, live && phi_base, pb);
+            tc::ld_row16(sig + k0, live, sg);
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
-            __syncthreads();
-            float pb[16], sg[16], v[16];
-            if (phi_base) tc::row_get16(s.stA, t, pb);
-            tc::row_get16(s.stB, t >> 1, sg);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                a[i] += phi_base ? pb[i] : 0.f;
+                a[i] += pb[i];
                 v[i] = live ? sg[i] * a[i] : 0.f;
             }
-            tc::row_put16(s.stC, t, a);
+            if (live) tc::st_row16(phi + row + k0, a);
             tc::store_split_row16(s.x_hi, s.x_lo, t, k0, v, N);
-            __syncthreads();
-            tc::stage_out(s.stC, phi + cb, N, ncols, k0);
         }
         if (!(ok = tc_gemm_streamed(s, ops.M, ops.M + opb, N, err))) break;
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            if (qang) tc::stage_in(s.stA, qang + cb, N, ncols, k0);
-            float a[16];
+        // q = M (Sigma phi) + q_ang
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            float a[16], qa[16];
+            tc::ld_row16(qang ? qang + row + k0 : nullptr, live && qang, qa);
             tc::tmem_ld16(s.tmem + lane_base + k0, a);
-            __syncthreads();
-            if (qang) {
-                float qa[16];
-                tc::row_get16(s.stA, t, qa);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) a[i] += qa[i];
-            }
-            tc::row_put16(s.stC, t, a);
-            __syncthreads();
-            tc::stage_out(s.stC, q + cb, N, ncols, k0);
+            for (int i = 0; i < 16; ++i) a[i] += qa[i];
+            if (live) tc::st_row16(q + row + k0, a);
         }
     }
     tc_big_teardown(s, N);
@@ -942,9 +957,10 @@ struct TcEngine {
     uint32_t tmem;
     __device__ __forceinline__ bool setup(unsigned char *smem, const TcOps &ops, int N, int *err) {
         bool ok = true;
-        if constexpr (kBig) {
+        if constexpr (kBig) {  // global I/O straight from the threads' rows: no staging buffers
             tc_big_setup(b, smem, N);
-            stA = b.stA; stB = b.stB; stC = b.stC; x_hi = b.x_hi; x_lo = b.x_lo; tmem = b.tmem;
+            stA = stB = stC = nullptr;
+            x_hi = b.x_hi; x_lo = b.x_lo; tmem = b.tmem;
         } else {
             ok = tc_cta_setup(a, smem, ops, N, err);
             stA = a.stA; stB = a.stB; stC = a.stC; x_hi = a.x_hi; x_lo = a.x_lo; tmem = a.tmem;
@@ -986,17 +1002,22 @@ __global__ void __launch_bounds__(128) k_tc_fp_rhs_moments(const float *__restri
         const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
         const float *sig = sigma_s + (size_t)(j0 >> 1) * N;
         // A = Sigma v
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            tc::stage_in(e.stA, v + cb, N, ncols, k0);
-            tc::stage_in(e.stB, sig, N, ncell, k0);
-            __syncthreads();
-            float vv[16], sg[16], a[16];
-            tc::row_get16(e.stA, t, vv);
-            tc::row_get16(e.stB, t >> 1, sg);
+        if constexpr (kBig) {
+            tc::load_split_row(v + cb + (size_t)t * N, sigma_s + (size_t)(live ? g : 0) * N, live, N, e.x_hi,
+                               e.x_lo, t);
+        } else {
+            for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+                tc::stage_in(e.stA, v + cb, N, ncols, k0);
+                tc::stage_in(e.stB, sig, N, ncell, k0);
+                __syncthreads();
+                float vv[16], sg[16], a[16];
+                tc::row_get16(e.stA, t, vv);
+                tc::row_get16(e.stB, t >> 1, sg);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) a[i] = live ? sg[i] * vv[i] : 0.f;
-            tc::store_split_row16(e.x_hi, e.x_lo, t, k0, a, N);
-            __syncthreads();
+                for (int i = 0; i < 16; ++i) a[i] = live ? sg[i] * vv[i] : 0.f;
+                tc::store_split_row16(e.x_hi, e.x_lo, t, k0, a, N);
+                __syncthreads();
+            }
         }
         if (!(ok = e.gemm(ops, false, N, err))) break;
         // rhs = m (x) r: node partner is the adjacent lane (column j ^ 1)
@@ -1009,10 +1030,14 @@ __global__ void __launch_bounds__(128) k_tc_fp_rhs_moments(const float *__restri
                 const float other = __shfl_xor_sync(0xffffffffu, a[i], 1);
                 o[i] = w * (2.f * a[i] + other);
             }
-            __syncthreads();  // stC of the previous chunk has been written out
-            tc::row_put16(e.stC, t, o);
-            __syncthreads();
-            tc::stage_out(e.stC, rhs + cb, N, ncols, k0);
+            if constexpr (kBig) {
+                if (live) tc::st_row16(rhs + cb + (size_t)t * N + k0, o);
+            } else {
+                __syncthreads();  // stC of the previous chunk has been written out
+                tc::row_put16(e.stC, t, o);
+                __syncthreads();
+                tc::stage_out(e.stC, rhs + cb, N, ncols, k0);
+            }
         }
     }
     e.teardown(N);
@@ -1033,28 +1058,43 @@ __global__ void __launch_bounds__(128) k_tc_moments_axpy(const float *__restrict
         const int r = tile / tiles_per_r, j0 = (tile % tiles_per_r) * 128;
         const int ncols = min(128, 2 * sumK - j0);
         const size_t cb = ((size_t)r * sumK * 2 + j0) * N;
-        for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            tc::stage_in(e.stA, psi + cb, N, ncols, k0);
-            __syncthreads();
-            float vv[16];
-            tc::row_get16(e.stA, t, vv);
-            tc::store_split_row16(e.x_hi, e.x_lo, t, k0, vv, N);
-            __syncthreads();
+        if constexpr (kBig) {
+            tc::load_split_row(psi + cb + (size_t)t * N, nullptr, t < ncols, N, e.x_hi, e.x_lo, t);
+        } else {
+            for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
+                tc::stage_in(e.stA, psi + cb, N, ncols, k0);
+                __syncthreads();
+                float vv[16];
+                tc::row_get16(e.stA, t, vv);
+                tc::store_split_row16(e.x_hi, e.x_lo, t, k0, vv, N);
+                __syncthreads();
+            }
         }
         if (!(ok = e.gemm(ops, true, N, err))) break;
         // out = base + sign D psi (base read chunk by chunk before out is written: it may alias)
         for (int k0 = 0; k0 < N; k0 += tc::kStageK) {
-            if (base) tc::stage_in(e.stA, base + cb, N, ncols, k0);
-            float a[16];
-            tc::tmem_ld16(e.tmem + lane_base + k0, a);
-            __syncthreads();
-            float bs[16];
-            if (base) tc::row_get16(e.stA, t, bs);
+            if constexpr (kBig) {
+                const bool live = t < ncols;
+                const size_t row = cb + (size_t)t * N + k0;
+                float a[16], bs[16];
+                tc::ld_row16(base ? base + row : nullptr, live && base, bs);
+                tc::tmem_ld16(e.tmem + lane_base + k0, a);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) a[i] = (base ? bs[i] : 0.f) + sign * a[i];
-            tc::row_put16(e.stC, t, a);
-            __syncthreads();
-            tc::stage_out(e.stC, out + cb, N, ncols, k0);
+                for (int i = 0; i < 16; ++i) a[i] = bs[i] + sign * a[i];
+                if (live) tc::st_row16(out + row, a);
+            } else {
+                if (base) tc::stage_in(e.stA, base + cb, N, ncols, k0);
+                float a[16];
+                tc::tmem_ld16(e.tmem + lane_base + k0, a);
+                __syncthreads();
+                float bs[16];
+                if (base) tc::row_get16(e.stA, t, bs);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a[i] = (base ? bs[i] : 0.f) + sign * a[i];
+                tc::row_put16(e.stC, t, a);
+                __syncthreads();
+                tc::stage_out(e.stC, out + cb, N, ncols, k0);
+            }
         }
     }
     e.teardown(N);

@@ -103,7 +103,7 @@ def test_tuning_entry_points_reject_a_null_context(lib):
     # argument checks come before any CUDA call
     from paper_1907_13013_gb300 import binding
     t = binding.FpsaTuning()
-    assert ctypes.sizeof(t) == 20  # five int32 fields, as in include/fpsa.h
+    assert ctypes.sizeof(t) == 24  # six int32 fields, as in include/fpsa.h
     ms = ctypes.c_double()
     assert lib.fpsa_get_tuning(None, ctypes.byref(t)) == binding.EINVAL
     assert lib.fpsa_set_tuning(None, None) == binding.EINVAL

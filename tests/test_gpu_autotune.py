@@ -158,7 +158,8 @@ def test_batch_driver_tuning_cache(binding, tmp_path):
         saved = json.load(f)
     assert 1 <= len(saved) <= len(stats)
     assert all(e["ms"] > 0 and set(e["shapes"]) == {"sweep_cells_per_thread", "solve_blocks_per_sm",
-                                                     "solve_max_slices", "factor_engine", "solve_engine"}
+                                                     "solve_max_slices", "factor_engine", "solve_engine",
+                                                     "residual_engine"}
                for e in saved.values())
     phis2, stats2 = batch.BatchSolver(probs, tuning=batch.TuningCache(path)).solve(tol=1e-12, max_iterations=200)
     assert {s["tuning_source"] for s in stats2} == {"cache"}

@@ -69,7 +69,7 @@ def test_graph_batch_matches_oracle_and_single_solves(binding, laplacian, inner)
                 assert relerr(got, oracle_ref(p, r)) < TOL, (g[0]["N"], r, relerr(got, oracle_ref(p, r)))
     # the same contexts one by one: the same converged flux, at most one refinement step more
     for c, phi, st in zip(ctxs, phis, sts):
-        one, st1 = c.solve("fpsa", tol=1e-13, max_iterations=200, inner_iterations=inner)
+        one, st1 = c.solve("fpsa", tol=1e-13, max_iterations=200, inner_iterations=inner or 4)
         assert np.abs(one - phi).max() <= 1e-10 * np.abs(one[..., 0]).max()
         assert st1["outer_iterations"] <= st["outer_iterations"] <= st1["outer_iterations"] + 1, (st1, st)
     # the contexts stay usable: a second graph solve gives the same answer

@@ -41,7 +41,8 @@ def solve_with(binding, probs, engine, laplacian):
     assert ctx.get_tuning()["factor_engine"] == engine
     ctx.set_xs(np.concatenate([p["sigma_t"] for p in probs]), np.concatenate([p["sigma_s"] for p in probs]),
                np.concatenate([p["Q"] for p in probs])[None])
-    phi, st = ctx.solve("fpsa", tol=1e-13, max_iterations=500)
+    # a fixed inner count: the engines are compared step for step
+    phi, st = ctx.solve("fpsa", tol=1e-13, max_iterations=500, inner_iterations=4)
     ctx.close()
     return phi[0], st
 

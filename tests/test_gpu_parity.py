@@ -187,6 +187,20 @@ def test_mixed_random_slabs(binding, N, K, seed, kernel, lap):
     assert relerr(phi[0], ref) < TOL, (relerr(phi[0], ref), st)
 
 
+@pytest.mark.parametrize("N,K,seed,c", [(16, 120, 8, (0.9, 0.9999)), (64, 200, 9, (0.99, 0.99999))])
+def test_mixed_adaptive_inner_count(binding, N, K, seed, c):
+    # the adaptive inner count (inner_iterations 0) reaches the oracle's solution in no more
+    # refinement steps than a fixed count of 4 and with inner iterations in [4, 16] per step
+    p = inputs.random_slab(K, N, N - 1, seed=seed, kernel="srk", thick=(5, 500), c=c)
+    ctx = binding.context_for(p, laplacian="wfd", precision="mixed")
+    phi_a, st_a = ctx.solve("fpsa", tol=1e-12, max_iterations=100)
+    phi_f, st_f = ctx.solve("fpsa", tol=1e-12, max_iterations=100, inner_iterations=4)
+    ref = oit.direct_solve(p)
+    assert relerr(phi_a[0], ref) < TOL and relerr(phi_f[0], ref) < TOL
+    assert st_a["outer_iterations"] <= st_f["outer_iterations"], (st_a, st_f)
+    assert st_a["sweeps"] <= 16 * (st_a["outer_iterations"] - 1), st_a
+
+
 def test_mixed_batch_and_si(binding):
     R = 2
     probs = [inputs.random_slab(K, 8, 7, seed=40 + i, kernel="hg", c=(0.3, 0.8), nrhs=R) for i, K in enumerate([1, 9, 40])]

@@ -43,7 +43,7 @@ CASES = [
 def test_tensor_core_solve_matches_dataflow_solve_and_oracle(binding, N, Ks, R, method, lap):
     probs = [inputs.random_slab(K, N, N - 1, seed=1200 + N + K + R + b, kernel="hg", thick=(1, 100),
                                 c=(0.5, 0.99), nrhs=R) for b, K in enumerate(Ks)]
-    kw = {"restart": 30} if method == "gmres" else {}
+    kw = {"restart": 30} if method == "gmres" else {"inner_iterations": 4}  # fixed: step-for-step comparison
     ctx = binding.context_for(probs, laplacian=lap, precision="mixed")
     assert ctx.get_tuning()["solve_engine"] == 2
     phi_t, st_t = ctx.solve(method, tol=1e-13, max_iterations=300, **kw)

@@ -33,8 +33,8 @@ def test_streamed_tensor_contractions_match_simt_and_oracle(binding, N, K, R, la
     rng = np.random.default_rng(N + K)
     p["Q"] = np.concatenate([p["Q"][None]] + [rng.uniform(0, 1, (1,) + p["Q"].shape) for _ in range(R - 1)])
     ctx = binding.context_for(p, laplacian=lap, precision="mixed")
-    phi_t, st_t = ctx.solve("fpsa", tol=1e-13, max_iterations=300, contraction="tensor")
-    phi_s, st_s = ctx.solve("fpsa", tol=1e-13, max_iterations=300, contraction="simt")
+    phi_t, st_t = ctx.solve("fpsa", tol=1e-13, max_iterations=300, contraction="tensor", inner_iterations=4)
+    phi_s, st_s = ctx.solve("fpsa", tol=1e-13, max_iterations=300, contraction="simt", inner_iterations=4)
     ctx.close()
     assert abs(st_t["outer_iterations"] - st_s["outer_iterations"]) <= 1, (st_t, st_s)
     for r in range(R):
