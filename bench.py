@@ -307,6 +307,15 @@ def scale_secondary(binding, inputs, dev, stream, hbm, bf16, precisions, K=20000
                 fl = 2.0 * N * (L + 1) * 2 * K * R
                 roof = {"kernel": "contractions (SIMT)", "bound": "alu", "achieved": fl / (per * 1e-3) / 1e12,
                         "peak": 1.20, "unit": "TFLOP/s", "peak_source": "FP64 FMA-chain probe on GB300 (1.20 TFLOP/s)"}
+            elif dom == "residual" and prec == "mixed" and ctx.get_tuning()["residual_engine"] == 2:
+                # the tensor-core residual: two contractions of 36 BF16 digit-pair products of
+                # 2 N^2 flop per column; a refinement step launches the residual and the
+                # accumulation of the correction, so the phase's launches are two per step
+                fl = 2 * 36 * 2.0 * N * N * 2 * K * R / 2
+                roof = {"kernel": "k_mixed_residual_tc", "bound": "tensor", "achieved": fl / (per * 1e-3) / 1e12,
+                        "peak": bf16, "unit": "TFLOP/s",
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)",
+                        "note": "achieved over the residual phase's launch pairs (residual + accumulation)"}
             elif dom == "residual" and prec == "mixed":
                 # the FP64 refinement residual: both contractions fold the mirror ordinates, N^2
                 # FP64 multiply-adds per column; a refinement step launches the residual and the
