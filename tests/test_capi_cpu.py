@@ -93,6 +93,30 @@ def test_boundary_condition_marshalling():
         binding._bc_array("periodic", 1)
 
 
+def test_batch_graph_rounds():
+    # graph mode of the batch driver: round r holds the r-th wave of every (N, L) group,
+    # so each wave is solved exactly once and no round holds two waves of one group
+    from paper_1907_13013_gb300 import batch, inputs
+    probs = inputs.batch_slabs(60, seed=4, K_range=(100, 5000))
+    solver = batch.BatchSolver(probs, precision="mixed", laplacian="wfd", budget_bytes=1 << 30, graph=True)
+    rounds = solver.rounds()
+    flat = [w for rnd in rounds for w in rnd]
+    assert sorted(map(id, flat)) == sorted(map(id, solver.waves))
+    for rnd in rounds:
+        keys = [(N, L) for N, L, _ in rnd]
+        assert len(keys) == len(set(keys))
+    groups = {(p["N"], p["L"]) for p in probs}
+    assert len(rounds[0]) == len(groups)
+    per_group = {}
+    for w in solver.waves:
+        per_group[(w[0], w[1])] = per_group.get((w[0], w[1]), 0) + 1
+    assert len(rounds) == max(per_group.values())
+    assert solver._round_bytes(rounds[0]) == sum(
+        batch.factor_bytes(sum(probs[i]["h"].size for i in w[2]), w[0], "mixed") for w in rounds[0])
+    with pytest.raises(ValueError):
+        batch.BatchSolver(probs, precision="fp64", graph=True)
+
+
 def test_limits_entry_point_rejects_a_null_context(lib):
     from paper_1907_13013_gb300 import binding
     assert lib.fpsa_set_limits(None, 0, 0.0) == binding.EINVAL
