@@ -117,6 +117,17 @@ def test_batch_graph_rounds():
         batch.BatchSolver(probs, precision="fp64", graph=True)
 
 
+def test_batch_solve_rejects_empty_and_null_arguments(lib):
+    # argument checks that precede any CUDA call (no GPU needed)
+    import ctypes as ct
+    from paper_1907_13013_gb300 import binding
+    binding.load()
+    assert lib.fpsa_solve_batch(None, 1, None, None, 0, None) == binding.EINVAL
+    handles = (ct.c_void_p * 1)(None)
+    assert lib.fpsa_solve_batch(handles, 0, None, None, 0, None) == binding.EINVAL
+    assert lib.fpsa_solve_batch(handles, 1, None, None, 0, None) == binding.EINVAL
+
+
 def test_limits_entry_point_rejects_a_null_context(lib):
     from paper_1907_13013_gb300 import binding
     assert lib.fpsa_set_limits(None, 0, 0.0) == binding.EINVAL
