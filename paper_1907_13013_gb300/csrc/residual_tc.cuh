@@ -7,9 +7,10 @@
 // makes the two N x N contractions the whole cost of the kernel. Here each contraction
 // is an exact integer computation on the BF16 tensor cores:
 //   - every row r of the input (a column's N values) is scaled by its own power of two,
-//     x~ = x 2^-e_r with |x~| < 1 (e_r from frexp of max |x|), and written as the 56-bit
-//     fixed-point integer q = rint(x~ 2^56); q = sign * sum_i dig_i 2^(49 - 7 i), i < 8,
-//     with 7-bit digits dig_i in [0, 127]: x~ = sum_i s_i 2^(-7 (i + 1)), s_i = sign dig_i;
+//     x~ = x 2^-e_r with |x~| < 1 (e_r the frexp exponent of max |x|), and written as the
+//     56-bit fixed-point integer q = x~ 2^56 rounded to nearest (taken from the bits of x
+//     with integer operations); q = sign * sum_i dig_i 2^(49 - 7 i), i < 8, with 7-bit
+//     digits dig_i in [0, 127]: x~ = sum_i s_i 2^(-7 (i + 1)), s_i = sign dig_i;
 //   - every row o of the operator likewise (host side, once per context): t_j, e_o;
 //   - x~ . op~ = sum_d 2^(-7 (d + 2)) A_d with A_d = sum_{i + j = d} sum_k s_i t_j over
 //     the 36 digit pairs with i + j <= 7 (the dropped pairs weigh 2^-70 or less).
@@ -21,15 +22,16 @@
 // truncation of each row relative to its largest entry and the FP64 combination, i.e.
 // the accuracy of an FP64 dot product.
 //
-// One CTA per tile of 64 cells x 2 nodes = 128 columns (tensor-memory lane = column),
-// 128 threads. For each output chunk of OC = 64 rows (32 where 64 does not divide N)
-// and each K-chunk of 32:
+// One CTA per tile of 64 cells x 2 nodes = 128 columns (tensor-memory lane = column)
+// and per SM (it holds all 512 TMEM columns), 256 threads: two per column, each taking
+// half of every K-chunk and of every output chunk. For each output chunk of OC = 64
+// rows (32 where 64 does not divide N) and each K-chunk of 32, in two pipelined stages:
 // thread 0 copies the operator's 8 digit slices of that block (OC x 32 BF16 each,
-// stored K-major in the core-matrix layout, one bulk copy), every thread writes the 8
-// digit slices of its column's 32 inputs (K-major), and thread 0 issues the 72 MMAs
-// (36 pairs, two K-steps; M = 128, N = OC, K = 16). Waits are bounded; on a timeout
-// the CTA records the error, waits (bounded) for its copies and products, frees its
-// tensor memory and stops.
+// stored K-major in the core-matrix layout, one bulk copy), the threads write the 8
+// digit slices of their columns' 32 inputs (K-major), and thread 0 issues the 72 MMAs
+// (36 pairs, two K-steps; M = 128, N = OC, K = 16) while the next chunk is prepared.
+// Waits are bounded; on a timeout the CTA records the error, waits (bounded) for its
+// copies and products, frees its tensor memory and stops.
 #pragma once
 
 #include "kernels.cuh"
