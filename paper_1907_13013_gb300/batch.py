@@ -109,10 +109,11 @@ class BatchSolver:
         concurrent waves would distort each other's timings), then every wave runs.
         profile: time every launch of each wave's solve with the library's profiler (CUDA
         event pairs) and return the per-kernel-class times in the wave's stats.
-        graph: solve in rounds, each holding one wave of every (N, L) group, as ONE launch
-        of a CUDA graph per round (fpsa_solve_batch: every group's refinement loop a
-        device-side while node, the groups concurrent branches); MIXED precision, SI or
-        FPSA. Contexts are still created and factorized on concurrent streams first."""
+        graph: solve in rounds of at most max_streams waves (different orders together,
+        see rounds()), each round ONE launch of a CUDA graph (fpsa_solve_batch: every
+        wave's refinement loop a device-side while node, the waves concurrent branches);
+        MIXED precision, SI or FPSA. Contexts are still created and factorized on
+        concurrent streams first."""
         self.problems = list(problems)
         self.precision, self.laplacian = precision, laplacian
         self.device = device
@@ -180,12 +181,28 @@ class BatchSolver:
                          tuning=tuned, tuning_source=source, **extra)
 
     def rounds(self):
-        """Graph mode: lists of waves, the r-th wave of every (N, L) group in round r."""
+        """Graph mode: lists of at most max_streams waves, each list one graph launch. A
+        round first takes the next wave of every (N, L) group that has one left, the
+        groups with the most remaining work first, then further waves of the groups with
+        the most work left while room remains, so orders mix in the early rounds and the
+        largest group keeps max_streams waves running concurrently at the end."""
         by_group = {}
         for w in self.waves:
             by_group.setdefault((w[0], w[1]), []).append(w)
-        n = max(len(v) for v in by_group.values())
-        return [[v[r] for v in by_group.values() if r < len(v)] for r in range(n)]
+        work = lambda w: sum(self.problems[i]["h"].size for i in w[2]) * w[0] ** 2  # noqa: E731
+        left = {k: list(v) for k, v in by_group.items()}
+        out = []
+        while any(left.values()):
+            rnd = []
+            order = sorted((k for k in left if left[k]), key=lambda k: -sum(work(w) for w in left[k]))
+            for k in order:
+                if len(rnd) < self.max_streams:
+                    rnd.append(left[k].pop(0))
+            while len(rnd) < self.max_streams and any(left.values()):
+                k = max((k for k in left if left[k]), key=lambda k: sum(work(w) for w in left[k]))
+                rnd.append(left[k].pop(0))
+            out.append(rnd)
+        return out
 
     def _prepare_wave(self, wave, method, searched):
         import torch

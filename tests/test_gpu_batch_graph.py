@@ -122,7 +122,7 @@ def test_batch_driver_graph_rounds(binding):
     probs = inputs.batch_slabs(40, seed=2, K_range=(20, 140))
     solver = batch.BatchSolver(probs, precision="mixed", laplacian="wfd", budget_bytes=48 << 20, graph=True)
     rounds = solver.rounds()
-    assert len(rounds) > 1 and max(len(r) for r in rounds) == 4  # every N in one graph, several rounds
+    assert len(rounds) > 1 and len({w[0] for w in rounds[0]}) == 4  # every N in the first graph, several rounds
     phis, stats = solver.solve(tol=1e-12, max_iterations=200)
     assert sum(s["instances"] for s in stats) == len(probs) and all(s["status"] == 0 for s in stats)
     rng = np.random.default_rng(3)
