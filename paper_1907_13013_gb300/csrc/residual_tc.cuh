@@ -9,15 +9,18 @@
 //   - every row r of the input (a column's N values) is scaled by its own power of two,
 //     x~ = x 2^-e_r with |x~| < 1 (e_r the frexp exponent of max |x|), and written as the
 //     56-bit fixed-point integer q = x~ 2^56 rounded to nearest (taken from the bits of x
-//     with integer operations); q = sign * sum_i dig_i 2^(49 - 7 i), i < 8, with 7-bit
-//     digits dig_i in [0, 127]: x~ = sum_i s_i 2^(-7 (i + 1)), s_i = sign dig_i;
+//     with integer operations), split into balanced base-128 digits:
+//     q = sum_{i < 8} s_i 2^(49 - 7 i) with s_0 in [-128, 128] and s_i in [-64, 63] for
+//     i >= 1 (each exact in BF16), i.e. x~ = sum_i s_i 2^(-7 (i + 1));
 //   - every row o of the operator likewise (host side, once per context): t_j, e_o;
 //   - x~ . op~ = sum_d 2^(-7 (d + 2)) A_d with A_d = sum_{i + j = d} sum_k s_i t_j over
 //     the 36 digit pairs with i + j <= 7 (the dropped pairs weigh 2^-70 or less).
-// Every product s_i t_j is an integer of magnitude below 2^14 and, for i + j = d >= 1,
-// below 2^13; over K <= 256 terms and d + 1 pairs every partial sum stays an integer of
-// magnitude at most 2^24, so the FP32 accumulation of the BF16 products in tensor
-// memory is exact (A_d in its own accumulator, 8 x OC TMEM columns). The A_d are then
+// A product s_i t_j is an integer of magnitude at most 2^14 (i = j = 0), 2^13 (one
+// index 0) or 2^12; the pairs of a diagonal d contribute at most (d + 3) 2^12 per k
+// (2^14 for d <= 1), so over K <= 256 terms the sum of the magnitudes of a diagonal's
+// products, and hence every partial sum in any order, is an integer of magnitude at
+// most 10 x 2^20 < 2^24: the FP32 accumulation of the BF16 products in tensor memory
+// is exact (A_d in its own accumulator, 8 x OC TMEM columns). The A_d are then
 // combined in FP64, scaled by 2^(e_r + e_o): the only roundings are the 56-bit
 // truncation of each row relative to its largest entry and the FP64 combination, i.e.
 // the accuracy of an FP64 dot product.
@@ -63,6 +66,19 @@ __host__ __device__ constexpr size_t block_offset(int N, int oc, int kc) {
     return ((size_t)oc * (N / KC) + kc) * b_block_bytes(N);
 }
 
+// Balanced base-128 digits of q (|q| <= 2^56): q = sum_{j < 8} s[j] 2^(49 - 7 j) with
+// s[0] in [-128, 128] and s[j] in [-64, 63] for j >= 1, from the least significant up.
+__host__ __device__ __forceinline__ void balanced_digits(long long q, int *sd) {
+    long long r = q;
+#pragma unroll
+    for (int j = S - 1; j >= 1; --j) {
+        const int d = (int)(((r & 127) ^ 64) - 64);  // r mod 128 in [-64, 63]
+        sd[j] = d;
+        r = (r - d) >> 7;  // exact: r - d is a multiple of 128
+    }
+    sd[0] = (int)r;
+}
+
 // The operator's digit slices (host side): op [No][K] row-major (No = K = N), out sized
 // (N / OC) (N / KC) b_block_bytes(N) bytes, exps [N]. Same digits as the device side.
 inline void slice_operator(const double *op, int N, unsigned char *out, int32_t *exps) {
@@ -75,12 +91,12 @@ inline void slice_operator(const double *op, int N, unsigned char *out, int32_t 
         exps[o] = e;
         for (int k = 0; k < N; ++k) {
             const long long q = std::llrint(std::ldexp(op[(size_t)o * N + k], 56 - e));
-            const unsigned long long u = (unsigned long long)(q < 0 ? -q : q);
+            int sd[S];
+            balanced_digits(q, sd);
             unsigned char *blk = out + block_offset(N, o / OC, k / KC);
             const uint32_t off = tc::kmajor_offset(o % OC, k % KC, KC);
             for (int j = 0; j < S; ++j) {
-                const int dig = (int)((u >> (49 - 7 * j)) & 127u);
-                const __nv_bfloat16 b = __float2bfloat16_rn((float)(q < 0 ? -dig : dig));
+                const __nv_bfloat16 b = __float2bfloat16_rn((float)sd[j]);
                 std::memcpy(blk + j * b_slice_bytes(N) + off, &b, 2);
             }
         }
@@ -113,18 +129,14 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
 // 8 FP64 inputs -> their 8 digit slices (BF16, one 16-byte row chunk per slice) at
 // element offset off of the K-major A-operand slices; e: the row's exponent.
 __device__ __forceinline__ void slice8(const double *x, int e, unsigned char *As, uint32_t off) {
-    long long q[8];
+    int sd[8][S];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) q[i] = fixed56(x[i], e);
+    for (int i = 0; i < 8; ++i) balanced_digits(fixed56(x[i], e), sd[i]);
 #pragma unroll
     for (int j = 0; j < S; ++j) {
         __align__(16) __nv_bfloat16 b[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const unsigned long long u = (unsigned long long)(q[i] < 0 ? -q[i] : q[i]);
-            const int dig = (int)((u >> (49 - 7 * j)) & 127u);
-            b[i] = __int2bfloat16_rn(q[i] < 0 ? -dig : dig);
-        }
+        for (int i = 0; i < 8; ++i) b[i] = __int2bfloat16_rn(sd[i][j]);
         *reinterpret_cast<uint4 *>(As + j * a_slice_bytes() + off) = *reinterpret_cast<const uint4 *>(b);
     }
 }
