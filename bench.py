@@ -93,7 +93,9 @@ def read_golden(name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms while running; start()
+    returns once the first sample has arrived (at most 3 s), so that the sampling loop
+    is already running when the timed region begins."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -107,16 +109,22 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+            self.first = threading.Event()
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(timeout=3.0)
+            n = len(self.lines)
+            self.pre = self.lines[n - 1:n]  # the last sample before the timed region
+            del self.lines[:n]
         except OSError:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
 
     def stop(self):
         if self.proc is None:
@@ -129,7 +137,11 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # a timed region shorter than the sampling interval may hold no sample: then the
+        # one taken just before it stands in (samples = 0 says so)
+        lines = [ln for ln in self.lines if ln]
+        in_region = len(lines)
+        for ln in lines or getattr(self, "pre", []):
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -142,7 +154,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": in_region}
 
 
 def run_reference(args):
