@@ -128,3 +128,29 @@ def test_batch_driver_graph_rounds(binding):
     rng = np.random.default_rng(3)
     for i in rng.choice(len(probs), 8, replace=False):
         assert relerr(phis[i], oit.direct_solve(probs[i])) < TOL, (i, probs[i]["N"])
+
+
+def test_graph_batch_with_tensor_core_residual(binding):
+    """The refinement residual on the tensor cores (exact digit-slice products) inside the
+    graph's while loops: the same fluxes as the FP64-core residual and the oracle's."""
+    gs = [[inputs.random_slab(K, 32, 31, seed=760 + K, kernel="srk", thick=(2, 300), c=(0.9, 0.999))
+           for K in (5, 77)],
+          [inputs.random_slab(120, 64, 63, seed=770, kernel="srk", thick=(5, 500), c=(0.99, 0.9999))],
+          [dict(inputs.random_slab(33, 128, 127, seed=780, kernel="hg", thick=(2, 200), c=(0.8, 0.999)),
+                bc=("reflective", "vacuum"))]]
+    out = {}
+    for engine in (2, 1):
+        ctxs = [make(binding, g) for g in gs]
+        for c in ctxs:
+            c.set_tuning({"residual_engine": engine})
+            assert c.get_tuning()["residual_engine"] == engine
+        out[engine] = binding.solve_batch(ctxs, tol=1e-13, max_iterations=200, inner_iterations=4)
+        for c in ctxs:
+            c.close()
+    (phis_t, sts_t), (phis_f, sts_f) = out[2], out[1]
+    for g, pt, pf, st, sf in zip(gs, phis_t, phis_f, sts_t, sts_f):
+        assert st["status"] == 0 and sf["status"] == 0
+        assert st["outer_iterations"] == sf["outer_iterations"], (st, sf)
+        assert np.abs(pt - pf).max() <= 1e-11 * np.abs(pf[..., 0]).max()
+        for p, got in zip(g, split(pt, g)):
+            assert relerr(got, oracle_ref(p)) < TOL, (g[0]["N"], relerr(got, oracle_ref(p)))
