@@ -67,16 +67,17 @@ __host__ __device__ constexpr size_t block_offset(int N, int oc, int kc) {
 }
 
 // Balanced base-128 digits of q (|q| <= 2^56): q = sum_{j < 8} s[j] 2^(49 - 7 j) with
-// s[0] in [-128, 128] and s[j] in [-64, 63] for j >= 1, from the least significant up.
+// s[0] in [-128, 128] and s[j] in [-64, 63] for j >= 1. With the bias
+// b = 64 sum_{j >= 1} 2^(49 - 7 j) (< 2^49), q + b = s[0] 2^49 + sum_{j >= 1} (s[j] + 64)
+// 2^(49 - 7 j) with every s[j] + 64 in [0, 127]: the plain base-128 digits of the low 49
+// bits of q + b, less 64, and its arithmetic shift by 49.
 __host__ __device__ __forceinline__ void balanced_digits(long long q, int *sd) {
-    long long r = q;
+    constexpr long long bias =
+        64LL * ((1LL << 42) + (1LL << 35) + (1LL << 28) + (1LL << 21) + (1LL << 14) + (1LL << 7) + 1LL);
+    const long long r = q + bias;
+    sd[0] = (int)(r >> 49);
 #pragma unroll
-    for (int j = S - 1; j >= 1; --j) {
-        const int d = (int)(((r & 127) ^ 64) - 64);  // r mod 128 in [-64, 63]
-        sd[j] = d;
-        r = (r - d) >> 7;  // exact: r - d is a multiple of 128
-    }
-    sd[0] = (int)r;
+    for (int j = 1; j < S; ++j) sd[j] = (int)((r >> (49 - 7 * j)) & 127) - 64;
 }
 
 // The operator's digit slices (host side): op [No][K] row-major (No = K = N), out sized

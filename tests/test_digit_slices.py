@@ -25,6 +25,12 @@ def balanced(q):
     return out
 
 
+def balanced_by_bias(q):
+    """The same digits from the plain base-128 digits of q + 64 sum_{j >= 1} 2^(49 - 7 j)."""
+    r = int(q) + 64 * sum(1 << (49 - BITS * j) for j in range(1, S))
+    return [r >> 49] + [((r >> (49 - BITS * j)) & 127) - 64 for j in range(1, S)]
+
+
 def row_digits(x):
     """Digits [S][len(x)] and the row exponent e of x (|x| < 2^e)."""
     mx = np.max(np.abs(x))
@@ -55,6 +61,7 @@ def test_balanced_digit_ranges_and_extremes():
     for q in (0, 1, -1, 63, 64, -64, -65, 2 ** 56, -(2 ** 56), 2 ** 56 - 1, -(2 ** 56) + 1,
               sum(64 << (7 * j) for j in range(8)), -sum(64 << (7 * j) for j in range(8))):
         d = balanced(q)
+        assert d == balanced_by_bias(q)
         assert sum(v << (49 - BITS * j) for j, v in enumerate(d)) == q
         assert abs(d[0]) <= 128 and all(-64 <= v <= 63 for v in d[1:]), (q, d)
 
@@ -66,6 +73,7 @@ def test_digits_reconstruct_the_fixed_point_value(K, seed):
     assert np.all(np.abs(dig[0]) <= 128) and np.all((dig[1:] >= -64) & (dig[1:] <= 63))
     for k in range(K):
         assert sum(int(dig[j][k]) << (49 - BITS * j) for j in range(S)) == q[k]
+        assert list(dig[:, k]) == balanced_by_bias(q[k])
     # the fixed point carries the row's entries to half a unit of 2^-56 of the row scale
     back = np.array([float(v) for v in q]) * 2.0 ** (e - 56)
     assert np.max(np.abs(back - x)) <= 2.0 ** (e - 57)
