@@ -667,7 +667,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "laplacian": args.laplacian,
                    "tol": TOL, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set (262 MB FP64 factors) larger than L2; no flush",
+                   "l2": ("working set larger than L2, no flush: each step rewrites and each BCR solve "
+                          "launch reads %s" % ("the 262 MB of FP64 factors" if args.precision == "fp64" else
+                                               "the 131 MB of FP32 factors and the 17 MB coarse inverse")),
                    "tuning": dict(shape, source=args.tune)},
         "cell_angles_per_s": dev_stats["cell_angles"] * world * args.steps / (ms * 1e-3),
         # the same numerator over the sweep kernels' own event time
