@@ -17,8 +17,9 @@ Workload (one step = one pass of the whole path over one problem):
   e2e   : the same step through the same C ABI with HOST numpy inputs/outputs, so
           the host->device input copies and the device->host flux copy are inside
           the timed region.
-  The factor storage of one step (2000 x 128 x 128 FP64 = 262 MB) exceeds the
-  L2 (126 MB), so each step streams its working set from HBM.
+  The factors of one step (2000 blocks of 128 x 128: 131 MB in FP32 on the default
+  mixed path, 262 MB in FP64) exceed the L2 (126 MB), so each step streams its
+  working set from HBM.
 
 Multi-GPU (torchrun): every rank solves its own replica of the problem (the
 workload does not shard); value = solves of all ranks / max rank time.
