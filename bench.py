@@ -158,6 +158,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": in_region}
 
 
+def run_config(args, world):
+    """The workload's `config` object, the same on both arms (how the GPU arm computes,
+    its precision and launch shapes, is reported beside it)."""
+    return {"workload": WORKLOAD, "laplacian": args.laplacian, "tol": TOL,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": ("working set larger than L2, no flush: each step rewrites and each BCR solve "
+                   "launch reads %s" % ("the 262 MB of FP64 factors" if args.precision == "fp64" else
+                                        "the 131 MB of FP32 factors and the 17 MB coarse inverse"))}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
     rank, world, _ = dist_env()
@@ -191,7 +201,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_per_solve,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64", "laplacian": args.laplacian},
+           "data": "synthetic", "config": run_config(args, world), "precision": "fp64",
            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": v, "unit": "solves/s"},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -666,12 +676,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64 (bf16x3 tensor-core contractions)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "laplacian": args.laplacian,
-                   "tol": TOL, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": ("working set larger than L2, no flush: each step rewrites and each BCR solve "
-                          "launch reads %s" % ("the 262 MB of FP64 factors" if args.precision == "fp64" else
-                                               "the 131 MB of FP32 factors and the 17 MB coarse inverse")),
-                   "tuning": dict(shape, source=args.tune)},
+        "config": run_config(args, world), "precision": args.precision,
+        "tuning": dict(shape, source=args.tune),
         "cell_angles_per_s": dev_stats["cell_angles"] * world * args.steps / (ms * 1e-3),
         # the same numerator over the sweep kernels' own event time
         "sweep_cell_angles_per_s": (dev_stats["cell_angles"] * world * args.steps

@@ -87,7 +87,7 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     monkeypatch.setattr(oit, "fpsa_source_iteration", fake)
     for v in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(v, raising=False)
-    args = argparse.Namespace(steps=2, warmup=3, gpus=1, laplacian="wfd")
+    args = argparse.Namespace(steps=2, warmup=3, gpus=1, laplacian="wfd", precision="mixed")
     bench.run_reference(args)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "solves/s" and line["higher_is_better"] is True
@@ -95,4 +95,5 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"].startswith("precision_srk_slab")
+    assert line["config"] == bench.run_config(args, 1)  # the GPU arm's config object
     assert calls == [3, 5] * (args.warmup + args.steps)  # setup + 3 and 5 iterations per step
