@@ -16,8 +16,6 @@ import json
 import os
 import threading
 
-import numpy as np
-
 from . import binding
 
 # fpsa_autotune takes the iteration settings of the solves it times
