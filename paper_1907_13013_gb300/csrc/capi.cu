@@ -1459,9 +1459,6 @@ int gm_axpy(fpsa_ctx *ctx, PathBuffers<T> &p, const T *psi, const T *base, T sig
 // out = (I - T)(I + C) v  (out may not alias v)
 template <typename T>
 int gm_apply(fpsa_ctx *ctx, PathBuffers<T> &p, const T *v, T *out) {
-    const Geometry &g = ctx->geo;
-    const int N = g.N;
-    cudaStream_t st = ctx->stream;
     int rc = gm_fp_rhs(ctx, p, v, p.rhs);
     if (rc) return rc;
     rc = bcr_solve(ctx, p, p.rhs);
