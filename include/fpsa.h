@@ -289,8 +289,9 @@ typedef struct {
                                        (phi = D psi, s = M (Sigma phi + Q)): 1 = FP64 FMA
                                        cores, 2 = tensor cores computing them exactly at FP64
                                        working accuracy (each column and operator row as a
-                                       56-bit fixed-point number in eight 7-bit BF16 digit
-                                       slices, the 36 digit-pair products summed exactly in
+                                       56-bit fixed-point number in eight balanced
+                                       base-128 digits, each exact in BF16; the 36
+                                       digit-pair products summed exactly in
                                        FP32 and recombined in FP64; N a multiple of 32 up to
                                        256, else FPSA_ENOTSUP); 0 = tensor cores where they
                                        apply, else FP64 cores. Results differ by rounding
