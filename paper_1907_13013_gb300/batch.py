@@ -233,30 +233,46 @@ class BatchSolver:
             def start(rnd):
                 return [ex.submit(self._prepare_wave, w, method, searched) for w in rnd]
 
+            def close_all(futures):
+                """Close every context of a round being prepared (on the way out of an error)."""
+                for f in futures or []:
+                    try:
+                        f.result()[0].close()
+                    except Exception:
+                        pass
+
             pending = start(rounds[0]) if rounds else None
-            for r, rnd in enumerate(rounds):
-                prepared = [f.result() for f in pending]
-                pending = None
-                if r + 1 < len(rounds):
-                    free, _ = torch.cuda.mem_get_info(self.device)
-                    if free > 1.25 * self._round_bytes(rounds[r + 1]) + (4 << 30):
+            try:
+                for r, rnd in enumerate(rounds):
+                    futures, pending = pending, None
+                    try:
+                        prepared = [f.result() for f in futures]
+                    except BaseException:
+                        close_all(futures)
+                        raise
+                    ctxs = [c for c, _, _ in prepared]
+                    try:
+                        if r + 1 < len(rounds):
+                            free, _ = torch.cuda.mem_get_info(self.device)
+                            if free > 1.25 * self._round_bytes(rounds[r + 1]) + (4 << 30):
+                                pending = start(rounds[r + 1])
+                        phis, sts = binding.solve_batch(ctxs, **kw)
+                        for (N, L, idx), phi, st, (ctx, _, source) in zip(rnd, phis, sts, prepared):
+                            off = 0
+                            for i in idx:
+                                K = self.problems[i]["h"].size
+                                results[i] = phi[0, off:off + K]
+                                off += K
+                            stats.append(dict(st, N=N, instances=len(idx), cells=int(off), tuning=ctx.get_tuning(),
+                                              tuning_source=source, graph_round=r))
+                    finally:
+                        for c in ctxs:
+                            c.close()
+                    if pending is None and r + 1 < len(rounds):
                         pending = start(rounds[r + 1])
-                ctxs = [c for c, _, _ in prepared]
-                try:
-                    phis, sts = binding.solve_batch(ctxs, **kw)
-                    for (N, L, idx), phi, st, (ctx, _, source) in zip(rnd, phis, sts, prepared):
-                        off = 0
-                        for i in idx:
-                            K = self.problems[i]["h"].size
-                            results[i] = phi[0, off:off + K]
-                            off += K
-                        stats.append(dict(st, N=N, instances=len(idx), cells=int(off), tuning=ctx.get_tuning(),
-                                          tuning_source=source, graph_round=r))
-                finally:
-                    for c in ctxs:
-                        c.close()
-                if pending is None and r + 1 < len(rounds):
-                    pending = start(rounds[r + 1])
+            except BaseException:
+                close_all(pending)
+                raise
         return results, stats
 
     def solve(self, method="fpsa", tol=1e-10, max_iterations=10000, **kw):
