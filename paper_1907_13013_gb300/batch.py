@@ -144,8 +144,10 @@ class BatchSolver:
             stream = torch.cuda.Stream(device=self.device)
             with torch.cuda.stream(stream):
                 ctx = self._context(wave, stream)
-                shapes, ms = ctx.autotune(**{k: v for k, v in solve_kw.items() if k in _TUNE_KEYS})
-                ctx.close()
+                try:
+                    shapes, ms = ctx.autotune(**{k: v for k, v in solve_kw.items() if k in _TUNE_KEYS})
+                finally:
+                    ctx.close()
             self.tuning.put(key, shapes, ms)
             searched.add(key)
         return searched
@@ -158,17 +160,19 @@ class BatchSolver:
         probs = [self.problems[i] for i in idx]
         with torch.cuda.stream(stream):
             ctx = self._context(wave, stream)
-            source = "library"
-            if self.tuning is not None:
-                key = self._key(wave, solve_kw.get("method", "fpsa"))
-                ctx.set_tuning(self.tuning.get(key))
-                source = "search" if key in searched else "cache"
-            tuned = ctx.get_tuning()
-            if self.profile:
-                ctx.profile_enable(True)
-            phi, st = ctx.solve(**solve_kw)
-            prof = ctx.profile_read() if self.profile else None
-            ctx.close()
+            try:
+                source = "library"
+                if self.tuning is not None:
+                    key = self._key(wave, solve_kw.get("method", "fpsa"))
+                    ctx.set_tuning(self.tuning.get(key))
+                    source = "search" if key in searched else "cache"
+                tuned = ctx.get_tuning()
+                if self.profile:
+                    ctx.profile_enable(True)
+                phi, st = ctx.solve(**solve_kw)
+                prof = ctx.profile_read() if self.profile else None
+            finally:
+                ctx.close()
         out, off = {}, 0
         for i, p in zip(idx, probs):
             K = p["h"].size
@@ -211,7 +215,11 @@ class BatchSolver:
             source = "library"
             if self.tuning is not None:
                 key = self._key(wave, method)
-                ctx.set_tuning(self.tuning.get(key))
+                try:
+                    ctx.set_tuning(self.tuning.get(key))
+                except BaseException:
+                    ctx.close()
+                    raise
                 source = "search" if key in searched else "cache"
         return ctx, stream, source
 

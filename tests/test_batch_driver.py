@@ -1,6 +1,7 @@
-"""The batch driver's graph rounds on the CPU, with stand-in contexts and a stand-in
-fpsa_solve_batch: every wave's flux lands at its problems, every context is closed once,
-also when a round's solve raises while the next round is being prepared."""
+"""The batch driver on the CPU, with stand-in contexts (and, for the graph rounds, a
+stand-in fpsa_solve_batch): every wave's flux lands at its problems and every context is
+closed once, also when a solve raises (in graph mode while the next round is being
+prepared; in thread mode while other waves run)."""
 import threading
 
 import numpy as np
@@ -78,3 +79,46 @@ def test_a_failing_round_closes_its_contexts_and_the_next_rounds(monkeypatch, fa
     # the failing round's contexts and the next round's, prepared meanwhile, are all closed
     assert len(FakeCtx.created) == sum(len(r) for r in rounds[:fail_round + 2])
     assert all(c.closed == 1 for c in FakeCtx.created)
+
+
+class FakeSolveCtx(FakeCtx):
+    def __init__(self, probs, wave, fail):
+        super().__init__(wave)
+        self.probs, self.fail = probs, fail
+
+    def set_tuning(self, t):
+        pass
+
+    def solve(self, **kw):
+        if self.fail:
+            from paper_1907_13013_gb300 import binding
+            raise binding.FpsaError(binding.ENOTCONV, "stand-in failure")
+        parts = [np.full((self.probs[i]["h"].size, 2, self.probs[i]["L"] + 1), float(i)) for i in self.wave[2]]
+        return np.concatenate(parts)[None], {"status": 0}
+
+
+@pytest.mark.parametrize("fail", [False, True])
+def test_thread_waves_deliver_every_flux_and_close_every_context(monkeypatch, fail):
+    import contextlib
+
+    import torch
+
+    from paper_1907_13013_gb300 import batch, binding, inputs
+    FakeCtx.created = []
+    probs = inputs.batch_slabs(30, seed=6, K_range=(20, 300))
+    solver = batch.BatchSolver(probs, precision="mixed", laplacian="wfd", budget_bytes=2 << 20)
+    first = id(solver.waves[len(solver.waves) // 2])
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda device=None: None)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(batch.BatchSolver, "_context",
+                        lambda self, wave, stream: FakeSolveCtx(probs, wave, fail and id(wave) == first))
+    if fail:
+        with pytest.raises(binding.FpsaError):
+            solver.solve(tol=1e-10)
+    else:
+        phis, stats = solver.solve(tol=1e-10)
+        for i, phi in enumerate(phis):
+            assert np.all(phi == i) and phi.shape == (probs[i]["h"].size, 2, probs[i]["L"] + 1)
+        assert len(stats) == len(solver.waves)
+    assert FakeCtx.created and all(c.closed == 1 for c in FakeCtx.created)
