@@ -404,13 +404,17 @@ def context_for(problems, n_rhs=None, **kw):
     if "bc" not in kw and any(p.get("bc", "vacuum") != "vacuum" for p in probs):
         kw["bc"] = [p.get("bc", "vacuum") for p in probs]
     ctx = Context(K, h, N, L, n_rhs=R, **kw)
-    ctx.set_xs(st, ss, q)
-    if any(p.get("psi_inc") is not None for p in probs):
-        inc = np.zeros((R, len(probs), 2, N))
-        for b, p in enumerate(probs):
-            if p.get("psi_inc") is not None:
-                inc[:, b] = np.broadcast_to(p["psi_inc"], (R, 2, N))
-        ctx.set_incident(inc)
+    try:
+        ctx.set_xs(st, ss, q)
+        if any(p.get("psi_inc") is not None for p in probs):
+            inc = np.zeros((R, len(probs), 2, N))
+            for b, p in enumerate(probs):
+                if p.get("psi_inc") is not None:
+                    inc[:, b] = np.broadcast_to(p["psi_inc"], (R, 2, N))
+            ctx.set_incident(inc)
+    except BaseException:
+        ctx.close()  # the context's device memory goes now, not when it is collected
+        raise
     return ctx
 
 
